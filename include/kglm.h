@@ -1,0 +1,178 @@
+/*
+ * kglm.h -- C ABI of the GB300 batched node-bound engine for certified
+ * k-sparse GLM branch and bound (Liu & Lodi, "From Sequential Nodes to GPU
+ * Batches: Parallel Branch and Bound for Optimal k-Sparse GLMs").
+ *
+ * Problem (§1, problem (intro_sparse_glm)):
+ *     min_beta  f(X beta, y) + lambda2 ||beta||_2^2
+ *     s.t.      ||beta||_0 <= k,  ||beta||_inf <= M
+ * with f(s, y) = sum_i l(s_i, y_i), l(s, y) = (s - y)^2 (least squares) or
+ * log(1 + exp(-y s)) with y in {-1, +1} (logistic).
+ *
+ * A BnB node N fixes z_j = 0 on J0(N) and z_j = 1 on J1(N); the other
+ * coordinates are free (§3, definition of g_N).  The engine evaluates a batch
+ * of m nodes at once (§4.2): FISTA iterations on the perspective relaxation
+ * Phi_N = F(X beta) + 2 lambda2 g_N(beta) (§3 Eq. (node_composite)), each
+ * iteration two dense products S = X B and G = X^T R (§4.2 Eq.
+ * (gradient_matrix_form)) and the column-wise proximal step of §3 Eq.
+ * (pgd_step_vector_form); then the Fenchel-dual certificate
+ * Psi_N(zeta) = -F*(-zeta) - G_N*(X^T zeta) (§3 Eq. (prelim_fenchel_dual),
+ * §4.4 Eq. (batched_dual_value_component)) evaluated in FP64, the rounding,
+ * re-optimization and branching index of §4.3, and the pruning test of §3.
+ *
+ * Conventions for every call:
+ *  - host arrays are read before the call returns and never kept; outputs go
+ *    to caller-owned host buffers (any output pointer may be NULL to skip it);
+ *  - the context owns all device memory; one context is used by one host
+ *    thread at a time and runs its work on the stream given at creation;
+ *  - no C++ exception crosses this ABI; every call returns a kglm_status and
+ *    kglm_last_error() gives a message;
+ *  - an argument error returns KGLM_EINVAL and leaves the context unchanged;
+ *  - indices are 0-based int32; matrices are row-major as stated per call.
+ */
+#ifndef KGLM_H
+#define KGLM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kglm_ctx kglm_ctx;
+
+typedef enum {
+    KGLM_OK = 0,
+    KGLM_EINVAL = -1,   /* bad argument (sizes, indices, overlapping fixings, y not +-1, ...) */
+    KGLM_ENOMEM = -2,   /* device or host allocation failed, or over the HBM budget */
+    KGLM_ECUDA = -3,    /* a CUDA call failed; the message names it */
+    KGLM_ETIMEOUT = -4, /* a bounded device wait ran out */
+    KGLM_ESTATE = -5,   /* call out of order (e.g. evaluate before push) */
+    KGLM_ENUMERIC = -6  /* non-finite X or y */
+} kglm_status;
+
+typedef enum { KGLM_LSQ = 0, KGLM_LOGISTIC = 1 } kglm_loss;
+
+/* Arithmetic of the FISTA iterations.  The certificate is FP64-valid in
+ * every mode (the bound of §3 holds for any dual point zeta; the engine
+ * evaluates Psi_N(zeta) with FP64 sums and FP64 X^T zeta). */
+typedef enum {
+    KGLM_FP64 = 0,  /* FP64 products and prox */
+    KGLM_FP32 = 1,  /* FP32 products (CUDA cores) and prox */
+    KGLM_BF16 = 2,  /* BF16 tensor-core products, FP32 accumulate and prox */
+    KGLM_TF32 = 3   /* TF32 tensor-core products, FP32 accumulate and prox */
+} kglm_prec;
+
+typedef struct {
+    int64_t n;            /* samples (rows of X), > 0 */
+    int64_t p;            /* features (columns of X), > 0 */
+    int32_t k;            /* sparsity budget, 1 <= k <= KGLM_MAX_K and k <= p */
+    int32_t loss;         /* kglm_loss */
+    int32_t prec;         /* kglm_prec */
+    int32_t restart;      /* 1: FISTA with gradient restart; 0: plain FISTA */
+    double lambda2;       /* ridge coefficient, > 0 */
+    double M;             /* box ||beta||_inf <= M, > 0 */
+    double lipschitz;     /* L of grad F; 0: the engine computes 2||X||^2 or ||X||^2/4 */
+    double gap_tol;       /* pruning slack delta = gap_tol*max(1,|UB|); 0 selects 1e-6 */
+    int32_t max_batch;    /* node-batch capacity m_max, >= 1 */
+    int32_t pool_slots;   /* warm-start slots kept on the device (0: 4*max_batch) */
+    int64_t hbm_budget;   /* bytes the context may hold on the device; 0: no limit */
+} kglm_desc;
+
+#define KGLM_MAX_K 64
+
+/* Create an instance (§1 problem (intro_sparse_glm)).
+ * X: host, n x p row-major FP64; y: host, n FP64 (logistic: every y_i is
+ * -1 or +1).  Both are copied to the device (FP64, plus the working copies of
+ * the chosen precision).  stream: a cudaStream_t to run on, or NULL for a
+ * stream the context creates.  On success *out owns the instance. */
+kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
+                        void* stream, kglm_ctx** out);
+
+/* Define the next node batch (§4.2, Fig. 1 "assemble a batch of open nodes").
+ * m nodes, 1 <= m <= max_batch.  Node b fixes J1(b) = in_idx[in_ptr[b] ..
+ * in_ptr[b+1]) and J0(b) = out_idx[out_ptr[b] .. out_ptr[b+1]) (CSR, m+1
+ * offsets each; indices in [0, p), no repeats, J0 and J1 disjoint,
+ * |J1| <= k).  Warm start of node b, first that applies:
+ *   warm_slot[b] >= 0: the beta stored in that pool slot (kglm_save_warm);
+ *   warm_B != NULL:    row b of warm_B (host, m x p row-major FP64);
+ *   otherwise beta = 0.
+ * J0 entries of the warm start are set to 0.  warm_slot may be NULL. */
+kglm_status kglm_push_nodes(kglm_ctx* ctx, int32_t m,
+                            const int32_t* in_ptr, const int32_t* in_idx,
+                            const int32_t* out_ptr, const int32_t* out_idx,
+                            const int32_t* warm_slot, const double* warm_B);
+
+/* Evaluate the pushed batch: `iters` FISTA iterations (§3 Eq.
+ * (pgd_step_vector_form) with acceleration and gradient restart), then the
+ * safe bound LB_b = Psi_{N_b}(zeta_b), zeta_b = -grad F(X beta_b) (§3 Eq.
+ * (dual_candidate_vector_form)), the primal value Phi_b with g by Theorem 4.1,
+ * the rounded support S_b = J1 cup top-kbar |beta| over Jf and its
+ * re-optimized objective v(S_b) (§4.3), and the branching index
+ * j*_b = argmax_{Jf} |beta_j| (§4.3; -1 for a leaf: kbar = 0 or
+ * |J1| + |Jf| <= k).  With check_every > 0 the certificate is also taken
+ * every check_every iterations; a node stops iterating once its bound
+ * reaches ub - delta (the incumbent of kglm_set_incumbent) or its relative
+ * gap falls below 1e-9, and lb is the best certificate seen.
+ * Outputs (host, m entries each unless stated):
+ *   lb       FP64 safe lower bounds;   primal  FP64 Phi_b at the last iterate;
+ *   ub_cand  FP64 v(S_b);              support m x k int32, S_b ascending, -1 padded;
+ *   beta_re  m x k FP64 coefficients of the re-optimized model on S_b;
+ *   branch_j int32 j*_b;               iters_done int32 iterations run per node. */
+kglm_status kglm_evaluate(kglm_ctx* ctx, int32_t iters, int32_t check_every,
+                          double* lb, double* primal, double* ub_cand,
+                          int32_t* support, double* beta_re,
+                          int32_t* branch_j, int32_t* iters_done);
+
+/* Read back the batch's final iterates B (host, m x p row-major FP64) and the
+ * dual points zeta used by the last certificate (host, m x n row-major FP64).
+ * Either pointer may be NULL. */
+kglm_status kglm_read_batch(kglm_ctx* ctx, double* beta, double* zeta);
+
+/* Store the final beta of batch rows rows[0..count) in pool slots
+ * slots[0..count) (warm starts for children, Fig. 1 "warm starts"). */
+kglm_status kglm_save_warm(kglm_ctx* ctx, int32_t count, const int32_t* rows, const int32_t* slots);
+
+/* Record the incumbent objective UB (§3): used by kglm_prune and by the early
+ * stop of kglm_evaluate. */
+kglm_status kglm_set_incumbent(kglm_ctx* ctx, double ub);
+
+/* Prune the evaluated batch against ub (§3 "Safe Lower Bound and Pruning"):
+ * pruned[b] = 1 iff lb_b >= ub - delta, delta = gap_tol * max(1, |ub|).
+ * *n_survivors counts the others.  pruned: host, m uint8 (may be NULL). */
+kglm_status kglm_prune(kglm_ctx* ctx, double ub, uint8_t* pruned, int32_t* n_survivors);
+
+/* Children of the surviving, non-leaf nodes of the evaluated batch whose own
+ * rounding is not within delta of their bound (§4.3 branching, App. A):
+ * child 2c is (batch row parent[c], fix z_j = 0 on j = branch_j), child 2c+1
+ * fixes z_j = 1.  parent: host, capacity m int32; *n_parents receives the
+ * number of branched rows. */
+kglm_status kglm_branch(kglm_ctx* ctx, double ub, int32_t* parent, int32_t* branch_j,
+                        int32_t* n_parents);
+
+/* Certify the instance with the built-in hybrid BnB loop of Fig. 1: best-bound
+ * node queue on the host, batches of up to `batch` nodes evaluated with
+ * `iters` iterations (certificate every `check_every`), incumbent from the
+ * batched rounding and re-optimization, pruning and branching on j*.
+ * time_limit_s <= 0 means none.  Outputs: *opt the certified objective,
+ * opt_support (k int32, ascending, -1 padded), opt_beta (p FP64), *gap the
+ * final relative gap (0 when certified), *nodes the evaluated node count,
+ * *batches the number of batches. */
+kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t check_every,
+                       double time_limit_s, double* opt, int32_t* opt_support,
+                       double* opt_beta, double* gap, int64_t* nodes, int64_t* batches);
+
+/* Message of the last failed call on ctx (never NULL). */
+const char* kglm_last_error(const kglm_ctx* ctx);
+
+/* Free the context and all its device memory.  NULL is ignored. */
+void kglm_destroy(kglm_ctx* ctx);
+
+/* Engine build string, e.g. "kglm sm_103a". */
+const char* kglm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KGLM_H */

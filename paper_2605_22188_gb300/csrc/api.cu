@@ -1,0 +1,713 @@
+// C ABI of the node-bound engine (include/kglm.h): instance setup, node-batch
+// push, the batched evaluation pipeline, pruning/branching, and the hybrid
+// CPU-GPU branch-and-bound loop of §4.1 (Fig. 1).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <exception>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "engine.h"
+#include "kglm.h"
+
+using namespace kglm;
+
+struct kglm_ctx {
+    kglm_desc d{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int n = 0, p = 0, k = 0, W = 0, kind = 0, prec = 0;
+    bool f64 = true;
+    double lam2 = 0, M = 0, L = 0, eta = 0, c = 0, gap_tol = 1e-6;
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    // instance (device)
+    double *X64 = nullptr, *Xt64 = nullptr, *y64 = nullptr, *gram = nullptr, *Xty = nullptr;
+    float *X32 = nullptr, *Xt32 = nullptr, *y32 = nullptr;
+    // node batch (device), capacity mcap
+    int mcap = 0, m = 0;
+    bool pushed = false, evaluated = false;
+    uint32_t *in_mask = nullptr, *out_mask = nullptr;
+    int *kbar = nullptr, *pf = nullptr;
+    void *B = nullptr, *V = nullptr, *G = nullptr, *R = nullptr;
+    double *tmom = nullptr, *zeta = nullptr, *Q = nullptr;
+    int *active = nullptr, *iters_done = nullptr, *support = nullptr, *jstar = nullptr;
+    double *sum_loss = nullptr, *sum_conj = nullptr, *lb_now = nullptr, *primal_now = nullptr;
+    double *lb_best = nullptr, *primal_last = nullptr, *ub = nullptr, *beta_re = nullptr;
+    uint8_t* pruned = nullptr;
+    int *d_in_ptr = nullptr, *d_out_ptr = nullptr, *d_slot = nullptr, *d_rows = nullptr, *d_slots = nullptr;
+    int *d_in_idx = nullptr, *d_out_idx = nullptr;
+    size_t idx_cap = 0;
+    double* d_warmB = nullptr;
+    void* pool = nullptr;
+    int pool_slots = 0;
+    double ub_inc = INFINITY;
+    // host mirror of the evaluated batch
+    std::vector<int> h_kbar, h_pf, h_jstar;
+    std::vector<double> h_lb, h_ub;
+};
+
+namespace {
+
+struct Fail {
+    kglm_status st;
+    std::string msg;
+};
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) throw Fail{KGLM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define REQ(cond, msg)                                      \
+    do {                                                    \
+        if (!(cond)) throw Fail{KGLM_EINVAL, (msg)};        \
+    } while (0)
+
+template <typename F>
+kglm_status guarded(kglm_ctx* ctx, F&& f) {
+    try {
+        f();
+        return KGLM_OK;
+    } catch (const Fail& e) {
+        if (ctx) ctx->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->err = "host allocation failed";
+        return KGLM_ENOMEM;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->err = e.what();
+        return KGLM_EINVAL;
+    }
+}
+
+void* dalloc(kglm_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c->d.hbm_budget > 0 && (int64_t)(c->bytes + bytes) > c->d.hbm_budget)
+        throw Fail{KGLM_ENOMEM, "over the HBM budget of the context"};
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{KGLM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    }
+    c->allocs.push_back(p);
+    c->bytes += bytes;
+    return p;
+}
+
+template <typename T>
+T* dalloc_t(kglm_ctx* c, size_t count) {
+    return static_cast<T*>(dalloc(c, count * sizeof(T)));
+}
+
+void check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Fail{KGLM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+void sync(kglm_ctx* c) { CK(cudaStreamSynchronize(c->st)); }
+
+double delta_of(const kglm_ctx* c, double ub) { return isfinite(ub) ? c->gap_tol * fmax(1.0, fabs(ub)) : 0.0; }
+
+// Largest eigenvalue of the FP64 Gram matrix by power iteration (the
+// Lipschitz constant of grad F is 2||X||^2 or ||X||^2/4).
+double gram_lambda_max(kglm_ctx* c) {
+    const int p = c->p;
+    double* v = dalloc_t<double>(c, p);
+    double* w = dalloc_t<double>(c, p);
+    std::vector<double> h(p, 1.0 / sqrt((double)p));
+    double lam = 0.0;
+    for (int it = 0; it < 500; ++it) {
+        CK(cudaMemcpyAsync(v, h.data(), sizeof(double) * p, cudaMemcpyHostToDevice, c->st));
+        gemm_nt_f64(c->st, p, 1, p, c->gram, p, v, p, w, 1);
+        check_launch();
+        CK(cudaMemcpyAsync(h.data(), w, sizeof(double) * p, cudaMemcpyDeviceToHost, c->st));
+        sync(c);
+        double nrm = 0.0;
+        for (double x : h) nrm += x * x;
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0)) break;
+        const double lam_new = nrm;   // ||G v|| with ||v|| = 1
+        for (double& x : h) x /= nrm;
+        if (it > 20 && fabs(lam_new - lam) <= 1e-13 * lam_new) { lam = lam_new; break; }
+        lam = lam_new;
+    }
+    return lam;
+}
+
+void certify(kglm_ctx* c) {
+    const int m = c->m, n = c->n, p = c->p;
+    CertArgs a{};
+    a.m = m; a.n = n; a.p = p; a.W = c->W; a.k = c->k; a.kind = c->kind;
+    a.lam2 = c->lam2; a.M = c->M;
+    a.S = c->R;                                         // the m x n buffer is free here
+    a.s_is_f64 = c->f64;
+    a.y = c->y64;
+    a.zeta = c->zeta; a.sum_loss = c->sum_loss; a.sum_conj = c->sum_conj;
+    a.Q = c->Q; a.B = c->B; a.b_is_f64 = c->f64;
+    a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
+    a.lb = c->lb_now; a.primal = c->primal_now; a.support = c->support; a.jstar = c->jstar;
+    if (c->f64) gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n);
+    else gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n);
+    check_launch();
+    cert_dual_point(c->st, a);
+    check_launch();
+    gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p);   // X^T zeta, FP64
+    check_launch();
+    if (cert_bound(c->st, a) != 0) throw Fail{KGLM_EINVAL, "p too large for the certificate kernel"};
+    check_launch();
+}
+
+__global__ void k_fold(int m, const double* lb_now, double* lb_best) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < m) lb_best[b] = fmax(lb_best[b], lb_now[b]);
+}
+__global__ void k_fill(int m, double* x, double v) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < m) x[b] = v;
+}
+__global__ void k_filli(int m, int* x, int v) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < m) x[b] = v;
+}
+
+void iterate(kglm_ctx* c) {
+    const int m = c->m, n = c->n, p = c->p;
+    if (c->f64) {
+        gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R);
+        check_launch();
+        gemm_nt_f64(c->st, m, p, n, (const double*)c->R, n, c->Xt64, n, (double*)c->G, p);
+    } else {
+        gemm_link_f32(c->st, m, n, p, (const float*)c->V, c->X32, c->y32, c->kind, (float*)c->R);
+        check_launch();
+        gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p);
+    }
+    check_launch();
+    ProxArgs a{};
+    a.m = m; a.p = p; a.W = c->W;
+    a.G = c->G; a.V = c->V; a.B = c->B; a.Vh = nullptr;
+    a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
+    a.tmom = c->tmom; a.active = c->active;
+    a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
+    const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
+    if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
+    check_launch();
+}
+
+void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
+    const int m = c->m;
+    const unsigned gb = (unsigned)((m + 255) / 256);
+    k_fill<<<gb, 256, 0, c->st>>>(m, c->lb_best, -INFINITY);
+    k_filli<<<gb, 256, 0, c->st>>>(m, c->iters_done, iters);
+    check_launch();
+    const double thr = c->ub_inc - delta_of(c, c->ub_inc);
+    std::vector<int> h_active;
+    for (int it = 1; it <= iters; ++it) {
+        iterate(c);
+        if (check_every > 0 && it % check_every == 0 && it < iters) {
+            certify(c);
+            check_update(c->st, m, c->lb_now, c->primal_now, c->lb_best, c->primal_last, c->active,
+                         c->iters_done, it, thr, 1e-9);
+            check_launch();
+            h_active.resize(m);
+            CK(cudaMemcpyAsync(h_active.data(), c->active, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+            sync(c);
+            bool any = false;
+            for (int v : h_active) any |= (v != 0);
+            if (!any) break;
+        }
+    }
+    certify(c);
+    k_fold<<<gb, 256, 0, c->st>>>(m, c->lb_now, c->lb_best);
+    check_launch();
+    ReoptArgs r{};
+    r.m = m; r.n = c->n; r.p = c->p; r.k = c->k; r.kind = c->kind;
+    r.max_iter = c->kind == KGLM_LSQ ? 20000 : 4000;
+    r.lam2 = c->lam2; r.M = c->M; r.tol = 1e-12;
+    r.Xt = c->Xt64; r.y = c->y64; r.gram = c->gram; r.Xty = c->Xty;
+    r.support = c->support; r.B = c->B; r.b_is_f64 = c->f64;
+    r.ub = c->ub; r.beta_re = c->beta_re;
+    reopt_launch(c->st, r);
+    check_launch();
+}
+
+void validate_nodes(const kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx,
+                    const int32_t* out_ptr, const int32_t* out_idx, const int32_t* warm_slot) {
+    REQ(m >= 1 && m <= c->mcap, "m must be in [1, max_batch]");
+    REQ(in_ptr && out_ptr, "in_ptr and out_ptr are required");
+    REQ(in_ptr[0] == 0 && out_ptr[0] == 0, "CSR offsets must start at 0");
+    std::vector<int> stamp(c->p, -1);
+    for (int b = 0; b < m; ++b) {
+        REQ(in_ptr[b + 1] >= in_ptr[b] && out_ptr[b + 1] >= out_ptr[b], "CSR offsets must be non-decreasing");
+        REQ(in_ptr[b + 1] - in_ptr[b] <= c->k, "|J1| > k");
+        for (int t = in_ptr[b]; t < in_ptr[b + 1]; ++t) {
+            const int j = in_idx[t];
+            REQ(j >= 0 && j < c->p, "J1 index out of range");
+            REQ(stamp[j] != 2 * b, "repeated J1 index");
+            stamp[j] = 2 * b;
+        }
+        for (int t = out_ptr[b]; t < out_ptr[b + 1]; ++t) {
+            const int j = out_idx[t];
+            REQ(j >= 0 && j < c->p, "J0 index out of range");
+            REQ(stamp[j] != 2 * b, "J0 and J1 overlap");
+            REQ(stamp[j] != 2 * b + 1, "repeated J0 index");
+            stamp[j] = 2 * b + 1;
+        }
+        if (warm_slot) REQ(warm_slot[b] >= -1 && warm_slot[b] < c->pool_slots, "warm slot out of range");
+    }
+}
+
+void push_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx, const int32_t* out_ptr,
+               const int32_t* out_idx, const int32_t* warm_slot, const double* warm_B) {
+    validate_nodes(c, m, in_ptr, in_idx, out_ptr, out_idx, warm_slot);
+    const size_t nnz_in = in_ptr[m], nnz_out = out_ptr[m];
+    const size_t need = std::max(nnz_in, nnz_out);
+    if (need > c->idx_cap) {
+        size_t cap = std::max(need, (size_t)c->mcap * (size_t)(c->k + 8));
+        c->d_in_idx = dalloc_t<int>(c, cap);
+        c->d_out_idx = dalloc_t<int>(c, cap);
+        c->idx_cap = cap;
+    }
+    CK(cudaMemcpyAsync(c->d_in_ptr, in_ptr, sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_out_ptr, out_ptr, sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c->st));
+    if (nnz_in) CK(cudaMemcpyAsync(c->d_in_idx, in_idx, sizeof(int) * nnz_in, cudaMemcpyHostToDevice, c->st));
+    if (nnz_out) CK(cudaMemcpyAsync(c->d_out_idx, out_idx, sizeof(int) * nnz_out, cudaMemcpyHostToDevice, c->st));
+    const int* slot = nullptr;
+    if (warm_slot) {
+        CK(cudaMemcpyAsync(c->d_slot, warm_slot, sizeof(int) * m, cudaMemcpyHostToDevice, c->st));
+        slot = c->d_slot;
+    }
+    const double* wb = nullptr;
+    if (warm_B) {
+        if (!c->d_warmB) c->d_warmB = dalloc_t<double>(c, (size_t)c->mcap * c->p);
+        CK(cudaMemcpyAsync(c->d_warmB, warm_B, sizeof(double) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
+        wb = c->d_warmB;
+    }
+    layout_masks(c->st, m, c->p, c->W, c->k, c->d_in_ptr, c->d_in_idx, c->d_out_ptr, c->d_out_idx, c->in_mask,
+                 c->out_mask, c->kbar, c->pf, (int)nnz_in, (int)nnz_out);
+    check_launch();
+    layout_warm(c->st, m, c->p, c->W, c->f64, slot, c->pool, wb, c->out_mask, c->B, c->V, nullptr, c->tmom,
+                c->active);
+    check_launch();
+    c->h_kbar.resize(m);
+    c->h_pf.resize(m);
+    for (int b = 0; b < m; ++b) {
+        const int n1 = in_ptr[b + 1] - in_ptr[b], n0 = out_ptr[b + 1] - out_ptr[b];
+        c->h_kbar[b] = c->k - n1;
+        c->h_pf[b] = c->p - n1 - n0;
+    }
+    sync(c);   // host arrays may be pageable and reused by the caller
+    c->m = m;
+    c->pushed = true;
+    c->evaluated = false;
+}
+
+void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, int32_t* support,
+                      double* beta_re, int32_t* branch_j, int32_t* iters_done) {
+    const int m = c->m;
+    c->h_lb.resize(m);
+    c->h_ub.resize(m);
+    c->h_jstar.resize(m);
+    CK(cudaMemcpyAsync(c->h_lb.data(), c->lb_best, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->h_ub.data(), c->ub, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->h_jstar.data(), c->jstar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+    if (primal) CK(cudaMemcpyAsync(primal, c->primal_now, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
+    if (support) CK(cudaMemcpyAsync(support, c->support, sizeof(int) * (size_t)m * c->k, cudaMemcpyDeviceToHost, c->st));
+    if (beta_re) CK(cudaMemcpyAsync(beta_re, c->beta_re, sizeof(double) * (size_t)m * c->k, cudaMemcpyDeviceToHost, c->st));
+    if (iters_done) CK(cudaMemcpyAsync(iters_done, c->iters_done, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    if (lb) memcpy(lb, c->h_lb.data(), sizeof(double) * m);
+    if (ub_cand) memcpy(ub_cand, c->h_ub.data(), sizeof(double) * m);
+    if (branch_j) memcpy(branch_j, c->h_jstar.data(), sizeof(int) * m);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kglm_version(void) { return "kglm 0.1 sm_103a"; }
+
+// Message of a failed kglm_create (the context does not survive it).
+static thread_local std::string g_create_err = "no error";
+
+const char* kglm_last_error(const kglm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+void kglm_destroy(kglm_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+    delete ctx;
+}
+
+kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y, void* stream, kglm_ctx** out) {
+    if (!out) return KGLM_EINVAL;
+    *out = nullptr;
+    if (!desc || !X || !y) return KGLM_EINVAL;
+    kglm_ctx* c = new (std::nothrow) kglm_ctx();
+    if (!c) return KGLM_ENOMEM;
+    kglm_status st = guarded(c, [&] {
+        const kglm_desc& d = *desc;
+        REQ(d.n > 0 && d.p > 0 && d.n < (1LL << 31) && d.p < (1LL << 31), "n and p must be positive");
+        REQ(d.k >= 1 && d.k <= KGLM_MAX_K && d.k <= d.p, "k must be in [1, min(p, KGLM_MAX_K)]");
+        REQ(d.lambda2 > 0 && isfinite(d.lambda2), "lambda2 must be positive");
+        REQ(d.M > 0 && isfinite(d.M), "M must be positive");
+        REQ(d.loss == KGLM_LSQ || d.loss == KGLM_LOGISTIC, "unknown loss");
+        REQ(d.prec == KGLM_FP64 || d.prec == KGLM_FP32, "precision not available in this build");
+        REQ(d.max_batch >= 1, "max_batch must be >= 1");
+        REQ(d.p <= (d.prec == KGLM_FP64 ? 4096 : 8192), "p above the prox kernel limit for this precision");
+        c->d = d;
+        c->n = (int)d.n; c->p = (int)d.p; c->k = d.k; c->kind = d.loss; c->prec = d.prec;
+        c->f64 = d.prec == KGLM_FP64;
+        c->W = (c->p + 31) / 32;
+        c->lam2 = d.lambda2; c->M = d.M;
+        c->gap_tol = d.gap_tol > 0 ? d.gap_tol : 1e-6;
+        const size_t n = c->n, p = c->p;
+        for (size_t t = 0; t < n * p; ++t)
+            if (!isfinite(X[t])) throw Fail{KGLM_ENUMERIC, "X has a non-finite entry"};
+        for (size_t i = 0; i < n; ++i) {
+            if (!isfinite(y[i])) throw Fail{KGLM_ENUMERIC, "y has a non-finite entry"};
+            if (d.loss == KGLM_LOGISTIC) REQ(y[i] == 1.0 || y[i] == -1.0, "logistic labels must be -1 or +1");
+        }
+        if (stream) {
+            c->st = (cudaStream_t)stream;
+        } else {
+            CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        // instance: FP64 X, X^T, y (+ FP32 working copies), Gram and X^T y for re-optimization
+        std::vector<double> Xt(n * p);
+        for (size_t i = 0; i < n; ++i)
+            for (size_t j = 0; j < p; ++j) Xt[j * n + i] = X[i * p + j];
+        c->X64 = dalloc_t<double>(c, n * p);
+        c->Xt64 = dalloc_t<double>(c, n * p);
+        c->y64 = dalloc_t<double>(c, n);
+        CK(cudaMemcpyAsync(c->X64, X, sizeof(double) * n * p, cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->Xt64, Xt.data(), sizeof(double) * n * p, cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->y64, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+        if (!c->f64) {
+            c->X32 = dalloc_t<float>(c, n * p);
+            c->Xt32 = dalloc_t<float>(c, n * p);
+            c->y32 = dalloc_t<float>(c, n);
+            convert_f64_to_f32(c->st, c->X64, c->X32, n * p);
+            convert_f64_to_f32(c->st, c->Xt64, c->Xt32, n * p);
+            convert_f64_to_f32(c->st, c->y64, c->y32, n);
+            check_launch();
+        }
+        c->gram = dalloc_t<double>(c, p * p);
+        c->Xty = dalloc_t<double>(c, p);
+        gemm_nt_f64(c->st, (int)p, (int)p, (int)n, c->Xt64, (int)n, c->Xt64, (int)n, c->gram, (int)p);
+        gemm_nt_f64(c->st, (int)p, 1, (int)n, c->Xt64, (int)n, c->y64, (int)n, c->Xty, 1);
+        check_launch();
+        if (d.lipschitz > 0) {
+            c->L = d.lipschitz;
+        } else {
+            const double lam = gram_lambda_max(c) * (1.0 + 1e-6);
+            c->L = d.loss == KGLM_LSQ ? 2.0 * lam : 0.25 * lam;
+        }
+        c->eta = 1.0 / c->L;
+        c->c = 2.0 * c->eta * c->lam2;
+        // node batch
+        const size_t mc = (size_t)d.max_batch;
+        c->mcap = d.max_batch;
+        const size_t ws = c->f64 ? sizeof(double) : sizeof(float);
+        c->in_mask = dalloc_t<uint32_t>(c, mc * c->W);
+        c->out_mask = dalloc_t<uint32_t>(c, mc * c->W);
+        c->kbar = dalloc_t<int>(c, mc);
+        c->pf = dalloc_t<int>(c, mc);
+        c->B = dalloc(c, mc * p * ws);
+        c->V = dalloc(c, mc * p * ws);
+        c->G = dalloc(c, mc * p * ws);
+        c->R = dalloc(c, mc * n * std::max(ws, sizeof(float)));
+        c->tmom = dalloc_t<double>(c, mc);
+        c->active = dalloc_t<int>(c, mc);
+        c->iters_done = dalloc_t<int>(c, mc);
+        c->zeta = dalloc_t<double>(c, mc * n);
+        c->Q = dalloc_t<double>(c, mc * p);
+        c->sum_loss = dalloc_t<double>(c, mc);
+        c->sum_conj = dalloc_t<double>(c, mc);
+        c->lb_now = dalloc_t<double>(c, mc);
+        c->primal_now = dalloc_t<double>(c, mc);
+        c->lb_best = dalloc_t<double>(c, mc);
+        c->primal_last = dalloc_t<double>(c, mc);
+        c->ub = dalloc_t<double>(c, mc);
+        c->beta_re = dalloc_t<double>(c, mc * c->k);
+        c->support = dalloc_t<int>(c, mc * c->k);
+        c->jstar = dalloc_t<int>(c, mc);
+        c->pruned = dalloc_t<uint8_t>(c, mc);
+        c->d_in_ptr = dalloc_t<int>(c, mc + 1);
+        c->d_out_ptr = dalloc_t<int>(c, mc + 1);
+        c->d_slot = dalloc_t<int>(c, mc);
+        c->d_rows = dalloc_t<int>(c, mc);
+        c->d_slots = dalloc_t<int>(c, mc);
+        c->pool_slots = d.pool_slots > 0 ? d.pool_slots : 4 * d.max_batch;
+        c->pool = dalloc(c, (size_t)c->pool_slots * p * ws);
+        sync(c);
+    });
+    if (st != KGLM_OK) {
+        g_create_err = c->err;                         // kglm_last_error(NULL) returns it
+        kglm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return KGLM_OK;
+}
+
+kglm_status kglm_push_nodes(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr, const int32_t* in_idx,
+                            const int32_t* out_ptr, const int32_t* out_idx, const int32_t* warm_slot,
+                            const double* warm_B) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] { push_impl(ctx, m, in_ptr, in_idx, out_ptr, out_idx, warm_slot, warm_B); });
+}
+
+kglm_status kglm_evaluate(kglm_ctx* ctx, int32_t iters, int32_t check_every, double* lb, double* primal,
+                          double* ub_cand, int32_t* support, double* beta_re, int32_t* branch_j,
+                          int32_t* iters_done) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (!ctx->pushed) throw Fail{KGLM_ESTATE, "no node batch pushed"};
+        REQ(iters >= 0 && check_every >= 0, "iters and check_every must be >= 0");
+        evaluate_impl(ctx, iters, check_every);
+        evaluate_outputs(ctx, lb, primal, ub_cand, support, beta_re, branch_j, iters_done);
+        ctx->evaluated = true;
+    });
+}
+
+kglm_status kglm_read_batch(kglm_ctx* ctx, double* beta, double* zeta) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (!ctx->evaluated) throw Fail{KGLM_ESTATE, "batch not evaluated"};
+        const size_t mp = (size_t)ctx->m * ctx->p, mn = (size_t)ctx->m * ctx->n;
+        if (beta) {
+            if (ctx->f64) {
+                CK(cudaMemcpyAsync(beta, ctx->B, sizeof(double) * mp, cudaMemcpyDeviceToHost, ctx->st));
+                sync(ctx);
+            } else {
+                std::vector<float> h(mp);
+                CK(cudaMemcpyAsync(h.data(), ctx->B, sizeof(float) * mp, cudaMemcpyDeviceToHost, ctx->st));
+                sync(ctx);
+                for (size_t t = 0; t < mp; ++t) beta[t] = h[t];
+            }
+        }
+        if (zeta) {
+            CK(cudaMemcpyAsync(zeta, ctx->zeta, sizeof(double) * mn, cudaMemcpyDeviceToHost, ctx->st));
+            sync(ctx);
+        }
+    });
+}
+
+kglm_status kglm_save_warm(kglm_ctx* ctx, int32_t count, const int32_t* rows, const int32_t* slots) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (!ctx->evaluated) throw Fail{KGLM_ESTATE, "batch not evaluated"};
+        REQ(count >= 0 && count <= ctx->m, "count out of range");
+        if (count == 0) return;
+        REQ(rows && slots, "rows and slots are required");
+        for (int t = 0; t < count; ++t) {
+            REQ(rows[t] >= 0 && rows[t] < ctx->m, "row out of range");
+            REQ(slots[t] >= 0 && slots[t] < ctx->pool_slots, "slot out of range");
+        }
+        CK(cudaMemcpyAsync(ctx->d_rows, rows, sizeof(int) * count, cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(ctx->d_slots, slots, sizeof(int) * count, cudaMemcpyHostToDevice, ctx->st));
+        pool_store(ctx->st, count, ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B, ctx->pool);
+        check_launch();
+        sync(ctx);
+    });
+}
+
+kglm_status kglm_set_incumbent(kglm_ctx* ctx, double ub) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(!isnan(ub), "ub is NaN");
+        ctx->ub_inc = ub;
+    });
+}
+
+kglm_status kglm_prune(kglm_ctx* ctx, double ub, uint8_t* pruned, int32_t* n_survivors) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (!ctx->evaluated) throw Fail{KGLM_ESTATE, "batch not evaluated"};
+        REQ(!isnan(ub), "ub is NaN");
+        const int m = ctx->m;
+        const double thr = ub - delta_of(ctx, ub);
+        prune_launch(ctx->st, m, ctx->lb_best, thr, ctx->pruned);
+        check_launch();
+        std::vector<uint8_t> h(m);
+        CK(cudaMemcpyAsync(h.data(), ctx->pruned, m, cudaMemcpyDeviceToHost, ctx->st));
+        sync(ctx);
+        int surv = 0;
+        for (uint8_t v : h) surv += v ? 0 : 1;
+        if (pruned) memcpy(pruned, h.data(), m);
+        if (n_survivors) *n_survivors = surv;
+    });
+}
+
+kglm_status kglm_branch(kglm_ctx* ctx, double ub, int32_t* parent, int32_t* branch_j, int32_t* n_parents) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (!ctx->evaluated) throw Fail{KGLM_ESTATE, "batch not evaluated"};
+        REQ(!isnan(ub), "ub is NaN");
+        const double dl = delta_of(ctx, ub);
+        int cnt = 0;
+        for (int b = 0; b < ctx->m; ++b) {
+            const double lb = ctx->h_lb[b];
+            if (lb >= ub - dl) continue;                   // pruned
+            if (ctx->h_jstar[b] < 0) continue;             // leaf
+            if (ctx->h_ub[b] - lb <= dl) continue;         // fathomed by its own rounding
+            if (parent) parent[cnt] = b;
+            if (branch_j) branch_j[cnt] = ctx->h_jstar[b];
+            ++cnt;
+        }
+        if (n_parents) *n_parents = cnt;
+    });
+}
+
+kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t check_every, double time_limit_s,
+                       double* opt, int32_t* opt_support, double* opt_beta, double* gap, int64_t* nodes,
+                       int64_t* batches) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(batch >= 1 && batch <= ctx->mcap, "batch must be in [1, max_batch]");
+        REQ(iters >= 1, "iters must be >= 1");
+        struct Open {
+            double lb;
+            int64_t id;
+            std::vector<int> J0, J1;
+            int slot;
+        };
+        struct Cmp {
+            bool operator()(const Open* a, const Open* b) const {
+                return a->lb > b->lb || (a->lb == b->lb && a->id > b->id);
+            }
+        };
+        const auto t0 = std::chrono::steady_clock::now();
+        auto elapsed = [&] {
+            return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        };
+        std::priority_queue<Open*, std::vector<Open*>, Cmp> open;
+        std::vector<int> slot_ref(ctx->pool_slots, 0), free_slots;
+        for (int s = ctx->pool_slots - 1; s >= 0; --s) free_slots.push_back(s);
+        auto release = [&](int s) {
+            if (s >= 0 && --slot_ref[s] == 0) free_slots.push_back(s);
+        };
+        int64_t next_id = 0, n_nodes = 0, n_batches = 0;
+        open.push(new Open{-INFINITY, next_id++, {}, {}, -1});
+        double ub = INFINITY;
+        std::vector<int> best_sup(ctx->k, -1);
+        std::vector<double> best_coef(ctx->k, 0.0);
+        const int k = ctx->k;
+        std::vector<int> in_ptr, in_idx, out_ptr, out_idx, wslot;
+        std::vector<double> lb(batch), ubc(batch), bre((size_t)batch * k);
+        std::vector<int> sup((size_t)batch * k), bj(batch);
+        std::vector<Open*> cur;
+        try {
+            while (!open.empty()) {
+                if (time_limit_s > 0 && elapsed() > time_limit_s) break;
+                cur.clear();
+                const double dl = delta_of(ctx, ub);
+                while (!open.empty() && (int)cur.size() < batch) {
+                    Open* o = open.top();
+                    open.pop();
+                    if (o->lb >= ub - dl) {
+                        release(o->slot);
+                        delete o;
+                        continue;
+                    }
+                    cur.push_back(o);
+                }
+                if (cur.empty()) break;
+                const int m = (int)cur.size();
+                in_ptr.assign(1, 0);
+                out_ptr.assign(1, 0);
+                in_idx.clear();
+                out_idx.clear();
+                wslot.resize(m);
+                for (int b = 0; b < m; ++b) {
+                    in_idx.insert(in_idx.end(), cur[b]->J1.begin(), cur[b]->J1.end());
+                    out_idx.insert(out_idx.end(), cur[b]->J0.begin(), cur[b]->J0.end());
+                    in_ptr.push_back((int)in_idx.size());
+                    out_ptr.push_back((int)out_idx.size());
+                    wslot[b] = cur[b]->slot;
+                }
+                push_impl(ctx, m, in_ptr.data(), in_idx.data(), out_ptr.data(), out_idx.data(), wslot.data(), nullptr);
+                ctx->ub_inc = ub;
+                evaluate_impl(ctx, iters, check_every);
+                evaluate_outputs(ctx, lb.data(), nullptr, ubc.data(), sup.data(), bre.data(), bj.data(), nullptr);
+                ctx->evaluated = true;
+                n_nodes += m;
+                ++n_batches;
+                for (int b = 0; b < m; ++b) {
+                    release(cur[b]->slot);
+                    if (ubc[b] < ub) {
+                        ub = ubc[b];
+                        std::copy(sup.begin() + (size_t)b * k, sup.begin() + (size_t)(b + 1) * k, best_sup.begin());
+                        std::copy(bre.begin() + (size_t)b * k, bre.begin() + (size_t)(b + 1) * k, best_coef.begin());
+                    }
+                }
+                const double dl2 = delta_of(ctx, ub);
+                std::vector<int> rows, slots;
+                for (int b = 0; b < m; ++b) {
+                    Open* o = cur[b];
+                    const double lbb = std::max(lb[b], o->lb);
+                    if (lbb >= ub - dl2 || bj[b] < 0 || ubc[b] - lbb <= dl2) {
+                        delete o;
+                        continue;
+                    }
+                    const int j = bj[b];
+                    int s = -1;
+                    if (!free_slots.empty()) {
+                        s = free_slots.back();
+                        free_slots.pop_back();
+                        slot_ref[s] = 2;
+                        rows.push_back(b);
+                        slots.push_back(s);
+                    }
+                    Open* c0 = new Open{lbb, next_id++, o->J0, o->J1, s};
+                    c0->J0.push_back(j);
+                    Open* c1 = new Open{lbb, next_id++, o->J0, o->J1, s};
+                    c1->J1.push_back(j);
+                    open.push(c0);
+                    open.push(c1);
+                    delete o;
+                }
+                if (!rows.empty()) {
+                    CK(cudaMemcpyAsync(ctx->d_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, ctx->st));
+                    CK(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, ctx->st));
+                    pool_store(ctx->st, (int)rows.size(), ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B, ctx->pool);
+                    check_launch();
+                    sync(ctx);
+                }
+            }
+        } catch (...) {
+            while (!open.empty()) { delete open.top(); open.pop(); }
+            throw;
+        }
+        double open_lb = INFINITY;
+        while (!open.empty()) {
+            open_lb = std::min(open_lb, open.top()->lb);
+            delete open.top();
+            open.pop();
+        }
+        const double glb = std::min(open_lb, ub);
+        if (opt) *opt = ub;
+        if (gap) *gap = isfinite(ub) ? (ub - glb) / fmax(1.0, fabs(ub)) : INFINITY;
+        if (nodes) *nodes = n_nodes;
+        if (batches) *batches = n_batches;
+        if (opt_support) std::copy(best_sup.begin(), best_sup.end(), opt_support);
+        if (opt_beta) {
+            std::fill(opt_beta, opt_beta + ctx->p, 0.0);
+            for (int r = 0; r < k; ++r)
+                if (best_sup[r] >= 0) opt_beta[best_sup[r]] = best_coef[r];
+        }
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+// Device helpers of the node-bound engine: GLM loss functions, CTA-wide
+// reductions and the CTA top-k selection that replaces the padded column sort
+// of §4.2 (Fig. 2): a radix select of the k-th largest key among a node's free
+// coordinates, ties broken by the smaller coordinate index.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace kglm {
+
+constexpr int kLSQ = 0;
+constexpr int kLOGISTIC = 1;
+constexpr int kMaxK = 64;
+
+// ------------------------------------------------------------------ losses
+// l(s, y) = (s - y)^2 or log(1 + exp(-y s)); dl/ds; l*(w, y)   (§4.2, §4.4)
+
+__device__ __forceinline__ float dloss(float s, float y, int kind) {
+    return kind == kLSQ ? 2.0f * (s - y) : -y / (1.0f + expf(y * s));
+}
+__device__ __forceinline__ double dloss(double s, double y, int kind) {
+    return kind == kLSQ ? 2.0 * (s - y) : -y / (1.0 + exp(y * s));
+}
+
+__device__ __forceinline__ double softplus(double t) {   // log(1 + e^t), no overflow
+    return t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t));
+}
+
+__device__ __forceinline__ double loss64(double s, double y, int kind) {
+    if (kind == kLSQ) { double r = s - y; return r * r; }
+    return softplus(-y * s);
+}
+
+__device__ __forceinline__ double xlogx(double a) { return a > 0.0 ? a * log(a) : 0.0; }
+
+// l*(w, y): least squares w*y + w^2/4; logistic a ln a + (1-a) ln(1-a), a = -w*y
+// clamped into [0, 1] (the dual point is built inside the domain).
+__device__ __forceinline__ double loss_conj64(double w, double y, int kind) {
+    if (kind == kLSQ) return w * y + 0.25 * w * w;
+    double a = fmin(1.0, fmax(0.0, -w * y));
+    return xlogx(a) + xlogx(1.0 - a);
+}
+
+// Huber H_M (§3 Eq. (prelim_node_conjugate)).
+__device__ __forceinline__ double huber64(double q, double M) {
+    double a = fabs(q);
+    return a <= M ? 0.5 * a * a : M * a - 0.5 * M * M;
+}
+
+// ------------------------------------------------------------------ reductions
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum of NV values over the CTA; every thread gets the totals, summed in a
+// fixed order (deterministic).  red: shared scratch of NV * (NT/32) entries.
+template <int NT, int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* red) {
+    constexpr int NW = NT / 32;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[q * NW + (threadIdx.x >> 5)] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        T s = T(0);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += red[q * NW + w];
+        v[q] = s;
+    }
+}
+
+template <int NT, typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+    constexpr int NW = NT / 32;
+    v = warp_max(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = red[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s = max(s, red[w]);
+    return s;
+}
+
+template <int NT>
+__device__ __forceinline__ int block_count(int v, int* red) {
+    int a[1] = {v};
+    block_sum<NT, 1, int>(a, red);
+    return a[0];
+}
+
+// ------------------------------------------------------------------ selection
+
+// Order-preserving unsigned key of a non-negative float / double magnitude.
+__device__ __forceinline__ uint32_t mag_key(float a) { return __float_as_uint(a); }
+__device__ __forceinline__ unsigned long long mag_key(double a) {
+    return (unsigned long long)__double_as_longlong(a);
+}
+
+struct SelectShared {
+    unsigned hist[256];
+    int digit;
+    unsigned above;
+};
+
+// Radix select over the CTA: the kth (1-based) largest key among the elements
+// whose bit is set in `valid`.  Returns the key and `need`, the number of
+// elements equal to it that belong to the kth largest.  Requires 1 <= kth <=
+// number of valid elements.
+template <int NT, int E, typename K>
+__device__ void block_kth_largest(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
+                                  K& thr, int& need) {
+    constexpr int BITS = int(sizeof(K)) * 8;
+    K prefix = 0, pmask = 0;
+    int rem = kth;
+#pragma unroll 1
+    for (int shift = BITS - 8; shift >= 0; shift -= 8) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 256; i += NT) sh.hist[i] = 0u;
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (((valid >> e) & 1u) && (key[e] & pmask) == prefix)
+                atomicAdd(&sh.hist[(unsigned)(key[e] >> shift) & 255u], 1u);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            unsigned c[8], tot = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { c[q] = sh.hist[l * 8 + q]; tot += c[q]; }
+            unsigned incl = tot;   // sum over lanes >= l (higher digits)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned x = __shfl_down_sync(0xffffffffu, incl, o);
+                if (l + o < 32) incl += x;
+            }
+            unsigned above = incl - tot;
+            if (above < (unsigned)rem && (unsigned)rem <= incl) {
+                unsigned acc = above;
+#pragma unroll
+                for (int q = 7; q >= 0; --q) {
+                    if (acc + c[q] >= (unsigned)rem) { sh.digit = l * 8 + q; sh.above = acc; break; }
+                    acc += c[q];
+                }
+            }
+        }
+        __syncthreads();
+        rem -= (int)sh.above;
+        prefix |= K(sh.digit) << shift;
+        pmask |= K(255) << shift;
+    }
+    __syncthreads();
+    thr = prefix;
+    need = rem;
+}
+
+// Selection of the kth largest keys with ties to the smaller index.  Element
+// e of thread t is coordinate j = t + e*NT.  On return sel has bit e set for
+// the selected elements (exactly kth of them).
+template <int NT, int E, typename K>
+__device__ uint32_t block_topk_select(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
+                                      int* ired) {
+    K thr;
+    int need;
+    block_kth_largest<NT, E, K>(key, valid, kth, sh, thr, need);
+    uint32_t gt = 0, eq = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if ((valid >> e) & 1u) {
+            if (key[e] > thr) gt |= 1u << e;
+            else if (key[e] == thr) eq |= 1u << e;
+        }
+    }
+    int n_eq = block_count<NT>(__popc(eq), ired);
+    if (n_eq == need) return gt | eq;
+    // ties straddle the threshold: take the `need` smallest indices among them
+    uint32_t ikey[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) ikey[e] = ~(uint32_t)(threadIdx.x + e * NT);
+    uint32_t ithr;
+    int ineed;
+    block_kth_largest<NT, E, uint32_t>(ikey, eq, need, sh, ithr, ineed);
+    uint32_t take = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (((eq >> e) & 1u) && ikey[e] >= ithr) take |= 1u << e;
+    return gt | take;
+}
+
+// Sort up to kMaxK (value, index) pairs held in shared memory by value
+// descending, index ascending; done by warp 0.  out arrays must not alias in.
+template <typename T>
+__device__ void warp_rank_sort_desc(const T* val, const int* idx, int cnt, T* oval, int* oidx) {
+    if (threadIdx.x >= 32) return;
+    for (int i = threadIdx.x; i < cnt; i += 32) {
+        T v = val[i];
+        int ix = idx[i];
+        int r = 0;
+        for (int j = 0; j < cnt; ++j) {
+            T w = val[j];
+            int jx = idx[j];
+            r += (w > v) || (w == v && jx < ix);
+        }
+        oval[r] = v;
+        oidx[r] = ix;
+    }
+}
+
+}  // namespace kglm

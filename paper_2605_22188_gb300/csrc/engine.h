@@ -1,0 +1,99 @@
+// Internal launchers of the node-bound engine (host side).  All matrices are
+// row-major; node-major batch buffers hold one node per row (B[b*p + j]).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace kglm {
+
+// C[r][c] = sum_k A[r*lda + k] * B[c*ldb + k]  (both operands K-contiguous)
+void gemm_nt_f64(cudaStream_t s, int R, int C, int K, const double* A, int lda,
+                 const double* B, int ldb, double* out, int ldo);
+void gemm_nt_f32(cudaStream_t s, int R, int C, int K, const float* A, int lda,
+                 const float* B, int ldb, float* out, int ldo);
+// S = V X^T fused with the link: out[b][i] = dl(S[b][i], y[i])   (§4.2 Eq. (gradient_matrix_form))
+void gemm_link_f64(cudaStream_t s, int m, int n, int p, const double* V, const double* X,
+                   const double* y, int kind, double* out);
+void gemm_link_f32(cudaStream_t s, int m, int n, int p, const float* V, const float* X,
+                   const float* y, int kind, float* out);
+
+struct ProxArgs {
+    int m, p, W;
+    const void* G;        // gradient X^T R, node-major m x p (working type)
+    void* V;              // extrapolated point v (in: v_k, out: v_{k+1})
+    void* B;              // iterate beta (in: beta_k, out: beta_{k+1})
+    __nv_bfloat16* Vh;    // optional BF16 shadow of V (tensor-core operand)
+    const uint32_t* in_mask;
+    const uint32_t* out_mask;
+    const int* kbar;
+    const int* pf;
+    double* tmom;         // FISTA t' per node
+    const int* active;    // 1 = iterate this node
+    double eta, c, M;     // step, c = 2 eta lambda2 = 1/rho, box
+    int restart;
+};
+// One FISTA step per node: u = v - eta*G, beta' = prox(u), restart, next v.
+int prox_fista_f64(cudaStream_t s, const ProxArgs& a);
+int prox_fista_f32(cudaStream_t s, const ProxArgs& a);
+
+struct CertArgs {
+    int m, n, p, W, k, kind;
+    double lam2, M;
+    const void* S;        // S = X beta (m x n), working type or FP64 (s_is_f64)
+    int s_is_f64;
+    const double* y;
+    double* zeta;         // out: m x n FP64 dual points
+    double* sum_loss;     // out: m
+    double* sum_conj;     // out: m
+    const double* Q;      // X^T zeta (m x p) FP64
+    const void* B;        // beta (m x p) working type
+    int b_is_f64;
+    const uint32_t* in_mask;
+    const uint32_t* out_mask;
+    const int* kbar;
+    const int* pf;
+    double* lb;           // out
+    double* primal;       // out
+    int* support;         // out m x k
+    int* jstar;           // out
+};
+// zeta = -dl(S), row sums of l and l*(-zeta)   (§4.4 Eq. (batched_dual_candidate_matrix_form))
+void cert_dual_point(cudaStream_t s, const CertArgs& a);
+// LB = -sum l* - 2 lambda2 g*(Q/(2 lambda2)), Phi, support, j*   (§4.4, §4.3)
+int cert_bound(cudaStream_t s, const CertArgs& a);
+
+struct ReoptArgs {
+    int m, n, p, k, kind, max_iter;
+    double lam2, M, tol;
+    const double* Xt;      // p x n FP64
+    const double* y;       // n
+    const double* gram;    // p x p FP64 X^T X
+    const double* Xty;     // p FP64
+    const int* support;    // m x k
+    const void* B;         // warm start beta (m x p)
+    int b_is_f64;
+    double* ub;            // out: v(S_b)
+    double* beta_re;       // out: m x k
+};
+void reopt_launch(cudaStream_t s, const ReoptArgs& a);
+
+// node-batch layout (a2): CSR fixing lists -> masks, kbar, pf; warm starts
+void layout_masks(cudaStream_t s, int m, int p, int W, int k, const int* in_ptr, const int* in_idx,
+                  const int* out_ptr, const int* out_idx, uint32_t* in_mask, uint32_t* out_mask,
+                  int* kbar, int* pf, int nnz_in, int nnz_out);
+void layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, const void* pool,
+                 const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
+                 double* tmom, int* active);
+void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots,
+                const void* B, void* pool);
+// a8: pruned[b] = lb[b] >= thr ; alive[b] &= !pruned
+void prune_launch(cudaStream_t s, int m, const double* lb, double thr, uint8_t* pruned);
+// early-stop bookkeeping at a check: best LB, freeze nodes
+void check_update(cudaStream_t s, int m, const double* lb_now, const double* primal_now, double* lb_best,
+                  double* primal_last, int* active, int* iters_done, int it, double ub_thr, double gap_rtol);
+void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count);
+void convert_to_f64(cudaStream_t s, const void* in, int is_f64, double* out, size_t count);
+
+}  // namespace kglm

@@ -1,0 +1,158 @@
+// Node-batch layout (§4.2, Fig. 2 "padding"): the CSR fixing lists of a batch
+// become two bit masks per node (J1 and J0, ceil(p/32) words each), the
+// reduced budget kbar = k - |J1| and the free count pf = p - |J0| - |J1|.
+// Coordinates outside Jf are the padded entries of Fig. 2: the prox and
+// certificate kernels skip them instead of sorting sentinel keys.  Also: warm
+// starts from the device pool, pool stores, the pruning test of §3 and the
+// per-node bookkeeping of the periodic certificate.
+#include "common.cuh"
+#include "engine.h"
+
+namespace kglm {
+namespace {
+
+__global__ void k_set_bits(int nnz, const int* __restrict__ ptr, int m, const int* __restrict__ idx, int W,
+                           uint32_t* __restrict__ mask) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz) return;
+    // node of entry t: largest b with ptr[b] <= t (binary search over m+1 offsets)
+    int lo = 0, hi = m;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ptr[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int j = idx[t];
+    atomicOr(&mask[(size_t)lo * W + (j >> 5)], 1u << (j & 31));
+}
+
+__global__ void k_counts(int m, int p, int k, const int* in_ptr, const int* out_ptr, int* kbar, int* pf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    const int n1 = in_ptr[b + 1] - in_ptr[b], n0 = out_ptr[b + 1] - out_ptr[b];
+    kbar[b] = k - n1;
+    pf[b] = p - n1 - n0;
+}
+
+template <typename T>
+__global__ void k_warm(int m, int p, int W, const int* slot, const T* pool, const double* warmB,
+                       const uint32_t* out_mask, T* B, T* V, __nv_bfloat16* Vh) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)m * p) return;
+    const int b = (int)(t / p), j = (int)(t % p);
+    T w = T(0);
+    const int s = slot ? slot[b] : -1;
+    if (s >= 0) w = pool[(size_t)s * p + j];
+    else if (warmB) w = T(warmB[t]);
+    if ((out_mask[(size_t)b * W + (j >> 5)] >> (j & 31)) & 1u) w = T(0);
+    B[t] = w;
+    V[t] = w;
+    if (Vh) Vh[t] = __float2bfloat16((float)w);
+}
+
+__global__ void k_node_init(int m, double t0, double* tmom, int* active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    tmom[b] = t0;
+    active[b] = 1;
+}
+
+template <typename T>
+__global__ void k_pool_store(int count, int p, const int* rows, const int* slots, const T* B, T* pool) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)count * p) return;
+    const int c = (int)(t / p), j = (int)(t % p);
+    pool[(size_t)slots[c] * p + j] = B[(size_t)rows[c] * p + j];
+}
+
+__global__ void k_prune(int m, const double* lb, double thr, uint8_t* pruned) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    pruned[b] = lb[b] >= thr ? 1 : 0;
+}
+
+// At a certificate check: keep the best bound; freeze nodes that are pruned
+// (LB >= UB - delta) or whose relative gap is below gap_rtol.
+__global__ void k_check(int m, const double* lb_now, const double* primal_now, double* lb_best,
+                        double* primal_last, int* active, int* iters_done, int it, double ub_thr,
+                        double gap_rtol) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m || !active[b]) return;
+    const double lb = fmax(lb_best[b], lb_now[b]);
+    lb_best[b] = lb;
+    primal_last[b] = primal_now[b];
+    const double ph = primal_now[b];
+    if (lb >= ub_thr || ph - lb <= gap_rtol * fmax(1.0, fabs(ph))) {
+        active[b] = 0;
+        iters_done[b] = it;
+    }
+}
+
+__global__ void k_f64_to_f32(const double* in, float* out, size_t n) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (float)in[t];
+}
+__global__ void k_f32_to_f64(const float* in, double* out, size_t n) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (double)in[t];
+}
+
+inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void layout_masks(cudaStream_t s, int m, int p, int W, int k, const int* in_ptr, const int* in_idx,
+                  const int* out_ptr, const int* out_idx, uint32_t* in_mask, uint32_t* out_mask,
+                  int* kbar, int* pf, int nnz_in, int nnz_out) {
+    cudaMemsetAsync(in_mask, 0, sizeof(uint32_t) * (size_t)m * W, s);
+    cudaMemsetAsync(out_mask, 0, sizeof(uint32_t) * (size_t)m * W, s);
+    if (nnz_in > 0) k_set_bits<<<blocks(nnz_in, 256), 256, 0, s>>>(nnz_in, in_ptr, m, in_idx, W, in_mask);
+    if (nnz_out > 0) k_set_bits<<<blocks(nnz_out, 256), 256, 0, s>>>(nnz_out, out_ptr, m, out_idx, W, out_mask);
+    k_counts<<<blocks(m, 256), 256, 0, s>>>(m, p, k, in_ptr, out_ptr, kbar, pf);
+}
+
+void layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, const void* pool,
+                 const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
+                 double* tmom, int* active) {
+    const size_t n = (size_t)m * p;
+    if (is_f64)
+        k_warm<double><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, (const double*)pool, warmB, out_mask,
+                                                      (double*)B, (double*)V, Vh);
+    else
+        k_warm<float><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, (const float*)pool, warmB, out_mask,
+                                                     (float*)B, (float*)V, Vh);
+    // t' = (1 + sqrt(5)) / 2: the FISTA t after t_0 = 1
+    k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 0.5 * (1.0 + sqrt(5.0)), tmom, active);
+}
+
+void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots, const void* B,
+                void* pool) {
+    const size_t n = (size_t)count * p;
+    if (n == 0) return;
+    if (is_f64)
+        k_pool_store<double><<<blocks(n, 256), 256, 0, s>>>(count, p, rows, slots, (const double*)B, (double*)pool);
+    else
+        k_pool_store<float><<<blocks(n, 256), 256, 0, s>>>(count, p, rows, slots, (const float*)B, (float*)pool);
+}
+
+void prune_launch(cudaStream_t s, int m, const double* lb, double thr, uint8_t* pruned) {
+    if (m > 0) k_prune<<<blocks(m, 256), 256, 0, s>>>(m, lb, thr, pruned);
+}
+
+void check_update(cudaStream_t s, int m, const double* lb_now, const double* primal_now, double* lb_best,
+                  double* primal_last, int* active, int* iters_done, int it, double ub_thr, double gap_rtol) {
+    if (m > 0)
+        k_check<<<blocks(m, 256), 256, 0, s>>>(m, lb_now, primal_now, lb_best, primal_last, active, iters_done, it,
+                                               ub_thr, gap_rtol);
+}
+
+void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count) {
+    if (count) k_f64_to_f32<<<blocks(count, 256), 256, 0, s>>>(in, out, count);
+}
+
+void convert_to_f64(cudaStream_t s, const void* in, int is_f64, double* out, size_t count) {
+    if (!count) return;
+    if (is_f64) cudaMemcpyAsync(out, in, count * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else k_f32_to_f64<<<blocks(count, 256), 256, 0, s>>>((const float*)in, out, count);
+}
+
+}  // namespace kglm

@@ -1,0 +1,251 @@
+// Masked proximal step of §3 Eq. (pgd_step_vector_form) for a batch of nodes,
+// fused with the FISTA extrapolation and gradient restart.  One CTA per node.
+//
+// For node N with step eta, c = 2*eta*lambda2 = 1/rho and u = v - eta*G:
+//   J0:  beta_j = 0
+//   J1:  beta_j = sign(u_j) min(|u_j|/(1+c), M)          (Huber prox, weight rho)
+//   Jf:  beta_j = u_j - rho^{-1} [prox_{rho g*}(rho u)]_j with prox_{rho g*} by
+//        Algorithm 1 (App. B) on the free coordinates, budget kbar.
+// Algorithm 1 sorts |rho u|, shrinks the kbar largest by the Huber prox and
+// pools adjacent violators.  Violations can only start at the kbar / kbar+1
+// boundary (App. B), so the pooled result has one block with common value
+// theta (here in the scale of u, theta' = theta/rho):
+//   top (the kbar largest |u|):  v_j = max(p(|u_j|), theta'),
+//   tail (the others):           v_j = min(|u_j|, theta'),
+// p(a) = prox_{rho H_M}(rho a)/rho.  theta' is the root of the block's
+// optimality condition
+//   f(x) = sum_tail (|u_j| - x)^+ - sum_top (h(x) - |u_j|)^+ = 0,
+//   h(x) = x + min(x/c, M),
+// a strictly decreasing function.  Instead of the padded column sort of §4.2
+// (Fig. 2) the kernel selects the kbar largest free magnitudes (radix select),
+// sorts only those, finds the piece of f between consecutive top entry points
+// p(|u_j|) that holds the root (binary search), and solves the piece by Newton
+// steps from its left end: f is convex there, so the steps never pass the
+// root, and a step that crosses no tail value lands on it exactly.
+// beta_j = sign(u_j)(|u_j| - v_j) then gives
+//   top:  sign(u_j) min(|u_j|/(1+c), M, |u_j| - theta'),  tail: sign(u_j)(|u_j| - theta')^+.
+#include <float.h>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace kglm {
+namespace {
+
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> { using type = uint32_t; };
+template <> struct KeyOf<double> { using type = unsigned long long; };
+
+template <typename T>
+struct ProxShared {
+    SelectShared sel;
+    T red[2 * 32];
+    int ired[32];
+    int topcnt;
+    T topv[kMaxK];
+    int topi[kMaxK];
+    T sv[kMaxK];      // top magnitudes, descending
+    int si[kMaxK];
+};
+
+// p(a) in the scale of u: the Huber prox of weight rho at rho*a, divided by rho.
+template <typename T>
+__device__ __forceinline__ T entry_point(T a, T c, T M) {
+    return a <= (T(1) + c) * M ? a * c / (T(1) + c) : a - M;
+}
+
+// Root of n_t (x + min(x/c, M)) - S_t = S_l - n_l x  (the merged block's
+// value: Algorithm 1's prox_{rho_bar H_M}(xi_bar) written in the scale of u).
+template <typename T>
+__device__ __forceinline__ T model_root(T nt, T St, T nl, T Sl, T c, T M) {
+    const T xa = c * (St + Sl) / (nt * (T(1) + c) + c * nl);
+    if (xa <= c * M) return xa;
+    return (St + Sl - nt * M) / (nt + nl);
+}
+
+template <typename T, int NT, int E>
+__global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
+    using K = typename KeyOf<T>::type;
+    __shared__ ProxShared<T> sh;
+    const int b = blockIdx.x;
+    if (a.active != nullptr && a.active[b] == 0) return;
+    const int p = a.p;
+    const size_t base = (size_t)b * p;
+    const T* __restrict__ G = static_cast<const T*>(a.G);
+    T* __restrict__ V = static_cast<T*>(a.V);
+    T* __restrict__ Bm = static_cast<T*>(a.B);
+    const T eta = T(a.eta), c = T(a.c), M = T(a.M);
+    const uint32_t* im = a.in_mask + (size_t)b * a.W;
+    const uint32_t* om = a.out_mask + (size_t)b * a.W;
+
+    T u[E], vv[E], bo[E];
+    uint32_t valid = 0, fin = 0, fout = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = threadIdx.x + e * NT;
+        u[e] = vv[e] = bo[e] = T(0);
+        if (j < p) {
+            valid |= 1u << e;
+            const T v = V[base + j];
+            vv[e] = v;
+            bo[e] = Bm[base + j];
+            u[e] = v - eta * G[base + j];
+            if ((im[j >> 5] >> (j & 31)) & 1u) fin |= 1u << e;
+            else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= 1u << e;
+        }
+    }
+    const uint32_t ffree = valid & ~fin & ~fout;
+    const int kb = a.kbar[b], pf = a.pf[b];
+
+    T theta = T(0);
+    uint32_t top = 0;
+    if (kb > 0 && pf > kb) {
+        K key[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) key[e] = mag_key(abs(u[e]));
+        top = block_topk_select<NT, E, K>(key, ffree, kb, sh.sel, sh.ired);
+        if (threadIdx.x == 0) sh.topcnt = 0;
+        __syncthreads();
+        T tmax = T(0);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if ((top >> e) & 1u) {
+                const int s = atomicAdd(&sh.topcnt, 1);
+                sh.topv[s] = abs(u[e]);
+                sh.topi[s] = threadIdx.x + e * NT;
+            } else if ((ffree >> e) & 1u) {
+                tmax = max(tmax, abs(u[e]));
+            }
+        }
+        const T amax = block_max<NT, T>(tmax, sh.red);   // also publishes topv
+        warp_rank_sort_desc<T>(sh.topv, sh.topi, kb, sh.sv, sh.si);
+        __syncthreads();
+        if (amax > T(0)) {
+            // entry points in ascending order: e_(i) = p(sv[kb-1-i])
+            const T emin = entry_point(sh.sv[kb - 1], c, M);
+            if (emin >= amax) {
+                theta = amax;                      // no violation: nothing pools
+            } else {
+                int r = 0;                         // entry points below amax
+                for (int i = 0; i < kb; ++i) r += entry_point(sh.sv[kb - 1 - i], c, M) < amax;
+                auto xval = [&](int i) -> T {
+                    return i == 0 ? T(0) : (i <= r ? entry_point(sh.sv[kb - i], c, M) : amax);
+                };
+                auto Pval = [&](T x) -> T {        // sum_top (h(x) - |u|)^+ over entry points < x
+                    const T h = x + min(x / c, M);
+                    T s = T(0);
+                    for (int i = 0; i < kb; ++i) {
+                        const T t = sh.sv[i];
+                        if (entry_point(t, c, M) < x) s += max(h - t, T(0));
+                    }
+                    return s;
+                };
+                int lo = 0, hi = r + 1;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    const T x = xval(mid);
+                    T part[1] = {T(0)};
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (((ffree & ~top) >> e) & 1u) part[0] += max(abs(u[e]) - x, T(0));
+                    block_sum<NT, 1, T>(part, sh.red);
+                    if (part[0] - Pval(x) > T(0)) lo = mid; else hi = mid;
+                }
+                const T xlo = xval(lo), xhi = xval(hi);
+                T nt = T(0), St = T(0);
+                for (int i = 0; i < kb; ++i) {
+                    const T t = sh.sv[i];
+                    if (entry_point(t, c, M) <= xlo) { nt += T(1); St += t; }
+                }
+                T th = xlo;
+                T q[2] = {T(0), T(0)};
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((((ffree & ~top) >> e) & 1u) && abs(u[e]) > th) { q[0] += T(1); q[1] += abs(u[e]); }
+                block_sum<NT, 2, T>(q, sh.red);
+                T nl = q[0], Sl = q[1];
+                for (int it = 0; it < 4 * kMaxK + 64; ++it) {
+                    T tn = model_root(nt, St, nl, Sl, c, M);
+                    tn = min(max(tn, th), xhi);
+                    q[0] = q[1] = T(0);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if ((((ffree & ~top) >> e) & 1u) && abs(u[e]) > tn) { q[0] += T(1); q[1] += abs(u[e]); }
+                    block_sum<NT, 2, T>(q, sh.red);
+                    const bool done = (q[0] == nl);
+                    th = tn;
+                    nl = q[0];
+                    Sl = q[1];
+                    if (done) break;
+                }
+                theta = th;
+            }
+        }
+    }
+
+    T bn[E];
+    T dot[1] = {T(0)};
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        bn[e] = T(0);
+        if (!((valid >> e) & 1u)) continue;
+        const T au = abs(u[e]);
+        T mag = T(0);
+        if ((fout >> e) & 1u) {
+            mag = T(0);
+        } else if ((fin >> e) & 1u) {
+            mag = min(au / (T(1) + c), M);
+        } else if (kb == 0) {
+            mag = T(0);
+        } else if (pf <= kb) {
+            mag = min(au / (T(1) + c), M);
+        } else if ((top >> e) & 1u) {
+            mag = max(min(min(au / (T(1) + c), M), au - theta), T(0));
+        } else {
+            mag = max(au - theta, T(0));
+        }
+        bn[e] = u[e] < T(0) ? -mag : mag;
+        dot[0] += (vv[e] - bn[e]) * (bn[e] - bo[e]);
+    }
+    block_sum<NT, 1, T>(dot, sh.red);
+    const double tp = a.tmom[b];
+    const double tk1 = (a.restart && dot[0] > T(0)) ? 1.0 : tp;
+    const double tpp = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk1 * tk1));
+    const T coef = T((tk1 - 1.0) / tpp);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int j = threadIdx.x + e * NT;
+        if ((valid >> e) & 1u) {
+            const T vn = bn[e] + coef * (bn[e] - bo[e]);
+            Bm[base + j] = bn[e];
+            V[base + j] = vn;
+            if (a.Vh != nullptr) a.Vh[base + j] = __float2bfloat16((float)vn);
+        }
+    }
+    if (threadIdx.x == 0) a.tmom[b] = tpp;
+}
+
+template <typename T>
+int dispatch(cudaStream_t s, const ProxArgs& a) {
+    const int p = a.p, m = a.m;
+    if (m <= 0) return 0;
+#define KGLM_PROX(NT_, E_) k_prox_fista<T, NT_, E_><<<m, NT_, 0, s>>>(a)
+    if (p <= 64) KGLM_PROX(32, 2);
+    else if (p <= 128) KGLM_PROX(64, 2);
+    else if (p <= 256) KGLM_PROX(64, 4);
+    else if (p <= 512) KGLM_PROX(128, 4);
+    else if (p <= 1024) KGLM_PROX(128, 8);
+    else if (p <= 2048) KGLM_PROX(256, 8);
+    else if (p <= 4096) KGLM_PROX(512, 8);
+    else if (sizeof(T) == 4 && p <= 8192) KGLM_PROX(512, 16);
+    else return -1;
+#undef KGLM_PROX
+    return 0;
+}
+
+}  // namespace
+
+int prox_fista_f64(cudaStream_t s, const ProxArgs& a) { return dispatch<double>(s, a); }
+int prox_fista_f32(cudaStream_t s, const ProxArgs& a) { return dispatch<float>(s, a); }
+
+}  // namespace kglm

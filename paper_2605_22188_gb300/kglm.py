@@ -1,0 +1,242 @@
+"""ctypes binding of libkglm.so (include/kglm.h): argument marshalling only.
+
+Every step of the node-bound path runs in the CUDA library; this module only
+converts numpy arrays to pointers and status codes to exceptions.  There is no
+CPU fallback: if the library is missing, ``lib()`` raises.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KGLM_OK, KGLM_EINVAL, KGLM_ENOMEM, KGLM_ECUDA, KGLM_ETIMEOUT, KGLM_ESTATE, KGLM_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENUMERIC"}
+LSQ, LOGISTIC = 0, 1
+FP64, FP32, BF16, TF32 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "tf32": TF32}
+MAX_K = 64
+
+
+class kglm_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("p", C.c_int64), ("k", C.c_int32), ("loss", C.c_int32),
+        ("prec", C.c_int32), ("restart", C.c_int32), ("lambda2", C.c_double), ("M", C.c_double),
+        ("lipschitz", C.c_double), ("gap_tol", C.c_double), ("max_batch", C.c_int32),
+        ("pool_slots", C.c_int32), ("hbm_budget", C.c_int64),
+    ]
+
+
+class KglmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_LIB = None
+P = C.c_void_p
+D = C.POINTER(C.c_double)
+I32 = C.POINTER(C.c_int32)
+I64 = C.POINTER(C.c_int64)
+U8 = C.POINTER(C.c_uint8)
+
+_SIGS = {
+    "kglm_create": (C.c_int, [C.POINTER(kglm_desc), D, D, P, C.POINTER(P)]),
+    "kglm_push_nodes": (C.c_int, [P, C.c_int32, I32, I32, I32, I32, I32, D]),
+    "kglm_evaluate": (C.c_int, [P, C.c_int32, C.c_int32, D, D, D, I32, D, I32, I32]),
+    "kglm_read_batch": (C.c_int, [P, D, D]),
+    "kglm_save_warm": (C.c_int, [P, C.c_int32, I32, I32]),
+    "kglm_set_incumbent": (C.c_int, [P, C.c_double]),
+    "kglm_prune": (C.c_int, [P, C.c_double, U8, I32]),
+    "kglm_branch": (C.c_int, [P, C.c_double, I32, I32, I32]),
+    "kglm_solve": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_double, D, I32, D, D, I64, I64]),
+    "kglm_last_error": (C.c_char_p, [P]),
+    "kglm_destroy": (None, [P]),
+    "kglm_version": (C.c_char_p, []),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded libkglm.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libkglm.so is not built (%s); run paper_2605_22188_gb300.build.build()" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check(st, ctx):
+    if st != KGLM_OK:
+        raise KglmError(st, lib().kglm_last_error(ctx).decode())
+
+
+# ------------------------------------------------------------------ C-named calls
+
+def kglm_version():
+    return lib().kglm_version().decode()
+
+
+def kglm_create(X, y, k, lambda2, M, loss, prec="fp64", max_batch=1024, lipschitz=0.0, gap_tol=0.0,
+                restart=True, pool_slots=0, hbm_budget=0, stream=None):
+    X = _f64(X)
+    n, p = X.shape
+    y = _f64(y, (n,))
+    d = kglm_desc(n=n, p=p, k=int(k), loss=int(loss), prec=PREC.get(prec, prec), restart=int(bool(restart)),
+                  lambda2=float(lambda2), M=float(M), lipschitz=float(lipschitz), gap_tol=float(gap_tol),
+                  max_batch=int(max_batch), pool_slots=int(pool_slots), hbm_budget=int(hbm_budget))
+    out = P()
+    st = lib().kglm_create(C.byref(d), _ptr(X, D), _ptr(y, D), P(stream) if stream else None, C.byref(out))
+    _check(st, None)
+    return out
+
+
+def kglm_push_nodes(ctx, in_ptr, in_idx, out_ptr, out_idx, warm_slot=None, warm_B=None):
+    in_ptr, in_idx, out_ptr, out_idx = map(_i32, (in_ptr, in_idx, out_ptr, out_idx))
+    m = len(in_ptr) - 1
+    ws = None if warm_slot is None else _i32(warm_slot)
+    wb = None if warm_B is None else _f64(warm_B)
+    st = lib().kglm_push_nodes(ctx, m, _ptr(in_ptr, I32), _ptr(in_idx, I32), _ptr(out_ptr, I32),
+                               _ptr(out_idx, I32), _ptr(ws, I32), _ptr(wb, D))
+    _check(st, ctx)
+    return m
+
+
+def kglm_evaluate(ctx, m, k, iters, check_every=0):
+    lb, primal, ub = np.empty(m), np.empty(m), np.empty(m)
+    support = np.empty((m, k), dtype=np.int32)
+    beta_re = np.empty((m, k))
+    bj = np.empty(m, dtype=np.int32)
+    done = np.empty(m, dtype=np.int32)
+    st = lib().kglm_evaluate(ctx, int(iters), int(check_every), _ptr(lb, D), _ptr(primal, D), _ptr(ub, D),
+                             _ptr(support, I32), _ptr(beta_re, D), _ptr(bj, I32), _ptr(done, I32))
+    _check(st, ctx)
+    return dict(lb=lb, primal=primal, ub=ub, support=support, beta_re=beta_re, branch_j=bj, iters_done=done)
+
+
+def kglm_read_batch(ctx, m, n, p, beta=True, zeta=True):
+    B = np.empty((m, p)) if beta else None
+    Z = np.empty((m, n)) if zeta else None
+    _check(lib().kglm_read_batch(ctx, _ptr(B, D), _ptr(Z, D)), ctx)
+    return B, Z
+
+
+def kglm_save_warm(ctx, rows, slots):
+    rows, slots = _i32(rows), _i32(slots)
+    _check(lib().kglm_save_warm(ctx, len(rows), _ptr(rows, I32), _ptr(slots, I32)), ctx)
+
+
+def kglm_set_incumbent(ctx, ub):
+    _check(lib().kglm_set_incumbent(ctx, float(ub)), ctx)
+
+
+def kglm_prune(ctx, m, ub):
+    pruned = np.empty(m, dtype=np.uint8)
+    ns = C.c_int32()
+    _check(lib().kglm_prune(ctx, float(ub), _ptr(pruned, U8), C.byref(ns)), ctx)
+    return pruned, ns.value
+
+
+def kglm_branch(ctx, m, ub):
+    parent = np.empty(m, dtype=np.int32)
+    j = np.empty(m, dtype=np.int32)
+    cnt = C.c_int32()
+    _check(lib().kglm_branch(ctx, float(ub), _ptr(parent, I32), _ptr(j, I32), C.byref(cnt)), ctx)
+    return parent[:cnt.value].copy(), j[:cnt.value].copy()
+
+
+def kglm_solve(ctx, k, p, batch, iters, check_every=10, time_limit=0.0):
+    opt, gap = C.c_double(), C.c_double()
+    nodes, batches = C.c_int64(), C.c_int64()
+    sup = np.empty(k, dtype=np.int32)
+    beta = np.empty(p)
+    st = lib().kglm_solve(ctx, int(batch), int(iters), int(check_every), float(time_limit), C.byref(opt),
+                          _ptr(sup, I32), _ptr(beta, D), C.byref(gap), C.byref(nodes), C.byref(batches))
+    _check(st, ctx)
+    return dict(opt=opt.value, support=[int(s) for s in sup if s >= 0], beta=beta, gap=gap.value,
+                nodes=nodes.value, batches=batches.value)
+
+
+def kglm_destroy(ctx):
+    if ctx:
+        lib().kglm_destroy(ctx)
+
+
+class Engine:
+    """One instance (X, y, k, lambda2, M, loss) on the GPU; thin wrapper over the calls above."""
+
+    def __init__(self, X, y, k, lambda2, M, loss, **kw):
+        X = np.asarray(X)
+        self.n, self.p = X.shape
+        self.k = int(k)
+        self.m = 0
+        self.ctx = kglm_create(X, y, k, lambda2, M, loss, **kw)
+
+    def push(self, in_ptr, in_idx, out_ptr, out_idx, warm_slot=None, warm_B=None):
+        self.m = kglm_push_nodes(self.ctx, in_ptr, in_idx, out_ptr, out_idx, warm_slot, warm_B)
+        return self.m
+
+    def evaluate(self, iters, check_every=0):
+        return kglm_evaluate(self.ctx, self.m, self.k, iters, check_every)
+
+    def read_batch(self, beta=True, zeta=True):
+        return kglm_read_batch(self.ctx, self.m, self.n, self.p, beta, zeta)
+
+    def save_warm(self, rows, slots):
+        kglm_save_warm(self.ctx, rows, slots)
+
+    def set_incumbent(self, ub):
+        kglm_set_incumbent(self.ctx, ub)
+
+    def prune(self, ub):
+        return kglm_prune(self.ctx, self.m, ub)
+
+    def branch(self, ub):
+        return kglm_branch(self.ctx, self.m, ub)
+
+    def solve(self, batch, iters, check_every=10, time_limit=0.0):
+        return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit)
+
+    def close(self):
+        if self.ctx:
+            kglm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

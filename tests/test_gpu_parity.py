@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA node-bound path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written here, derived from the arithmetic):
+* FP64 path: iterates, bounds, primal values and re-optimized objectives
+  agree with the oracle to 1e-9 relative (summation order is the only
+  difference; FISTA is non-expansive so it does not amplify it);
+* every path: the GPU bound equals the oracle's Psi_N evaluated at the GPU's
+  own dual point to 1e-9 relative (the certificate arithmetic is FP64);
+* integer outputs (support, branching index, pruned flags) are compared
+  bit-exactly with the oracle's decision taken on the GPU's own iterate.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import node as on
+from oracle import reopt as ro
+from oracle import bnb as ob
+from paper_2605_22188_gb300 import kglm, synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-9
+
+
+def rel(a, b):
+    return abs(a - b) / max(1.0, abs(b))
+
+
+def special_nodes(p, k, rng):
+    """Edge cases: root, kbar = 0, pf <= kbar, almost everything fixed out, a J1-only leaf."""
+    nodes = [([], []),
+             ([], list(range(k))),                                   # kbar = 0
+             (list(range(p - k + 1)), []),                           # pf = k - 1 < kbar
+             (list(range(1, p - 2)), [0]),                           # pf = 2 <= kbar
+             (sorted(rng.choice(p, p // 2, replace=False).tolist()), []),
+             ([j for j in range(p) if j % 3], [0, 3])]
+    return nodes
+
+
+def make_batch(p, k, m, rng, max_out=None):
+    nodes = special_nodes(p, k, rng)
+    rest = synth.csr_to_sets(*synth.random_nodes(m - len(nodes), p, k, rng, max_out=max_out))
+    return nodes + rest
+
+
+@pytest.mark.parametrize("kind", [synth.LSQ, synth.LOGISTIC])
+def test_fp64_batch_matches_oracle(kind):
+    n, p, k = 300, 150, 6
+    X, y, _ = synth.instance(n, p, k, kind, rho=0.6, snr=3.0, seed=21)
+    lam2, M, T = 0.05, 2.0, 40
+    L = on.lipschitz(X, kind)
+    rng = np.random.default_rng(7)
+    nodes = make_batch(p, k, 70, rng)
+    csr = synth.sets_to_csr(nodes)
+    with kglm.Engine(X, y, k, lam2, M, kind, prec="fp64", max_batch=80, lipschitz=L) as eng:
+        eng.push(*csr)
+        res = eng.evaluate(T)
+        B, Z = eng.read_batch()
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        ref = on.solve_node(X, y, nd, lam2, M, kind, L, T)
+        scale = max(1.0, np.max(np.abs(ref["beta"])))
+        assert np.max(np.abs(B[b] - ref["beta"])) <= RTOL * scale, b
+        assert rel(res["lb"][b], ref["lb"]) <= RTOL, (b, res["lb"][b], ref["lb"])
+        if np.isfinite(ref["primal"]):
+            assert rel(res["primal"][b], ref["primal"]) <= RTOL, (b, res["primal"][b], ref["primal"])
+        # certificate arithmetic at the GPU's own dual point
+        assert rel(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind)) <= RTOL
+        # rounding and branching decided on the GPU's iterate
+        S = on.round_support(B[b], nd)
+        got = [int(s) for s in res["support"][b] if s >= 0]
+        assert got == S, (b, got, S)
+        assert res["branch_j"][b] == on.branch_index(B[b], nd), b
+        # re-optimization on that support
+        _, v = ro.reopt(X, y, S, lam2, M, kind, beta0=B[b])
+        assert rel(res["ub"][b], v) <= RTOL, (b, res["ub"][b], v)
+
+
+@pytest.mark.parametrize("kind", [synth.LSQ, synth.LOGISTIC])
+def test_fp32_certificate_is_fp64_exact_at_its_dual_point(kind):
+    n, p, k = 500, 200, 8
+    X, y, _ = synth.instance(n, p, k, kind, rho=0.5, snr=5.0, seed=5)
+    lam2, M, T = 1e-2, 2.0, 30
+    L = on.lipschitz(X, kind)
+    rng = np.random.default_rng(3)
+    nodes = make_batch(p, k, 40, rng)
+    with kglm.Engine(X, y, k, lam2, M, kind, prec="fp32", max_batch=64, lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(T)
+        B, Z = eng.read_batch()
+    worst = 0.0
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        assert rel(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind)) <= RTOL
+        assert [int(s) for s in res["support"][b] if s >= 0] == on.round_support(B[b], nd)
+        assert res["branch_j"][b] == on.branch_index(B[b], nd)
+        ref = on.solve_node(X, y, nd, lam2, M, kind, L, T)
+        worst = max(worst, rel(res["lb"][b], ref["lb"]))
+    # FP32 iterations against the FP64 trajectory after the same T: reported, loosely bounded
+    print("fp32 vs fp64 oracle, max rel LB difference after %d iterations: %.3e" % (T, worst))
+    assert worst <= 1e-4
+
+
+def test_check_every_and_incumbent_freeze():
+    """Periodic certificates: the bound is the best one seen; nodes above UB stop iterating."""
+    c, X, y, _ = synth.config_instance("c1_lsq_n200_p30_k5", seed=1)
+    L = on.lipschitz(X, c["kind"])
+    rng = np.random.default_rng(11)
+    nodes = make_batch(c["p"], c["k"], 24, rng, max_out=12)
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=32, lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        full = eng.evaluate(60)
+        ub = float(np.median(full["lb"]))
+        eng.set_incumbent(ub)
+        eng.push(*synth.sets_to_csr(nodes))
+        chk = eng.evaluate(60, check_every=10)
+    delta = 1e-6 * max(1.0, abs(ub))
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(c["p"], c["k"], J0, J1)
+        ref = on.solve_node(X, y, nd, c["lam2"], c["M"], c["kind"], L, 60, check_every=10, ub=ub,
+                            delta=delta, gap_rtol=1e-9)
+        assert chk["iters_done"][b] == ref["iters"], (b, chk["iters_done"][b], ref["iters"])
+        assert rel(chk["lb"][b], ref["lb"]) <= RTOL
+
+
+def test_prune_and_branch_follow_their_definitions():
+    c, X, y, _ = synth.config_instance("c1_lsq_n200_p30_k5", seed=2)
+    rng = np.random.default_rng(5)
+    nodes = make_batch(c["p"], c["k"], 30, rng, max_out=12)
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=32) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(50)
+        ub = float(np.min(res["ub"]))
+        pruned, ns = eng.prune(ub)
+        parent, jj = eng.branch(ub)
+    delta = 1e-6 * max(1.0, abs(ub))
+    exp = (res["lb"] >= ub - delta).astype(np.uint8)
+    assert np.array_equal(pruned, exp) and ns == int(np.sum(exp == 0))
+    want = [b for b in range(len(nodes)) if not exp[b] and res["branch_j"][b] >= 0
+            and res["ub"][b] - res["lb"][b] > delta]
+    assert parent.tolist() == want
+    assert jj.tolist() == [int(res["branch_j"][b]) for b in want]
+
+
+def test_warm_start_pool_equals_host_warm_start():
+    c, X, y, _ = synth.config_instance("c1_lsq_n200_p30_k5", seed=3)
+    nodes = [([], []), ([1, 2], [0])]
+    csr = synth.sets_to_csr(nodes)
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=4, pool_slots=4) as eng:
+        eng.push(*csr)
+        eng.evaluate(15)
+        B0, _ = eng.read_batch(zeta=False)
+        eng.save_warm([0, 1], [3, 1])
+        eng.push(*csr, warm_slot=[3, 1])
+        a = eng.evaluate(10)
+        Ba, _ = eng.read_batch(zeta=False)
+        eng.push(*csr, warm_B=B0)
+        b = eng.evaluate(10)
+        Bb, _ = eng.read_batch(zeta=False)
+    assert np.array_equal(Ba, Bb) and np.array_equal(a["lb"], b["lb"])
+
+
+def test_invalid_node_batches_are_rejected():
+    c, X, y, _ = synth.config_instance("c1_lsq_n200_p30_k5", seed=0)
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=4) as eng:
+        bad = [
+            ([0, 1], [1]),                   # overlap
+            ([], [0, 1, 2, 3, 4, 5]),        # |J1| > k
+            ([31], []),                      # out of range (p = 30)
+            ([2, 2], []),                    # repeat
+        ]
+        for nd in bad:
+            with pytest.raises(kglm.KglmError) as ei:
+                eng.push(*synth.sets_to_csr([nd]))
+            assert ei.value.status == kglm.KGLM_EINVAL
+        with pytest.raises(kglm.KglmError):
+            eng.push(*synth.sets_to_csr([([], [])] * 5))   # m > max_batch
+
+
+def _solve_and_compare(X, y, k, lam2, M, kind, batch, iters, check_every, prec="fp64"):
+    with kglm.Engine(X, y, k, lam2, M, kind, prec=prec, max_batch=batch) as eng:
+        res = eng.solve(batch, iters, check_every)
+    top = ro.brute_force(X, y, k, lam2, M, kind, top=2)
+    best, second = top[0], top[1]
+    delta = 1e-6 * max(1.0, abs(best[0]))
+    assert res["gap"] <= 1e-6
+    assert abs(res["opt"] - best[0]) <= RTOL * abs(best[0]) + delta
+    if second[0] - best[0] > delta:
+        assert tuple(res["support"]) == tuple(best[1])
+    return res
+
+
+def test_solve_c1_matches_brute_force():
+    c, X, y, _ = synth.config_instance("c1_lsq_n200_p30_k5", seed=0)
+    for batch in (1, 64):
+        _solve_and_compare(X, y, c["k"], c["lam2"], c["M"], c["kind"], batch, 400, 20)
+
+
+def test_solve_hard_lsq_and_logistic_match_brute_force():
+    X, y, _ = synth.instance(40, 16, 4, synth.LSQ, rho=0.9, snr=1.0, seed=3)
+    r = _solve_and_compare(X, y, 4, 1e-3, 2.0, synth.LSQ, 32, 400, 20)
+    assert r["nodes"] > 3
+    X, y, _ = synth.instance(60, 12, 3, synth.LOGISTIC, rho=0.7, seed=4)
+    _solve_and_compare(X, y, 3, 0.05, 2.0, synth.LOGISTIC, 16, 400, 20)
+
+
+def test_solve_matches_oracle_bnb_fp32():
+    X, y, _ = synth.instance(80, 20, 4, synth.LSQ, rho=0.8, snr=2.0, seed=9)
+    ref = ob.solve(X, y, 4, 1e-3, 2.0, synth.LSQ)
+    with kglm.Engine(X, y, 4, 1e-3, 2.0, synth.LSQ, prec="fp32", max_batch=64) as eng:
+        res = eng.solve(64, 300, 20)
+    assert res["gap"] <= 1e-6
+    assert rel(res["opt"], ref["opt"]) <= 1e-6
+    assert res["support"] == ref["support"]
