@@ -1,0 +1,470 @@
+#!/usr/bin/env python
+"""Certified node bounds per second of the batched node-bound engine (one JSON line).
+
+A step is one pass of the whole hot path over one node batch: layout of the
+batch's fixing masks, `iters` FISTA iterations (X*V with the fused link,
+X^T*R, masked prox), the FP64 certificate, rounding, re-optimization,
+branching index, pruning and branching.  The workload is the k-sparse
+logistic regression instance n=2000, p=200, k=10, lambda2=1e-2, M=2 with
+node batches of 1024 random fixing patterns (|J1| ~ U{0..k},
+|J0| ~ U{0..p/2}), FP32 products and the FP64 certificate.
+
+  value  nodes certified per second with the instance and the node batches
+         already in device memory (kglm_push_nodes_dev);
+  e2e    the same through kglm_push_nodes from pinned host buffers, the
+         host->device copy of the batch and the device->host read of the
+         per-node results inside each timed step.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one rank per GPU, each rank evaluating its own
+batches (node batches are independent: weak scaling, no data-path
+collective).  --impl reference times the FP64 oracle on the host cores on
+bounded samples of the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_22188_gb300 import synth  # noqa: E402
+
+WORKLOAD = "c2_logistic_n2000_p200_k10"
+METRIC = "certified node bounds/sec"
+UNIT = "nodes/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Fallback peaks of the profiling recipe when MEASURED_PEAKS.json is absent.
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+SMS = 152
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 partitions x 32)
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64, nominal
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    d = dict(FALLBACK)
+    d["source"] = "fallback"
+    return d
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def reduce_max_sum(seconds, units):
+    """Max of the elapsed times and sum of the units over ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return seconds, units
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+PHASE_KERNEL_SOURCES = {
+    "gemm_xv_link": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
+    "gemm_xtr": ["paper_2605_22188_gb300/csrc/gemm_simt.cu"],
+    "prox_fista": ["paper_2605_22188_gb300/csrc/prox.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
+    "cert_xtzeta": ["paper_2605_22188_gb300/csrc/gemm_simt.cu"],
+    "cert_xb": ["paper_2605_22188_gb300/csrc/gemm_simt.cu"],
+    "cert_bound": ["paper_2605_22188_gb300/csrc/cert.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
+    "cert_dual_point": ["paper_2605_22188_gb300/csrc/cert.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
+    "reopt": ["paper_2605_22188_gb300/csrc/reopt.cu"],
+}
+
+
+def traffic_for(phase, workload):
+    """DRAM bytes per launch from the committed ncu summary, if its kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(workload, {}).get(phase)
+    if not e or phase not in PHASE_KERNEL_SOURCES:
+        return None
+    if e.get("source_sha") != source_sha(PHASE_KERNEL_SOURCES[phase]):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def roofline(stats, prec, pk):
+    """Achieved rate of the phase with the largest device time, against its peak."""
+    best = None
+    for name, s in stats.items():
+        if s["launches"] > 0 and s["work"] > 0 and s["ms"] > 0:
+            if best is None or s["ms"] > stats[best]["ms"]:
+                best = name
+    if best is None:
+        return None
+    s = stats[best]
+    per_launch_s = s["ms"] / 1e3 / s["launches"]
+    work = s["work"] / s["launches"]
+    sm_max = pk.get("sm_max_mhz", 2070.0) * 1e6
+    if best in ("gemm_xv_link", "gemm_xtr", "cert_xb", "cert_xtzeta"):
+        fp64 = prec == "fp64" or best == "cert_xtzeta"
+        if fp64:
+            peak, note = FP64_NOMINAL_TFLOPS, "FP64 nominal of the recipe"
+        else:
+            peak = SMS * FP32_LANES_PER_SM * 2 * sm_max / 1e12
+            note = "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"
+        achieved = work / per_launch_s / 1e12
+        return {"kernel": best, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for(best, WORKLOAD),
+                "peak_note": note, "launches": s["launches"], "avg_launch_us": per_launch_s * 1e6}
+    peak = pk["hbm_gbs"]
+    achieved = work / per_launch_s / 1e9
+    return {"kernel": best, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic_for(best, WORKLOAD),
+            "peak_note": "HBM copy bandwidth, %s" % pk["source"], "launches": s["launches"],
+            "avg_launch_us": per_launch_s * 1e6}
+
+
+# ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
+
+_ORACLE_STATE = {}
+
+
+def _oracle_init(X, y, c, L):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    _ORACLE_STATE.update(X=X, y=y, c=c, L=L)
+
+
+def _oracle_node(args):
+    """One node through the oracle: T FISTA iterations, certificate, rounding, re-opt, branch index."""
+    from oracle import node as on
+    from oracle import reopt as ro
+    J0, J1, T = args
+    s = _ORACLE_STATE
+    c = s["c"]
+    nd = on.Node(c["p"], c["k"], J0, J1)
+    r = on.solve_node(s["X"], s["y"], nd, c["lam2"], c["M"], c["kind"], s["L"], T)
+    S = on.round_support(r["beta"], nd)
+    ro.reopt(s["X"], s["y"], S, c["lam2"], c["M"], c["kind"], beta0=r["beta"])
+    on.branch_index(r["beta"], nd)
+    return r["lb"]
+
+
+def oracle_pool(X, y, c, L, cores):
+    ctx = mp.get_context("spawn")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    return ctx.Pool(cores, initializer=_oracle_init, initargs=(X, y, c, L))
+
+
+def oracle_rate(pool, nodes, T, cores):
+    t0 = time.perf_counter()
+    pool.map(_oracle_node, [(J0, J1, T) for J0, J1 in nodes], chunksize=1)
+    dt = time.perf_counter() - t0
+    return len(nodes) / dt, dt
+
+
+# ------------------------------------------------------------------ the engine arm
+
+def make_batches(c, nb, m, seed):
+    rng = np.random.default_rng(seed)
+    return [synth.random_nodes(m, c["p"], c["k"], rng) for _ in range(nb)]
+
+
+def run_ours(args):
+    import torch
+    from paper_2605_22188_gb300 import kglm
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    c, X, y, _ = synth.config_instance(args.workload, seed=0)
+    m, T = c.get("m", 1024), args.iters
+    pk = peaks()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X, y, c, T, args)      # spawn pool before the first CUDA call
+
+    stream = torch.cuda.Stream()
+    eng = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=args.prec, max_batch=m,
+                      stream=stream.cuda_stream)
+    batches = make_batches(c, 8, m, seed=1000 + rank)
+    dev = []
+    for (ip, ii, op, oi) in batches:
+        t = [torch.from_numpy(a).to("cuda") for a in (ip, ii, op, oi)]
+        dev.append((t, int(ip[-1]), int(op[-1])))
+    pinned = [tuple(torch.from_numpy(a).pin_memory().numpy() for a in bt) for bt in batches]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step_dev(i):
+        t, nin, nout = dev[i % len(dev)]
+        eng.push_dev(m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(), nin, nout)
+        res = eng.evaluate(T)
+        eng.prune(ub)
+        eng.branch(ub)
+        return res
+
+    def step_host(i):
+        eng.push(*pinned[i % len(pinned)])
+        res = eng.evaluate(T)
+        eng.prune(ub)
+        eng.branch(ub)
+        return res
+
+    def timed(fn, steps):
+        total = 0.0
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn(i)
+                b.record(stream)
+                b.synchronize()
+                total += a.elapsed_time(b) / 1e3
+        return total
+
+    ub = math.inf
+    for i in range(max(args.warmup, 3)):
+        r = step_dev(i)
+        ub = min(ub, float(np.min(r["ub"])))
+    torch.cuda.synchronize()
+
+    eng.stats_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        dt = timed(step_dev, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    stats = eng.stats()
+    eng.stats_enable(False)
+    launches = sum(s["launches"] for s in stats.values())
+    secs, units = reduce_max_sum(dt, float(m * args.steps))
+    value = units / secs
+
+    # end to end from pinned host buffers
+    for i in range(2):
+        step_host(i)
+    barrier()
+    dt_e2e = timed(step_host, args.steps)
+    secs_e, units_e = reduce_max_sum(dt_e2e, float(m * args.steps))
+    ip, ii, op, oi = batches[0]
+    h2d = 4 * (len(ip) + len(ii) + len(op) + len(oi))
+    d2h = m * (8 * 3 + 4 * c["k"] + 8 * c["k"] + 4 + 4) + m      # lb, primal, ub, support, beta_re, j*, iters, pruned
+
+    # the same workload with FP64 products (the "mixed vs FP64" comparison of the metric)
+    fp64 = None
+    if args.prec != "fp64" and not args.no_fp64:
+        e64 = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=m,
+                          stream=stream.cuda_stream)
+        eng_keep, eng = eng, e64
+        step_dev(0)
+        n64 = max(2, args.steps // 4)
+        dt64 = timed(step_dev, n64)
+        fp64 = {"value": m * n64 / dt64, "unit": UNIT, "steps": n64}
+        eng = eng_keep
+        e64.close()
+
+    if rank != 0:
+        eng.close()
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": c["n"], "p": c["p"], "k": c["k"], "lambda2": c["lam2"],
+                   "M": c["M"], "loss": "logistic" if c["kind"] == synth.LOGISTIC else "least_squares",
+                   "nodes_per_batch": m, "iters": T, "products": args.prec, "certificate": "fp64",
+                   "masks": "|J1|~U{0..k}, |J0|~U{0..p/2}", "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": units_e / secs_e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline(stats, args.prec, pk),
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "fp64_products": fp64,
+        "phase_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stats.items() if v["ms"] > 0},
+    }
+    if fp64:
+        line["mixed_over_fp64"] = value / fp64["value"]
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
+def cpu_baseline(X, y, c, T, args):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload's nodes."""
+    from oracle import node as on
+    L = on.lipschitz(X, c["kind"])
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(77)
+    nodes = synth.csr_to_sets(*synth.random_nodes(cores * args.cpu_nodes_per_core, c["p"], c["k"], rng))
+    pool = oracle_pool(X, y, c, L, cores)
+    try:
+        pool.map(_oracle_node, [(J0, J1, 2) for J0, J1 in nodes[:cores]], chunksize=1)   # warm the workers
+        rate, dt = oracle_rate(pool, nodes, T, cores)
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d nodes of the workload (T=%d, certificate, rounding, re-opt, branch index), "
+                      "one process per core, %.1f s" % (len(nodes), T, dt)}
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores: same metric, bounded samples per step."""
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    from oracle import node as on
+    c, X, y, _ = synth.config_instance(args.workload, seed=0)
+    T = args.iters
+    L = on.lipschitz(X, c["kind"])
+    cores = os.cpu_count() or 1
+    per_step = cores * args.ref_nodes_per_core
+    rng = np.random.default_rng(1000)
+    pool = oracle_pool(X, y, c, L, cores)
+    total_nodes, total_s = 0, 0.0
+    try:
+        for i in range(args.warmup + args.steps):
+            nodes = synth.csr_to_sets(*synth.random_nodes(per_step, c["p"], c["k"], rng))
+            _, dt = oracle_rate(pool, nodes, T, cores)
+            if i >= args.warmup:
+                total_nodes += len(nodes)
+                total_s += dt
+    finally:
+        pool.close()
+        pool.join()
+    value = total_nodes / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": c["n"], "p": c["p"], "k": c["k"], "lambda2": c["lam2"],
+                   "M": c["M"], "iters": T, "sample_nodes_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d nodes per step, one process per core" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "tf32"])
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--cpu-nodes-per-core", type=int, default=150)
+    ap.add_argument("--ref-nodes-per-core", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            run_reference(args)
+        else:
+            run_ours(args)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

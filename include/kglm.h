@@ -162,6 +162,29 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
                        double time_limit_s, double* opt, int32_t* opt_support,
                        double* opt_beta, double* gap, int64_t* nodes, int64_t* batches);
 
+/* kglm_push_nodes with the CSR arrays (and warm_slot, if not NULL) already
+ * in device memory: in_ptr/out_ptr hold m+1 offsets, nnz_in = in_ptr[m] and
+ * nnz_out = out_ptr[m] are passed by value.  The arrays are read on the
+ * device before the call returns; the same checks as kglm_push_nodes run
+ * there and a failure returns KGLM_EINVAL (the batch is then undefined and
+ * must be pushed again).  No warm_B variant: use pool slots. */
+kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr, const int32_t* in_idx,
+                                const int32_t* out_ptr, const int32_t* out_idx, int32_t nnz_in,
+                                int32_t nnz_out, const int32_t* warm_slot);
+
+/* Per-phase device timers: a tracing aid in the spirit of the paper's
+ * per-component runtime breakdown (App. F).  While enabled, every kernel the context
+ * launches is bracketed by CUDA events on the context's stream; kglm_stats_read
+ * returns, per phase, the summed device milliseconds (0 while disabled), the
+ * kernel launch count (always counted) and the algorithmic work (FLOPs for
+ * products, bytes for the others; 0 when not defined).  Any output pointer may
+ * be NULL; arrays hold KGLM_NPHASE entries.  Phases: see kglm_phase_name.
+ * kglm_stats_enable resets the counters. */
+#define KGLM_NPHASE 11
+kglm_status kglm_stats_enable(kglm_ctx* ctx, int32_t enable);
+kglm_status kglm_stats_read(kglm_ctx* ctx, double* ms, int64_t* launches, double* work);
+const char* kglm_phase_name(int32_t phase);
+
 /* Message of the last failed call on ctx (never NULL). */
 const char* kglm_last_error(const kglm_ctx* ctx);
 

@@ -48,9 +48,22 @@ struct kglm_ctx {
     void* pool = nullptr;
     int pool_slots = 0;
     double ub_inc = INFINITY;
+    int* d_err = nullptr;
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
     std::vector<double> h_lb, h_ub;
+    double sum_pa = 0.0;   // sum over the batch of p - |J0(b)|
+    // per-phase device timers and launch counters
+    struct Rec {
+        int ph;
+        cudaEvent_t a, b;
+    };
+    bool stats_on = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<Rec> pending;
+    double st_ms[KGLM_NPHASE] = {};
+    double st_work[KGLM_NPHASE] = {};
+    int64_t st_n[KGLM_NPHASE] = {};
 };
 
 namespace {
@@ -115,6 +128,65 @@ void check_launch() {
 
 void sync(kglm_ctx* c) { CK(cudaStreamSynchronize(c->st)); }
 
+enum Phase {
+    PH_LAYOUT = 0, PH_GEMM_LINK, PH_GEMM_GRAD, PH_PROX, PH_CERT_XB, PH_CERT_DUAL, PH_CERT_Q, PH_CERT_BOUND,
+    PH_REOPT, PH_SMALL, PH_COPY
+};
+const char* const kPhaseNames[KGLM_NPHASE] = {
+    "layout", "gemm_xv_link", "gemm_xtr", "prox_fista", "cert_xb", "cert_dual_point", "cert_xtzeta",
+    "cert_bound", "reopt", "prune_check", "copies"};
+
+cudaEvent_t take_event(kglm_ctx* c) {
+    if (c->ev_free.empty()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        return e;
+    }
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+}
+
+// Brackets the launches of one phase with events on the context's stream
+// (only while timing is enabled) and adds the phase's algorithmic work.
+struct Scope {
+    kglm_ctx* c;
+    int ph;
+    cudaEvent_t a = nullptr;
+    Scope(kglm_ctx* c_, int ph_, int launches, double work) : c(c_), ph(ph_) {
+        c->st_n[ph] += launches;
+        c->st_work[ph] += work;
+        if (c->stats_on) {
+            a = take_event(c);
+            cudaEventRecord(a, c->st);
+        }
+    }
+    ~Scope() {
+        if (!a) return;
+        cudaEvent_t b = nullptr;
+        if (c->ev_free.empty()) {
+            if (cudaEventCreate(&b) != cudaSuccess) { c->ev_free.push_back(a); return; }
+        } else {
+            b = c->ev_free.back();
+            c->ev_free.pop_back();
+        }
+        cudaEventRecord(b, c->st);
+        c->pending.push_back({ph, a, b});
+    }
+};
+
+void harvest(kglm_ctx* c) {
+    for (auto& r : c->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+            c->st_ms[r.ph] += ms;
+        c->ev_free.push_back(r.a);
+        c->ev_free.push_back(r.b);
+    }
+    c->pending.clear();
+    cudaGetLastError();
+}
+
 double delta_of(const kglm_ctx* c, double ub) { return isfinite(ub) ? c->gap_tol * fmax(1.0, fabs(ub)) : 0.0; }
 
 // Largest eigenvalue of the FP64 Gram matrix by power iteration (the
@@ -155,15 +227,28 @@ void certify(kglm_ctx* c) {
     a.Q = c->Q; a.B = c->B; a.b_is_f64 = c->f64;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.lb = c->lb_now; a.primal = c->primal_now; a.support = c->support; a.jstar = c->jstar;
-    if (c->f64) gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n);
-    else gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n);
-    check_launch();
-    cert_dual_point(c->st, a);
-    check_launch();
-    gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p);   // X^T zeta, FP64
-    check_launch();
-    if (cert_bound(c->st, a) != 0) throw Fail{KGLM_EINVAL, "p too large for the certificate kernel"};
-    check_launch();
+    const double ws = c->f64 ? 8.0 : 4.0;
+    {
+        Scope sc(c, PH_CERT_XB, 1, 2.0 * n * c->sum_pa);
+        if (c->f64) gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n);
+        else gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n);
+        check_launch();
+    }
+    {
+        Scope sc(c, PH_CERT_DUAL, 1, (ws + 8.0) * (double)m * n);
+        cert_dual_point(c->st, a);
+        check_launch();
+    }
+    {
+        Scope sc(c, PH_CERT_Q, 1, 2.0 * n * c->sum_pa);
+        gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p);   // X^T zeta, FP64
+        check_launch();
+    }
+    {
+        Scope sc(c, PH_CERT_BOUND, 1, (8.0 + ws) * c->sum_pa);
+        if (cert_bound(c->st, a) != 0) throw Fail{KGLM_EINVAL, "p too large for the certificate kernel"};
+        check_launch();
+    }
 }
 
 __global__ void k_fold(int m, const double* lb_now, double* lb_best) {
@@ -181,22 +266,26 @@ __global__ void k_filli(int m, int* x, int v) {
 
 void iterate(kglm_ctx* c) {
     const int m = c->m, n = c->n, p = c->p;
-    if (c->f64) {
-        gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R);
+    const double flops = 2.0 * n * c->sum_pa;
+    {
+        Scope sc(c, PH_GEMM_LINK, 1, flops);
+        if (c->f64) gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R);
+        else gemm_link_f32(c->st, m, n, p, (const float*)c->V, c->X32, c->y32, c->kind, (float*)c->R);
         check_launch();
-        gemm_nt_f64(c->st, m, p, n, (const double*)c->R, n, c->Xt64, n, (double*)c->G, p);
-    } else {
-        gemm_link_f32(c->st, m, n, p, (const float*)c->V, c->X32, c->y32, c->kind, (float*)c->R);
-        check_launch();
-        gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p);
     }
-    check_launch();
+    {
+        Scope sc(c, PH_GEMM_GRAD, 1, flops);
+        if (c->f64) gemm_nt_f64(c->st, m, p, n, (const double*)c->R, n, c->Xt64, n, (double*)c->G, p);
+        else gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p);
+        check_launch();
+    }
     ProxArgs a{};
     a.m = m; a.p = p; a.W = c->W;
     a.G = c->G; a.V = c->V; a.B = c->B; a.Vh = nullptr;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
+    Scope sc(c, PH_PROX, 1, (c->f64 ? 8.0 : 4.0) * 5.0 * c->sum_pa);
     const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
     if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
     check_launch();
@@ -205,20 +294,29 @@ void iterate(kglm_ctx* c) {
 void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
     const int m = c->m;
     const unsigned gb = (unsigned)((m + 255) / 256);
-    k_fill<<<gb, 256, 0, c->st>>>(m, c->lb_best, -INFINITY);
-    k_filli<<<gb, 256, 0, c->st>>>(m, c->iters_done, iters);
-    check_launch();
+    {
+        Scope sc(c, PH_SMALL, 2, 0.0);
+        k_fill<<<gb, 256, 0, c->st>>>(m, c->lb_best, -INFINITY);
+        k_filli<<<gb, 256, 0, c->st>>>(m, c->iters_done, iters);
+        check_launch();
+    }
     const double thr = c->ub_inc - delta_of(c, c->ub_inc);
     std::vector<int> h_active;
     for (int it = 1; it <= iters; ++it) {
         iterate(c);
         if (check_every > 0 && it % check_every == 0 && it < iters) {
             certify(c);
-            check_update(c->st, m, c->lb_now, c->primal_now, c->lb_best, c->primal_last, c->active,
-                         c->iters_done, it, thr, 1e-9);
-            check_launch();
+            {
+                Scope sc(c, PH_SMALL, 1, 0.0);
+                check_update(c->st, m, c->lb_now, c->primal_now, c->lb_best, c->primal_last, c->active,
+                             c->iters_done, it, thr, 1e-9);
+                check_launch();
+            }
             h_active.resize(m);
-            CK(cudaMemcpyAsync(h_active.data(), c->active, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+            {
+                Scope sc(c, PH_COPY, 0, 4.0 * m);
+                CK(cudaMemcpyAsync(h_active.data(), c->active, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+            }
             sync(c);
             bool any = false;
             for (int v : h_active) any |= (v != 0);
@@ -226,8 +324,11 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
         }
     }
     certify(c);
-    k_fold<<<gb, 256, 0, c->st>>>(m, c->lb_now, c->lb_best);
-    check_launch();
+    {
+        Scope sc(c, PH_SMALL, 1, 0.0);
+        k_fold<<<gb, 256, 0, c->st>>>(m, c->lb_now, c->lb_best);
+        check_launch();
+    }
     ReoptArgs r{};
     r.m = m; r.n = c->n; r.p = c->p; r.k = c->k; r.kind = c->kind;
     r.max_iter = c->kind == KGLM_LSQ ? 20000 : 4000;
@@ -235,6 +336,7 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
     r.Xt = c->Xt64; r.y = c->y64; r.gram = c->gram; r.Xty = c->Xty;
     r.support = c->support; r.B = c->B; r.b_is_f64 = c->f64;
     r.ub = c->ub; r.beta_re = c->beta_re;
+    Scope sc(c, PH_REOPT, 1, 0.0);
     reopt_launch(c->st, r);
     check_launch();
 }
@@ -276,38 +378,85 @@ void push_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx,
         c->d_out_idx = dalloc_t<int>(c, cap);
         c->idx_cap = cap;
     }
-    CK(cudaMemcpyAsync(c->d_in_ptr, in_ptr, sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->d_out_ptr, out_ptr, sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c->st));
-    if (nnz_in) CK(cudaMemcpyAsync(c->d_in_idx, in_idx, sizeof(int) * nnz_in, cudaMemcpyHostToDevice, c->st));
-    if (nnz_out) CK(cudaMemcpyAsync(c->d_out_idx, out_idx, sizeof(int) * nnz_out, cudaMemcpyHostToDevice, c->st));
-    const int* slot = nullptr;
-    if (warm_slot) {
-        CK(cudaMemcpyAsync(c->d_slot, warm_slot, sizeof(int) * m, cudaMemcpyHostToDevice, c->st));
-        slot = c->d_slot;
+    if (!c->d_warmB && warm_B) c->d_warmB = dalloc_t<double>(c, (size_t)c->mcap * c->p);
+    const int* slot = warm_slot ? c->d_slot : nullptr;
+    const double* wb = warm_B ? c->d_warmB : nullptr;
+    {
+        Scope sc(c, PH_COPY, 0, 4.0 * (2.0 * (m + 1) + nnz_in + nnz_out + (warm_slot ? m : 0)) +
+                                    (warm_B ? 8.0 * m * c->p : 0.0));
+        CK(cudaMemcpyAsync(c->d_in_ptr, in_ptr, sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->d_out_ptr, out_ptr, sizeof(int) * (m + 1), cudaMemcpyHostToDevice, c->st));
+        if (nnz_in) CK(cudaMemcpyAsync(c->d_in_idx, in_idx, sizeof(int) * nnz_in, cudaMemcpyHostToDevice, c->st));
+        if (nnz_out) CK(cudaMemcpyAsync(c->d_out_idx, out_idx, sizeof(int) * nnz_out, cudaMemcpyHostToDevice, c->st));
+        if (warm_slot) CK(cudaMemcpyAsync(c->d_slot, warm_slot, sizeof(int) * m, cudaMemcpyHostToDevice, c->st));
+        if (warm_B)
+            CK(cudaMemcpyAsync(c->d_warmB, warm_B, sizeof(double) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
     }
-    const double* wb = nullptr;
-    if (warm_B) {
-        if (!c->d_warmB) c->d_warmB = dalloc_t<double>(c, (size_t)c->mcap * c->p);
-        CK(cudaMemcpyAsync(c->d_warmB, warm_B, sizeof(double) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
-        wb = c->d_warmB;
-    }
-    layout_masks(c->st, m, c->p, c->W, c->k, c->d_in_ptr, c->d_in_idx, c->d_out_ptr, c->d_out_idx, c->in_mask,
-                 c->out_mask, c->kbar, c->pf, (int)nnz_in, (int)nnz_out);
-    check_launch();
-    layout_warm(c->st, m, c->p, c->W, c->f64, slot, c->pool, wb, c->out_mask, c->B, c->V, nullptr, c->tmom,
-                c->active);
-    check_launch();
     c->h_kbar.resize(m);
     c->h_pf.resize(m);
+    c->sum_pa = 0.0;
     for (int b = 0; b < m; ++b) {
         const int n1 = in_ptr[b + 1] - in_ptr[b], n0 = out_ptr[b + 1] - out_ptr[b];
         c->h_kbar[b] = c->k - n1;
         c->h_pf[b] = c->p - n1 - n0;
+        c->sum_pa += c->p - n0;
+    }
+    {
+        Scope sc(c, PH_LAYOUT, 0, (c->f64 ? 16.0 : 8.0) * m * c->p);
+        c->st_n[PH_LAYOUT] += layout_masks(c->st, m, c->p, c->W, c->k, c->d_in_ptr, c->d_in_idx, c->d_out_ptr,
+                                           c->d_out_idx, c->in_mask, c->out_mask, c->kbar, c->pf, (int)nnz_in,
+                                           (int)nnz_out, nullptr);
+        check_launch();
+        c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, slot, c->pool_slots, c->pool, wb,
+                                          c->out_mask, c->B, c->V, nullptr, c->tmom, c->active);
+        check_launch();
     }
     sync(c);   // host arrays may be pageable and reused by the caller
     c->m = m;
     c->pushed = true;
     c->evaluated = false;
+}
+
+void push_dev_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx, const int32_t* out_ptr,
+                   const int32_t* out_idx, int nnz_in, int nnz_out, const int32_t* warm_slot) {
+    REQ(m >= 1 && m <= c->mcap, "m must be in [1, max_batch]");
+    REQ(in_ptr && out_ptr, "in_ptr and out_ptr are required");
+    REQ(nnz_in >= 0 && nnz_out >= 0, "nnz must be >= 0");
+    REQ((nnz_in == 0 || in_idx) && (nnz_out == 0 || out_idx), "index arrays are required");
+    c->pushed = false;
+    c->evaluated = false;
+    std::vector<int> hk(m), hp(m);
+    int herr = 0;
+    {
+        Scope sc(c, PH_LAYOUT, 0, (c->f64 ? 16.0 : 8.0) * m * c->p);
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+        c->st_n[PH_LAYOUT] += layout_masks(c->st, m, c->p, c->W, c->k, in_ptr, in_idx, out_ptr, out_idx, c->in_mask,
+                                           c->out_mask, c->kbar, c->pf, nnz_in, nnz_out, c->d_err);
+        check_launch();
+        c->st_n[PH_LAYOUT] += layout_validate(c->st, m, c->k, c->W, nnz_in, nnz_out, in_ptr, out_ptr, c->in_mask,
+                                              c->out_mask, warm_slot, c->pool_slots, c->d_err);
+        check_launch();
+        c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, warm_slot, c->pool_slots, c->pool, nullptr,
+                                          c->out_mask, c->B, c->V, nullptr, c->tmom, c->active);
+        check_launch();
+    }
+    {
+        Scope sc(c, PH_COPY, 0, 4.0 + 8.0 * m);
+        CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(hk.data(), c->kbar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(hp.data(), c->pf, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+    }
+    sync(c);
+    if (herr) throw Fail{KGLM_EINVAL, std::string("device checks of the pushed batch failed (") +
+                                          ((herr & 1) ? "index out of range " : "") +
+                                          ((herr & 2) ? "bad offsets, |J1| > k, repeat or J0/J1 overlap " : "") +
+                                          ((herr & 4) ? "warm slot out of range" : "") + ")"};
+    c->h_kbar = hk;
+    c->h_pf = hp;
+    c->sum_pa = 0.0;
+    for (int b = 0; b < m; ++b) c->sum_pa += hp[b] + (c->k - hk[b]);
+    c->m = m;
+    c->pushed = true;
 }
 
 void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, int32_t* support,
@@ -316,6 +465,8 @@ void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, 
     c->h_lb.resize(m);
     c->h_ub.resize(m);
     c->h_jstar.resize(m);
+    Scope sc(c, PH_COPY, 0, (double)m * (20.0 + (primal ? 8 : 0) + (support ? 4.0 * c->k : 0) +
+                                         (beta_re ? 8.0 * c->k : 0) + (iters_done ? 4 : 0)));
     CK(cudaMemcpyAsync(c->h_lb.data(), c->lb_best, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(c->h_ub.data(), c->ub, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(c->h_jstar.data(), c->jstar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
@@ -324,6 +475,7 @@ void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, 
     if (beta_re) CK(cudaMemcpyAsync(beta_re, c->beta_re, sizeof(double) * (size_t)m * c->k, cudaMemcpyDeviceToHost, c->st));
     if (iters_done) CK(cudaMemcpyAsync(iters_done, c->iters_done, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
     sync(c);
+    harvest(c);
     if (lb) memcpy(lb, c->h_lb.data(), sizeof(double) * m);
     if (ub_cand) memcpy(ub_cand, c->h_ub.data(), sizeof(double) * m);
     if (branch_j) memcpy(branch_j, c->h_jstar.data(), sizeof(int) * m);
@@ -343,6 +495,8 @@ const char* kglm_last_error(const kglm_ctx* ctx) { return ctx ? ctx->err.c_str()
 void kglm_destroy(kglm_ctx* ctx) {
     if (!ctx) return;
     if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (auto& r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
@@ -448,6 +602,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->d_slot = dalloc_t<int>(c, mc);
         c->d_rows = dalloc_t<int>(c, mc);
         c->d_slots = dalloc_t<int>(c, mc);
+        c->d_err = dalloc_t<int>(c, 1);
         c->pool_slots = d.pool_slots > 0 ? d.pool_slots : 4 * d.max_batch;
         c->pool = dalloc(c, (size_t)c->pool_slots * p * ws);
         sync(c);
@@ -466,6 +621,40 @@ kglm_status kglm_push_nodes(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr, con
                             const double* warm_B) {
     if (!ctx) return KGLM_EINVAL;
     return guarded(ctx, [&] { push_impl(ctx, m, in_ptr, in_idx, out_ptr, out_idx, warm_slot, warm_B); });
+}
+
+kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr, const int32_t* in_idx,
+                                const int32_t* out_ptr, const int32_t* out_idx, int32_t nnz_in, int32_t nnz_out,
+                                const int32_t* warm_slot) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] { push_dev_impl(ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_out, warm_slot); });
+}
+
+kglm_status kglm_stats_enable(kglm_ctx* ctx, int32_t enable) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        sync(ctx);
+        harvest(ctx);
+        for (int i = 0; i < KGLM_NPHASE; ++i) ctx->st_ms[i] = ctx->st_work[i] = 0.0, ctx->st_n[i] = 0;
+        ctx->stats_on = enable != 0;
+    });
+}
+
+kglm_status kglm_stats_read(kglm_ctx* ctx, double* ms, int64_t* launches, double* work) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        sync(ctx);
+        harvest(ctx);
+        for (int i = 0; i < KGLM_NPHASE; ++i) {
+            if (ms) ms[i] = ctx->st_ms[i];
+            if (launches) launches[i] = ctx->st_n[i];
+            if (work) work[i] = ctx->st_work[i];
+        }
+    });
+}
+
+const char* kglm_phase_name(int32_t phase) {
+    return (phase >= 0 && phase < KGLM_NPHASE) ? kPhaseNames[phase] : "unknown";
 }
 
 kglm_status kglm_evaluate(kglm_ctx* ctx, int32_t iters, int32_t check_every, double* lb, double* primal,
@@ -517,8 +706,11 @@ kglm_status kglm_save_warm(kglm_ctx* ctx, int32_t count, const int32_t* rows, co
         }
         CK(cudaMemcpyAsync(ctx->d_rows, rows, sizeof(int) * count, cudaMemcpyHostToDevice, ctx->st));
         CK(cudaMemcpyAsync(ctx->d_slots, slots, sizeof(int) * count, cudaMemcpyHostToDevice, ctx->st));
-        pool_store(ctx->st, count, ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B, ctx->pool);
-        check_launch();
+        {
+            Scope sc(ctx, PH_SMALL, 1, 2.0 * (ctx->f64 ? 8 : 4) * (double)count * ctx->p);
+            pool_store(ctx->st, count, ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B, ctx->pool);
+            check_launch();
+        }
         sync(ctx);
     });
 }
@@ -538,8 +730,11 @@ kglm_status kglm_prune(kglm_ctx* ctx, double ub, uint8_t* pruned, int32_t* n_sur
         REQ(!isnan(ub), "ub is NaN");
         const int m = ctx->m;
         const double thr = ub - delta_of(ctx, ub);
-        prune_launch(ctx->st, m, ctx->lb_best, thr, ctx->pruned);
-        check_launch();
+        {
+            Scope sc(ctx, PH_SMALL, 1, 9.0 * m);
+            prune_launch(ctx->st, m, ctx->lb_best, thr, ctx->pruned);
+            check_launch();
+        }
         std::vector<uint8_t> h(m);
         CK(cudaMemcpyAsync(h.data(), ctx->pruned, m, cudaMemcpyDeviceToHost, ctx->st));
         sync(ctx);
@@ -681,8 +876,12 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
                 if (!rows.empty()) {
                     CK(cudaMemcpyAsync(ctx->d_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, ctx->st));
                     CK(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, ctx->st));
-                    pool_store(ctx->st, (int)rows.size(), ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B, ctx->pool);
-                    check_launch();
+                    {
+                        Scope sc(ctx, PH_SMALL, 1, 2.0 * (ctx->f64 ? 8 : 4) * (double)rows.size() * ctx->p);
+                        pool_store(ctx->st, (int)rows.size(), ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B,
+                                   ctx->pool);
+                        check_launch();
+                    }
                     sync(ctx);
                 }
             }

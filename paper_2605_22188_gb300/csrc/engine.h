@@ -80,12 +80,16 @@ struct ReoptArgs {
 void reopt_launch(cudaStream_t s, const ReoptArgs& a);
 
 // node-batch layout (a2): CSR fixing lists -> masks, kbar, pf; warm starts
-void layout_masks(cudaStream_t s, int m, int p, int W, int k, const int* in_ptr, const int* in_idx,
-                  const int* out_ptr, const int* out_idx, uint32_t* in_mask, uint32_t* out_mask,
-                  int* kbar, int* pf, int nnz_in, int nnz_out);
-void layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, const void* pool,
-                 const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
-                 double* tmom, int* active);
+// (layout launchers return the number of kernels they launched)
+int layout_masks(cudaStream_t s, int m, int p, int W, int k, const int* in_ptr, const int* in_idx,
+                 const int* out_ptr, const int* out_idx, uint32_t* in_mask, uint32_t* out_mask,
+                 int* kbar, int* pf, int nnz_in, int nnz_out, int* err);
+int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out, const int* in_ptr,
+                    const int* out_ptr, const uint32_t* in_mask, const uint32_t* out_mask, const int* slot,
+                    int nslots, int* err);
+int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
+                const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
+                double* tmom, int* active);
 void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots,
                 const void* B, void* pool);
 // a8: pruned[b] = lb[b] >= thr ; alive[b] &= !pruned

@@ -12,9 +12,13 @@ namespace kglm {
 namespace {
 
 __global__ void k_set_bits(int nnz, const int* __restrict__ ptr, int m, const int* __restrict__ idx, int W,
-                           uint32_t* __restrict__ mask) {
+                           int p, uint32_t* __restrict__ mask, int* err) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nnz) return;
+    if (idx[t] < 0 || idx[t] >= p) {                  // out of range: flag and skip
+        if (err) atomicOr(err, 1);
+        return;
+    }
     // node of entry t: largest b with ptr[b] <= t (binary search over m+1 offsets)
     int lo = 0, hi = m;
     while (hi - lo > 1) {
@@ -23,6 +27,34 @@ __global__ void k_set_bits(int nnz, const int* __restrict__ ptr, int m, const in
     }
     const int j = idx[t];
     atomicOr(&mask[(size_t)lo * W + (j >> 5)], 1u << (j & 31));
+}
+
+// Device-side checks of a pushed batch (CSR offsets, |J1| <= k, no repeats,
+// J0 and J1 disjoint) after the masks are built: a repeat collapses a bit, so
+// it shows up as a popcount below the list length.
+__global__ void k_validate(int m, int k, int W, int nnz_in, int nnz_out, const int* in_ptr, const int* out_ptr,
+                           const uint32_t* in_mask, const uint32_t* out_mask, int* err) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    int bad = 0;
+    const int n1 = in_ptr[b + 1] - in_ptr[b], n0 = out_ptr[b + 1] - out_ptr[b];
+    if (b == 0 && (in_ptr[0] != 0 || out_ptr[0] != 0)) bad = 1;
+    if (b == m - 1 && (in_ptr[m] != nnz_in || out_ptr[m] != nnz_out)) bad = 1;
+    if (n1 < 0 || n0 < 0 || n1 > k) bad = 1;
+    int c1 = 0, c0 = 0;
+    for (int w = 0; w < W; ++w) {
+        const uint32_t a = in_mask[(size_t)b * W + w], o = out_mask[(size_t)b * W + w];
+        if (a & o) bad = 1;
+        c1 += __popc(a);
+        c0 += __popc(o);
+    }
+    if (c1 != n1 || c0 != n0) bad = 1;
+    if (bad) atomicOr(err, 2);
+}
+
+__global__ void k_check_slots(int m, const int* slot, int nslots, int* err) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < m && (slot[b] < -1 || slot[b] >= nslots)) atomicOr(err, 4);
 }
 
 __global__ void k_counts(int m, int p, int k, const int* in_ptr, const int* out_ptr, int* kbar, int* pf) {
@@ -34,14 +66,14 @@ __global__ void k_counts(int m, int p, int k, const int* in_ptr, const int* out_
 }
 
 template <typename T>
-__global__ void k_warm(int m, int p, int W, const int* slot, const T* pool, const double* warmB,
+__global__ void k_warm(int m, int p, int W, const int* slot, int nslots, const T* pool, const double* warmB,
                        const uint32_t* out_mask, T* B, T* V, __nv_bfloat16* Vh) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)m * p) return;
     const int b = (int)(t / p), j = (int)(t % p);
     T w = T(0);
     const int s = slot ? slot[b] : -1;
-    if (s >= 0) w = pool[(size_t)s * p + j];
+    if (s >= 0 && s < nslots) w = pool[(size_t)s * p + j];
     else if (warmB) w = T(warmB[t]);
     if ((out_mask[(size_t)b * W + (j >> 5)] >> (j & 31)) & 1u) w = T(0);
     B[t] = w;
@@ -100,28 +132,45 @@ inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-void layout_masks(cudaStream_t s, int m, int p, int W, int k, const int* in_ptr, const int* in_idx,
-                  const int* out_ptr, const int* out_idx, uint32_t* in_mask, uint32_t* out_mask,
-                  int* kbar, int* pf, int nnz_in, int nnz_out) {
+int layout_masks(cudaStream_t s, int m, int p, int W, int k, const int* in_ptr, const int* in_idx,
+                 const int* out_ptr, const int* out_idx, uint32_t* in_mask, uint32_t* out_mask,
+                 int* kbar, int* pf, int nnz_in, int nnz_out, int* err) {
+    int launches = 1;
     cudaMemsetAsync(in_mask, 0, sizeof(uint32_t) * (size_t)m * W, s);
     cudaMemsetAsync(out_mask, 0, sizeof(uint32_t) * (size_t)m * W, s);
-    if (nnz_in > 0) k_set_bits<<<blocks(nnz_in, 256), 256, 0, s>>>(nnz_in, in_ptr, m, in_idx, W, in_mask);
-    if (nnz_out > 0) k_set_bits<<<blocks(nnz_out, 256), 256, 0, s>>>(nnz_out, out_ptr, m, out_idx, W, out_mask);
+    if (nnz_in > 0) {
+        k_set_bits<<<blocks(nnz_in, 256), 256, 0, s>>>(nnz_in, in_ptr, m, in_idx, W, p, in_mask, err);
+        ++launches;
+    }
+    if (nnz_out > 0) {
+        k_set_bits<<<blocks(nnz_out, 256), 256, 0, s>>>(nnz_out, out_ptr, m, out_idx, W, p, out_mask, err);
+        ++launches;
+    }
     k_counts<<<blocks(m, 256), 256, 0, s>>>(m, p, k, in_ptr, out_ptr, kbar, pf);
+    return launches;
 }
 
-void layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, const void* pool,
-                 const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
-                 double* tmom, int* active) {
+int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out, const int* in_ptr,
+                    const int* out_ptr, const uint32_t* in_mask, const uint32_t* out_mask, const int* slot,
+                    int nslots, int* err) {
+    k_validate<<<blocks(m, 128), 128, 0, s>>>(m, k, W, nnz_in, nnz_out, in_ptr, out_ptr, in_mask, out_mask, err);
+    if (slot) k_check_slots<<<blocks(m, 256), 256, 0, s>>>(m, slot, nslots, err);
+    return slot ? 2 : 1;
+}
+
+int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
+                const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
+                double* tmom, int* active) {
     const size_t n = (size_t)m * p;
     if (is_f64)
-        k_warm<double><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, (const double*)pool, warmB, out_mask,
+        k_warm<double><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const double*)pool, warmB, out_mask,
                                                       (double*)B, (double*)V, Vh);
     else
-        k_warm<float><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, (const float*)pool, warmB, out_mask,
+        k_warm<float><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const float*)pool, warmB, out_mask,
                                                      (float*)B, (float*)V, Vh);
     // t' = (1 + sqrt(5)) / 2: the FISTA t after t_0 = 1
     k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 0.5 * (1.0 + sqrt(5.0)), tmom, active);
+    return 2;
 }
 
 void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots, const void* B,

@@ -55,7 +55,12 @@ _SIGS = {
     "kglm_last_error": (C.c_char_p, [P]),
     "kglm_destroy": (None, [P]),
     "kglm_version": (C.c_char_p, []),
+    "kglm_push_nodes_dev": (C.c_int, [P, C.c_int32, P, P, P, P, C.c_int32, C.c_int32, P]),
+    "kglm_stats_enable": (C.c_int, [P, C.c_int32]),
+    "kglm_stats_read": (C.c_int, [P, D, I64, D]),
+    "kglm_phase_name": (C.c_char_p, [C.c_int32]),
 }
+NPHASE = 11
 
 
 def lib_path():
@@ -127,6 +132,27 @@ def kglm_push_nodes(ctx, in_ptr, in_idx, out_ptr, out_idx, warm_slot=None, warm_
                                _ptr(out_idx, I32), _ptr(ws, I32), _ptr(wb, D))
     _check(st, ctx)
     return m
+
+
+def kglm_push_nodes_dev(ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_out, warm_slot=0):
+    """Device-pointer variant: the arguments are integer device addresses (e.g. torch tensor.data_ptr())."""
+    st = lib().kglm_push_nodes_dev(ctx, int(m), P(in_ptr), P(in_idx or None), P(out_ptr), P(out_idx or None),
+                                   int(nnz_in), int(nnz_out), P(warm_slot or None))
+    _check(st, ctx)
+    return int(m)
+
+
+def kglm_stats_enable(ctx, enable=True):
+    _check(lib().kglm_stats_enable(ctx, int(bool(enable))), ctx)
+
+
+def kglm_stats_read(ctx):
+    ms = np.zeros(NPHASE)
+    n = np.zeros(NPHASE, dtype=np.int64)
+    work = np.zeros(NPHASE)
+    _check(lib().kglm_stats_read(ctx, _ptr(ms, D), _ptr(n, I64), _ptr(work, D)), ctx)
+    names = [lib().kglm_phase_name(i).decode() for i in range(NPHASE)]
+    return {names[i]: dict(ms=float(ms[i]), launches=int(n[i]), work=float(work[i])) for i in range(NPHASE)}
 
 
 def kglm_evaluate(ctx, m, k, iters, check_every=0):
@@ -202,6 +228,16 @@ class Engine:
     def push(self, in_ptr, in_idx, out_ptr, out_idx, warm_slot=None, warm_B=None):
         self.m = kglm_push_nodes(self.ctx, in_ptr, in_idx, out_ptr, out_idx, warm_slot, warm_B)
         return self.m
+
+    def push_dev(self, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_out, warm_slot=0):
+        self.m = kglm_push_nodes_dev(self.ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_out, warm_slot)
+        return self.m
+
+    def stats_enable(self, enable=True):
+        kglm_stats_enable(self.ctx, enable)
+
+    def stats(self):
+        return kglm_stats_read(self.ctx)
 
     def evaluate(self, iters, check_every=0):
         return kglm_evaluate(self.ctx, self.m, self.k, iters, check_every)
