@@ -49,6 +49,7 @@ struct kglm_ctx {
     int pool_slots = 0;
     double ub_inc = INFINITY;
     int* d_err = nullptr;
+    GemmScratch gs32{}, gs64{};   // split-K scratch of the CUDA-core GEMMs
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
     std::vector<double> h_lb, h_ub;
@@ -199,7 +200,7 @@ double gram_lambda_max(kglm_ctx* c) {
     double lam = 0.0;
     for (int it = 0; it < 500; ++it) {
         CK(cudaMemcpyAsync(v, h.data(), sizeof(double) * p, cudaMemcpyHostToDevice, c->st));
-        gemm_nt_f64(c->st, p, 1, p, c->gram, p, v, p, w, 1);
+        gemm_nt_f64(c->st, p, 1, p, c->gram, p, v, p, w, 1, &c->gs64);
         check_launch();
         CK(cudaMemcpyAsync(h.data(), w, sizeof(double) * p, cudaMemcpyDeviceToHost, c->st));
         sync(c);
@@ -230,8 +231,8 @@ void certify(kglm_ctx* c) {
     const double ws = c->f64 ? 8.0 : 4.0;
     {
         Scope sc(c, PH_CERT_XB, 1, 2.0 * n * c->sum_pa);
-        if (c->f64) gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n);
-        else gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n);
+        if (c->f64) gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n, &c->gs64);
+        else gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n, &c->gs32);
         check_launch();
     }
     {
@@ -241,7 +242,7 @@ void certify(kglm_ctx* c) {
     }
     {
         Scope sc(c, PH_CERT_Q, 1, 2.0 * n * c->sum_pa);
-        gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p);   // X^T zeta, FP64
+        gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p, &c->gs64);   // X^T zeta, FP64
         check_launch();
     }
     {
@@ -269,14 +270,14 @@ void iterate(kglm_ctx* c) {
     const double flops = 2.0 * n * c->sum_pa;
     {
         Scope sc(c, PH_GEMM_LINK, 1, flops);
-        if (c->f64) gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R);
-        else gemm_link_f32(c->st, m, n, p, (const float*)c->V, c->X32, c->y32, c->kind, (float*)c->R);
+        if (c->f64) gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R, &c->gs64);
+        else gemm_link_f32(c->st, m, n, p, (const float*)c->V, c->X32, c->y32, c->kind, (float*)c->R, &c->gs32);
         check_launch();
     }
     {
         Scope sc(c, PH_GEMM_GRAD, 1, flops);
-        if (c->f64) gemm_nt_f64(c->st, m, p, n, (const double*)c->R, n, c->Xt64, n, (double*)c->G, p);
-        else gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p);
+        if (c->f64) gemm_nt_f64(c->st, m, p, n, (const double*)c->R, n, c->Xt64, n, (double*)c->G, p, &c->gs64);
+        else gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p, &c->gs32);
         check_launch();
     }
     ProxArgs a{};
@@ -331,13 +332,15 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
     }
     ReoptArgs r{};
     r.m = m; r.n = c->n; r.p = c->p; r.k = c->k; r.kind = c->kind;
-    r.max_iter = c->kind == KGLM_LSQ ? 20000 : 4000;
+    r.max_iter = 100;                                   // projected Newton steps
     r.lam2 = c->lam2; r.M = c->M; r.tol = 1e-12;
     r.Xt = c->Xt64; r.y = c->y64; r.gram = c->gram; r.Xty = c->Xty;
+    r.Xt32 = c->f64 ? nullptr : c->Xt32;
+    r.y32 = c->f64 ? nullptr : c->y32;
     r.support = c->support; r.B = c->B; r.b_is_f64 = c->f64;
     r.ub = c->ub; r.beta_re = c->beta_re;
     Scope sc(c, PH_REOPT, 1, 0.0);
-    reopt_launch(c->st, r);
+    if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
     check_launch();
 }
 
@@ -556,10 +559,22 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             convert_f64_to_f32(c->st, c->y64, c->y32, n);
             check_launch();
         }
+        // split-K scratch: a plan splits only when its tiles do not fill the GPU,
+        // so (splits x tiles) stays below two waves plus one wave of tiles
+        auto scratch = [&](GemmScratch& g, size_t elem_bytes, size_t tile_elems) {
+            // splits x tiles <= 64 x (fewer than one wave of tiles) and <= a few waves
+            g.part_bytes = (size_t)(8 * 152 * 4) * tile_elems * elem_bytes;
+            g.part = dalloc(c, g.part_bytes);
+            g.n_counters = 8 * 152;
+            g.counters = dalloc_t<int>(c, g.n_counters);
+            CK(cudaMemsetAsync(g.counters, 0, sizeof(int) * g.n_counters, c->st));
+        };
+        scratch(c->gs64, sizeof(double), 64 * 64);
+        if (!c->f64) scratch(c->gs32, sizeof(float), 128 * 128);
         c->gram = dalloc_t<double>(c, p * p);
         c->Xty = dalloc_t<double>(c, p);
-        gemm_nt_f64(c->st, (int)p, (int)p, (int)n, c->Xt64, (int)n, c->Xt64, (int)n, c->gram, (int)p);
-        gemm_nt_f64(c->st, (int)p, 1, (int)n, c->Xt64, (int)n, c->y64, (int)n, c->Xty, 1);
+        gemm_nt_f64(c->st, (int)p, (int)p, (int)n, c->Xt64, (int)n, c->Xt64, (int)n, c->gram, (int)p, &c->gs64);
+        gemm_nt_f64(c->st, (int)p, 1, (int)n, c->Xt64, (int)n, c->y64, (int)n, c->Xty, 1, &c->gs64);
         check_launch();
         if (d.lipschitz > 0) {
             c->L = d.lipschitz;

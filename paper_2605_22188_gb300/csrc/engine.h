@@ -8,16 +8,32 @@
 
 namespace kglm {
 
-// C[r][c] = sum_k A[r*lda + k] * B[c*ldb + k]  (both operands K-contiguous)
+// Split-K scratch of the CUDA-core GEMMs: partial tiles and per-tile arrival
+// counters (zero between launches; the reducing CTA resets them).
+struct GemmScratch {
+    void* part;
+    size_t part_bytes;
+    int* counters;
+    int n_counters;
+};
+struct GemmPlan {
+    int gx, gy, splits, kchunk, tiles;
+    size_t part_elems;
+};
+// Bytes of scratch the launch plan needs are part_elems * sizeof(T).
+GemmPlan gemm_plan(int R, int C, int K, int is_f64);
+
+// C[r][c] = sum_k A[r*lda + k] * B[c*ldb + k]  (both operands K-contiguous).
+// scr may be NULL (then no split-K).
 void gemm_nt_f64(cudaStream_t s, int R, int C, int K, const double* A, int lda,
-                 const double* B, int ldb, double* out, int ldo);
+                 const double* B, int ldb, double* out, int ldo, const GemmScratch* scr);
 void gemm_nt_f32(cudaStream_t s, int R, int C, int K, const float* A, int lda,
-                 const float* B, int ldb, float* out, int ldo);
+                 const float* B, int ldb, float* out, int ldo, const GemmScratch* scr);
 // S = V X^T fused with the link: out[b][i] = dl(S[b][i], y[i])   (§4.2 Eq. (gradient_matrix_form))
 void gemm_link_f64(cudaStream_t s, int m, int n, int p, const double* V, const double* X,
-                   const double* y, int kind, double* out);
+                   const double* y, int kind, double* out, const GemmScratch* scr);
 void gemm_link_f32(cudaStream_t s, int m, int n, int p, const float* V, const float* X,
-                   const float* y, int kind, float* out);
+                   const float* y, int kind, float* out, const GemmScratch* scr);
 
 struct ProxArgs {
     int m, p, W;
@@ -69,6 +85,8 @@ struct ReoptArgs {
     double lam2, M, tol;
     const double* Xt;      // p x n FP64
     const double* y;       // n
+    const float* Xt32;     // p x n FP32 copy (NULL in the FP64 mode)
+    const float* y32;
     const double* gram;    // p x p FP64 X^T X
     const double* Xty;     // p FP64
     const int* support;    // m x k
@@ -77,7 +95,9 @@ struct ReoptArgs {
     double* ub;            // out: v(S_b)
     double* beta_re;       // out: m x k
 };
-void reopt_launch(cudaStream_t s, const ReoptArgs& a);
+// returns 0, or -1 if the dynamic shared memory for k cannot be granted
+int reopt_launch(cudaStream_t s, const ReoptArgs& a);
+size_t reopt_smem_bytes(int k);
 
 // node-batch layout (a2): CSR fixing lists -> masks, kbar, pf; warm starts
 // (layout launchers return the number of kernels they launched)

@@ -1,160 +1,329 @@
-// Re-optimization on the rounded support of each node (§4.3): projected
-// FISTA (the prox is the projection onto [-M, M]) for
+// Re-optimization on the rounded support of each node (§4.3):
 //   v(S) = min { F(X_S b) + lambda2 ||b||^2 : ||b||_inf <= M },
 // one CTA per node, FP64, warm-started from the node's relaxed beta on S.
-// Least squares runs on the k x k Gram block (X^T X)_SS and (X^T y)_S; the
-// logistic loss needs the gather-and-reduce passes over the n samples of
-// §4.3 (s_i = sum_r X_{i,S_r} b_r and grad_r = sum_i X_{i,S_r} R_i).  The step
-// is 1/L with L from the Gershgorin bound of the Gram block (an upper bound
-// of the largest eigenvalue).  The objective v(S) is recomputed exactly in a
-// final pass over the samples.
+//
+// §4.3 allows any proximal-gradient method whose prox is the projection onto
+// [-M, M]; the problem has at most k variables, so this kernel takes
+// projected Newton steps instead (Bertsekas, "Projected Newton methods for
+// optimization problems with simple constraints", SIAM J. Control Optim.
+// 1982): coordinates at a bound whose gradient points outward (within
+// eps = min(eps0, ||b - P(b - g)||)) are held, the Newton system is solved on
+// the others by Cholesky, and the step is backtracked along the projection
+// arc P(b + alpha d) until the Armijo condition holds.  It stops when the
+// projected gradient ||b - P(b - g)|| <= tol * max(1, ||g(b_0)||), the same
+// optimum the FISTA re-optimization reaches.  In the reduced-precision modes
+// the logistic steps run in FP32 (tolerance 2e-5): v(S) is flat at its
+// minimizer, so the FP64 objective at an FP32-accurate minimizer is within
+// O(tol^2) of the minimum.
+//
+// Least squares uses the Gram block (X^T X)_SS and (X^T y)_S; the logistic
+// gradient and Hessian are the gather-and-reduce passes of §4.3 over the n
+// samples (chunks of CH samples of X_S staged in shared memory).  The
+// returned v(S) is recomputed exactly in a final pass over the samples.
 #include "common.cuh"
 #include "engine.h"
 
 namespace kglm {
+
+// Samples per staged chunk: as many as fit 24 KB of X_S, a multiple of 32, at most one per thread.
+__host__ __device__ inline int reopt_chunk(int k) {
+    int ch = (24576 / (8 * (k > 0 ? k : 1))) / 32 * 32;
+    return ch < 32 ? 32 : (ch > 256 ? 256 : ch);
+}
+
 namespace {
 
 constexpr int NT = 256;
-constexpr int NW = NT / 32;
+constexpr int MAXOWN = (kMaxK * (kMaxK + 1) / 2 + kMaxK + NT - 1) / NT;
 
-struct ReoptShared {
+struct RS {
     int S[kMaxK];
-    double A[kMaxK * kMaxK];
-    double c[kMaxK];
-    double bcur[kMaxK], bold[kMaxK], v[kMaxK], grad[kMaxK], bnew[kMaxK];
-    double part[NW][kMaxK];
-    double red[4 * NW];
-    double L;
-    int ks;
+    double b[kMaxK], bn[kMaxK], g[kMaxK], d[kMaxK], c[kMaxK];
+    int fr[kMaxK];
+    double red[NT / 32];
+    double f, fn, alpha, gnorm0;
+    int ks, done, accept;
 };
 
-// grad = gradient of F(X_S b) + lambda2 ||b||^2 at sh.v (in sh.grad)
-__device__ void gradient(const ReoptArgs& a, ReoptShared& sh, const double* vec) {
-    const int ks = sh.ks;
+// Dynamic shared memory: H[k*k], Lc[k*k], Xs[k*ch], dv[ch], wv[ch] (ch samples per staged chunk).
+struct Dyn {
+    double *H, *Lc, *Xs, *dv, *wv;
+    int ch;
+};
+
+__device__ double block_total(double v, double* red) {
+    double a[1] = {v};
+    block_sum<NT, 1, double>(a, red);
+    return a[0];
+}
+
+__device__ __forceinline__ float softplusf(float t) { return t > 0.f ? t + log1pf(expf(-t)) : log1pf(expf(t)); }
+__device__ __forceinline__ float softplus_t(float t) { return softplusf(t); }
+__device__ __forceinline__ double softplus_t(double t) { return softplus(t); }
+__device__ __forceinline__ float exp_t(float t) { return expf(t); }
+__device__ __forceinline__ double exp_t(double t) { return exp(t); }
+
+// f at vec (up to the constant y^T y for least squares); with `full`, also g and H at vec.
+// The logistic passes run in TI (float in the reduced-precision modes, using
+// the FP32 copy of X^T; double in the FP64 mode).
+template <typename TI>
+__device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec, bool full) {
+    const int ks = sh.ks, k = a.k, tid = threadIdx.x;
     if (a.kind == kLSQ) {
-        // 2 (A b - c) with A = G_SS + lambda2 I
-        for (int r = threadIdx.x; r < ks; r += NT) {
+        // f = b^T (G + lambda2 I) b - 2 c^T b ; g = 2 ((G + lambda2 I) b - c) ; H = 2 (G + lambda2 I)
+        double part = 0.0;
+        for (int r = tid; r < ks; r += NT) {
             double s = 0.0;
-            for (int t = 0; t < ks; ++t) s += sh.A[r * kMaxK + t] * vec[t];
-            sh.grad[r] = 2.0 * (s - sh.c[r]);
+            for (int q = 0; q < ks; ++q) s += a.gram[(size_t)sh.S[r] * a.p + sh.S[q]] * vec[q];
+            s += a.lam2 * vec[r];
+            part += vec[r] * s - 2.0 * sh.c[r] * vec[r];
+            if (full) sh.g[r] = 2.0 * (s - sh.c[r]);
         }
+        if (full)
+            for (int t = tid; t < ks * ks; t += NT) {
+                const int r = t / ks, q = t % ks;
+                dy.H[r * k + q] = 2.0 * (a.gram[(size_t)sh.S[r] * a.p + sh.S[q]] + (r == q ? a.lam2 : 0.0));
+            }
+        const double f = block_total(part, sh.red);
+        if (tid == 0) { if (full) sh.f = f; else sh.fn = f; }
         __syncthreads();
         return;
     }
-    double acc[kMaxK];
-    for (int r = 0; r < ks; ++r) acc[r] = 0.0;
-    for (int i = threadIdx.x; i < a.n; i += NT) {
-        double s = 0.0;
-        for (int r = 0; r < ks; ++r) s += a.Xt[(size_t)sh.S[r] * a.n + i] * vec[r];
-        const double d = dloss(s, a.y[i], a.kind);
-        for (int r = 0; r < ks; ++r) acc[r] += a.Xt[(size_t)sh.S[r] * a.n + i] * d;
+    const int npairs = ks * (ks + 1) / 2;
+    const TI* Xt = static_cast<const TI*>(sizeof(TI) == 8 ? (const void*)a.Xt : (const void*)a.Xt32);
+    const TI* yv = static_cast<const TI*>(sizeof(TI) == 8 ? (const void*)a.y : (const void*)a.y32);
+    TI* Xs = reinterpret_cast<TI*>(dy.Xs);
+    TI* dv = reinterpret_cast<TI*>(dy.dv);
+    TI* wv = reinterpret_cast<TI*>(dy.wv);
+    TI acc[MAXOWN];
+#pragma unroll
+    for (int o = 0; o < MAXOWN; ++o) acc[o] = TI(0);
+    TI floss = TI(0);
+    const int CH = dy.ch;
+    for (int i0 = 0; i0 < a.n; i0 += CH) {
+        if (tid < CH) {
+            const int i = i0 + tid;
+            TI s = TI(0);
+            if (i < a.n) {
+                for (int r = 0; r < ks; ++r) {
+                    const TI x = Xt[(size_t)sh.S[r] * a.n + i];
+                    Xs[r * CH + tid] = x;
+                    s += x * TI(vec[r]);
+                }
+                const TI yi = yv[i];
+                floss += softplus_t(-yi * s);
+                const TI sg = TI(1) / (TI(1) + exp_t(yi * s));   // sigma(-y s)
+                dv[tid] = -yi * sg;
+                wv[tid] = sg * (TI(1) - sg);
+            } else {
+                for (int r = 0; r < ks; ++r) Xs[r * CH + tid] = TI(0);
+                dv[tid] = wv[tid] = TI(0);
+            }
+        }
+        __syncthreads();
+        if (full) {
+#pragma unroll
+            for (int o = 0; o < MAXOWN; ++o) {
+                const int P = tid + o * NT;
+                if (P < ks) {
+                    TI s = TI(0);
+                    for (int t = 0; t < CH; ++t) s += Xs[P * CH + t] * dv[t];
+                    acc[o] += s;
+                } else if (P < ks + npairs) {
+                    int q = P - ks, r = 0;
+                    while (q > r) { q -= r + 1; ++r; }          // pair (r, q), q <= r
+                    TI s = TI(0);
+                    for (int t = 0; t < CH; ++t) s += Xs[r * CH + t] * Xs[q * CH + t] * wv[t];
+                    acc[o] += s;
+                }
+            }
+        }
+        __syncthreads();
     }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int r = 0; r < ks; ++r) {
-        const double x = warp_sum(acc[r]);
-        if (l == 0) sh.part[w][r] = x;
+    double ridge = 0.0;
+    for (int r = 0; r < ks; ++r) ridge += vec[r] * vec[r];
+    const double f = block_total((double)floss, sh.red) + a.lam2 * ridge;
+    if (full) {
+#pragma unroll
+        for (int o = 0; o < MAXOWN; ++o) {
+            const int P = tid + o * NT;
+            if (P < ks) {
+                sh.g[P] = (double)acc[o] + 2.0 * a.lam2 * vec[P];
+            } else if (P < ks + npairs) {
+                int q = P - ks, r = 0;
+                while (q > r) { q -= r + 1; ++r; }
+                const double h = (double)acc[o] + (r == q ? 2.0 * a.lam2 : 0.0);
+                dy.H[r * k + q] = h;
+                dy.H[q * k + r] = h;
+            }
+        }
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < ks; r += NT) {
-        double s = 0.0;
-        for (int q = 0; q < NW; ++q) s += sh.part[q][r];
-        sh.grad[r] = s + 2.0 * a.lam2 * vec[r];
-    }
+    if (tid == 0) { if (full) sh.f = f; else sh.fn = f; }
     __syncthreads();
 }
 
+template <typename TI>
 __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
-    __shared__ ReoptShared sh;
-    const int b = blockIdx.x, k = a.k, p = a.p;
-    if (threadIdx.x == 0) {
+    // stopping levels of the working precision: projected-gradient tolerance,
+    // and the predicted decrease below which f cannot check Armijo
+    const double tol = sizeof(TI) == 8 ? a.tol : fmax(a.tol, 2e-5);
+    const double tiny_rel = sizeof(TI) == 8 ? 1e-14 : 3e-7;
+    __shared__ RS sh;
+    extern __shared__ __align__(16) double dyn[];
+    const int k = a.k, p = a.p, b = blockIdx.x, tid = threadIdx.x;
+    const int CH = reopt_chunk(k);
+    Dyn dy{dyn, dyn + k * k, dyn + 2 * k * k, dyn + 2 * k * k + k * CH, dyn + 2 * k * k + k * CH + CH, CH};
+    const double M = a.M;
+    if (tid == 0) {
         int ks = 0;
         for (int r = 0; r < k; ++r) {
             const int j = a.support[(size_t)b * k + r];
             if (j >= 0) sh.S[ks++] = j;
         }
         sh.ks = ks;
+        sh.done = 0;
     }
     __syncthreads();
     const int ks = sh.ks;
-    const double M = a.M;
-    for (int t = threadIdx.x; t < ks * ks; t += NT) {
-        const int r = t / ks, q = t % ks;
-        double g = a.gram[(size_t)sh.S[r] * p + sh.S[q]];
-        if (a.kind == kLSQ && r == q) g += a.lam2;
-        sh.A[r * kMaxK + q] = g;
-    }
-    for (int r = threadIdx.x; r < ks; r += NT) {
+    for (int r = tid; r < ks; r += NT) {
         sh.c[r] = a.Xty[sh.S[r]];
         const size_t bj = (size_t)b * p + sh.S[r];
         const double w = a.b_is_f64 ? static_cast<const double*>(a.B)[bj] : (double)static_cast<const float*>(a.B)[bj];
-        sh.bcur[r] = sh.bold[r] = fmin(M, fmax(-M, w));
+        sh.b[r] = fmin(M, fmax(-M, w));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double gmax = 0.0;                             // Gershgorin bound of the Gram block
-        for (int r = 0; r < ks; ++r) {
-            double s = 0.0;
-            for (int q = 0; q < ks; ++q) s += fabs(sh.A[r * kMaxK + q]);
-            gmax = fmax(gmax, s);
-        }
-        sh.L = a.kind == kLSQ ? 2.0 * gmax : 0.25 * gmax + 2.0 * a.lam2;
-        if (!(sh.L > 0.0)) sh.L = 1.0;
-    }
-    __syncthreads();
-    const double L = sh.L;
     if (ks > 0) {
-        gradient(a, sh, sh.bcur);
-        double g0 = 0.0;
-        for (int r = 0; r < ks; ++r) g0 += sh.grad[r] * sh.grad[r];
-        const double stop = a.tol * fmax(1.0, sqrt(g0));
-        double t = 1.0;
+        evaluate<TI>(a, sh, dy, sh.b, true);
+        if (tid == 0) {
+            double g2 = 0.0;
+            for (int r = 0; r < ks; ++r) g2 += sh.g[r] * sh.g[r];
+            sh.gnorm0 = fmax(1.0, sqrt(g2));
+        }
+        __syncthreads();
         for (int it = 0; it < a.max_iter; ++it) {
-            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-            const double coef = (t - 1.0) / tn;
-            for (int r = threadIdx.x; r < ks; r += NT) sh.v[r] = sh.bcur[r] + coef * (sh.bcur[r] - sh.bold[r]);
-            __syncthreads();
-            gradient(a, sh, sh.v);
-            for (int r = threadIdx.x; r < ks; r += NT) sh.bnew[r] = fmin(M, fmax(-M, sh.v[r] - sh.grad[r] / L));
-            __syncthreads();
-            double dot = 0.0;
-            for (int r = 0; r < ks; ++r) dot += (sh.v[r] - sh.bnew[r]) * (sh.bnew[r] - sh.bcur[r]);
-            t = dot > 0.0 ? 1.0 : tn;
-            __syncthreads();
-            for (int r = threadIdx.x; r < ks; r += NT) { sh.bold[r] = sh.bcur[r]; sh.bcur[r] = sh.bnew[r]; }
-            __syncthreads();
-            if ((it & 7) == 7) {                        // gradient-mapping test
-                gradient(a, sh, sh.bcur);
-                double gm = 0.0;
+            if (tid == 0) {
+                double pg = 0.0;
                 for (int r = 0; r < ks; ++r) {
-                    const double d = sh.bcur[r] - fmin(M, fmax(-M, sh.bcur[r] - sh.grad[r] / L));
-                    gm += d * d;
+                    const double t = sh.b[r] - fmin(M, fmax(-M, sh.b[r] - sh.g[r]));
+                    pg += t * t;
+                }
+                pg = sqrt(pg);
+                if (pg <= tol * sh.gnorm0) {
+                    sh.done = 1;
+                } else {
+                    const double eps = fmin(1e-3 * M, pg);
+                    int nf = 0;
+                    for (int r = 0; r < ks; ++r) {
+                        const bool held = (sh.b[r] <= -M + eps && sh.g[r] > 0.0) || (sh.b[r] >= M - eps && sh.g[r] < 0.0);
+                        sh.fr[r] = held ? -1 : nf++;
+                        sh.d[r] = 0.0;
+                    }
+                    // Cholesky of H_FF, then d_F = -H_FF^{-1} g_F
+                    double* L = dy.Lc;
+                    for (int r = 0, ir = 0; r < ks; ++r) {
+                        if (sh.fr[r] < 0) continue;
+                        for (int q = 0, iq = 0; q < ks; ++q) {
+                            if (sh.fr[q] < 0) continue;
+                            L[ir * k + iq] = dy.H[r * k + q];
+                            ++iq;
+                        }
+                        ++ir;
+                    }
+                    for (int j = 0; j < nf; ++j) {
+                        double s = L[j * k + j];
+                        for (int t = 0; t < j; ++t) s -= L[j * k + t] * L[j * k + t];
+                        s = s > 1e-300 ? sqrt(s) : 1e-150;
+                        L[j * k + j] = s;
+                        for (int i = j + 1; i < nf; ++i) {
+                            double v = L[i * k + j];
+                            for (int t = 0; t < j; ++t) v -= L[i * k + t] * L[j * k + t];
+                            L[i * k + j] = v / s;
+                        }
+                    }
+                    double z[kMaxK];
+                    for (int r = 0, ir = 0; r < ks; ++r) {
+                        if (sh.fr[r] < 0) continue;
+                        double v = -sh.g[r];
+                        for (int t = 0; t < ir; ++t) v -= L[ir * k + t] * z[t];
+                        z[ir] = v / L[ir * k + ir];
+                        ++ir;
+                    }
+                    for (int ir = nf - 1; ir >= 0; --ir) {
+                        double v = z[ir];
+                        for (int t = ir + 1; t < nf; ++t) v -= L[t * k + ir] * z[t];
+                        z[ir] = v / L[ir * k + ir];
+                    }
+                    for (int r = 0; r < ks; ++r)
+                        if (sh.fr[r] >= 0) sh.d[r] = z[sh.fr[r]];
+                    sh.alpha = 1.0;
+                }
+            }
+            __syncthreads();
+            if (sh.done) break;
+            // Armijo backtracking along the projection arc
+            bool moved = false;
+            for (int ls = 0; ls < 40; ++ls) {
+                for (int r = tid; r < ks; r += NT) sh.bn[r] = fmin(M, fmax(-M, sh.b[r] + sh.alpha * sh.d[r]));
+                __syncthreads();
+                evaluate<TI>(a, sh, dy, sh.bn, false);
+                if (tid == 0) {
+                    double dec = 0.0, step = 0.0;
+                    for (int r = 0; r < ks; ++r) {
+                        dec += sh.g[r] * (sh.bn[r] - sh.b[r]);
+                        step = fmax(step, fabs(sh.bn[r] - sh.b[r]));
+                    }
+                    // a predicted decrease below the rounding level of f cannot be checked:
+                    // take the step (Newton is then in its quadratic region)
+                    const bool tiny = fabs(dec) <= tiny_rel * (1.0 + fabs(sh.f));
+                    sh.accept = (sh.fn <= sh.f + 1e-4 * dec || tiny) ? 1 : (step <= 1e-16 * M ? 2 : 0);
+                    if (sh.accept == 1 && step <= 1e-15 * M) sh.done = 1;   // converged to FP64 resolution
+                    if (!sh.accept) sh.alpha *= 0.5;
                 }
                 __syncthreads();
-                if (L * sqrt(gm) <= stop) break;
+                if (sh.accept) { moved = (sh.accept == 1); break; }
             }
+            if (!moved) break;                                   // no progress possible in FP64
+            for (int r = tid; r < ks; r += NT) sh.b[r] = sh.bn[r];
+            __syncthreads();
+            if (sh.done) break;
+            evaluate<TI>(a, sh, dy, sh.b, true);
         }
     }
     // exact objective: sum_i l((X_S b)_i, y_i) + lambda2 ||b||^2
-    double acc[1] = {0.0};
-    for (int i = threadIdx.x; i < a.n; i += NT) {
+    double part = 0.0;
+    for (int i = tid; i < a.n; i += NT) {
         double s = 0.0;
-        for (int r = 0; r < ks; ++r) s += a.Xt[(size_t)sh.S[r] * a.n + i] * sh.bcur[r];
-        acc[0] += loss64(s, a.y[i], a.kind);
+        for (int r = 0; r < ks; ++r) s += a.Xt[(size_t)sh.S[r] * a.n + i] * sh.b[r];
+        part += loss64(s, a.y[i], a.kind);
     }
-    block_sum<NT, 1, double>(acc, sh.red);
-    if (threadIdx.x == 0) {
+    const double tot = block_total(part, sh.red);
+    if (tid == 0) {
         double rid = 0.0;
-        for (int r = 0; r < ks; ++r) rid += sh.bcur[r] * sh.bcur[r];
-        a.ub[b] = acc[0] + a.lam2 * rid;
+        for (int r = 0; r < ks; ++r) rid += sh.b[r] * sh.b[r];
+        a.ub[b] = tot + a.lam2 * rid;
     }
-    for (int r = threadIdx.x; r < k; r += NT) a.beta_re[(size_t)b * k + r] = r < ks ? sh.bcur[r] : 0.0;
+    for (int r = tid; r < k; r += NT) a.beta_re[(size_t)b * k + r] = r < ks ? sh.b[r] : 0.0;
 }
 
 }  // namespace
 
-void reopt_launch(cudaStream_t s, const ReoptArgs& a) {
-    if (a.m <= 0) return;
-    k_reopt<<<a.m, NT, 0, s>>>(a);
+size_t reopt_smem_bytes(int k) {
+    const int ch = reopt_chunk(k);
+    return sizeof(double) * (size_t)(2 * k * k + k * ch + 2 * ch);
+}
+
+int reopt_launch(cudaStream_t s, const ReoptArgs& a) {
+    if (a.m <= 0) return 0;
+    const size_t smem = reopt_smem_bytes(a.k);
+    const bool f32 = a.kind == kLOGISTIC && a.Xt32 != nullptr && a.y32 != nullptr;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(f32 ? k_reopt<float> : k_reopt<double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return -1;
+    }
+    if (f32) k_reopt<float><<<a.m, NT, smem, s>>>(a);
+    else k_reopt<double><<<a.m, NT, smem, s>>>(a);
+    return 0;
 }
 
 }  // namespace kglm

@@ -95,6 +95,9 @@ def test_fp32_certificate_is_fp64_exact_at_its_dual_point(kind):
         assert rel(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind)) <= RTOL
         assert [int(s) for s in res["support"][b] if s >= 0] == on.round_support(B[b], nd)
         assert res["branch_j"][b] == on.branch_index(B[b], nd)
+        S = on.round_support(B[b], nd)
+        _, v = ro.reopt(X, y, S, lam2, M, kind, beta0=B[b])
+        assert rel(res["ub"][b], v) <= RTOL, (b, res["ub"][b], v)
         ref = on.solve_node(X, y, nd, lam2, M, kind, L, T)
         worst = max(worst, rel(res["lb"][b], ref["lb"]))
     # FP32 iterations against the FP64 trajectory after the same T: reported, loosely bounded
