@@ -172,6 +172,14 @@ kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr,
                                 const int32_t* out_ptr, const int32_t* out_idx, int32_t nnz_in,
                                 int32_t nnz_out, const int32_t* warm_slot);
 
+/* The batched product G = R X of §4.2 Eq. (gradient_matrix_form) for the
+ * instance's X: G[b][j] = sum_i R[b][i] X[i][j], i.e. column b of X^T R.
+ * R: device, m x n row-major; G: device, m x p row-major; both in the
+ * context's working type (double in KGLM_FP64, float otherwise).
+ * 1 <= m <= max_batch.  Runs on the context's stream with the context's
+ * split-K scratch and returns when G is written. */
+kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G);
+
 /* Per-phase device timers: a tracing aid in the spirit of the paper's
  * per-component runtime breakdown (App. F).  While enabled, every kernel the context
  * launches is bracketed by CUDA events on the context's stream; kglm_stats_read

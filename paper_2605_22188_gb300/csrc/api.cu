@@ -561,16 +561,15 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         }
         // split-K scratch: a plan splits only when its tiles do not fill the GPU,
         // so (splits x tiles) stays below two waves plus one wave of tiles
-        auto scratch = [&](GemmScratch& g, size_t elem_bytes, size_t tile_elems) {
-            // splits x tiles <= 64 x (fewer than one wave of tiles) and <= a few waves
-            g.part_bytes = (size_t)(8 * 152 * 4) * tile_elems * elem_bytes;
+        auto scratch = [&](GemmScratch& g, int is_f64) {
+            g.part_bytes = gemm_scratch_bytes(is_f64);
             g.part = dalloc(c, g.part_bytes);
-            g.n_counters = 8 * 152;
+            g.n_counters = gemm_scratch_counters(is_f64);
             g.counters = dalloc_t<int>(c, g.n_counters);
             CK(cudaMemsetAsync(g.counters, 0, sizeof(int) * g.n_counters, c->st));
         };
-        scratch(c->gs64, sizeof(double), 64 * 64);
-        if (!c->f64) scratch(c->gs32, sizeof(float), 128 * 128);
+        scratch(c->gs64, 1);
+        if (!c->f64) scratch(c->gs32, 0);
         c->gram = dalloc_t<double>(c, p * p);
         c->Xty = dalloc_t<double>(c, p);
         gemm_nt_f64(c->st, (int)p, (int)p, (int)n, c->Xt64, (int)n, c->Xt64, (int)n, c->gram, (int)p, &c->gs64);
@@ -643,6 +642,23 @@ kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr,
                                 const int32_t* warm_slot) {
     if (!ctx) return KGLM_EINVAL;
     return guarded(ctx, [&] { push_dev_impl(ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_out, warm_slot); });
+}
+
+kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(m >= 1 && m <= ctx->mcap, "m must be in [1, max_batch]");
+        REQ(R && G, "R and G are required");
+        Scope sc(ctx, PH_GEMM_GRAD, 1, 2.0 * ctx->n * (double)m * ctx->p);
+        if (ctx->f64)
+            gemm_nt_f64(ctx->st, m, ctx->p, ctx->n, (const double*)R, ctx->n, ctx->Xt64, ctx->n, (double*)G, ctx->p,
+                        &ctx->gs64);
+        else
+            gemm_nt_f32(ctx->st, m, ctx->p, ctx->n, (const float*)R, ctx->n, ctx->Xt32, ctx->n, (float*)G, ctx->p,
+                        &ctx->gs32);
+        check_launch();
+        sync(ctx);
+    });
 }
 
 kglm_status kglm_stats_enable(kglm_ctx* ctx, int32_t enable) {

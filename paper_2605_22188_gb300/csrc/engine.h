@@ -22,6 +22,9 @@ struct GemmPlan {
 };
 // Bytes of scratch the launch plan needs are part_elems * sizeof(T).
 GemmPlan gemm_plan(int R, int C, int K, int is_f64);
+// Scratch that covers every plan (partial bytes and tile counters).
+size_t gemm_scratch_bytes(int is_f64);
+int gemm_scratch_counters(int is_f64);
 
 // C[r][c] = sum_k A[r*lda + k] * B[c*ldb + k]  (both operands K-contiguous).
 // scr may be NULL (then no split-K).

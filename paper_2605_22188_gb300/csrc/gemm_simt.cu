@@ -216,11 +216,13 @@ int ctas_per_sm();
 
 // Split-K factor: the one whose CTA count best fills whole waves of
 // (SMs x resident CTAs), with a small penalty per split for the partial-tile
-// traffic; each CTA keeps at least 64 of the K range.
+// traffic; each CTA keeps at least 64 of the K range and the grid stays
+// within about two waves (so splits x tiles < 3 x SMs x resident CTAs).
 inline int choose_splits(int tiles, int K, int BK, int per_sm) {
     const int slots = kSMs * per_sm;
     if (tiles >= slots) return 1;
-    const int max_split = max(1, min(64, K / 64));   // at least 64 of K per CTA
+    // at least 64 of K per CTA, and at most about two waves of CTAs
+    const int max_split = max(1, min(min(64, K / 64), (2 * slots + tiles - 1) / tiles));
     int best = 1;
     double best_score = -1.0;
     for (int s = 1; s <= max_split; ++s) {
@@ -301,6 +303,13 @@ int ctas_per_sm() {
 }
 
 }  // namespace
+
+size_t gemm_scratch_bytes(int is_f64) {
+    // splits x tiles < 3 x (SMs x resident CTAs), each partial tile BM x BN
+    if (is_f64) return (size_t)3 * kSMs * ctas_per_sm<double>() * Tile<double>::BM * Tile<double>::BN * sizeof(double);
+    return (size_t)3 * kSMs * ctas_per_sm<float>() * Tile<float>::BM * Tile<float>::BN * sizeof(float);
+}
+int gemm_scratch_counters(int is_f64) { return 3 * kSMs * (is_f64 ? ctas_per_sm<double>() : ctas_per_sm<float>()); }
 
 GemmPlan gemm_plan(int R, int C, int K, int is_f64) {
     return is_f64 ? plan_for<double>(R, C, K) : plan_for<float>(R, C, K);

@@ -59,6 +59,7 @@ _SIGS = {
     "kglm_stats_enable": (C.c_int, [P, C.c_int32]),
     "kglm_stats_read": (C.c_int, [P, D, I64, D]),
     "kglm_phase_name": (C.c_char_p, [C.c_int32]),
+    "kglm_xtr": (C.c_int, [P, C.c_int32, P, P]),
 }
 NPHASE = 11
 
@@ -140,6 +141,11 @@ def kglm_push_nodes_dev(ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_ou
                                    int(nnz_in), int(nnz_out), P(warm_slot or None))
     _check(st, ctx)
     return int(m)
+
+
+def kglm_xtr(ctx, m, R_ptr, G_ptr):
+    """G = R X for device buffers (integer addresses) of the context's working type."""
+    _check(lib().kglm_xtr(ctx, int(m), P(R_ptr), P(G_ptr)), ctx)
 
 
 def kglm_stats_enable(ctx, enable=True):
