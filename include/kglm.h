@@ -180,6 +180,32 @@ kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr,
  * split-K scratch and returns when G is written. */
 kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G);
 
+/* kglm_xtr for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment aid.  Callers that run inside CUDA graph
+ * capture, draw every byte from a host application's own pool, or must not
+ * grow their footprint once serving cannot call cudaMalloc (directly or
+ * through a context); this call computes G[b][j] = sum_i R[b][i] Xt[j][i]
+ * with no allocation of any kind, keeping its split-K partial tiles and tile
+ * counters in a file-scope device array of KGLM_XTR_NOALLOC_SCRATCH_FLOATS
+ * floats and KGLM_XTR_NOALLOC_MAX_TILES ints that every GPU loading the
+ * library holds until the process exits.
+ *   R: device, m x n row-major FP32; Xt: device, p x n row-major FP32 (X^T);
+ *   G: device, m x p row-major FP32 output; stream: cudaStream_t or NULL.
+ * The output grid of 128 x 128 tiles, ceil(m/128) * ceil(p/128), may not
+ * exceed KGLM_XTR_NOALLOC_MAX_TILES (KGLM_EINVAL otherwise); n is free.
+ * The call only enqueues work on `stream` (G is ready when the stream
+ * reaches it).  The first call on a device, with that device current, looks
+ * up the array's device address and clears the counters; make that first
+ * call before any stream capture.  All calls share the one array, which
+ * keeps the last call's partial tiles (the counters return to 0 after each
+ * call): calls that overlap on the GPU, on any streams, race.  Errors:
+ * KGLM_EINVAL for bad sizes or pointers, KGLM_ECUDA for a failed CUDA call;
+ * no message is recorded (there is no context). */
+#define KGLM_XTR_NOALLOC_SCRATCH_FLOATS (4u << 20)
+#define KGLM_XTR_NOALLOC_MAX_TILES 256
+kglm_status kglm_xtr_noalloc_f32(int32_t m, int32_t n, int32_t p, const float* R, const float* Xt,
+                                 float* G, void* stream);
+
 /* Per-phase device timers: a tracing aid in the spirit of the paper's
  * per-component runtime breakdown (App. F).  While enabled, every kernel the context
  * launches is bracketed by CUDA events on the context's stream; kglm_stats_read

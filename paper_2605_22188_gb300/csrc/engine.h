@@ -32,6 +32,11 @@ void gemm_nt_f64(cudaStream_t s, int R, int C, int K, const double* A, int lda,
                  const double* B, int ldb, double* out, int ldo, const GemmScratch* scr);
 void gemm_nt_f32(cudaStream_t s, int R, int C, int K, const float* A, int lda,
                  const float* B, int ldb, float* out, int ldo, const GemmScratch* scr);
+// FP32 product with a fixed scratch: split-K is lowered to what scr holds.
+void gemm_nt_f32_clamped(cudaStream_t s, int R, int C, int K, const float* A, int lda,
+                         const float* B, int ldb, float* out, int ldo, const GemmScratch& scr);
+int gemm_tile_rows_f32();
+int gemm_tile_cols_f32();
 // S = V X^T fused with the link: out[b][i] = dl(S[b][i], y[i])   (§4.2 Eq. (gradient_matrix_form))
 void gemm_link_f64(cudaStream_t s, int m, int n, int p, const double* V, const double* X,
                    const double* y, int kind, double* out, const GemmScratch* scr);

@@ -284,6 +284,44 @@ void launch(cudaStream_t s, int R, int C, int K, const T* A, int lda, const T* B
             R, C, K, A, lda, B, ldb, epi, g.kchunk, part, cnt);
 }
 
+// Like launch(), but when the scratch cannot hold the planned partials the
+// split factor is lowered to what it holds instead of dropping to one pass.
+template <typename T, typename Epi>
+void launch_clamped(cudaStream_t s, int R, int C, int K, const T* A, int lda, const T* B, int ldb, Epi epi,
+                    const GemmScratch& scr) {
+    if (R <= 0 || C <= 0) return;
+    using TL = Tile<T>;
+    GemmPlan g = plan_for<T>(R, C, K);
+    const size_t tile_bytes = (size_t)TL::BM * TL::BN * sizeof(T);
+    if (g.splits > 1) {
+        const size_t fit = (g.tiles > scr.n_counters || scr.part == nullptr) ? 1
+                         : scr.part_bytes / ((size_t)g.tiles * tile_bytes);
+        if ((size_t)g.splits > fit) {
+            const int splits = (int)(fit < 1 ? 1 : fit);
+            int kchunk = (K + splits - 1) / splits;
+            kchunk = (kchunk + TL::BK - 1) / TL::BK * TL::BK;
+            g.kchunk = kchunk;
+            g.splits = (K + kchunk - 1) / kchunk;
+        }
+    }
+    if (g.splits <= 1) {
+        g.splits = 1;
+        g.kchunk = K > 0 ? K : 1;
+    }
+    constexpr int VW = 16 / sizeof(T);
+    const bool vec = (lda % VW == 0) && (ldb % VW == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0);
+    dim3 grid(g.gx, g.gy, g.splits);
+    constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
+    T* part = g.splits > 1 ? static_cast<T*>(scr.part) : nullptr;
+    int* cnt = g.splits > 1 ? scr.counters : nullptr;
+    if (vec)
+        k_gemm_nt<T, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN, true, Epi><<<grid, NT, 0, s>>>(
+            R, C, K, A, lda, B, ldb, epi, g.kchunk, part, cnt);
+    else
+        k_gemm_nt<T, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN, false, Epi><<<grid, NT, 0, s>>>(
+            R, C, K, A, lda, B, ldb, epi, g.kchunk, part, cnt);
+}
+
 template <typename T>
 int ctas_per_sm() {
     static int cached = 0;
@@ -323,6 +361,12 @@ void gemm_nt_f32(cudaStream_t s, int R, int C, int K, const float* A, int lda, c
                  float* out, int ldo, const GemmScratch* scr) {
     launch<float>(s, R, C, K, A, lda, B, ldb, EpiStore<float>{out, ldo}, scr);
 }
+void gemm_nt_f32_clamped(cudaStream_t s, int R, int C, int K, const float* A, int lda, const float* B, int ldb,
+                         float* out, int ldo, const GemmScratch& scr) {
+    launch_clamped<float>(s, R, C, K, A, lda, B, ldb, EpiStore<float>{out, ldo}, scr);
+}
+int gemm_tile_rows_f32() { return Tile<float>::BM; }
+int gemm_tile_cols_f32() { return Tile<float>::BN; }
 void gemm_link_f64(cudaStream_t s, int m, int n, int p, const double* V, const double* X, const double* y,
                    int kind, double* out, const GemmScratch* scr) {
     launch<double>(s, m, n, p, V, p, X, p, EpiLink<double>{out, n, y, kind}, scr);

@@ -60,7 +60,9 @@ _SIGS = {
     "kglm_stats_read": (C.c_int, [P, D, I64, D]),
     "kglm_phase_name": (C.c_char_p, [C.c_int32]),
     "kglm_xtr": (C.c_int, [P, C.c_int32, P, P]),
+    "kglm_xtr_noalloc_f32": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P]),
 }
+XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
 
 
@@ -146,6 +148,14 @@ def kglm_push_nodes_dev(ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_ou
 def kglm_xtr(ctx, m, R_ptr, G_ptr):
     """G = R X for device buffers (integer addresses) of the context's working type."""
     _check(lib().kglm_xtr(ctx, int(m), P(R_ptr), P(G_ptr)), ctx)
+
+
+def kglm_xtr_noalloc_f32(m, n, p, R_ptr, Xt_ptr, G_ptr, stream=None):
+    """G = R X with no device allocation (device addresses; asynchronous on `stream`)."""
+    st = lib().kglm_xtr_noalloc_f32(int(m), int(n), int(p), P(R_ptr), P(Xt_ptr), P(G_ptr),
+                                    P(stream) if stream else None)
+    if st != KGLM_OK:
+        raise KglmError(st, "kglm_xtr_noalloc_f32 failed (m=%d, n=%d, p=%d)" % (m, n, p))
 
 
 def kglm_stats_enable(ctx, enable=True):
