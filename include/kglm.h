@@ -175,9 +175,11 @@ kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr,
 /* The batched product G = R X of §4.2 Eq. (gradient_matrix_form) for the
  * instance's X: G[b][j] = sum_i R[b][i] X[i][j], i.e. column b of X^T R.
  * R: device, m x n row-major; G: device, m x p row-major; both in the
- * context's working type (double in KGLM_FP64, float otherwise).
- * 1 <= m <= max_batch.  Runs on the context's stream with the context's
- * split-K scratch and returns when G is written. */
+ * context's working type (double in KGLM_FP64, float otherwise).  In the
+ * BF16 and TF32 modes the product runs on the tensor cores (R is first
+ * rounded to the operand type).  1 <= m <= max_batch.  Runs on the context's
+ * stream with the context's split-K scratch and returns when G is written;
+ * KGLM_ETIMEOUT if a tensor-core pipeline wait ran out. */
 kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G);
 
 /* kglm_xtr for callers that cannot allocate device memory.  The paper has no

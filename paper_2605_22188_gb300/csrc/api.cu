@@ -50,6 +50,15 @@ struct kglm_ctx {
     double ub_inc = INFINITY;
     int* d_err = nullptr;
     GemmScratch gs32{}, gs64{};   // split-K scratch of the CUDA-core GEMMs
+    // tensor-core products (BF16 / TF32 modes): padded operand copies and TMA maps
+    bool tc = false;
+    int tc_kind = 0;              // 0: BF16 operands, 1: TF32
+    int pK = 0, nK = 0;           // operand row strides (multiples of 8 elements)
+    void *Xop = nullptr, *Xop_lo = nullptr, *Xtop = nullptr, *Vop = nullptr, *Rop = nullptr;
+    TcMap mA1{}, mB1{}, mB1lo{}, mA2{}, mB2{};
+    int bn1 = 0, bn2 = 0;
+    GemmScratch gtc{};
+    int* d_tcerr = nullptr;
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
     std::vector<double> h_lb, h_ub;
@@ -188,6 +197,8 @@ void harvest(kglm_ctx* c) {
     cudaGetLastError();
 }
 
+void check_tc_error(kglm_ctx* c);
+
 double delta_of(const kglm_ctx* c, double ub) { return isfinite(ub) ? c->gap_tol * fmax(1.0, fabs(ub)) : 0.0; }
 
 // Largest eigenvalue of the FP64 Gram matrix by power iteration (the
@@ -268,6 +279,26 @@ __global__ void k_filli(int m, int* x, int v) {
 void iterate(kglm_ctx* c) {
     const int m = c->m, n = c->n, p = c->p;
     const double flops = 2.0 * n * c->sum_pa;
+    if (c->tc) {
+        {
+            Scope sc(c, PH_GEMM_LINK, 1, flops);
+            TcGemm g{};
+            g.kind = c->tc_kind; g.M = m; g.N = n; g.K = p; g.bn = c->bn1;
+            g.epi = c->tc_kind == 0 ? TC_EPI_LINK_BF16 : TC_EPI_LINK_F32;
+            g.out = c->Rop; g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
+            if (tc_gemm(c->st, c->mA1, c->mB1, &c->mB1lo, g, &c->gtc) != 0)
+                throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+            check_launch();
+        }
+        {
+            Scope sc(c, PH_GEMM_GRAD, 1, flops);
+            TcGemm g{};
+            g.kind = c->tc_kind; g.M = m; g.N = p; g.K = n; g.bn = c->bn2;
+            g.epi = TC_EPI_STORE_F32; g.out = c->G; g.ldo = p; g.err = c->d_tcerr;
+            if (tc_gemm(c->st, c->mA2, c->mB2, nullptr, g, &c->gtc) != 0) throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+            check_launch();
+        }
+    } else {
     {
         Scope sc(c, PH_GEMM_LINK, 1, flops);
         if (c->f64) gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R, &c->gs64);
@@ -280,9 +311,11 @@ void iterate(kglm_ctx* c) {
         else gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p, &c->gs32);
         check_launch();
     }
+    }
     ProxArgs a{};
     a.m = m; a.p = p; a.W = c->W;
-    a.G = c->G; a.V = c->V; a.B = c->B; a.Vh = nullptr;
+    a.G = c->G; a.V = c->V; a.B = c->B;
+    a.Vop = c->Vop; a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
@@ -339,9 +372,24 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
     r.y32 = c->f64 ? nullptr : c->y32;
     r.support = c->support; r.B = c->B; r.b_is_f64 = c->f64;
     r.ub = c->ub; r.beta_re = c->beta_re;
-    Scope sc(c, PH_REOPT, 1, 0.0);
-    if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
-    check_launch();
+    {
+        Scope sc(c, PH_REOPT, 1, 0.0);
+        if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
+        check_launch();
+    }
+    if (c->tc) check_tc_error(c);
+}
+
+// A tensor-core product whose mbarrier wait ran out leaves a flag (the kernel
+// drained its work and freed its tensor memory before returning).
+void check_tc_error(kglm_ctx* c) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    if (h) {
+        CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));
+        throw Fail{KGLM_ETIMEOUT, "a tensor-core product's pipeline wait ran out"};
+    }
 }
 
 void validate_nodes(const kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx,
@@ -411,7 +459,7 @@ void push_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx,
                                            (int)nnz_out, nullptr);
         check_launch();
         c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, slot, c->pool_slots, c->pool, wb,
-                                          c->out_mask, c->B, c->V, nullptr, c->tmom, c->active);
+                                          c->out_mask, c->B, c->V, c->Vop, c->pK, c->tc_kind == 0, c->tmom, c->active);
         check_launch();
     }
     sync(c);   // host arrays may be pageable and reused by the caller
@@ -440,7 +488,7 @@ void push_dev_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_
                                               c->out_mask, warm_slot, c->pool_slots, c->d_err);
         check_launch();
         c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, warm_slot, c->pool_slots, c->pool, nullptr,
-                                          c->out_mask, c->B, c->V, nullptr, c->tmom, c->active);
+                                          c->out_mask, c->B, c->V, c->Vop, c->pK, c->tc_kind == 0, c->tmom, c->active);
         check_launch();
     }
     {
@@ -518,12 +566,15 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         REQ(d.lambda2 > 0 && isfinite(d.lambda2), "lambda2 must be positive");
         REQ(d.M > 0 && isfinite(d.M), "M must be positive");
         REQ(d.loss == KGLM_LSQ || d.loss == KGLM_LOGISTIC, "unknown loss");
-        REQ(d.prec == KGLM_FP64 || d.prec == KGLM_FP32, "precision not available in this build");
+        REQ(d.prec == KGLM_FP64 || d.prec == KGLM_FP32 || d.prec == KGLM_BF16 || d.prec == KGLM_TF32,
+            "unknown precision");
         REQ(d.max_batch >= 1, "max_batch must be >= 1");
         REQ(d.p <= (d.prec == KGLM_FP64 ? 4096 : 8192), "p above the prox kernel limit for this precision");
         c->d = d;
         c->n = (int)d.n; c->p = (int)d.p; c->k = d.k; c->kind = d.loss; c->prec = d.prec;
         c->f64 = d.prec == KGLM_FP64;
+        c->tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32;
+        c->tc_kind = d.prec == KGLM_BF16 ? 0 : 1;
         c->W = (c->p + 31) / 32;
         c->lam2 = d.lambda2; c->M = d.M;
         c->gap_tol = d.gap_tol > 0 ? d.gap_tol : 1e-6;
@@ -570,6 +621,40 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         };
         scratch(c->gs64, 1);
         if (!c->f64) scratch(c->gs32, 0);
+        if (c->tc) {
+            // padded operand copies (TMA rows must be 16-byte multiples), their
+            // maps, the split-K scratch of the tensor-core products
+            const int ob = c->tc_kind == 0;
+            const size_t es = ob ? 2 : 4;
+            c->pK = (int)((p + 7) / 8 * 8);
+            c->nK = (int)((n + 7) / 8 * 8);
+            c->Xop = dalloc(c, n * c->pK * es);
+            c->Xop_lo = dalloc(c, n * c->pK * es);
+            c->Xtop = dalloc(c, p * c->nK * es);
+            convert_pad(c->st, c->X64, (int)n, (int)p, (int)p, c->Xop, c->pK, ob, c->Xop_lo);
+            convert_pad(c->st, c->Xt64, (int)p, (int)n, (int)n, c->Xtop, c->nK, ob);
+            check_launch();
+            const size_t mc = (size_t)d.max_batch;
+            c->Vop = dalloc(c, mc * c->pK * es);
+            c->Rop = dalloc(c, mc * c->nK * es);
+            CK(cudaMemsetAsync(c->Vop, 0, mc * c->pK * es, c->st));
+            CK(cudaMemsetAsync(c->Rop, 0, mc * c->nK * es, c->st));
+            c->bn1 = tc_tile_cols((int)n);
+            c->bn2 = tc_tile_cols((int)p);
+            if (tc_make_map(&c->mA1, c->Vop, ob, (int)mc, (int)p, c->pK, 128) ||
+                tc_make_map(&c->mB1, c->Xop, ob, (int)n, (int)p, c->pK, c->bn1) ||
+                tc_make_map(&c->mB1lo, c->Xop_lo, ob, (int)n, (int)p, c->pK, c->bn1) ||
+                tc_make_map(&c->mA2, c->Rop, ob, (int)mc, (int)n, c->nK, 128) ||
+                tc_make_map(&c->mB2, c->Xtop, ob, (int)p, (int)n, c->nK, c->bn2))
+                throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for an operand"};
+            c->gtc.part_bytes = tc_scratch_bytes();
+            c->gtc.part = dalloc(c, c->gtc.part_bytes);
+            c->gtc.n_counters = tc_scratch_counters();
+            c->gtc.counters = dalloc_t<int>(c, c->gtc.n_counters);
+            CK(cudaMemsetAsync(c->gtc.counters, 0, sizeof(int) * c->gtc.n_counters, c->st));
+            c->d_tcerr = dalloc_t<int>(c, 1);
+            CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));
+        }
         c->gram = dalloc_t<double>(c, p * p);
         c->Xty = dalloc_t<double>(c, p);
         gemm_nt_f64(c->st, (int)p, (int)p, (int)n, c->Xt64, (int)n, c->Xt64, (int)n, c->gram, (int)p, &c->gs64);
@@ -650,6 +735,18 @@ kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G) {
         REQ(m >= 1 && m <= ctx->mcap, "m must be in [1, max_batch]");
         REQ(R && G, "R and G are required");
         Scope sc(ctx, PH_GEMM_GRAD, 1, 2.0 * ctx->n * (double)m * ctx->p);
+        if (ctx->tc) {
+            convert_pad_f32(ctx->st, (const float*)R, m, ctx->n, ctx->Rop, ctx->nK, ctx->tc_kind == 0);
+            check_launch();
+            TcGemm g{};
+            g.kind = ctx->tc_kind; g.M = m; g.N = ctx->p; g.K = ctx->n; g.bn = ctx->bn2;
+            g.epi = TC_EPI_STORE_F32; g.out = G; g.ldo = ctx->p; g.err = ctx->d_tcerr;
+            if (tc_gemm(ctx->st, ctx->mA2, ctx->mB2, nullptr, g, &ctx->gtc) != 0) throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+            check_launch();
+            sync(ctx);
+            check_tc_error(ctx);
+            return;
+        }
         if (ctx->f64)
             gemm_nt_f64(ctx->st, m, ctx->p, ctx->n, (const double*)R, ctx->n, ctx->Xt64, ctx->n, (double*)G, ctx->p,
                         &ctx->gs64);

@@ -49,6 +49,19 @@ __device__ __forceinline__ double huber64(double q, double M) {
     return a <= M ? 0.5 * a * a : M * a - 0.5 * M * M;
 }
 
+// FP32 rounded to the nearest TF32 value (low 13 mantissa bits cleared).
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Store of a tensor-core operand: BF16 or TF32 (in an FP32 word).
+__device__ __forceinline__ void store_operand(void* base, size_t i, float v, int bf16) {
+    if (bf16) static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16(v);
+    else static_cast<float*>(base)[i] = to_tf32(v);
+}
+
 // ------------------------------------------------------------------ reductions
 
 template <typename T>

@@ -43,12 +43,40 @@ void gemm_link_f64(cudaStream_t s, int m, int n, int p, const double* V, const d
 void gemm_link_f32(cudaStream_t s, int m, int n, int p, const float* V, const float* X,
                    const float* y, int kind, float* out, const GemmScratch* scr);
 
+// ---- tensor-core products (tcgen05, TMA); see gemm_tc.cu
+struct TcMap {
+    alignas(64) unsigned char bytes[128];   // a CUtensorMap
+};
+enum { TC_EPI_STORE_F32 = 0, TC_EPI_LINK_F32 = 1, TC_EPI_LINK_BF16 = 2 };
+struct TcGemm {
+    int kind;        // 0: BF16 operands (kind::f16), 1: FP32 operands read as TF32 (kind::tf32)
+    int M, N, K;     // out[r][c] = sum_k A[r][k] B[c][k], r < M, c < N, k < K
+    int bn;          // tile columns (tc_tile_cols(N)); the B map's box rows
+    int epi;         // TC_EPI_*
+    void* out;
+    int ldo;
+    const float* y;  // link: y per output column
+    int loss;
+    int* err;        // device flag for a wait that ran out (may be NULL)
+};
+// TMA map of a row-major rows x cols matrix (row stride ld elements) with
+// 128-byte boxes along cols and box_rows rows.  0 on success.
+int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, int ld, int box_rows);
+int tc_tile_cols(int N);
+size_t tc_scratch_bytes();
+int tc_scratch_counters();
+// B2: optional low part of B (out = A (B + B2)^T); NULL for a single B.
+int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, const TcGemm& g,
+            const GemmScratch* scr);
+
 struct ProxArgs {
     int m, p, W;
     const void* G;        // gradient X^T R, node-major m x p (working type)
     void* V;              // extrapolated point v (in: v_k, out: v_{k+1})
     void* B;              // iterate beta (in: beta_k, out: beta_{k+1})
-    __nv_bfloat16* Vh;    // optional BF16 shadow of V (tensor-core operand)
+    void* Vop;            // optional copy of V for the tensor-core products (row stride op_ld)
+    int op_ld;
+    int op_bf16;          // 1: BF16, 0: FP32 rounded to TF32 (nearest)
     const uint32_t* in_mask;
     const uint32_t* out_mask;
     const int* kbar;
@@ -116,8 +144,14 @@ int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out
                     const int* out_ptr, const uint32_t* in_mask, const uint32_t* out_mask, const int* slot,
                     int nslots, int* err);
 int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
-                const double* warmB, const uint32_t* out_mask, void* B, void* V, __nv_bfloat16* Vh,
-                double* tmom, int* active);
+                const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, int op_ld,
+                int op_bf16, double* tmom, int* active);
+// rows x cols FP64 (row stride ld_in) -> BF16 or TF32-in-FP32 with row stride ld_out, zero padded;
+// with lo != NULL also the low part bf16/tf32(x - hi) into lo.
+void convert_pad(cudaStream_t s, const double* in, int rows, int cols, int ld_in, void* out, int ld_out, int to_bf16,
+                 void* lo = nullptr);
+// rows x cols FP32 (stride cols) -> BF16 or TF32-in-FP32 with row stride ld_out
+void convert_pad_f32(cudaStream_t s, const float* in, int rows, int cols, void* out, int ld_out, int to_bf16);
 void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots,
                 const void* B, void* pool);
 // a8: pruned[b] = lb[b] >= thr ; alive[b] &= !pruned

@@ -219,7 +219,7 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
             const T vn = bn[e] + coef * (bn[e] - bo[e]);
             Bm[base + j] = bn[e];
             V[base + j] = vn;
-            if (a.Vh != nullptr) a.Vh[base + j] = __float2bfloat16((float)vn);
+            if (a.Vop != nullptr) store_operand(a.Vop, (size_t)b * a.op_ld + j, (float)vn, a.op_bf16);
         }
     }
     if (threadIdx.x == 0) a.tmom[b] = tpp;

@@ -105,6 +105,41 @@ def test_fp32_certificate_is_fp64_exact_at_its_dual_point(kind):
     assert worst <= 1e-4
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("kind", [synth.LSQ, synth.LOGISTIC])
+def test_tensor_core_modes_certificate_and_decisions(prec, kind):
+    """BF16/TF32 products: the FP64 certificate at the GPU's own dual point, the
+    rounding/branching decisions on the GPU's iterate and the re-optimized
+    objective all match the oracle; the bound after T iterations is close to
+    the FP64 trajectory's (reported)."""
+    n, p, k = 600, 200, 8
+    X, y, _ = synth.instance(n, p, k, kind, rho=0.5, snr=5.0, seed=15)
+    lam2, M, T = 1e-2, 2.0, 30
+    L = on.lipschitz(X, kind)
+    rng = np.random.default_rng(9)
+    nodes = make_batch(p, k, 150, rng)
+    with kglm.Engine(X, y, k, lam2, M, kind, prec=prec, max_batch=160, lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(T)
+        B, Z = eng.read_batch()
+    worst = 0.0
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        assert rel(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind)) <= RTOL
+        S = on.round_support(B[b], nd)
+        assert [int(s) for s in res["support"][b] if s >= 0] == S
+        assert res["branch_j"][b] == on.branch_index(B[b], nd)
+        if b % 10 == 0:
+            _, v = ro.reopt(X, y, S, lam2, M, kind, beta0=B[b])
+            assert rel(res["ub"][b], v) <= RTOL, (b, res["ub"][b], v)
+            ref = on.solve_node(X, y, nd, lam2, M, kind, L, T)
+            worst = max(worst, rel(res["lb"][b], ref["lb"]))
+    # reported: reduced-precision products move the trajectory; the certificate stays FP64-valid
+    print("%s %s vs fp64 oracle, max rel LB difference after %d iterations: %.3e"
+          % (prec, "lsq" if kind == synth.LSQ else "logistic", T, worst))
+    assert worst <= (0.15 if prec == "bf16" else 0.05)
+
+
 def test_check_every_and_incumbent_freeze():
     """Periodic certificates: the bound is the best one seen; nodes above UB stop iterating."""
     c, X, y, _ = synth.config_instance("c1_lsq_n200_p30_k5", seed=1)
