@@ -53,9 +53,12 @@ typedef enum {
 
 typedef enum { KGLM_LSQ = 0, KGLM_LOGISTIC = 1 } kglm_loss;
 
-/* Arithmetic of the FISTA iterations.  The certificate is FP64-valid in
- * every mode (the bound of §3 holds for any dual point zeta; the engine
- * evaluates Psi_N(zeta) with FP64 sums and FP64 X^T zeta). */
+/* Arithmetic of the FISTA iterations.  The certificate is valid in every
+ * mode: the bound of §3 holds for any dual point zeta, and the engine returns
+ * Psi_N(zeta) evaluated with FP64 X^T zeta and FP64 sums (KGLM_FP64), or a
+ * rigorous lower estimate of it whose conjugate terms are FP32 evaluations
+ * plus explicit rounding margins (the other modes; looser by ~1e-7
+ * relative). */
 typedef enum {
     KGLM_FP64 = 0,  /* FP64 products and prox */
     KGLM_FP32 = 1,  /* FP32 products (CUDA cores) and prox */

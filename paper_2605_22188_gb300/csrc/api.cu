@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <exception>
+#include <map>
 #include <queue>
 #include <string>
 #include <vector>
@@ -59,6 +60,9 @@ struct kglm_ctx {
     int bn1 = 0, bn2 = 0;
     GemmScratch gtc{};
     int* d_tcerr = nullptr;
+    float* Gpart = nullptr;       // split slices of X^T R (summed by the prox kernel)
+    int gsplit_max = 16;
+    int gsplits = 0;
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
     std::vector<double> h_lb, h_ub;
@@ -74,6 +78,16 @@ struct kglm_ctx {
     double st_ms[KGLM_NPHASE] = {};
     double st_work[KGLM_NPHASE] = {};
     int64_t st_n[KGLM_NPHASE] = {};
+    // CUDA graphs of the iteration loop, one per (batch size, iterations, timing on/off)
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<Rec> recs;           // event pairs inside the graph (timing on)
+        double work[KGLM_NPHASE] = {};
+        int64_t launches[KGLM_NPHASE] = {};
+    };
+    std::map<std::tuple<int, int, int>, Graph> graphs;
+    bool capturing = false;
+    Graph* cap = nullptr;
 };
 
 namespace {
@@ -164,6 +178,14 @@ struct Scope {
     int ph;
     cudaEvent_t a = nullptr;
     Scope(kglm_ctx* c_, int ph_, int launches, double work) : c(c_), ph(ph_) {
+        if (c->capturing) {                        // counted per graph launch instead
+            c->cap->launches[ph] += launches;
+            c->cap->work[ph] += work;
+            // an external record becomes a graph node (a plain record would only order the capture)
+            if (c->stats_on && cudaEventCreate(&a) == cudaSuccess)
+                cudaEventRecordWithFlags(a, c->st, cudaEventRecordExternal);
+            return;
+        }
         c->st_n[ph] += launches;
         c->st_work[ph] += work;
         if (c->stats_on) {
@@ -174,6 +196,12 @@ struct Scope {
     ~Scope() {
         if (!a) return;
         cudaEvent_t b = nullptr;
+        if (c->capturing) {
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            cudaEventRecordWithFlags(b, c->st, cudaEventRecordExternal);
+            c->cap->recs.push_back({ph, a, b});
+            return;
+        }
         if (c->ev_free.empty()) {
             if (cudaEventCreate(&b) != cudaSuccess) { c->ev_free.push_back(a); return; }
         } else {
@@ -294,7 +322,9 @@ void iterate(kglm_ctx* c) {
             Scope sc(c, PH_GEMM_GRAD, 1, flops);
             TcGemm g{};
             g.kind = c->tc_kind; g.M = m; g.N = p; g.K = n; g.bn = c->bn2;
-            g.epi = TC_EPI_STORE_F32; g.out = c->G; g.ldo = p; g.err = c->d_tcerr;
+            g.epi = TC_EPI_PARTIAL; g.err = c->d_tcerr;
+            g.pout = c->Gpart; g.pstride = (size_t)c->mcap * p; g.pld = p;
+            g.max_splits = c->gsplit_max; g.splits_used = &c->gsplits;
             if (tc_gemm(c->st, c->mA2, c->mB2, nullptr, g, &c->gtc) != 0) throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
             check_launch();
         }
@@ -315,6 +345,11 @@ void iterate(kglm_ctx* c) {
     ProxArgs a{};
     a.m = m; a.p = p; a.W = c->W;
     a.G = c->G; a.V = c->V; a.B = c->B;
+    if (c->tc) {
+        a.Gpart = c->Gpart;
+        a.gsplits = c->gsplits;
+        a.gstride = (size_t)c->mcap * p;
+    }
     a.Vop = c->Vop; a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
@@ -323,6 +358,67 @@ void iterate(kglm_ctx* c) {
     const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
     if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
     check_launch();
+}
+
+void destroy_graphs(kglm_ctx* c) {
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto& r : kv.second.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    }
+    c->graphs.clear();
+}
+
+// `count` FISTA iterations of the pushed batch, replayed from a CUDA graph
+// captured on first use (kernel arguments depend only on the batch size).
+void run_iters(kglm_ctx* c, int count) {
+    if (count <= 0) return;
+    if (c->st == nullptr || c->st == cudaStreamLegacy || c->st == cudaStreamPerThread) {
+        for (int i = 0; i < count; ++i) iterate(c);   // the legacy streams cannot be captured
+        return;
+    }
+    const auto key = std::make_tuple(c->m, count, c->stats_on ? 1 : 0);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        if (c->graphs.size() >= 16) destroy_graphs(c);
+        kglm_ctx::Graph& g = c->graphs[key];
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
+        c->cap = &g;
+        try {
+            for (int i = 0; i < count; ++i) iterate(c);
+        } catch (...) {
+            c->capturing = false;
+            cudaStreamEndCapture(c->st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            c->graphs.erase(key);
+            throw;
+        }
+        c->capturing = false;
+        c->cap = nullptr;
+        CK(cudaStreamEndCapture(c->st, &graph));
+        const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->graphs.erase(key);
+            throw Fail{KGLM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+        }
+        it = c->graphs.find(key);
+    }
+    kglm_ctx::Graph& g = it->second;
+    CK(cudaGraphLaunch(g.exec, c->st));
+    for (int ph = 0; ph < KGLM_NPHASE; ++ph) {
+        c->st_n[ph] += g.launches[ph];
+        c->st_work[ph] += g.work[ph];
+    }
+    if (!g.recs.empty()) {                          // timing on: read the graph's events
+        sync(c);
+        for (auto& r : g.recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) c->st_ms[r.ph] += ms;
+        }
+        cudaGetLastError();
+    }
 }
 
 void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
@@ -336,8 +432,10 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
     }
     const double thr = c->ub_inc - delta_of(c, c->ub_inc);
     std::vector<int> h_active;
-    for (int it = 1; it <= iters; ++it) {
-        iterate(c);
+    for (int it = 0; it < iters;) {
+        const int seg = check_every > 0 ? std::min(check_every, iters - it) : iters - it;
+        run_iters(c, seg);
+        it += seg;
         if (check_every > 0 && it % check_every == 0 && it < iters) {
             certify(c);
             {
@@ -546,6 +644,7 @@ const char* kglm_last_error(const kglm_ctx* ctx) { return ctx ? ctx->err.c_str()
 void kglm_destroy(kglm_ctx* ctx) {
     if (!ctx) return;
     if (ctx->st) cudaStreamSynchronize(ctx->st);
+    destroy_graphs(ctx);
     for (auto& r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
@@ -639,7 +738,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->Rop = dalloc(c, mc * c->nK * es);
             CK(cudaMemsetAsync(c->Vop, 0, mc * c->pK * es, c->st));
             CK(cudaMemsetAsync(c->Rop, 0, mc * c->nK * es, c->st));
-            c->bn1 = tc_tile_cols((int)n);
+            c->bn1 = tc_tile_cols_wide((int)n);
             c->bn2 = tc_tile_cols((int)p);
             if (tc_make_map(&c->mA1, c->Vop, ob, (int)mc, (int)p, c->pK, 128) ||
                 tc_make_map(&c->mB1, c->Xop, ob, (int)n, (int)p, c->pK, c->bn1) ||
@@ -647,11 +746,13 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
                 tc_make_map(&c->mA2, c->Rop, ob, (int)mc, (int)n, c->nK, 128) ||
                 tc_make_map(&c->mB2, c->Xtop, ob, (int)p, (int)n, c->nK, c->bn2))
                 throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for an operand"};
+            if (tc_prepare() != 0) throw Fail{KGLM_ECUDA, "tensor-core kernels: shared memory attribute refused"};
             c->gtc.part_bytes = tc_scratch_bytes();
             c->gtc.part = dalloc(c, c->gtc.part_bytes);
             c->gtc.n_counters = tc_scratch_counters();
             c->gtc.counters = dalloc_t<int>(c, c->gtc.n_counters);
             CK(cudaMemsetAsync(c->gtc.counters, 0, sizeof(int) * c->gtc.n_counters, c->st));
+            c->Gpart = dalloc_t<float>(c, (size_t)c->gsplit_max * mc * p);
             c->d_tcerr = dalloc_t<int>(c, 1);
             CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));
         }

@@ -3,8 +3,11 @@
 //   q_b    = X^T zeta_b / (2 lambda2)               (Eq. (batched_dual_candidate_matrix_form))
 //   LB_b   = -sum_i l*(-zeta_ib, y_i) - 2 lambda2 [ sum_{J1} H_M(q_j) + TopSum_kbar {H_M(q_j)}_{Jf} ]
 //                                                   (Eq. (batched_dual_value_component))
-// evaluated in FP64 for every node, whatever precision the iterations used:
-// by weak duality it is a valid bound for any zeta.  The same per-node pass
+// for every node whatever precision the iterations used: by weak duality it
+// is a valid bound for any zeta.  X^T zeta, the Huber/TopSum terms and all
+// sums are FP64; in the reduced-precision modes the conjugate terms are FP32
+// evaluations with explicit rounding margins (k_dual_point_f32), so the
+// returned value is a rigorous lower estimate of Psi(zeta).  The same per-node pass
 // evaluates Phi_b = sum l + 2 lambda2 g(beta_b) with g from Theorem 4.1, the
 // rounded support J1 cup top-kbar |beta| and the branching index
 // argmax_{Jf} |beta_j| of §4.3 (ties to the smaller index).
@@ -17,6 +20,58 @@ namespace kglm {
 namespace {
 
 constexpr double kFeasRtol = 1e-12;
+
+// Reduced-precision modes: the dual point is built in FP32 and the conjugate
+// sum is an upper bound with an explicit rounding margin, so that the bound
+// stays below Psi(zeta) for the zeta actually used (the FP32 value, exact in
+// FP64).  Least squares: zeta = -2(s - y) in FP32 (any zeta is admissible),
+// l*(-zeta) = -zeta*y + zeta^2/4 in FP64 with the FP64 data y (exact up to
+// FP64 rounding, no transcendental).  Logistic:
+// a = sigma(-y s) in FP32, zeta = y a (exact), and
+//   l*(-zeta) = a ln a + (1-a) ln(1-a)
+// with logf / log1pf, whose maximum errors in the CUDA C Programming Guide's
+// accuracy table are 1 and 2 ulp (taken as 2^-23 and 2^-22 relative).  With
+// one rounding per product and 1-a exact for a >= 1/2 (one rounding below):
+//   |t1 - a ln a| <= (2^-23 + 2^-24)|a ln a|             <= 2^-22 |t1|,
+//   |t2 - (1-a) ln(1-a)| <= (2^-22 + 2 * 2^-24)|...|     <= 2^-21 |t2|,
+// so each term carries the margin 2^-22|t1| + 2^-21|t2| + 2^-125 (the last
+// for denormal products), and terms plus margins are summed in FP64.
+template <int NT>
+__global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
+    __shared__ double red[2 * (NT / 32)];
+    const int b = blockIdx.x;
+    const size_t base = (size_t)b * a.n;
+    double acc[2] = {0.0, 0.0};
+    const float* S = static_cast<const float*>(a.S);
+    for (int i = threadIdx.x; i < a.n; i += NT) {
+        const float s = S[base + i];
+        const float yi = (float)a.y[i];
+        if (a.kind == kLSQ) {
+            const float z = -2.0f * (s - yi);
+            a.zeta[base + i] = (double)z;
+            const float r = s - yi;
+            acc[0] += (double)(r * r);
+            const double w = -(double)z;
+            acc[1] += w * a.y[i] + 0.25 * w * w;          // the exact FP64 y: l* is of the data
+        } else {
+            const float t = yi * s;
+            const float e = __expf(-fabsf(t));
+            const float sg = t >= 0.f ? e / (1.0f + e) : 1.0f / (1.0f + e);     // sigma(-t)
+            a.zeta[base + i] = (double)(yi * sg);
+            acc[0] += (double)(fmaxf(-t, 0.f) + log1pf(e));
+            float t1 = 0.f, t2 = 0.f;
+            if (sg > 0.f) t1 = sg * logf(sg);
+            if (sg < 1.f) t2 = (1.0f - sg) * log1pf(-sg);
+            acc[1] += (double)t1 + (double)t2 +
+                      (ldexp(fabs((double)t1), -22) + ldexp(fabs((double)t2), -21) + 0x1p-125);
+        }
+    }
+    block_sum<NT, 2, double>(acc, red);
+    if (threadIdx.x == 0) {
+        a.sum_loss[b] = acc[0];
+        a.sum_conj[b] = acc[1];
+    }
+}
 
 template <int NT>
 __global__ __launch_bounds__(NT) void k_dual_point(CertArgs a) {
@@ -209,7 +264,8 @@ __global__ __launch_bounds__(NT) void k_cert_bound(CertArgs a) {
 
 void cert_dual_point(cudaStream_t s, const CertArgs& a) {
     if (a.m <= 0) return;
-    k_dual_point<256><<<a.m, 256, 0, s>>>(a);
+    if (a.s_is_f64) k_dual_point<256><<<a.m, 256, 0, s>>>(a);
+    else k_dual_point_f32<256><<<a.m, 256, 0, s>>>(a);
 }
 
 int cert_bound(cudaStream_t s, const CertArgs& a) {

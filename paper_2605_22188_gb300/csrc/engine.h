@@ -47,7 +47,9 @@ void gemm_link_f32(cudaStream_t s, int m, int n, int p, const float* V, const fl
 struct TcMap {
     alignas(64) unsigned char bytes[128];   // a CUtensorMap
 };
-enum { TC_EPI_STORE_F32 = 0, TC_EPI_LINK_F32 = 1, TC_EPI_LINK_BF16 = 2 };
+// TC_EPI_PARTIAL: split z writes its partial product to pout + z*pstride (row
+// stride pld); the consumer sums the slices (no reduction in the kernel).
+enum { TC_EPI_STORE_F32 = 0, TC_EPI_LINK_F32 = 1, TC_EPI_LINK_BF16 = 2, TC_EPI_PARTIAL = 3 };
 struct TcGemm {
     int kind;        // 0: BF16 operands (kind::f16), 1: FP32 operands read as TF32 (kind::tf32)
     int M, N, K;     // out[r][c] = sum_k A[r][k] B[c][k], r < M, c < N, k < K
@@ -58,11 +60,19 @@ struct TcGemm {
     const float* y;  // link: y per output column
     int loss;
     int* err;        // device flag for a wait that ran out (may be NULL)
+    float* pout;     // TC_EPI_PARTIAL destination, slice stride and row stride
+    size_t pstride;
+    int pld;
+    int max_splits;  // TC_EPI_PARTIAL: upper bound on the number of slices
+    int* splits_used;
 };
 // TMA map of a row-major rows x cols matrix (row stride ld elements) with
 // 128-byte boxes along cols and box_rows rows.  0 on success.
 int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, int ld, int box_rows);
+// Sets the kernels' shared-memory attributes (call before any stream capture).
+int tc_prepare();
 int tc_tile_cols(int N);
+int tc_tile_cols_wide(int N);   // 128-column tiles for N > 256 (more CTAs for a wide output)
 size_t tc_scratch_bytes();
 int tc_scratch_counters();
 // B2: optional low part of B (out = A (B + B2)^T); NULL for a single B.
@@ -72,6 +82,9 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
 struct ProxArgs {
     int m, p, W;
     const void* G;        // gradient X^T R, node-major m x p (working type)
+    const float* Gpart;   // or: gsplits FP32 slices of it, slice s at Gpart + s*gstride (summed in order)
+    int gsplits;
+    size_t gstride;
     void* V;              // extrapolated point v (in: v_k, out: v_{k+1})
     void* B;              // iterate beta (in: beta_k, out: beta_{k+1})
     void* Vop;            // optional copy of V for the tensor-core products (row stride op_ld)

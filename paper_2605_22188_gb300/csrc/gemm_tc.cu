@@ -9,9 +9,10 @@
 //   warp 1, lane 0   MMA issuer: tcgen05.mma.cta_group::1 (kind::f16 with BF16
 //                    operands, or kind::tf32), FP32 accumulator in tensor
 //                    memory; tcgen05.commit frees a stage / signals the tile;
-//   warps 0-3        epilogue: tcgen05.ld of the accumulator (warp w owns
-//                    TMEM lanes 32w..32w+31, i.e. tile rows), then the link
-//                    or a plain store, or a split-K partial.
+//   warps 0-7        epilogue: tcgen05.ld of the accumulator (warp w reads
+//                    TMEM lanes 32(w%4).. , i.e. tile rows, and every other
+//                    32-column chunk), then the link, a plain store or a
+//                    split-K partial.
 // The B operand can be given as two parts (hi + lo, both multiplied into the
 // same accumulator): the engine does this for X in S = X V, so that X enters
 // one of the two products of an iteration with ~16 (BF16) or ~22 (TF32) bits.
@@ -38,7 +39,7 @@ namespace {
 constexpr int BM = 128;                 // rows per tile (one UMMA M = 128)
 constexpr int ROWB = 128;               // bytes of K per stage and row (one swizzle row)
 constexpr int MAXBN = 256;
-constexpr int NT = 128;                 // four warps
+constexpr int NT = 256;                 // eight warps
 constexpr uint32_t STAGE_A = BM * ROWB;
 constexpr uint32_t STAGE_B = MAXBN * ROWB;
 constexpr uint32_t TMEM_COLS = 256;
@@ -57,6 +58,9 @@ struct TcArgs {
     uint32_t idesc;           // instruction descriptor
     int epi;                  // TC_EPI_*
     int round_tf32;           // round FP32 link outputs to TF32 (nearest) for the next product
+    float* pout;              // TC_EPI_PARTIAL: slice z at pout + z * pstride, row stride pld
+    size_t pstride;
+    int pld;
     void* out;
     int ldo;
     const float* y;
@@ -72,10 +76,22 @@ __device__ __forceinline__ float tf32_rn(float x) {
     return __uint_as_float(r);
 }
 
-// Writes columns c0 .. c0+31 of output row r (columns >= N are skipped).
-__device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, const float (&v)[32]) {
+// Loss derivative for operands that are rounded to BF16/TF32 next: fast
+// exponential and reciprocal (relative error far below the operand rounding).
+__device__ __forceinline__ float dloss_fast(float s, float y, int kind) {
+    return kind == kLSQ ? 2.0f * (s - y) : -y * __frcp_rn(1.0f + __expf(y * s));
+}
+
+// Writes columns c0 .. c0+31 of output row r (columns >= N are skipped); ys:
+// the tile's y values staged in shared memory (index c0 - n0 + j).
+__device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, const float (&v)[32], const float* ys) {
     if (r >= a.M) return;
-    if (a.epi == TC_EPI_STORE_F32) {
+    if (a.epi == TC_EPI_PARTIAL) {
+        float* o = a.pout + (size_t)blockIdx.z * a.pstride + (size_t)r * a.pld;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < a.N) o[c0 + j] = v[j];
+    } else if (a.epi == TC_EPI_STORE_F32) {
         float* o = static_cast<float*>(a.out) + (size_t)r * a.ldo;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
@@ -85,7 +101,7 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, cons
 #pragma unroll
         for (int j = 0; j < 32; ++j)
             if (c0 + j < a.N) {
-                const float d = dloss(v[j], a.y[c0 + j], a.loss);
+                const float d = dloss_fast(v[j], ys[j], a.loss);
                 o[c0 + j] = a.round_tf32 ? tf32_rn(d) : d;
             }
     } else {
@@ -96,14 +112,14 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, cons
                 __nv_bfloat162 h[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    h[q] = __floats2bfloat162_rn(dloss(v[j + 2 * q], a.y[c0 + j + 2 * q], a.loss),
-                                                 dloss(v[j + 2 * q + 1], a.y[c0 + j + 2 * q + 1], a.loss));
+                    h[q] = __floats2bfloat162_rn(dloss_fast(v[j + 2 * q], ys[j + 2 * q], a.loss),
+                                                 dloss_fast(v[j + 2 * q + 1], ys[j + 2 * q + 1], a.loss));
                 *reinterpret_cast<uint4*>(o + c0 + j) = *reinterpret_cast<const uint4*>(h);
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (c0 + j < a.N) o[c0 + j] = __float2bfloat16(dloss(v[j], a.y[c0 + j], a.loss));
+                if (c0 + j < a.N) o[c0 + j] = __float2bfloat16(dloss_fast(v[j], ys[j], a.loss));
         }
     }
 }
@@ -234,6 +250,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + NB * STAGES * STAGE_B);   // full[S], empty[S], accum
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
     __shared__ int s_last;
+    __shared__ float ys[MAXBN + 32];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * a.bn;
@@ -288,23 +305,29 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     }
     __syncwarp();
 
-    // epilogue: all four warps
+    // epilogue: all eight warps; warp w reads TMEM lanes 32*(w%4).. (tile rows)
+    // and the 32-column chunks of parity w/4
+    if (a.y != nullptr)
+        for (int c = threadIdx.x; c < a.bn + 32; c += NT) ys[c] = (n0 + c < a.N) ? a.y[n0 + c] : 0.f;
+    __syncthreads();
     // warp-uniform: tcgen05.ld below is .sync.aligned
     const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[2 * STAGES]), 0u, a.err) && nloc > 0);
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    const bool split = gridDim.z > 1;
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = m0 + quad * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    // split-K with the last-CTA reduction (TC_EPI_PARTIAL keeps every slice instead)
+    const bool split = gridDim.z > 1 && a.epi != TC_EPI_PARTIAL;
     const int ntile = gridDim.x * gridDim.y;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     if (ok) {
-        for (int c = 0; c < a.bn; c += 32) {
+        for (int c = half * 32; c < a.bn; c += 64) {
             float v[32];
             tmem_ld32(tl + (uint32_t)c, v);
             if (!split) {
-                tc_epilogue(a, row, n0 + c, v);
+                tc_epilogue(a, row, n0 + c, v, ys + c);
             } else {
-                float* my = a.part + (((size_t)blockIdx.z * ntile + tile) * BM + warp * 32 + lane) * MAXBN + c;
+                float* my = a.part + (((size_t)blockIdx.z * ntile + tile) * BM + quad * 32 + lane) * MAXBN + c;
 #pragma unroll
                 for (int q = 0; q < 32; q += 4) *reinterpret_cast<float4*>(my + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
             }
@@ -318,19 +341,19 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
         __syncthreads();
         if (s_last) {
             __threadfence();
-            for (int c = 0; c < a.bn; c += 32) {
+            for (int c = half * 32; c < a.bn; c += 64) {
                 float v[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q) v[q] = 0.f;
                 for (int s = 0; s < (int)gridDim.z; ++s) {
-                    const float* ps = a.part + (((size_t)s * ntile + tile) * BM + warp * 32 + lane) * MAXBN + c;
+                    const float* ps = a.part + (((size_t)s * ntile + tile) * BM + quad * 32 + lane) * MAXBN + c;
 #pragma unroll
                     for (int q = 0; q < 32; q += 4) {
                         const float4 x = __ldcg(reinterpret_cast<const float4*>(ps + q));
                         v[q] += x.x; v[q + 1] += x.y; v[q + 2] += x.z; v[q + 3] += x.w;
                     }
                 }
-                tc_epilogue(a, row, n0 + c, v);
+                tc_epilogue(a, row, n0 + c, v, ys + c);
             }
             if (threadIdx.x == 0) a.counters[tile] = 0;
         }
@@ -371,6 +394,10 @@ int set_smem_attr() {
 
 }  // namespace
 
+int tc_prepare() {
+    return set_smem_attr<0, 1>() | set_smem_attr<0, 2>() | set_smem_attr<1, 1>() | set_smem_attr<1, 2>();
+}
+
 int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, int ld, int box_rows) {
     static_assert(sizeof(TcMap) >= sizeof(CUtensorMap), "TcMap too small");
     auto fn = encode_fn();
@@ -388,6 +415,7 @@ int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, i
 }
 
 int tc_tile_cols(int N) { return N >= MAXBN ? MAXBN : ((N + 15) / 16) * 16; }
+int tc_tile_cols_wide(int N) { return N > MAXBN ? 128 : tc_tile_cols(N); }
 
 size_t tc_scratch_bytes() { return (size_t)3 * 152 * BM * MAXBN * sizeof(float); }
 int tc_scratch_counters() { return 3 * 152; }
@@ -408,13 +436,17 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const int tiles = gx * gy;
     // split-K: at least 4 slices of K per CTA, at most one wave of CTAs
     int splits = 1;
-    if (tiles < 152 && scr && scr->part && scr->counters && scr->n_counters >= tiles) {
+    if (g.epi == TC_EPI_PARTIAL) {
+        splits = std::max(1, std::min(g.max_splits, std::min((a.nkb + 3) / 4, std::max(1, 152 / tiles))));
+    } else if (tiles < 152 && scr && scr->part && scr->counters && scr->n_counters >= tiles) {
         splits = std::min((a.nkb + 3) / 4, std::max(1, 152 / tiles));
         const size_t need = (size_t)splits * tiles * BM * MAXBN * sizeof(float);
         if (need > scr->part_bytes) splits = (int)std::max<size_t>(1, scr->part_bytes / ((size_t)tiles * BM * MAXBN * sizeof(float)));
     }
     a.kb_per_split = (a.nkb + splits - 1) / splits;
     splits = (a.nkb + a.kb_per_split - 1) / a.kb_per_split;
+    if (g.splits_used) *g.splits_used = splits;
+    a.pout = g.pout; a.pstride = g.pstride; a.pld = g.pld;
     // instruction descriptor: D F32 (bits 4-5 = 1), A/B format (bits 7-9, 10-12:
     // BF16 = 1 for kind::f16, TF32 = 2 for kind::tf32), K-major A and B, N>>3 at
     // bit 17, M>>4 at bit 24

@@ -89,7 +89,15 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
             const T v = V[base + j];
             vv[e] = v;
             bo[e] = Bm[base + j];
-            u[e] = v - eta * G[base + j];
+            T g;
+            if (a.gsplits > 0) {
+                float acc = 0.f;
+                for (int q = 0; q < a.gsplits; ++q) acc += a.Gpart[(size_t)q * a.gstride + base + j];
+                g = T(acc);
+            } else {
+                g = G[base + j];
+            }
+            u[e] = v - eta * g;
             if ((im[j >> 5] >> (j & 31)) & 1u) fin |= 1u << e;
             else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= 1u << e;
         }

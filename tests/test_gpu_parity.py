@@ -4,8 +4,11 @@ Tolerances (written here, derived from the arithmetic):
 * FP64 path: iterates, bounds, primal values and re-optimized objectives
   agree with the oracle to 1e-9 relative (summation order is the only
   difference; FISTA is non-expansive so it does not amplify it);
-* every path: the GPU bound equals the oracle's Psi_N evaluated at the GPU's
+* FP64 path: the GPU bound equals the oracle's Psi_N evaluated at the GPU's
   own dual point to 1e-9 relative (the certificate arithmetic is FP64);
+* reduced-precision paths: the GPU bound never exceeds Psi_N at its own dual
+  point and is within 1e-6 relative of it (FP32 conjugate terms with explicit
+  rounding margins);
 * integer outputs (support, branching index, pruned flags) are compared
   bit-exactly with the oracle's decision taken on the GPU's own iterate.
 """
@@ -25,6 +28,17 @@ RTOL = 1e-9
 
 def rel(a, b):
     return abs(a - b) / max(1.0, abs(b))
+
+
+CERT_RTOL_REDUCED = 1e-6
+
+
+def check_reduced_certificate(lb, psi):
+    """Reduced-precision modes: the bound is a rigorous lower estimate of Psi_N at
+    the GPU's own dual point (never above it, up to FP64 summation order) and
+    within 1e-6 relative of it."""
+    assert lb <= psi + 1e-12 * max(1.0, abs(psi)), (lb, psi)
+    assert psi - lb <= CERT_RTOL_REDUCED * max(1.0, abs(psi)), (lb, psi)
 
 
 def special_nodes(p, k, rng):
@@ -92,7 +106,7 @@ def test_fp32_certificate_is_fp64_exact_at_its_dual_point(kind):
     worst = 0.0
     for b, (J0, J1) in enumerate(nodes):
         nd = on.Node(p, k, J0, J1)
-        assert rel(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind)) <= RTOL
+        check_reduced_certificate(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind))
         assert [int(s) for s in res["support"][b] if s >= 0] == on.round_support(B[b], nd)
         assert res["branch_j"][b] == on.branch_index(B[b], nd)
         S = on.round_support(B[b], nd)
@@ -125,7 +139,7 @@ def test_tensor_core_modes_certificate_and_decisions(prec, kind):
     worst = 0.0
     for b, (J0, J1) in enumerate(nodes):
         nd = on.Node(p, k, J0, J1)
-        assert rel(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind)) <= RTOL
+        check_reduced_certificate(res["lb"][b], on.dual_value(X, y, Z[b], nd, lam2, M, kind))
         S = on.round_support(B[b], nd)
         assert [int(s) for s in res["support"][b] if s >= 0] == S
         assert res["branch_j"][b] == on.branch_index(B[b], nd)
