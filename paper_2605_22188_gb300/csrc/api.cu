@@ -61,7 +61,7 @@ struct kglm_ctx {
     GemmScratch gtc{};
     int* d_tcerr = nullptr;
     float* Gpart = nullptr;       // split slices of X^T R (summed by the prox kernel)
-    int gsplit_max = 16;
+    int gsplit_max = 4;
     int gsplits = 0;
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
@@ -1117,6 +1117,26 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
         } catch (...) {
             while (!open.empty()) { delete open.top(); open.pop(); }
             throw;
+        }
+        // the reduced-precision modes keep an upper bound of each incumbent's
+        // objective during the search; report the exact FP64 objective
+        if (!ctx->f64 && isfinite(ub)) {
+            std::vector<int> Sv;
+            std::vector<double> bv;
+            for (int r = 0; r < k; ++r)
+                if (best_sup[r] >= 0) { Sv.push_back(best_sup[r]); bv.push_back(best_coef[r]); }
+            const int ks = (int)Sv.size();
+            if (ks > 0) {
+                CK(cudaMemcpyAsync(ctx->d_rows, Sv.data(), sizeof(int) * ks, cudaMemcpyHostToDevice, ctx->st));
+                CK(cudaMemcpyAsync(ctx->beta_re, bv.data(), sizeof(double) * ks, cudaMemcpyHostToDevice, ctx->st));
+                objective64_launch(ctx->st, ctx->Xt64, ctx->y64, ctx->n, ctx->kind, ctx->lam2, ctx->d_rows,
+                                   ctx->beta_re, ks, ctx->ub);
+                check_launch();
+                double exact = ub;
+                CK(cudaMemcpyAsync(&exact, ctx->ub, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+                sync(ctx);
+                ub = exact;
+            }
         }
         double open_lb = INFINITY;
         while (!open.empty()) {

@@ -119,6 +119,39 @@ __device__ __forceinline__ int block_count(int v, int* red) {
     return a[0];
 }
 
+// ------------------------------------------------------------------ groups
+// A per-node kernel is written once over a group policy: a CTA of NT threads
+// (one node per CTA) or one warp (one node per warp).  Reductions give every
+// member the total, summed in a fixed order.
+
+template <int NT>
+struct CtaGroup {
+    static constexpr int N = NT;
+    __device__ static int rank() { return threadIdx.x; }
+    __device__ static void sync() { __syncthreads(); }
+    __device__ static bool first_warp() { return threadIdx.x < 32; }
+    template <int NV, typename T>
+    __device__ static void sum(T (&v)[NV], T* red) { block_sum<NT, NV, T>(v, red); }
+    template <typename T>
+    __device__ static T max(T v, T* red) { return block_max<NT, T>(v, red); }
+    __device__ static int count(int v, int* red) { return block_count<NT>(v, red); }
+};
+
+struct WarpGroup {
+    static constexpr int N = 32;
+    __device__ static int rank() { return threadIdx.x & 31; }
+    __device__ static void sync() { __syncwarp(); }
+    __device__ static bool first_warp() { return true; }
+    template <int NV, typename T>
+    __device__ static void sum(T (&v)[NV], T*) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    }
+    template <typename T>
+    __device__ static T max(T v, T*) { return warp_max(v); }
+    __device__ static int count(int v, int*) { return warp_sum(v); }
+};
+
 // ------------------------------------------------------------------ selection
 
 // Order-preserving unsigned key of a non-negative float / double magnitude.
@@ -137,24 +170,29 @@ struct SelectShared {
 // whose bit is set in `valid`.  Returns the key and `need`, the number of
 // elements equal to it that belong to the kth largest.  Requires 1 <= kth <=
 // number of valid elements.
-template <int NT, int E, typename K>
-__device__ void block_kth_largest(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
+template <typename G, int E, typename K>
+__device__ void group_kth_largest(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
                                   K& thr, int& need) {
     constexpr int BITS = int(sizeof(K)) * 8;
     K prefix = 0, pmask = 0;
     int rem = kth;
 #pragma unroll 1
     for (int shift = BITS - 8; shift >= 0; shift -= 8) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 256; i += NT) sh.hist[i] = 0u;
-        __syncthreads();
+        G::sync();
+        for (int i = G::rank(); i < 256; i += G::N) sh.hist[i] = 0u;
+        G::sync();
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-            if (((valid >> e) & 1u) && (key[e] & pmask) == prefix)
-                atomicAdd(&sh.hist[(unsigned)(key[e] >> shift) & 255u], 1u);
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const int l = threadIdx.x;
+        for (int e = 0; e < E; ++e) {
+            // warp-aggregated: lanes hitting the same bin add once (magnitudes
+            // mostly share their exponent byte, so the first passes collide)
+            const bool in = ((valid >> e) & 1u) && (key[e] & pmask) == prefix;
+            const unsigned bin = in ? ((unsigned)(key[e] >> shift) & 255u) : 256u;
+            const unsigned same = __match_any_sync(0xffffffffu, bin);
+            if (in && (threadIdx.x & 31) == (unsigned)(__ffs(same) - 1)) atomicAdd(&sh.hist[bin], (unsigned)__popc(same));
+        }
+        G::sync();
+        if (G::rank() < 32) {
+            const int l = G::rank();
             unsigned c[8], tot = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) { c[q] = sh.hist[l * 8 + q]; tot += c[q]; }
@@ -174,25 +212,31 @@ __device__ void block_kth_largest(const K (&key)[E], uint32_t valid, int kth, Se
                 }
             }
         }
-        __syncthreads();
+        G::sync();
         rem -= (int)sh.above;
         prefix |= K(sh.digit) << shift;
         pmask |= K(255) << shift;
     }
-    __syncthreads();
+    G::sync();
     thr = prefix;
     need = rem;
+}
+
+template <int NT, int E, typename K>
+__device__ void block_kth_largest(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
+                                  K& thr, int& need) {
+    group_kth_largest<CtaGroup<NT>, E, K>(key, valid, kth, sh, thr, need);
 }
 
 // Selection of the kth largest keys with ties to the smaller index.  Element
 // e of thread t is coordinate j = t + e*NT.  On return sel has bit e set for
 // the selected elements (exactly kth of them).
-template <int NT, int E, typename K>
-__device__ uint32_t block_topk_select(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
+template <typename G, int E, typename K>
+__device__ uint32_t group_topk_select(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
                                       int* ired) {
     K thr;
     int need;
-    block_kth_largest<NT, E, K>(key, valid, kth, sh, thr, need);
+    group_kth_largest<G, E, K>(key, valid, kth, sh, thr, need);
     uint32_t gt = 0, eq = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -201,15 +245,15 @@ __device__ uint32_t block_topk_select(const K (&key)[E], uint32_t valid, int kth
             else if (key[e] == thr) eq |= 1u << e;
         }
     }
-    int n_eq = block_count<NT>(__popc(eq), ired);
+    int n_eq = G::count(__popc(eq), ired);
     if (n_eq == need) return gt | eq;
     // ties straddle the threshold: take the `need` smallest indices among them
     uint32_t ikey[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) ikey[e] = ~(uint32_t)(threadIdx.x + e * NT);
+    for (int e = 0; e < E; ++e) ikey[e] = ~(uint32_t)(G::rank() + e * G::N);
     uint32_t ithr;
     int ineed;
-    block_kth_largest<NT, E, uint32_t>(ikey, eq, need, sh, ithr, ineed);
+    group_kth_largest<G, E, uint32_t>(ikey, eq, need, sh, ithr, ineed);
     uint32_t take = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e)
@@ -217,12 +261,52 @@ __device__ uint32_t block_topk_select(const K (&key)[E], uint32_t valid, int kth
     return gt | take;
 }
 
+// Warp tournament: the kth largest of the valid values of the warp, ties to
+// the smaller index (element e of lane l is index l + 32e), in kth rounds of a
+// warp-wide argmax over each lane's best untaken element.  Writes the
+// selection sorted (value descending) to sv/si (lane 0) and returns the
+// lane's bit mask of selected elements.  Values must be >= 0.
+template <int E, typename T>
+__device__ uint32_t warp_topk_tournament(const T (&val)[E], uint32_t valid, int kth, T* sv, int* si) {
+    const int lane = threadIdx.x & 31;
+    uint32_t taken = 0;
+    for (int r = 0; r < kth; ++r) {
+        T best = T(-1);
+        int bidx = 0x7fffffff, be = -1;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (((valid & ~taken) >> e) & 1u) {
+                const int idx = lane + 32 * e;
+                if (val[e] > best || (val[e] == best && idx < bidx)) { best = val[e]; bidx = idx; be = e; }
+            }
+        T wv = best;
+        int wi = bidx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, wv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+            if (ov > wv || (ov == wv && oi < wi)) { wv = ov; wi = oi; }
+        }
+        if (be >= 0 && bidx == wi) taken |= 1u << be;
+        if (lane == 0) { sv[r] = wv; si[r] = wi; }
+    }
+    __syncwarp();
+    return taken;
+}
+
+template <int NT, int E, typename K>
+__device__ uint32_t block_topk_select(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
+                                      int* ired) {
+    return group_topk_select<CtaGroup<NT>, E, K>(key, valid, kth, sh, ired);
+}
+
 // Sort up to kMaxK (value, index) pairs held in shared memory by value
-// descending, index ascending; done by warp 0.  out arrays must not alias in.
-template <typename T>
+// descending, index ascending; done by the group's first warp (the warp
+// itself for a warp group).  out arrays must not alias in.
+template <typename T, typename G = CtaGroup<64>>
 __device__ void warp_rank_sort_desc(const T* val, const int* idx, int cnt, T* oval, int* oidx) {
-    if (threadIdx.x >= 32) return;
-    for (int i = threadIdx.x; i < cnt; i += 32) {
+    if (!G::first_warp()) return;
+    for (int i = (threadIdx.x & 31); i < cnt; i += 32) {
         T v = val[i];
         int ix = idx[i];
         int r = 0;

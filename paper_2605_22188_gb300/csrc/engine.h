@@ -147,6 +147,9 @@ struct ReoptArgs {
 // returns 0, or -1 if the dynamic shared memory for k cannot be granted
 int reopt_launch(cudaStream_t s, const ReoptArgs& a);
 size_t reopt_smem_bytes(int k);
+// FP64 objective F(X_S b) + lambda2 ||b||^2 of one support (device S[ks], b[ks]) into *out.
+void objective64_launch(cudaStream_t s, const double* Xt, const double* y, int n, int kind, double lam2,
+                        const int* S, const double* b, int ks, double* out);
 
 // node-batch layout (a2): CSR fixing lists -> masks, kbar, pf; warm starts
 // (layout launchers return the number of kernels they launched)

@@ -46,6 +46,9 @@ struct ProxShared {
     int topi[kMaxK];
     T sv[kMaxK];      // top magnitudes, descending
     int si[kMaxK];
+    T ep[kMaxK];      // their entry points p(sv[i]), descending
+    T coef;           // FISTA momentum coefficient of this step
+    int r;
 };
 
 // p(a) in the scale of u: the Huber prox of weight rho at rho*a, divided by rho.
@@ -63,15 +66,21 @@ __device__ __forceinline__ T model_root(T nt, T St, T nl, T Sl, T c, T M) {
     return (St + Sl - nt * M) / (nt + nl);
 }
 
-template <typename T, int NT, int E>
-__global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
+// One node per group (a CTA of NT threads, or a warp with GPC groups per CTA).
+template <typename T, typename Grp, int E, int GPC>
+__global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
+    using G = Grp;
     using K = typename KeyOf<T>::type;
-    __shared__ ProxShared<T> sh;
-    const int b = blockIdx.x;
+    constexpr int NT = G::N;
+    __shared__ ProxShared<T> shared_all[GPC];
+    const int grp = GPC == 1 ? 0 : (int)(threadIdx.x / 32);
+    ProxShared<T>& sh = shared_all[grp];
+    const int b = blockIdx.x * GPC + grp;
+    if (b >= a.m) return;
     if (a.active != nullptr && a.active[b] == 0) return;
     const int p = a.p;
     const size_t base = (size_t)b * p;
-    const T* __restrict__ G = static_cast<const T*>(a.G);
+    const T* __restrict__ Gm = static_cast<const T*>(a.G);
     T* __restrict__ V = static_cast<T*>(a.V);
     T* __restrict__ Bm = static_cast<T*>(a.B);
     const T eta = T(a.eta), c = T(a.c), M = T(a.M);
@@ -80,24 +89,37 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
 
     T u[E], vv[E], bo[E];
     uint32_t valid = 0, fin = 0, fout = 0;
+    // gradient: G, or the sum of its split slices (slice-outer so that the E
+    // loads of a slice are in flight together; order of the sum fixed)
+    T gsum[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) gsum[e] = T(0);
+    if (a.gsplits > 0) {
+        for (int q = 0; q < a.gsplits; ++q) {
+            const float* gp = a.Gpart + (size_t)q * a.gstride + base;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = G::rank() + e * NT;
+                if (j < p) gsum[e] += T(gp[j]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = G::rank() + e * NT;
+            if (j < p) gsum[e] = Gm[base + j];
+        }
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int j = threadIdx.x + e * NT;
+        const int j = G::rank() + e * NT;
         u[e] = vv[e] = bo[e] = T(0);
         if (j < p) {
             valid |= 1u << e;
             const T v = V[base + j];
             vv[e] = v;
             bo[e] = Bm[base + j];
-            T g;
-            if (a.gsplits > 0) {
-                float acc = 0.f;
-                for (int q = 0; q < a.gsplits; ++q) acc += a.Gpart[(size_t)q * a.gstride + base + j];
-                g = T(acc);
-            } else {
-                g = G[base + j];
-            }
-            u[e] = v - eta * g;
+            u[e] = v - eta * gsum[e];
             if ((im[j >> 5] >> (j & 31)) & 1u) fin |= 1u << e;
             else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= 1u << e;
         }
@@ -108,69 +130,81 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
     T theta = T(0);
     uint32_t top = 0;
     if (kb > 0 && pf > kb) {
-        K key[E];
+        T amax;
+        if constexpr (NT == 32) {
+            // one warp per node: tournament selection, already sorted
+            T mag[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) key[e] = mag_key(abs(u[e]));
-        top = block_topk_select<NT, E, K>(key, ffree, kb, sh.sel, sh.ired);
-        if (threadIdx.x == 0) sh.topcnt = 0;
-        __syncthreads();
-        T tmax = T(0);
+            for (int e = 0; e < E; ++e) mag[e] = abs(u[e]);
+            top = warp_topk_tournament<E, T>(mag, ffree, kb, sh.sv, sh.si);
+            T tmax = T(0);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            if ((top >> e) & 1u) {
-                const int s = atomicAdd(&sh.topcnt, 1);
-                sh.topv[s] = abs(u[e]);
-                sh.topi[s] = threadIdx.x + e * NT;
-            } else if ((ffree >> e) & 1u) {
-                tmax = max(tmax, abs(u[e]));
+            for (int e = 0; e < E; ++e)
+                if (((ffree & ~top) >> e) & 1u) tmax = max(tmax, mag[e]);
+            amax = G::max(tmax, sh.red);
+        } else {
+            K key[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) key[e] = mag_key(abs(u[e]));
+            top = group_topk_select<G, E, K>(key, ffree, kb, sh.sel, sh.ired);
+            if (G::rank() == 0) sh.topcnt = 0;
+            G::sync();
+            T tmax = T(0);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if ((top >> e) & 1u) {
+                    const int s = atomicAdd(&sh.topcnt, 1);
+                    sh.topv[s] = abs(u[e]);
+                    sh.topi[s] = G::rank() + e * NT;
+                } else if ((ffree >> e) & 1u) {
+                    tmax = max(tmax, abs(u[e]));
+                }
             }
+            amax = G::max(tmax, sh.red);   // also publishes topv (via its barriers)
+            G::sync();
+            warp_rank_sort_desc<T, G>(sh.topv, sh.topi, kb, sh.sv, sh.si);
         }
-        const T amax = block_max<NT, T>(tmax, sh.red);   // also publishes topv
-        warp_rank_sort_desc<T>(sh.topv, sh.topi, kb, sh.sv, sh.si);
-        __syncthreads();
+        G::sync();
+        // entry points p(sv[i]) of the top values, one per group member
+        for (int i = G::rank(); i < kb; i += NT) sh.ep[i] = entry_point(sh.sv[i], c, M);
+        G::sync();
         if (amax > T(0)) {
-            // entry points in ascending order: e_(i) = p(sv[kb-1-i])
-            const T emin = entry_point(sh.sv[kb - 1], c, M);
+            // entry points in ascending order: e_(i) = ep[kb - i], i = 1..kb
+            const T emin = sh.ep[kb - 1];
             if (emin >= amax) {
                 theta = amax;                      // no violation: nothing pools
             } else {
-                int r = 0;                         // entry points below amax
-                for (int i = 0; i < kb; ++i) r += entry_point(sh.sv[kb - 1 - i], c, M) < amax;
-                auto xval = [&](int i) -> T {
-                    return i == 0 ? T(0) : (i <= r ? entry_point(sh.sv[kb - i], c, M) : amax);
-                };
-                auto Pval = [&](T x) -> T {        // sum_top (h(x) - |u|)^+ over entry points < x
-                    const T h = x + min(x / c, M);
-                    T s = T(0);
-                    for (int i = 0; i < kb; ++i) {
-                        const T t = sh.sv[i];
-                        if (entry_point(t, c, M) < x) s += max(h - t, T(0));
-                    }
-                    return s;
-                };
+                int cnt = 0;                       // entry points below amax
+                for (int i = G::rank(); i < kb; i += NT) cnt += sh.ep[i] < amax;
+                const int r = G::count(cnt, sh.ired);
+                auto xval = [&](int i) -> T { return i == 0 ? T(0) : (i <= r ? sh.ep[kb - i] : amax); };
                 int lo = 0, hi = r + 1;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
                     const T x = xval(mid);
+                    const T h = x + min(x / c, M);
+                    // f(x) = sum_tail (|u| - x)^+ - sum_{top, p(t) < x} (h(x) - t)
                     T part[1] = {T(0)};
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if (((ffree & ~top) >> e) & 1u) part[0] += max(abs(u[e]) - x, T(0));
-                    block_sum<NT, 1, T>(part, sh.red);
-                    if (part[0] - Pval(x) > T(0)) lo = mid; else hi = mid;
+                    for (int i = G::rank(); i < kb; i += NT)
+                        if (sh.ep[i] < x) part[0] -= max(h - sh.sv[i], T(0));
+                    G::template sum<1, T>(part, sh.red);
+                    if (part[0] > T(0)) lo = mid; else hi = mid;
                 }
                 const T xlo = xval(lo), xhi = xval(hi);
-                T nt = T(0), St = T(0);
-                for (int i = 0; i < kb; ++i) {
-                    const T t = sh.sv[i];
-                    if (entry_point(t, c, M) <= xlo) { nt += T(1); St += t; }
-                }
+                T ns[2] = {T(0), T(0)};
+                for (int i = G::rank(); i < kb; i += NT)
+                    if (sh.ep[i] <= xlo) { ns[0] += T(1); ns[1] += sh.sv[i]; }
+                G::template sum<2, T>(ns, sh.red);
+                const T nt = ns[0], St = ns[1];
                 T th = xlo;
                 T q[2] = {T(0), T(0)};
 #pragma unroll
                 for (int e = 0; e < E; ++e)
                     if ((((ffree & ~top) >> e) & 1u) && abs(u[e]) > th) { q[0] += T(1); q[1] += abs(u[e]); }
-                block_sum<NT, 2, T>(q, sh.red);
+                G::template sum<2, T>(q, sh.red);
                 T nl = q[0], Sl = q[1];
                 for (int it = 0; it < 4 * kMaxK + 64; ++it) {
                     T tn = model_root(nt, St, nl, Sl, c, M);
@@ -179,7 +213,7 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if ((((ffree & ~top) >> e) & 1u) && abs(u[e]) > tn) { q[0] += T(1); q[1] += abs(u[e]); }
-                    block_sum<NT, 2, T>(q, sh.red);
+                    G::template sum<2, T>(q, sh.red);
                     const bool done = (q[0] == nl);
                     th = tn;
                     nl = q[0];
@@ -215,14 +249,19 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
         bn[e] = u[e] < T(0) ? -mag : mag;
         dot[0] += (vv[e] - bn[e]) * (bn[e] - bo[e]);
     }
-    block_sum<NT, 1, T>(dot, sh.red);
-    const double tp = a.tmom[b];
-    const double tk1 = (a.restart && dot[0] > T(0)) ? 1.0 : tp;
-    const double tpp = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk1 * tk1));
-    const T coef = T((tk1 - 1.0) / tpp);
+    G::template sum<1, T>(dot, sh.red);
+    if (G::rank() == 0) {                  // FISTA t update, once per node, in FP64
+        const double tp = a.tmom[b];
+        const double tk1 = (a.restart && dot[0] > T(0)) ? 1.0 : tp;
+        const double tpp = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk1 * tk1));
+        sh.coef = T((tk1 - 1.0) / tpp);
+        a.tmom[b] = tpp;
+    }
+    G::sync();
+    const T coef = sh.coef;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int j = threadIdx.x + e * NT;
+        const int j = G::rank() + e * NT;
         if ((valid >> e) & 1u) {
             const T vn = bn[e] + coef * (bn[e] - bo[e]);
             Bm[base + j] = bn[e];
@@ -230,24 +269,27 @@ __global__ __launch_bounds__(NT) void k_prox_fista(ProxArgs a) {
             if (a.Vop != nullptr) store_operand(a.Vop, (size_t)b * a.op_ld + j, (float)vn, a.op_bf16);
         }
     }
-    if (threadIdx.x == 0) a.tmom[b] = tpp;
 }
 
 template <typename T>
 int dispatch(cudaStream_t s, const ProxArgs& a) {
     const int p = a.p, m = a.m;
     if (m <= 0) return 0;
-#define KGLM_PROX(NT_, E_) k_prox_fista<T, NT_, E_><<<m, NT_, 0, s>>>(a)
-    if (p <= 64) KGLM_PROX(32, 2);
-    else if (p <= 128) KGLM_PROX(64, 2);
-    else if (p <= 256) KGLM_PROX(64, 4);
-    else if (p <= 512) KGLM_PROX(128, 4);
+#define KGLM_PROX(NT_, E_) k_prox_fista<T, CtaGroup<NT_>, E_, 1><<<m, NT_, 0, s>>>(a)
+#define KGLM_PROX_WARP(E_) k_prox_fista<T, WarpGroup, E_, 4><<<(m + 3) / 4, 128, 0, s>>>(a)
+    // up to 512 coordinates: one warp per node, four nodes per CTA
+    if (p <= 32) KGLM_PROX_WARP(1);
+    else if (p <= 64) KGLM_PROX_WARP(2);
+    else if (p <= 128) KGLM_PROX_WARP(4);
+    else if (p <= 256) KGLM_PROX_WARP(8);
+    else if (p <= 512) KGLM_PROX_WARP(16);
     else if (p <= 1024) KGLM_PROX(128, 8);
     else if (p <= 2048) KGLM_PROX(256, 8);
     else if (p <= 4096) KGLM_PROX(512, 8);
     else if (sizeof(T) == 4 && p <= 8192) KGLM_PROX(512, 16);
     else return -1;
 #undef KGLM_PROX
+#undef KGLM_PROX_WARP
     return 0;
 }
 

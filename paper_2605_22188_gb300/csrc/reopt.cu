@@ -30,6 +30,8 @@ __host__ __device__ inline int reopt_chunk(int k) {
     int ch = (24576 / (8 * (k > 0 ? k : 1))) / 32 * 32;
     return ch < 32 ? 32 : (ch > 256 ? 256 : ch);
 }
+// Row stride of the staged X_S chunk: CH + 1 keeps the rows of a pair loop in different banks.
+__host__ __device__ inline int reopt_stride(int k) { return reopt_chunk(k) + 1; }
 
 namespace {
 
@@ -99,7 +101,7 @@ __device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec,
 #pragma unroll
     for (int o = 0; o < MAXOWN; ++o) acc[o] = TI(0);
     TI floss = TI(0);
-    const int CH = dy.ch;
+    const int CH = dy.ch, XS = CH + 1;
     for (int i0 = 0; i0 < a.n; i0 += CH) {
         if (tid < CH) {
             const int i = i0 + tid;
@@ -107,7 +109,7 @@ __device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec,
             if (i < a.n) {
                 for (int r = 0; r < ks; ++r) {
                     const TI x = Xt[(size_t)sh.S[r] * a.n + i];
-                    Xs[r * CH + tid] = x;
+                    Xs[r * XS + tid] = x;
                     s += x * TI(vec[r]);
                 }
                 const TI yi = yv[i];
@@ -116,7 +118,7 @@ __device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec,
                 dv[tid] = -yi * sg;
                 wv[tid] = sg * (TI(1) - sg);
             } else {
-                for (int r = 0; r < ks; ++r) Xs[r * CH + tid] = TI(0);
+                for (int r = 0; r < ks; ++r) Xs[r * XS + tid] = TI(0);
                 dv[tid] = wv[tid] = TI(0);
             }
         }
@@ -127,13 +129,13 @@ __device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec,
                 const int P = tid + o * NT;
                 if (P < ks) {
                     TI s = TI(0);
-                    for (int t = 0; t < CH; ++t) s += Xs[P * CH + t] * dv[t];
+                    for (int t = 0; t < CH; ++t) s += Xs[P * XS + t] * dv[t];
                     acc[o] += s;
                 } else if (P < ks + npairs) {
                     int q = P - ks, r = 0;
                     while (q > r) { q -= r + 1; ++r; }          // pair (r, q), q <= r
                     TI s = TI(0);
-                    for (int t = 0; t < CH; ++t) s += Xs[r * CH + t] * Xs[q * CH + t] * wv[t];
+                    for (int t = 0; t < CH; ++t) s += Xs[r * XS + t] * Xs[q * XS + t] * wv[t];
                     acc[o] += s;
                 }
             }
@@ -171,8 +173,8 @@ __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
     __shared__ RS sh;
     extern __shared__ __align__(16) double dyn[];
     const int k = a.k, p = a.p, b = blockIdx.x, tid = threadIdx.x;
-    const int CH = reopt_chunk(k);
-    Dyn dy{dyn, dyn + k * k, dyn + 2 * k * k, dyn + 2 * k * k + k * CH, dyn + 2 * k * k + k * CH + CH, CH};
+    const int CH = reopt_chunk(k), XS = reopt_stride(k);
+    Dyn dy{dyn, dyn + k * k, dyn + 2 * k * k, dyn + 2 * k * k + k * XS, dyn + 2 * k * k + k * XS + CH, CH};
     const double M = a.M;
     if (tid == 0) {
         int ks = 0;
@@ -289,12 +291,26 @@ __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
             evaluate<TI>(a, sh, dy, sh.b, true);
         }
     }
-    // exact objective: sum_i l((X_S b)_i, y_i) + lambda2 ||b||^2
+    // objective of the returned coefficients b: sum_i l((X_S b)_i, y_i) + lambda2 ||b||^2,
+    // the predictor in FP64; the logistic loss in the reduced-precision modes
+    // as an FP32 evaluation plus a margin that makes the sum an upper bound:
+    // t = y s rounded to FP32 moves the 1-Lipschitz loss by <= 2^-24 |t|;
+    // expf (2 ulp) and log1pf (1 ulp, documented maxima) give <= 2^-21 relative
+    // on log1p(e^-|t|) [d/dE log1p(E) * E <= log1p(E)], one more rounding for
+    // the sum: margin 2^-23 |t| + 2^-20 l~ + 2^-125 per sample.
     double part = 0.0;
+    const bool fast = sizeof(TI) == 4 && a.kind == kLOGISTIC;
     for (int i = tid; i < a.n; i += NT) {
         double s = 0.0;
         for (int r = 0; r < ks; ++r) s += a.Xt[(size_t)sh.S[r] * a.n + i] * sh.b[r];
-        part += loss64(s, a.y[i], a.kind);
+        if (fast) {
+            const double t = a.y[i] * s;
+            const float tf = (float)t;
+            const float l = fmaxf(-tf, 0.f) + log1pf(expf(-fabsf(tf)));
+            part += (double)l + (ldexp(fabs(t), -23) + ldexp((double)l, -20) + 0x1p-125);
+        } else {
+            part += loss64(s, a.y[i], a.kind);
+        }
     }
     const double tot = block_total(part, sh.red);
     if (tid == 0) {
@@ -305,11 +321,35 @@ __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
     for (int r = tid; r < k; r += NT) a.beta_re[(size_t)b * k + r] = r < ks ? sh.b[r] : 0.0;
 }
 
+// FP64 objective F(X_S b) + lambda2 ||b||^2 of one coefficient vector (one CTA).
+__global__ __launch_bounds__(NT) void k_objective64(const double* Xt, const double* y, int n, int kind,
+                                                    double lam2, const int* S, const double* b, int ks,
+                                                    double* out) {
+    __shared__ double red[NT / 32];
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+        double s = 0.0;
+        for (int r = 0; r < ks; ++r) s += Xt[(size_t)S[r] * n + i] * b[r];
+        part += loss64(s, y[i], kind);
+    }
+    const double tot = block_total(part, red);
+    if (threadIdx.x == 0) {
+        double rid = 0.0;
+        for (int r = 0; r < ks; ++r) rid += b[r] * b[r];
+        *out = tot + lam2 * rid;
+    }
+}
+
 }  // namespace
+
+void objective64_launch(cudaStream_t s, const double* Xt, const double* y, int n, int kind, double lam2,
+                        const int* S, const double* b, int ks, double* out) {
+    k_objective64<<<1, NT, 0, s>>>(Xt, y, n, kind, lam2, S, b, ks, out);
+}
 
 size_t reopt_smem_bytes(int k) {
     const int ch = reopt_chunk(k);
-    return sizeof(double) * (size_t)(2 * k * k + k * ch + 2 * ch);
+    return sizeof(double) * (size_t)(2 * k * k + k * reopt_stride(k) + 2 * ch);
 }
 
 int reopt_launch(cudaStream_t s, const ReoptArgs& a) {
