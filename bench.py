@@ -256,6 +256,10 @@ def oracle_rate(pool, nodes, T, cores):
 
 # ------------------------------------------------------------------ the engine arm
 
+def loss_kind(args):
+    return None if args.loss is None else (synth.LSQ if args.loss == "lsq" else synth.LOGISTIC)
+
+
 def make_batches(c, nb, m, seed):
     rng = np.random.default_rng(seed)
     return [synth.random_nodes(m, c["p"], c["k"], rng) for _ in range(nb)]
@@ -266,7 +270,7 @@ def run_ours(args):
     from paper_2605_22188_gb300 import kglm
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
-    c, X, y, _ = synth.config_instance(args.workload, seed=0)
+    c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
     m, T = c.get("m", 1024), args.iters
     pk = peaks()
 
@@ -416,7 +420,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import node as on
-    c, X, y, _ = synth.config_instance(args.workload, seed=0)
+    c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
     T = args.iters
     L = on.lipschitz(X, c["kind"])
     cores = os.cpu_count() or 1
@@ -457,6 +461,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "tf32"])
     ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--loss", default=None, choices=[None, "lsq", "logistic"],
+                    help="override the workload's loss (the microbench runs both)")
     ap.add_argument("--cpu-nodes-per-core", type=int, default=150)
     ap.add_argument("--ref-nodes-per-core", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
