@@ -1,6 +1,6 @@
 // Re-optimization on the rounded support of each node (§4.3):
 //   v(S) = min { F(X_S b) + lambda2 ||b||^2 : ||b||_inf <= M },
-// one CTA per node, FP64, warm-started from the node's relaxed beta on S.
+// one CTA per node, warm-started from the node's relaxed beta on S.
 //
 // §4.3 allows any proximal-gradient method whose prox is the projection onto
 // [-M, M]; the problem has at most k variables, so this kernel takes
@@ -11,47 +11,110 @@
 // the others by Cholesky, and the step is backtracked along the projection
 // arc P(b + alpha d) until the Armijo condition holds.  It stops when the
 // projected gradient ||b - P(b - g)|| <= tol * max(1, ||g(b_0)||), the same
-// optimum the FISTA re-optimization reaches.  In the reduced-precision modes
-// the logistic steps run in FP32 (tolerance 2e-5): v(S) is flat at its
-// minimizer, so the FP64 objective at an FP32-accurate minimizer is within
-// O(tol^2) of the minimum.
+// optimum the FISTA re-optimization reaches, or once an accepted Newton step
+// predicts a decrease below the working precision's resolution of f (for a
+// Newton step the predicted decrease g.d is twice the model's f - f*).  In
+// the reduced-precision modes the logistic steps run in FP32: v(S) is flat at
+// its minimizer, so the FP64 objective at an FP32-accurate minimizer is within
+// O(eps32) relative of the minimum.
 //
-// Least squares uses the Gram block (X^T X)_SS and (X^T y)_S; the logistic
-// gradient and Hessian are the gather-and-reduce passes of §4.3 over the n
-// samples (chunks of CH samples of X_S staged in shared memory).  The
-// returned v(S) is recomputed exactly in a final pass over the samples.
+// Least squares uses the Gram block (X^T X)_SS and (X^T y)_S.  The logistic
+// loss, gradient and Hessian are the gather-and-reduce passes of §4.3 over the
+// n samples: chunks of X_S are staged in shared memory (one sample per
+// thread), and H = X_S^T diag(w) X_S is accumulated in 4 x 4 register blocks
+// on and above the diagonal, each block's samples split over a power-of-two
+// group of lanes that is summed by shuffles.  Every line-search trial is a
+// full evaluation (f, g, H), so an accepted step needs no further pass.  The
+// returned v(S) is recomputed in a final FP64 pass over the samples.
 #include "common.cuh"
 #include "engine.h"
 
 namespace kglm {
 
-// Samples per staged chunk: as many as fit 24 KB of X_S, a multiple of 32, at most one per thread.
-__host__ __device__ inline int reopt_chunk(int k) {
-    int ch = (24576 / (8 * (k > 0 ? k : 1))) / 32 * 32;
-    return ch < 32 ? 32 : (ch > 256 ? 256 : ch);
-}
-// Row stride of the staged X_S chunk: CH + 1 keeps the rows of a pair loop in different banks.
-__host__ __device__ inline int reopt_stride(int k) { return reopt_chunk(k) + 1; }
-
 namespace {
 
 constexpr int NT = 256;
-constexpr int MAXOWN = (kMaxK * (kMaxK + 1) / 2 + kMaxK + NT - 1) / NT;
+
+// Hessian block map: nb = ceil(ks / 4) block rows, nbp = nb (nb + 1) / 2 blocks
+// on and above the diagonal, ss lanes (a power of two <= 32) per block.
+struct PairMap {
+    int nb, nbp, ss;
+};
+__host__ __device__ inline PairMap pair_map(int ks) {
+    PairMap pm;
+    pm.nb = (ks + 3) / 4;
+    pm.nbp = pm.nb * (pm.nb + 1) / 2;
+    pm.ss = 1;
+    while (pm.ss < 32 && 2 * pm.ss * pm.nbp <= NT) pm.ss *= 2;
+    return pm;
+}
+
+// Row stride (elements) of the staged sample-major X_S chunk: 4 nb columns
+// plus padding that makes the number of 16-byte segments per row odd, so that
+// eight consecutive rows read through 16-byte loads fall in distinct banks.
+__host__ __device__ inline int xs_stride(int k, int esize) {
+    const int nb = (k + 3) / 4;
+    if (esize == 4) return nb % 2 ? 4 * nb : 4 * nb + 4;
+    return 4 * nb + 2;
+}
+// Samples per staged chunk: about 40 KB of X_S, a multiple of 32 in [32, 1024].
+__host__ __device__ inline int xs_chunk(int k, int esize) {
+    int ch = 40960 / (xs_stride(k, esize) * esize) / 32 * 32;
+    return ch < 32 ? 32 : (ch > 1024 ? 1024 : ch);
+}
 
 struct RS {
     int S[kMaxK];
-    double b[kMaxK], bn[kMaxK], g[kMaxK], d[kMaxK], c[kMaxK];
-    int fr[kMaxK];
+    int fidx[kMaxK];
+    double b[kMaxK], bn[kMaxK], d[kMaxK], c[kMaxK];
+    double g[2][kMaxK];
+    double vt[kMaxK];        // evaluation point in the working precision
     double red[NT / 32];
-    double f, fn, alpha, gnorm0;
-    int ks, done, accept;
+    double f[2], alpha, gnorm0;
+    int ks, done, accept, cur;
 };
 
-// Dynamic shared memory: H[k*k], Lc[k*k], Xs[k*ch], dv[ch], wv[ch] (ch samples per staged chunk).
+// Dynamic shared memory: H[2][k*k] (FP64), the Cholesky factor L[k*k] and
+// right-hand side z[k] (working precision), the X_S chunk Xs[ch * stride] and
+// (w, d) per staged sample.
+template <typename TI>
 struct Dyn {
-    double *H, *Lc, *Xs, *dv, *wv;
-    int ch;
+    double* H[2];
+    TI* L;
+    TI* z;
+    TI* Xs;
+    TI* wd;
+    int ch, xs;
 };
+
+// (least squares never touches the X_S chunk: with_xs = false leaves it out)
+template <typename TI>
+__host__ __device__ inline size_t dyn_bytes(int k, bool with_xs) {
+    const int es = (int)sizeof(TI);
+    const int ch = xs_chunk(k, es), xs = xs_stride(k, es);
+    size_t b = sizeof(double) * 2 * (size_t)k * k;
+    b += (size_t)es * ((size_t)k * k + k);
+    b = (b + 15) / 16 * 16;
+    if (with_xs) b += (size_t)es * ((size_t)ch * xs + 2 * (size_t)ch);
+    return b;
+}
+
+template <typename TI>
+__device__ Dyn<TI> carve(unsigned char* base, int k) {
+    const int es = (int)sizeof(TI);
+    Dyn<TI> d;
+    d.ch = xs_chunk(k, es);
+    d.xs = xs_stride(k, es);
+    d.H[0] = reinterpret_cast<double*>(base);
+    d.H[1] = d.H[0] + (size_t)k * k;
+    d.L = reinterpret_cast<TI*>(d.H[1] + (size_t)k * k);
+    d.z = d.L + (size_t)k * k;
+    size_t off = sizeof(double) * 2 * (size_t)k * k + (size_t)es * ((size_t)k * k + k);
+    off = (off + 15) / 16 * 16;
+    d.Xs = reinterpret_cast<TI*>(base + off);
+    d.wd = d.Xs + (size_t)d.ch * d.xs;
+    return d;
+}
 
 __device__ double block_total(double v, double* red) {
     double a[1] = {v};
@@ -59,18 +122,48 @@ __device__ double block_total(double v, double* red) {
     return a[0];
 }
 
-__device__ __forceinline__ float softplusf(float t) { return t > 0.f ? t + log1pf(expf(-t)) : log1pf(expf(t)); }
-__device__ __forceinline__ float softplus_t(float t) { return softplusf(t); }
+__device__ __forceinline__ float softplus_t(float t) { return t > 0.f ? t + log1pf(expf(-t)) : log1pf(expf(t)); }
 __device__ __forceinline__ double softplus_t(double t) { return softplus(t); }
 __device__ __forceinline__ float exp_t(float t) { return expf(t); }
 __device__ __forceinline__ double exp_t(double t) { return exp(t); }
+__device__ __forceinline__ float sqrt_t(float t) { return sqrtf(t); }
+__device__ __forceinline__ double sqrt_t(double t) { return sqrt(t); }
 
-// f at vec (up to the constant y^T y for least squares); with `full`, also g and H at vec.
-// The logistic passes run in TI (float in the reduced-precision modes, using
-// the FP32 copy of X^T; double in the FP64 mode).
+// 4 consecutive elements from / to 16-byte aligned shared memory.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    a = q.x; b = q.y;
+}
+__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    a = q.x; b = q.y;
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(double* p, double a, double b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
+
+// Full evaluation at vec: f into sh.f[buf], g into sh.g[buf], H into dy.H[buf]
+// (least squares: f up to the constant y^T y).
 template <typename TI>
-__device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec, bool full) {
+__device__ void evaluate(const ReoptArgs& a, RS& sh, const Dyn<TI>& dy, const double* vec, int buf) {
     const int ks = sh.ks, k = a.k, tid = threadIdx.x;
+    double* H = dy.H[buf];
+    double* g = sh.g[buf];
     if (a.kind == kLSQ) {
         // f = b^T (G + lambda2 I) b - 2 c^T b ; g = 2 ((G + lambda2 I) b - c) ; H = 2 (G + lambda2 I)
         double part = 0.0;
@@ -79,102 +172,212 @@ __device__ void evaluate(const ReoptArgs& a, RS& sh, Dyn& dy, const double* vec,
             for (int q = 0; q < ks; ++q) s += a.gram[(size_t)sh.S[r] * a.p + sh.S[q]] * vec[q];
             s += a.lam2 * vec[r];
             part += vec[r] * s - 2.0 * sh.c[r] * vec[r];
-            if (full) sh.g[r] = 2.0 * (s - sh.c[r]);
+            g[r] = 2.0 * (s - sh.c[r]);
         }
-        if (full)
-            for (int t = tid; t < ks * ks; t += NT) {
-                const int r = t / ks, q = t % ks;
-                dy.H[r * k + q] = 2.0 * (a.gram[(size_t)sh.S[r] * a.p + sh.S[q]] + (r == q ? a.lam2 : 0.0));
-            }
+        for (int t = tid; t < ks * ks; t += NT) {
+            const int r = t / ks, q = t % ks;
+            H[r * k + q] = 2.0 * (a.gram[(size_t)sh.S[r] * a.p + sh.S[q]] + (r == q ? a.lam2 : 0.0));
+        }
         const double f = block_total(part, sh.red);
-        if (tid == 0) { if (full) sh.f = f; else sh.fn = f; }
+        if (tid == 0) sh.f[buf] = f;
         __syncthreads();
         return;
     }
-    const int npairs = ks * (ks + 1) / 2;
     const TI* Xt = static_cast<const TI*>(sizeof(TI) == 8 ? (const void*)a.Xt : (const void*)a.Xt32);
     const TI* yv = static_cast<const TI*>(sizeof(TI) == 8 ? (const void*)a.y : (const void*)a.y32);
-    TI* Xs = reinterpret_cast<TI*>(dy.Xs);
-    TI* dv = reinterpret_cast<TI*>(dy.dv);
-    TI* wv = reinterpret_cast<TI*>(dy.wv);
-    TI acc[MAXOWN];
+    TI* vt = reinterpret_cast<TI*>(sh.vt);
+    for (int r = tid; r < 4 * ((ks + 3) / 4); r += NT) vt[r] = r < ks ? (TI)vec[r] : TI(0);
+    __syncthreads();
+    const PairMap pm = pair_map(ks);
+    const int bp = tid / pm.ss, sl = tid % pm.ss;
+    int R = 0, Q = 0;
+    if (bp < pm.nbp) {                       // block (R, Q), R <= Q, row-major over the upper triangle
+        int t = bp;
+        while (t >= pm.nb - R) { t -= pm.nb - R; ++R; }
+        Q = R + t;
+    }
+    TI acc[16], gacc[4];
 #pragma unroll
-    for (int o = 0; o < MAXOWN; ++o) acc[o] = TI(0);
+    for (int o = 0; o < 16; ++o) acc[o] = TI(0);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) gacc[o] = TI(0);
     TI floss = TI(0);
-    const int CH = dy.ch, XS = CH + 1;
+    const int CH = dy.ch, XS = dy.xs;
     for (int i0 = 0; i0 < a.n; i0 += CH) {
-        if (tid < CH) {
-            const int i = i0 + tid;
+        const int cn = min(CH, a.n - i0);
+        // stage: one sample per thread; s = x_S . vec, loss, w = sigma (1 - sigma), d = dl/ds
+        for (int t = tid; t < cn; t += NT) {
+            const int i = i0 + t;
             TI s = TI(0);
-            if (i < a.n) {
-                for (int r = 0; r < ks; ++r) {
-                    const TI x = Xt[(size_t)sh.S[r] * a.n + i];
-                    Xs[r * XS + tid] = x;
-                    s += x * TI(vec[r]);
-                }
-                const TI yi = yv[i];
-                floss += softplus_t(-yi * s);
-                const TI sg = TI(1) / (TI(1) + exp_t(yi * s));   // sigma(-y s)
-                dv[tid] = -yi * sg;
-                wv[tid] = sg * (TI(1) - sg);
-            } else {
-                for (int r = 0; r < ks; ++r) Xs[r * XS + tid] = TI(0);
-                dv[tid] = wv[tid] = TI(0);
-            }
-        }
-        __syncthreads();
-        if (full) {
+            for (int r4 = 0; r4 < pm.nb; ++r4) {
+                TI x[4];
 #pragma unroll
-            for (int o = 0; o < MAXOWN; ++o) {
-                const int P = tid + o * NT;
-                if (P < ks) {
-                    TI s = TI(0);
-                    for (int t = 0; t < CH; ++t) s += Xs[P * XS + t] * dv[t];
-                    acc[o] += s;
-                } else if (P < ks + npairs) {
-                    int q = P - ks, r = 0;
-                    while (q > r) { q -= r + 1; ++r; }          // pair (r, q), q <= r
-                    TI s = TI(0);
-                    for (int t = 0; t < CH; ++t) s += Xs[r * XS + t] * Xs[q * XS + t] * wv[t];
-                    acc[o] += s;
+                for (int e = 0; e < 4; ++e) {
+                    const int r = 4 * r4 + e;
+                    x[e] = r < ks ? Xt[(size_t)sh.S[r] * a.n + i] : TI(0);
+                    s += x[e] * vt[r];
+                }
+                st4(dy.Xs + (size_t)t * XS + 4 * r4, x);
+            }
+            const TI yi = yv[i];
+            floss += softplus_t(-yi * s);
+            const TI sg = TI(1) / (TI(1) + exp_t(yi * s));   // sigma(-y s)
+            st2(dy.wd + 2 * t, sg * (TI(1) - sg), -yi * sg);
+        }
+        __syncthreads();
+        if (bp < pm.nbp) {
+            const TI* xr_base = dy.Xs + 4 * R;
+            const TI* xq_base = dy.Xs + 4 * Q;
+            if (R == Q) {
+                for (int t = sl; t < cn; t += pm.ss) {
+                    TI xr[4], w, dd;
+                    ld4(xr_base + (size_t)t * XS, xr);
+                    ld2(dy.wd + 2 * t, w, dd);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const TI xw = xr[e] * w;
+                        gacc[e] += xr[e] * dd;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) acc[e * 4 + f] += xw * xr[f];
+                    }
+                }
+            } else {
+                for (int t = sl; t < cn; t += pm.ss) {
+                    TI xr[4], xq[4], w, dd;
+                    ld4(xr_base + (size_t)t * XS, xr);
+                    ld4(xq_base + (size_t)t * XS, xq);
+                    ld2(dy.wd + 2 * t, w, dd);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const TI xw = xr[e] * w;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) acc[e * 4 + f] += xw * xq[f];
+                    }
                 }
             }
         }
         __syncthreads();
+    }
+    // sum each block over its ss lanes (aligned power-of-two lane groups)
+    for (int o = pm.ss / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) gacc[e] += __shfl_xor_sync(0xffffffffu, gacc[e], o);
+    }
+    if (bp < pm.nbp && sl == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 4 * R + e;
+            if (r >= ks) continue;
+            if (R == Q) g[r] = (double)gacc[e] + 2.0 * a.lam2 * vec[r];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const int q = 4 * Q + f;
+                if (q >= ks || (R == Q && f < e)) continue;
+                const double h = (double)acc[e * 4 + f] + (r == q ? 2.0 * a.lam2 : 0.0);
+                H[r * k + q] = h;
+                H[q * k + r] = h;
+            }
+        }
     }
     double ridge = 0.0;
     for (int r = 0; r < ks; ++r) ridge += vec[r] * vec[r];
     const double f = block_total((double)floss, sh.red) + a.lam2 * ridge;
-    if (full) {
-#pragma unroll
-        for (int o = 0; o < MAXOWN; ++o) {
-            const int P = tid + o * NT;
-            if (P < ks) {
-                sh.g[P] = (double)acc[o] + 2.0 * a.lam2 * vec[P];
-            } else if (P < ks + npairs) {
-                int q = P - ks, r = 0;
-                while (q > r) { q -= r + 1; ++r; }
-                const double h = (double)acc[o] + (r == q ? 2.0 * a.lam2 : 0.0);
-                dy.H[r * k + q] = h;
-                dy.H[q * k + r] = h;
-            }
-        }
-    }
-    if (tid == 0) { if (full) sh.f = f; else sh.fn = f; }
+    if (tid == 0) sh.f[buf] = f;
     __syncthreads();
 }
 
+// Newton direction on the free set (warp 0): the projected-gradient test,
+// the held set, then d_F = -H_FF^{-1} g_F by a right-looking Cholesky
+// factorization in the working precision, lane l owning the factor rows
+// l, l + 32.  Sets sh.done when the projected gradient is below tolerance.
 template <typename TI>
-__global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
-    // stopping levels of the working precision: projected-gradient tolerance,
-    // and the predicted decrease below which f cannot check Armijo
-    const double tol = sizeof(TI) == 8 ? a.tol : fmax(a.tol, 2e-5);
+__device__ void newton_direction(RS& sh, const Dyn<TI>& dy, int k, double M, double tol) {
+    const int lane = threadIdx.x & 31, ks = sh.ks, cur = sh.cur;
+    const double* H = dy.H[cur];
+    const double* g = sh.g[cur];
+    double pg = 0.0;
+    for (int r = lane; r < ks; r += 32) {
+        const double t = sh.b[r] - fmin(M, fmax(-M, sh.b[r] - g[r]));
+        pg += t * t;
+    }
+    pg = sqrt(warp_sum(pg));
+    if (pg <= tol * sh.gnorm0) {
+        if (lane == 0) sh.done = 1;
+        return;
+    }
+    const double eps = fmin(1e-3 * M, pg);
+    int nf = 0;
+    for (int base = 0; base < ks; base += 32) {
+        const int r = base + lane;
+        bool fr = false;
+        if (r < ks) {
+            const bool held = (sh.b[r] <= -M + eps && g[r] > 0.0) || (sh.b[r] >= M - eps && g[r] < 0.0);
+            fr = !held;
+            sh.d[r] = 0.0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, fr);
+        if (fr) sh.fidx[nf + __popc(bal & ((1u << lane) - 1u))] = r;
+        nf += __popc(bal);
+    }
+    __syncwarp();
+    TI* L = dy.L;
+    TI* z = dy.z;
+    for (int i = lane; i < nf; i += 32) {
+        const int ri = sh.fidx[i];
+        for (int j = 0; j <= i; ++j) L[i * k + j] = (TI)H[ri * k + sh.fidx[j]];
+        z[i] = -(TI)g[ri];
+    }
+    __syncwarp();
+    for (int j = 0; j < nf; ++j) {
+        // H_FF is positive definite (>= 2 lambda2 I); a pivot lost to rounding is floored
+        const TI floor_j = TI(1e-7) * (TI)H[sh.fidx[j] * k + sh.fidx[j]];
+        const TI piv = L[j * k + j];
+        const TI dj = sqrt_t(piv > floor_j ? piv : floor_j);
+        __syncwarp();
+        for (int i = lane; i < nf; i += 32) {
+            if (i == j) L[j * k + j] = dj;
+            else if (i > j) L[i * k + j] /= dj;
+        }
+        __syncwarp();
+        for (int i = lane; i < nf; i += 32) {
+            if (i <= j) continue;
+            const TI lij = L[i * k + j];
+            for (int q = j + 1; q <= i; ++q) L[i * k + q] -= lij * L[q * k + j];
+        }
+        __syncwarp();
+    }
+    for (int j = 0; j < nf; ++j) {            // L y = -g_F
+        if (lane == (j & 31)) z[j] /= L[j * k + j];
+        __syncwarp();
+        const TI zj = z[j];
+        for (int i = lane; i < nf; i += 32)
+            if (i > j) z[i] -= L[i * k + j] * zj;
+        __syncwarp();
+    }
+    for (int j = nf - 1; j >= 0; --j) {       // L^T d = y
+        if (lane == (j & 31)) z[j] /= L[j * k + j];
+        __syncwarp();
+        const TI zj = z[j];
+        for (int i = lane; i < nf; i += 32)
+            if (i < j) z[i] -= L[j * k + i] * zj;
+        __syncwarp();
+    }
+    for (int i = lane; i < nf; i += 32) sh.d[sh.fidx[i]] = (double)z[i];
+    if (lane == 0) sh.alpha = 1.0;
+}
+
+template <typename TI>
+__global__ __launch_bounds__(NT, sizeof(TI) == 4 ? 4 : 1) void k_reopt(ReoptArgs a) {
+    // stopping level of the working precision: the predicted decrease below
+    // which f can neither check Armijo nor improve
+    const double tol = a.tol;
     const double tiny_rel = sizeof(TI) == 8 ? 1e-14 : 3e-7;
     __shared__ RS sh;
-    extern __shared__ __align__(16) double dyn[];
-    const int k = a.k, p = a.p, b = blockIdx.x, tid = threadIdx.x;
-    const int CH = reopt_chunk(k), XS = reopt_stride(k);
-    Dyn dy{dyn, dyn + k * k, dyn + 2 * k * k, dyn + 2 * k * k + k * XS, dyn + 2 * k * k + k * XS + CH, CH};
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    const int k = a.k, p = a.p, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const Dyn<TI> dy = carve<TI>(dyn_raw, k);
     const double M = a.M;
     if (tid == 0) {
         int ks = 0;
@@ -184,6 +387,7 @@ __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
         }
         sh.ks = ks;
         sh.done = 0;
+        sh.cur = 0;
     }
     __syncthreads();
     const int ks = sh.ks;
@@ -195,109 +399,64 @@ __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
     }
     __syncthreads();
     if (ks > 0) {
-        evaluate<TI>(a, sh, dy, sh.b, true);
-        if (tid == 0) {
+        evaluate<TI>(a, sh, dy, sh.b, 0);
+        if (tid < 32) {
             double g2 = 0.0;
-            for (int r = 0; r < ks; ++r) g2 += sh.g[r] * sh.g[r];
-            sh.gnorm0 = fmax(1.0, sqrt(g2));
+            for (int r = lane; r < ks; r += 32) g2 += sh.g[0][r] * sh.g[0][r];
+            g2 = warp_sum(g2);
+            if (lane == 0) sh.gnorm0 = fmax(1.0, sqrt(g2));
         }
         __syncthreads();
         for (int it = 0; it < a.max_iter; ++it) {
-            if (tid == 0) {
-                double pg = 0.0;
-                for (int r = 0; r < ks; ++r) {
-                    const double t = sh.b[r] - fmin(M, fmax(-M, sh.b[r] - sh.g[r]));
-                    pg += t * t;
-                }
-                pg = sqrt(pg);
-                if (pg <= tol * sh.gnorm0) {
-                    sh.done = 1;
-                } else {
-                    const double eps = fmin(1e-3 * M, pg);
-                    int nf = 0;
-                    for (int r = 0; r < ks; ++r) {
-                        const bool held = (sh.b[r] <= -M + eps && sh.g[r] > 0.0) || (sh.b[r] >= M - eps && sh.g[r] < 0.0);
-                        sh.fr[r] = held ? -1 : nf++;
-                        sh.d[r] = 0.0;
-                    }
-                    // Cholesky of H_FF, then d_F = -H_FF^{-1} g_F
-                    double* L = dy.Lc;
-                    for (int r = 0, ir = 0; r < ks; ++r) {
-                        if (sh.fr[r] < 0) continue;
-                        for (int q = 0, iq = 0; q < ks; ++q) {
-                            if (sh.fr[q] < 0) continue;
-                            L[ir * k + iq] = dy.H[r * k + q];
-                            ++iq;
-                        }
-                        ++ir;
-                    }
-                    for (int j = 0; j < nf; ++j) {
-                        double s = L[j * k + j];
-                        for (int t = 0; t < j; ++t) s -= L[j * k + t] * L[j * k + t];
-                        s = s > 1e-300 ? sqrt(s) : 1e-150;
-                        L[j * k + j] = s;
-                        for (int i = j + 1; i < nf; ++i) {
-                            double v = L[i * k + j];
-                            for (int t = 0; t < j; ++t) v -= L[i * k + t] * L[j * k + t];
-                            L[i * k + j] = v / s;
-                        }
-                    }
-                    double z[kMaxK];
-                    for (int r = 0, ir = 0; r < ks; ++r) {
-                        if (sh.fr[r] < 0) continue;
-                        double v = -sh.g[r];
-                        for (int t = 0; t < ir; ++t) v -= L[ir * k + t] * z[t];
-                        z[ir] = v / L[ir * k + ir];
-                        ++ir;
-                    }
-                    for (int ir = nf - 1; ir >= 0; --ir) {
-                        double v = z[ir];
-                        for (int t = ir + 1; t < nf; ++t) v -= L[t * k + ir] * z[t];
-                        z[ir] = v / L[ir * k + ir];
-                    }
-                    for (int r = 0; r < ks; ++r)
-                        if (sh.fr[r] >= 0) sh.d[r] = z[sh.fr[r]];
-                    sh.alpha = 1.0;
-                }
-            }
+            if (tid < 32) newton_direction<TI>(sh, dy, k, M, tol);
             __syncthreads();
             if (sh.done) break;
-            // Armijo backtracking along the projection arc
+            const int cur = sh.cur, nxt = 1 - cur;
+            // Armijo backtracking along the projection arc; every trial is a full evaluation
             bool moved = false;
             for (int ls = 0; ls < 40; ++ls) {
                 for (int r = tid; r < ks; r += NT) sh.bn[r] = fmin(M, fmax(-M, sh.b[r] + sh.alpha * sh.d[r]));
                 __syncthreads();
-                evaluate<TI>(a, sh, dy, sh.bn, false);
-                if (tid == 0) {
+                evaluate<TI>(a, sh, dy, sh.bn, nxt);
+                if (tid < 32) {
                     double dec = 0.0, step = 0.0;
-                    for (int r = 0; r < ks; ++r) {
-                        dec += sh.g[r] * (sh.bn[r] - sh.b[r]);
+                    for (int r = lane; r < ks; r += 32) {
+                        dec += sh.g[cur][r] * (sh.bn[r] - sh.b[r]);
                         step = fmax(step, fabs(sh.bn[r] - sh.b[r]));
                     }
-                    // a predicted decrease below the rounding level of f cannot be checked:
-                    // take the step (Newton is then in its quadratic region)
-                    const bool tiny = fabs(dec) <= tiny_rel * (1.0 + fabs(sh.f));
-                    sh.accept = (sh.fn <= sh.f + 1e-4 * dec || tiny) ? 1 : (step <= 1e-16 * M ? 2 : 0);
-                    if (sh.accept == 1 && step <= 1e-15 * M) sh.done = 1;   // converged to FP64 resolution
-                    if (!sh.accept) sh.alpha *= 0.5;
+                    dec = warp_sum(dec);
+                    step = warp_max(step);
+                    if (lane == 0) {
+                        // a predicted decrease below the rounding level of f cannot be checked:
+                        // take the step (Newton is then in its quadratic region)
+                        const bool tiny = fabs(dec) <= tiny_rel * (1.0 + fabs(sh.f[cur]));
+                        sh.accept = (sh.f[nxt] <= sh.f[cur] + 1e-4 * dec || tiny) ? 1 : (step <= 1e-16 * M ? 2 : 0);
+                        // converged: the full step's predicted decrease is below resolution
+                        if (sh.accept == 1 && ((tiny && ls == 0) || step <= 1e-15 * M)) sh.done = 1;
+                        if (!sh.accept) sh.alpha *= 0.5;
+                    }
                 }
                 __syncthreads();
                 if (sh.accept) { moved = (sh.accept == 1); break; }
             }
-            if (!moved) break;                                   // no progress possible in FP64
+            if (!moved) break;                                   // no progress possible
             for (int r = tid; r < ks; r += NT) sh.b[r] = sh.bn[r];
             __syncthreads();
+            if (tid == 0) sh.cur = nxt;
+            __syncthreads();
             if (sh.done) break;
-            evaluate<TI>(a, sh, dy, sh.b, true);
         }
     }
     // objective of the returned coefficients b: sum_i l((X_S b)_i, y_i) + lambda2 ||b||^2,
     // the predictor in FP64; the logistic loss in the reduced-precision modes
-    // as an FP32 evaluation plus a margin that makes the sum an upper bound:
-    // t = y s rounded to FP32 moves the 1-Lipschitz loss by <= 2^-24 |t|;
-    // expf (2 ulp) and log1pf (1 ulp, documented maxima) give <= 2^-21 relative
-    // on log1p(e^-|t|) [d/dE log1p(E) * E <= log1p(E)], one more rounding for
-    // the sum: margin 2^-23 |t| + 2^-20 l~ + 2^-125 per sample.
+    // as an FP32 evaluation plus a margin that makes the sum an upper bound.
+    // (i) t = y s rounded to FP32 moves t by <= 2^-24 |t| (< 1 for |t| < 2^24),
+    // and |l'(xi)| = 1 / (1 + e^xi) <= min(1, e^(1 - tf)) on that interval:
+    // margin 2^-23 |t| min(1, e^(1 - tf) (1 + 2^-20)) (expf within 2 ulp).
+    // (ii) expf (2 ulp) and log1pf (1 ulp), documented maxima, and the final
+    // addition give l~ within 2^-22 + 2^-23 + 2^-24 < 2^-21 relative of l(tf)
+    // [the relative error of E passes to log1p(E) damped, since
+    // d log1p(E)/dE * E <= log1p(E)]: margin 2^-21 l~ + 2^-125 per sample.
     double part = 0.0;
     const bool fast = sizeof(TI) == 4 && a.kind == kLOGISTIC;
     for (int i = tid; i < a.n; i += NT) {
@@ -307,7 +466,8 @@ __global__ __launch_bounds__(NT) void k_reopt(ReoptArgs a) {
             const double t = a.y[i] * s;
             const float tf = (float)t;
             const float l = fmaxf(-tf, 0.f) + log1pf(expf(-fabsf(tf)));
-            part += (double)l + (ldexp(fabs(t), -23) + ldexp((double)l, -20) + 0x1p-125);
+            const double slope = tf > 1.f ? fmin(1.0, (double)expf(1.f - tf) * (1.0 + 0x1p-20)) : 1.0;
+            part += (double)l + (ldexp(fabs(t), -23) * slope + ldexp((double)l, -21) + 0x1p-125);
         } else {
             part += loss64(s, a.y[i], a.kind);
         }
@@ -348,19 +508,18 @@ void objective64_launch(cudaStream_t s, const double* Xt, const double* y, int n
 }
 
 size_t reopt_smem_bytes(int k) {
-    const int ch = reopt_chunk(k);
-    return sizeof(double) * (size_t)(2 * k * k + k * reopt_stride(k) + 2 * ch);
+    const size_t a = dyn_bytes<double>(k, true), b = dyn_bytes<float>(k, true);
+    return a > b ? a : b;
 }
 
 int reopt_launch(cudaStream_t s, const ReoptArgs& a) {
     if (a.m <= 0) return 0;
-    const size_t smem = reopt_smem_bytes(a.k);
     const bool f32 = a.kind == kLOGISTIC && a.Xt32 != nullptr && a.y32 != nullptr;
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(f32 ? k_reopt<float> : k_reopt<double>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return -1;
-    }
+    const size_t smem = f32 ? dyn_bytes<float>(a.k, true) : dyn_bytes<double>(a.k, a.kind == kLOGISTIC);
+    // the opt-in covers static + dynamic shared memory above the 48 KB default
+    if (cudaFuncSetAttribute(f32 ? k_reopt<float> : k_reopt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return -1;
     if (f32) k_reopt<float><<<a.m, NT, smem, s>>>(a);
     else k_reopt<double><<<a.m, NT, smem, s>>>(a);
     return 0;

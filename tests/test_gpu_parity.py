@@ -281,3 +281,31 @@ def test_solve_logistic_reduced_precision_matches_brute_force(prec):
     """Reduced-precision products: the certified optimum and support equal brute force."""
     X, y, _ = synth.instance(80, 14, 3, synth.LOGISTIC, rho=0.6, seed=12)
     _solve_and_compare(X, y, 3, 0.05, 2.0, synth.LOGISTIC, 32, 300, 20, prec=prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", [synth.LSQ, synth.LOGISTIC])
+@pytest.mark.parametrize("k", [33, 64])
+def test_reopt_large_supports(k, kind, prec):
+    """Supports past one warp (k > 32: two factor rows per lane) up to the
+    largest k the engine takes, against the oracle's re-optimization."""
+    n, p = 700, 2 * k + 10
+    X, y, _ = synth.instance(n, p, k, kind, rho=0.5, snr=5.0, seed=40 + k)
+    lam2, M, T = 1e-2, 2.0, 20
+    L = on.lipschitz(X, kind)
+    rng = np.random.default_rng(k)
+    nodes = [([], []), ([], list(range(k - 3))), (list(range(0, p, 7)), [1, 2])]
+    nodes += synth.csr_to_sets(*synth.random_nodes(9, p, k, rng))
+    with kglm.Engine(X, y, k, lam2, M, kind, prec=prec, max_batch=16, lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(T)
+        B, _ = eng.read_batch()
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        S = on.round_support(B[b], nd)
+        assert [int(s) for s in res["support"][b] if s >= 0] == S, b
+        _, v = ro.reopt(X, y, S, lam2, M, kind, beta0=B[b])
+        if prec == "fp64":
+            assert rel(res["ub"][b], v) <= RTOL, (b, res["ub"][b], v)
+        else:
+            check_reduced_objective(res["ub"][b], v)
