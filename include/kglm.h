@@ -185,6 +185,22 @@ kglm_status kglm_push_nodes_dev(kglm_ctx* ctx, int32_t m, const int32_t* in_ptr,
  * KGLM_ETIMEOUT if a tensor-core pipeline wait ran out. */
 kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G);
 
+/* The certificate product of the context: Q[b][j] = sum_i Z[b][i] X[i][j]
+ * (X^T zeta of §4.4 Eq. (batched_dual_candidate_matrix_form), one dual point
+ * per row of Z) with an entrywise bound Qerr[b][j] >= |Q[b][j] - exact|.
+ *   Z: host, m x n row-major FP64; Q, Qerr: host, m x p row-major FP64
+ *   outputs (Qerr may be NULL); 1 <= m <= max_batch.
+ * The FP64 mode computes Q by an FP64 GEMM and writes Qerr = 0 (FP64
+ * rounding only).  The reduced-precision modes use the engine's
+ * exact-splitting product on the BF16 tensor cores (6-bit digits of X and
+ * Z, integer-exact FP32 accumulation, FP64 combine) with its rigorous bound
+ * in Qerr; where that product is not set up (job count or HBM budget) they
+ * fall back to the FP64 GEMM with Qerr = 0.  Uses the batch buffers: call
+ * it between evaluations, not between a push and its evaluation (the pushed
+ * batch's dual points are overwritten).  KGLM_ETIMEOUT if a tensor-core
+ * pipeline wait ran out. */
+kglm_status kglm_xtz(kglm_ctx* ctx, int32_t m, const double* Z, double* Q, double* Qerr);
+
 /* kglm_xtr for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment aid.  Callers that run inside CUDA graph
  * capture, draw every byte from a host application's own pool, or must not

@@ -61,6 +61,16 @@ struct kglm_ctx {
     GemmScratch gtc{};
     int* d_tcerr = nullptr;
     float* Gpart = nullptr;       // split slices of X^T R (summed by the prox kernel)
+    // exact-splitting certificate product (reduced-precision modes): digits of
+    // X (features x K) and of the batch's dual points (nodes x K), job partials
+    bool cexact = false;
+    ExactPlan xplan{};
+    __nv_bfloat16 *DX = nullptr, *DZ = nullptr;
+    double *xsig = nullptr, *ztau = nullptr, *Qerr = nullptr;
+    float* Qs = nullptr;
+    size_t qs_slices = 0;         // partial slices of mcap x p
+    TcMap mAz{}, mBx{};
+    int bnx = 0;
     int gsplit_max = 4;
     int gsplits = 0;
     // host mirror of the evaluated batch
@@ -255,6 +265,33 @@ double gram_lambda_max(kglm_ctx* c) {
     return lam;
 }
 
+// X^T zeta of the batch's dual points (c->zeta, m x n): FP64 GEMM into c->Q,
+// or in the reduced-precision modes the exact-splitting product on the
+// tensor cores, whose partials and bound are recorded in the certificate's
+// arguments.
+void xtzeta(kglm_ctx* c, int m, CertArgs& a) {
+    const int n = c->n, p = c->p;
+    a.Qs = nullptr;
+    if (!c->cexact) {
+        gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p, &c->gs64);
+        return;
+    }
+    const ExactPlan& x = c->xplan;
+    exact_digits(c->st, c->zeta, m, n, (size_t)n, x.npad, x.nd, x.beta, 1, c->DZ, c->ztau);
+    ExactPlan pl = x;
+    const int tiles = ((p + c->bnx - 1) / c->bnx) * ((m + 127) / 128);
+    exact_plan_widen(&pl, tiles, c->qs_slices * (size_t)c->mcap / (size_t)m);
+    if (tc_gemm_jobs(c->st, c->mAz, c->mBx, m, p, c->bnx, pl.jobs, pl.njobs, c->Qs, (size_t)m * p, p, c->d_tcerr) != 0)
+        throw Fail{KGLM_ECUDA, "tensor-core certificate product setup failed"};
+    a.Qs = c->Qs;
+    a.nqs = pl.njobs;
+    a.qs_stride = (size_t)m * p;
+    for (int t = 0; t < pl.njobs; ++t) a.qs_w[t] = pl.w[t];
+    a.xsig = c->xsig;
+    a.ztau = c->ztau;
+    a.ebound = pl.ebound;
+}
+
 void certify(kglm_ctx* c) {
     const int m = c->m, n = c->n, p = c->p;
     CertArgs a{};
@@ -280,8 +317,8 @@ void certify(kglm_ctx* c) {
         check_launch();
     }
     {
-        Scope sc(c, PH_CERT_Q, 1, 2.0 * n * c->sum_pa);
-        gemm_nt_f64(c->st, m, p, n, c->zeta, n, c->Xt64, n, c->Q, p, &c->gs64);   // X^T zeta, FP64
+        Scope sc(c, PH_CERT_Q, c->cexact ? 2 : 1, 2.0 * n * c->sum_pa);
+        xtzeta(c, m, a);
         check_launch();
     }
     {
@@ -475,7 +512,7 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
         if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
         check_launch();
     }
-    if (c->tc) check_tc_error(c);
+    if (c->tc || c->cexact) check_tc_error(c);
 }
 
 // A tensor-core product whose mbarrier wait ran out leaves a flag (the kernel
@@ -805,6 +842,34 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->d_err = dalloc_t<int>(c, 1);
         c->pool_slots = d.pool_slots > 0 ? d.pool_slots : 4 * d.max_batch;
         c->pool = dalloc(c, (size_t)c->pool_slots * p * ws);
+        // reduced-precision modes: digits of X for the exact certificate product
+        // (6-bit digits, 7 per value), when the jobs and the HBM budget allow
+        if (!c->f64 && exact_plan((int)n, 6, 7, &c->xplan)) {
+            const ExactPlan& x = c->xplan;
+            const size_t K2 = (size_t)x.nd * x.npad;
+            const size_t need = 2 * K2 * (p + mc) + 8 * (p + mc) + 4 * (size_t)x.njobs * mc * p + 64;
+            if (c->d.hbm_budget <= 0 || (int64_t)(c->bytes + need) <= c->d.hbm_budget) {
+                c->DX = dalloc_t<__nv_bfloat16>(c, p * K2);
+                c->xsig = dalloc_t<double>(c, p);
+                exact_digits(c->st, c->Xt64, (int)p, (int)n, n, x.npad, x.nd, x.beta, 0, c->DX, c->xsig);
+                check_launch();
+                c->DZ = dalloc_t<__nv_bfloat16>(c, mc * K2);
+                CK(cudaMemsetAsync(c->DZ, 0, sizeof(__nv_bfloat16) * mc * K2, c->st));
+                c->ztau = dalloc_t<double>(c, mc);
+                c->qs_slices = (size_t)x.njobs;
+                c->Qs = dalloc_t<float>(c, c->qs_slices * mc * p);
+                c->bnx = tc_tile_cols((int)p);
+                if (tc_make_map(&c->mBx, c->DX, 1, (int)p, (int)K2, (int)K2, c->bnx) ||
+                    tc_make_map(&c->mAz, c->DZ, 1, (int)mc, (int)K2, (int)K2, 128))
+                    throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for the certificate digits"};
+                if (tc_prepare() != 0) throw Fail{KGLM_ECUDA, "tensor-core kernels: shared memory attribute refused"};
+                if (!c->d_tcerr) {
+                    c->d_tcerr = dalloc_t<int>(c, 1);
+                    CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));
+                }
+                c->cexact = true;
+            }
+        }
         sync(c);
     });
     if (st != KGLM_OK) {
@@ -856,6 +921,35 @@ kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G) {
                         &ctx->gs32);
         check_launch();
         sync(ctx);
+    });
+}
+
+kglm_status kglm_xtz(kglm_ctx* ctx, int32_t m, const double* Z, double* Q, double* Qerr) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(m >= 1 && m <= ctx->mcap, "m must be in [1, max_batch]");
+        REQ(Z && Q, "Z and Q are required");
+        kglm_ctx* c = ctx;
+        const size_t mp = (size_t)m * c->p;
+        CK(cudaMemcpyAsync(c->zeta, Z, sizeof(double) * m * (size_t)c->n, cudaMemcpyHostToDevice, c->st));
+        CertArgs a{};
+        {
+            Scope sc(c, PH_CERT_Q, c->cexact ? 2 : 1, 2.0 * c->n * (double)mp);
+            xtzeta(c, m, a);
+            check_launch();
+        }
+        if (!c->Qerr) c->Qerr = dalloc_t<double>(c, (size_t)c->mcap * c->p);
+        if (a.Qs) {
+            exact_combine(c->st, m, c->p, a.Qs, a.nqs, a.qs_stride, a.qs_w, c->xsig, c->ztau, a.ebound, c->Q,
+                          c->Qerr);
+            check_launch();
+        } else {
+            CK(cudaMemsetAsync(c->Qerr, 0, sizeof(double) * mp, c->st));
+        }
+        CK(cudaMemcpyAsync(Q, c->Q, sizeof(double) * mp, cudaMemcpyDeviceToHost, c->st));
+        if (Qerr) CK(cudaMemcpyAsync(Qerr, c->Qerr, sizeof(double) * mp, cudaMemcpyDeviceToHost, c->st));
+        sync(c);
+        if (c->cexact) check_tc_error(c);
     });
 }
 

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "exact.cuh"
 
 namespace kglm {
 namespace {
@@ -110,7 +111,7 @@ struct CertShared {
 };
 
 template <int NT, int E>
-__global__ __launch_bounds__(NT) void k_cert_bound(CertArgs a) {
+__global__ __launch_bounds__(NT) void k_cert_bound(const __grid_constant__ CertArgs a) {
     using K = unsigned long long;
     __shared__ CertShared sh;
     const int b = blockIdx.x, p = a.p;
@@ -126,7 +127,14 @@ __global__ __launch_bounds__(NT) void k_cert_bound(CertArgs a) {
         q[e] = be[e] = 0.0;
         if (j < p) {
             valid |= 1u << e;
-            q[e] = a.Q[base + j] * inv2l;
+            if (a.Qs) {
+                // |X^T zeta| bounded from above: |Q~| + its distance bound (H_M, TopSum increase in |q|)
+                double err;
+                const double qv = exact_q(a.Qs, a.nqs, a.qs_stride, a.qs_w, base + j, a.xsig[j] * a.ztau[b], a.ebound, &err);
+                q[e] = (fabs(qv) + err) * inv2l;
+            } else {
+                q[e] = a.Q[base + j] * inv2l;
+            }
             be[e] = a.b_is_f64 ? static_cast<const double*>(a.B)[base + j]
                                : (double)static_cast<const float*>(a.B)[base + j];
             if ((im[j >> 5] >> (j & 31)) & 1u) fin |= 1u << e;

@@ -76,6 +76,38 @@ int tc_tile_cols_wide(int N);   // 128-column tiles for N > 256 (more CTAs for a
 size_t tc_scratch_bytes();
 int tc_scratch_counters();
 // B2: optional low part of B (out = A (B + B2)^T); NULL for a single B.
+// One job of a grouped BF16 product: K slices [ka, ka + nkb) of A against
+// [kb, kb + nkb) of B (128-byte slices), written as partial slice `slice`.
+constexpr int kTcMaxJobs = 64;
+struct TcJob {
+    int ka, kb, nkb, slice;
+};
+// out slice jobs[z].slice (at pout + slice * pstride, row stride pld) =
+// A[:, K range of job z] . B[:, K range of job z]^T for every job, in one launch.
+int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, int bn, const TcJob* jobs,
+                 int njobs, float* pout, size_t pstride, int pld, int* err);
+// Exact-splitting certificate product (cert_exact.cu): jobs of the level
+// products, their weights 2^(-beta l) and the bound n E per unit sigma tau.
+struct ExactPlan {
+    int beta, nd, npad, kbs;     // digit bits, digits per value, K padded to 64, 64-wide K slices per digit
+    int njobs;
+    TcJob jobs[kTcMaxJobs];
+    double w[kTcMaxJobs];
+    double ebound;
+};
+// Jobs whose FP32 accumulations are exact; false if they do not fit kTcMaxJobs.
+bool exact_plan(int n, int beta, int nd, ExactPlan* pl);
+// Halves jobs while fewer than two waves of CTAs would run (tiles per job) and
+// the slices fit max_slices.
+void exact_plan_widen(ExactPlan* pl, int tiles, size_t max_slices);
+// Digits of the rows of V (rows x n, row stride ldv) into D (rows x nd*npad BF16)
+// and the row scales 2^e > max |V_r|.
+void exact_digits(cudaStream_t s, const double* V, int rows, int n, size_t ldv, int npad, int nd, int beta,
+                  int reversed, __nv_bfloat16* D, double* scale);
+// Q (m x p) and its entrywise bound E (nullable) from the job partials; w: the
+// jobs' weights (host array of nq values).
+void exact_combine(cudaStream_t s, int m, int p, const float* Qs, int nq, size_t stride, const double* w,
+                   const double* sigma, const double* tau, double ebound, double* Q, double* E);
 int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, const TcGemm& g,
             const GemmScratch* scr);
 
@@ -123,6 +155,15 @@ struct CertArgs {
     double* primal;       // out
     int* support;         // out m x k
     int* jstar;           // out
+    // reduced-precision modes: X^T zeta from the exact-splitting partials
+    // (Qs != NULL) with the entrywise bound xsig_j ztau_b ebound, instead of Q
+    const float* Qs;
+    int nqs;
+    size_t qs_stride;
+    double qs_w[kTcMaxJobs];
+    const double* xsig;
+    const double* ztau;
+    double ebound;
 };
 // zeta = -dl(S), row sums of l and l*(-zeta)   (§4.4 Eq. (batched_dual_candidate_matrix_form))
 void cert_dual_point(cudaStream_t s, const CertArgs& a);

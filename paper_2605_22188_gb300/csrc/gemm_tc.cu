@@ -68,6 +68,8 @@ struct TcArgs {
     float* part;
     int* counters;
     int* err;
+    int njobs;                // > 0: job z = blockIdx.z takes its own K ranges and slice
+    TcJob jobs[kTcMaxJobs];
 };
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -83,11 +85,13 @@ __device__ __forceinline__ float dloss_fast(float s, float y, int kind) {
 }
 
 // Writes columns c0 .. c0+31 of output row r (columns >= N are skipped); ys:
-// the tile's y values staged in shared memory (index c0 - n0 + j).
-__device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, const float (&v)[32], const float* ys) {
+// the tile's y values staged in shared memory (index c0 - n0 + j); zs: the
+// slice of a partial product.
+__device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, const float (&v)[32], const float* ys,
+                                            int zs) {
     if (r >= a.M) return;
     if (a.epi == TC_EPI_PARTIAL) {
-        float* o = a.pout + (size_t)blockIdx.z * a.pstride + (size_t)r * a.pld;
+        float* o = a.pout + (size_t)zs * a.pstride + (size_t)r * a.pld;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
             if (c0 + j < a.N) o[c0 + j] = v[j];
@@ -241,7 +245,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 template <int KIND, int NB>
 __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB,
-                                                   const __grid_constant__ CUtensorMap tmB2, TcArgs a) {
+                                                   const __grid_constant__ CUtensorMap tmB2,
+                                                   const __grid_constant__ TcArgs a) {
     constexpr int STAGES = stages<NB>();
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -254,9 +259,16 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * a.bn;
-    const int kb0 = blockIdx.z * a.kb_per_split;
-    const int kb1 = min(a.nkb, kb0 + a.kb_per_split);
-    const int nloc = kb1 - kb0;
+    // K slices of this CTA: a split of [0, nkb), or the job's own ranges of A and B
+    int ka0, kbb0, nloc, zs;
+    if (a.njobs > 0) {
+        const TcJob& jb = a.jobs[blockIdx.z];
+        ka0 = jb.ka; kbb0 = jb.kb; nloc = jb.nkb; zs = jb.slice;
+    } else {
+        ka0 = kbb0 = blockIdx.z * a.kb_per_split;
+        nloc = min(a.nkb, ka0 + a.kb_per_split) - ka0;
+        zs = blockIdx.z;
+    }
     constexpr int KE = KIND == 0 ? 64 : 32;          // elements per 128-byte row
     const uint32_t stage_bytes = STAGE_A + (uint32_t)NB * a.bn * ROWB;
 
@@ -278,10 +290,10 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u, a.err)) break;
             const uint32_t full = smem_u32(&bars[s]);
             mbar_expect_tx(full, stage_bytes);
-            const int kx = (kb0 + i) * KE;
-            tma_load_2d(smem_u32(sA + s * STAGE_A), &tmA, kx, m0, full);
-            tma_load_2d(smem_u32(sB + s * STAGE_B), &tmB, kx, n0, full);
-            if (NB == 2) tma_load_2d(smem_u32(sB + (STAGES + s) * STAGE_B), &tmB2, kx, n0, full);
+            const int kxa = (ka0 + i) * KE, kxb = (kbb0 + i) * KE;
+            tma_load_2d(smem_u32(sA + s * STAGE_A), &tmA, kxa, m0, full);
+            tma_load_2d(smem_u32(sB + s * STAGE_B), &tmB, kxb, n0, full);
+            if (NB == 2) tma_load_2d(smem_u32(sB + (STAGES + s) * STAGE_B), &tmB2, kxb, n0, full);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -325,7 +337,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             float v[32];
             tmem_ld32(tl + (uint32_t)c, v);
             if (!split) {
-                tc_epilogue(a, row, n0 + c, v, ys + c);
+                tc_epilogue(a, row, n0 + c, v, ys + c, zs);
             } else {
                 float* my = a.part + (((size_t)blockIdx.z * ntile + tile) * BM + quad * 32 + lane) * MAXBN + c;
 #pragma unroll
@@ -353,7 +365,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                         v[q] += x.x; v[q + 1] += x.y; v[q + 2] += x.z; v[q + 3] += x.w;
                     }
                 }
-                tc_epilogue(a, row, n0 + c, v, ys + c);
+                tc_epilogue(a, row, n0 + c, v, ys + c, 0);
             }
             if (threadIdx.x == 0) a.counters[tile] = 0;
         }
@@ -468,6 +480,26 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
         if (nb == 1) k_tc_gemm<1, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb2, a);
         else k_tc_gemm<1, 2><<<grid, NT, smem_bytes<2>(), s>>>(ma, mb, mb2, a);
     }
+    return 0;
+}
+
+int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, int bn, const TcJob* jobs,
+                 int njobs, float* pout, size_t pstride, int pld, int* err) {
+    if (M <= 0 || N <= 0 || njobs <= 0) return 0;
+    if (bn < 16 || bn > MAXBN || bn % 16 != 0 || njobs > kTcMaxJobs) return -4;
+    if (set_smem_attr<0, 1>()) return -5;
+    TcArgs a{};
+    a.M = M; a.N = N; a.bn = bn;
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    a.epi = TC_EPI_PARTIAL;
+    a.pout = pout; a.pstride = pstride; a.pld = pld;
+    a.err = err;
+    a.njobs = njobs;
+    for (int j = 0; j < njobs; ++j) a.jobs[j] = jobs[j];
+    const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
+    const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
+    dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM, njobs);
+    k_tc_gemm<0, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb, a);
     return 0;
 }
 

@@ -60,6 +60,7 @@ _SIGS = {
     "kglm_stats_read": (C.c_int, [P, D, I64, D]),
     "kglm_phase_name": (C.c_char_p, [C.c_int32]),
     "kglm_xtr": (C.c_int, [P, C.c_int32, P, P]),
+    "kglm_xtz": (C.c_int, [P, C.c_int32, P, P, P]),
     "kglm_xtr_noalloc_f32": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P]),
 }
 XTR_NOALLOC_MAX_TILES = 256
@@ -148,6 +149,16 @@ def kglm_push_nodes_dev(ctx, m, in_ptr, in_idx, out_ptr, out_idx, nnz_in, nnz_ou
 def kglm_xtr(ctx, m, R_ptr, G_ptr):
     """G = R X for device buffers (integer addresses) of the context's working type."""
     _check(lib().kglm_xtr(ctx, int(m), P(R_ptr), P(G_ptr)), ctx)
+
+
+def kglm_xtz(ctx, Z, p):
+    """Certificate product Q = Z X (host FP64, Z: m x n) and its entrywise error bound."""
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    m = Z.shape[0]
+    Q = np.empty((m, p))
+    E = np.empty((m, p))
+    _check(lib().kglm_xtz(ctx, int(m), Z.ctypes.data, Q.ctypes.data, E.ctypes.data), ctx)
+    return Q, E
 
 
 def kglm_xtr_noalloc_f32(m, n, p, R_ptr, Xt_ptr, G_ptr, stream=None):
@@ -257,6 +268,9 @@ class Engine:
 
     def evaluate(self, iters, check_every=0):
         return kglm_evaluate(self.ctx, self.m, self.k, iters, check_every)
+
+    def xtz(self, Z):
+        return kglm_xtz(self.ctx, Z, self.p)
 
     def read_batch(self, beta=True, zeta=True):
         return kglm_read_batch(self.ctx, self.m, self.n, self.p, beta, zeta)

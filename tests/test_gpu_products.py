@@ -33,3 +33,74 @@ def test_xtr_matches_fp64_product(prec, m, n, p):
     tol = ((1 + u) ** 2 - 1 + n * 2.0 ** -24) * scale * 1.01 + 1e-30
     assert np.all(np.isfinite(G))
     assert np.all(np.abs(G - ref) <= tol), float(np.max(np.abs(G - ref) / tol))
+
+
+def _exact_products(Z, X, rows, cols):
+    """sum_i Z[b, i] X[i, j] in exact rational arithmetic for the given (b, j)."""
+    from fractions import Fraction
+    out = {}
+    for b in rows:
+        zb = [Fraction(float(v)) for v in Z[b]]
+        for j in cols:
+            out[(b, j)] = sum((zi * Fraction(float(xi)) for zi, xi in zip(zb, X[:, j]) if zi != 0), Fraction(0))
+    return out
+
+
+def _dual_rows(n, rng):
+    """Dual points of assorted scales and structure: Gaussian, tiny, huge, zero,
+    logistic-like in [-1, 1], one nonzero, mixed magnitudes, integers."""
+    Z = np.zeros((9, n))
+    Z[0] = rng.standard_normal(n)
+    Z[1] = 1e-8 * rng.standard_normal(n)
+    Z[2] = 1e6 * rng.standard_normal(n)
+    Z[4] = rng.uniform(-1, 1, n)
+    Z[5, n // 3] = -0.7
+    Z[6] = rng.standard_normal(n) * np.where(np.arange(n) % 2, 1e-9, 1e3)
+    Z[7] = rng.integers(-5, 6, n)
+    Z[8] = np.float32(rng.standard_normal(n)).astype(np.float64)   # FP32-valued, as in the engine
+    return Z
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "tf32"])
+def test_certificate_product_is_within_its_bound(prec):
+    """kglm_xtz: |Q - Z X| <= Qerr entrywise against exact rational sums, and the
+    bound of the reduced modes' exact-splitting product is tiny: at most
+    2^-38 n max|X_j| max|Z_b| (6-bit digits, 7 per value)."""
+    n, p = 300, 24
+    rng = np.random.default_rng(11)
+    X, y, _ = synth.instance(n, p, 3, synth.LSQ, seed=2)
+    Z = _dual_rows(n, rng)
+    with kglm.Engine(X, y, 3, 0.1, 2.0, synth.LSQ, prec=prec, max_batch=16) as eng:
+        Q, E = eng.xtz(Z)
+    ex = _exact_products(Z, X, range(Z.shape[0]), range(p))
+    for (b, j), v in ex.items():
+        d = abs(Q[b, j] - float(v))
+        if prec == "fp64":
+            assert E[b, j] == 0.0
+            assert d <= 1e-12 * (np.abs(Z[b]) @ np.abs(X[:, j])) + 1e-300
+        else:
+            assert d <= E[b, j], (b, j, d, E[b, j])
+            assert E[b, j] <= 2.0 ** -38 * n * 2 * np.max(np.abs(X[:, j])) * 2 * np.max(np.abs(Z[b])) + 1e-300
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_certificate_product_exact_at_the_accumulator_limit(sign):
+    """Constant X and Z whose leading digits are both 64: level 2 of the split
+    sums n 64^2 = 2^24 per job at n = 8192 (two jobs of 4096 samples), the
+    largest integer the planner lets an FP32 accumulation reach.  The result
+    must equal the exact product to within the (tiny) bound: an accumulator
+    that dropped a unit there would miss by 2^-12 relative."""
+    n, p, m = 8192, 16, 4
+    X = np.full((n, p), 0.99999 * sign)
+    X[:, 1::2] = 0.999999999                     # other digit patterns in odd columns
+    y = np.linspace(-1, 1, n)
+    Z = np.full((m, n), -0.99999)
+    Z[1] = 0.999999999
+    Z[2, ::2] = 0.5
+    with kglm.Engine(X, y, 2, 0.1, 2.0, synth.LSQ, prec="bf16", max_batch=m) as eng:
+        Q, E = eng.xtz(Z)
+    ex = _exact_products(Z, X, range(m), range(4))
+    for (b, j), v in ex.items():
+        d = abs(Q[b, j] - float(v))
+        assert d <= E[b, j], (b, j, d, E[b, j])
+        assert E[b, j] <= 1e-7, E[b, j]
