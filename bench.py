@@ -152,7 +152,8 @@ PHASE_KERNEL_SOURCES = {
                      "paper_2605_22188_gb300/csrc/common.cuh"],
     "gemm_xtr": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu"],
     "prox_fista": ["paper_2605_22188_gb300/csrc/prox.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
-    "cert_xtzeta": ["paper_2605_22188_gb300/csrc/gemm_simt.cu"],
+    "cert_xtzeta": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu",
+                    "paper_2605_22188_gb300/csrc/cert_exact.cu"],
     "cert_xb": ["paper_2605_22188_gb300/csrc/gemm_simt.cu"],
     "cert_bound": ["paper_2605_22188_gb300/csrc/cert.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
     "cert_dual_point": ["paper_2605_22188_gb300/csrc/cert.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
@@ -160,13 +161,14 @@ PHASE_KERNEL_SOURCES = {
 }
 
 
-def traffic_for(phase, workload):
-    """DRAM bytes per launch from the committed ncu summary, if its kernel source is unchanged."""
+def traffic_for(phase, workload, prec, nodes):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json) for this
+    workload, product precision and batch size, if the kernel's source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    e = d.get(workload, {}).get(phase)
+    e = d.get("%s/%s/m%d" % (workload, prec, nodes), {}).get(phase)
     if not e or phase not in PHASE_KERNEL_SOURCES:
         return None
     if e.get("source_sha") != source_sha(PHASE_KERNEL_SOURCES[phase]):
@@ -174,7 +176,7 @@ def traffic_for(phase, workload):
     return e.get("dram_bytes_per_launch")
 
 
-def roofline(stats, prec, pk):
+def roofline(stats, prec, pk, workload=WORKLOAD, nodes=1024):
     """Achieved rate of the phase with the largest device time, against its peak."""
     best = None
     for name, s in stats.items():
@@ -194,7 +196,7 @@ def roofline(stats, prec, pk):
         peak = base if prec == "bf16" else base * 1.1 / 2.25
         achieved = work / per_launch_s / 1e12
         return {"kernel": best, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for(best, WORKLOAD),
+                "frac": achieved / peak, "traffic": traffic_for(best, workload, prec, nodes),
                 "peak_note": "%s sustained dense peak, %s" % (prec.upper(), pk["source"]),
                 "launches": s["launches"], "avg_launch_us": per_launch_s * 1e6}
     if best in ("gemm_xv_link", "gemm_xtr", "cert_xb", "cert_xtzeta"):
@@ -206,12 +208,12 @@ def roofline(stats, prec, pk):
             note = "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"
         achieved = work / per_launch_s / 1e12
         return {"kernel": best, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_for(best, WORKLOAD),
+                "frac": achieved / peak, "traffic": traffic_for(best, workload, prec, nodes),
                 "peak_note": note, "launches": s["launches"], "avg_launch_us": per_launch_s * 1e6}
     peak = pk["hbm_gbs"]
     achieved = work / per_launch_s / 1e9
     return {"kernel": best, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic_for(best, WORKLOAD),
+            "frac": achieved / peak, "traffic": traffic_for(best, workload, prec, nodes),
             "peak_note": "HBM copy bandwidth, %s" % pk["source"], "launches": s["launches"],
             "avg_launch_us": per_launch_s * 1e6}
 
@@ -271,7 +273,7 @@ def run_ours(args):
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
     c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
-    m, T = c.get("m", 1024), args.iters
+    m, T = args.nodes or c.get("m", 1024), args.iters
     pk = peaks()
 
     cpu = None
@@ -367,6 +369,10 @@ def run_ours(args):
         eng = eng_keep
         e64.close()
 
+    ttz = None
+    if not args.no_ttz:
+        ttz = time_to_zero_gap(X, y, c, args.prec, stream, m)
+
     if rank != 0:
         eng.close()
         return
@@ -383,16 +389,45 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": units_e / secs_e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": roofline(stats, args.prec, pk),
+        "roofline": roofline(stats, args.prec, pk, args.workload, m),
         "cpu_baseline": cpu,
         "clocks": clocks,
         "fp64_products": fp64,
+        "time_to_zero_gap": ttz,
         "phase_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stats.items() if v["ms"] > 0},
     }
     if fp64:
         line["mixed_over_fp64"] = value / fp64["value"]
     print(json.dumps(line), flush=True)
     eng.close()
+
+
+def time_to_zero_gap(X, y, c, prec, stream, m):
+    """Wall time of a full certified solve (kglm_solve, the hybrid loop of Fig. 1) of the
+    workload's instance in the bench precision and with FP64 products.  Each solve runs
+    once untimed (CUDA-graph capture) and once timed; both must close the gap and agree
+    on the support."""
+    from paper_2605_22188_gb300 import kglm
+    out = {"batch": m, "iters": 200, "check_every": 10}
+    sols = {}
+    for label, pr in (("mixed", prec), ("fp64", "fp64")):
+        with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=pr, max_batch=m,
+                         stream=stream.cuda_stream) as e:
+            e.solve(m, 200, 10, 600.0)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            r = e.solve(m, 200, 10, 600.0)
+            dt = time.perf_counter() - t0
+        sols[label] = r
+        out[label + "_s"] = dt
+        out[label + "_nodes"] = r["nodes"]
+        out[label + "_gap"] = r["gap"]
+        out[label + "_opt"] = r["opt"]
+    out["mixed_products"] = prec
+    out["support"] = sols["mixed"]["support"]
+    out["support_equal"] = sols["mixed"]["support"] == sols["fp64"]["support"]
+    out["fp64_over_mixed_time"] = out["fp64_s"] / out["mixed_s"]
+    return out
 
 
 def cpu_baseline(X, y, c, T, args):
@@ -455,18 +490,20 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "tf32"])
     ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--nodes", type=int, default=0, help="nodes per batch (0: the workload's)")
     ap.add_argument("--loss", default=None, choices=[None, "lsq", "logistic"],
                     help="override the workload's loss (the microbench runs both)")
     ap.add_argument("--cpu-nodes-per-core", type=int, default=150)
     ap.add_argument("--ref-nodes-per-core", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ttz", action="store_true", help="skip the time-to-zero-gap solves")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank, world, local = rank_info()

@@ -240,6 +240,24 @@ kglm_status kglm_stats_enable(kglm_ctx* ctx, int32_t enable);
 kglm_status kglm_stats_read(kglm_ctx* ctx, double* ms, int64_t* launches, double* work);
 const char* kglm_phase_name(int32_t phase);
 
+/* Device bytes kglm_create allocates for *desc (App. E.4 sizes the batch from
+ * the memory per node; admission control needs the whole footprint before
+ * any allocation).  Host-only arithmetic, no CUDA call.  Not included: one
+ * max_batch x p FP64 buffer that kglm_push_nodes with warm_B, and one that
+ * kglm_xtz, allocate on first use.  KGLM_EINVAL for a desc kglm_create would
+ * reject on its sizes, ranges or enums. */
+kglm_status kglm_estimate_bytes(const kglm_desc* desc, int64_t* bytes);
+
+/* Device bytes the context holds (what kglm_estimate_bytes predicted, plus
+ * the first-use buffers above once allocated). */
+kglm_status kglm_device_bytes(const kglm_ctx* ctx, int64_t* bytes);
+
+/* Automatic batch size of App. E.4: the largest power of two m <= cap such
+ * that the instance with max_batch = m (and desc's other fields; pool_slots 0
+ * scales with m) fits in `budget` device bytes.  KGLM_ENOMEM if even m = 1
+ * does not fit; KGLM_EINVAL for bad arguments. */
+kglm_status kglm_suggest_batch(const kglm_desc* desc, int64_t budget, int32_t cap, int32_t* batch);
+
 /* Message of the last failed call on ctx (never NULL). */
 const char* kglm_last_error(const kglm_ctx* ctx);
 

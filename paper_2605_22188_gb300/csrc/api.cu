@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <exception>
 #include <map>
@@ -43,8 +44,7 @@ struct kglm_ctx {
     double *lb_best = nullptr, *primal_last = nullptr, *ub = nullptr, *beta_re = nullptr;
     uint8_t* pruned = nullptr;
     int *d_in_ptr = nullptr, *d_out_ptr = nullptr, *d_slot = nullptr, *d_rows = nullptr, *d_slots = nullptr;
-    int *d_in_idx = nullptr, *d_out_idx = nullptr;
-    size_t idx_cap = 0;
+    int *d_in_idx = nullptr, *d_out_idx = nullptr;   // CSR index staging: mcap*k and mcap*p entries
     double* d_warmB = nullptr;
     void* pool = nullptr;
     int pool_slots = 0;
@@ -140,10 +140,12 @@ void* dalloc(kglm_ctx* c, size_t bytes) {
     if (c->d.hbm_budget > 0 && (int64_t)(c->bytes + bytes) > c->d.hbm_budget)
         throw Fail{KGLM_ENOMEM, "over the HBM budget of the context"};
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    // stream-ordered: no device-wide synchronization when contexts come and go
+    // while others run (the serving loop)
+    cudaError_t e = cudaMallocAsync(&p, bytes, c->st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        throw Fail{KGLM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        throw Fail{KGLM_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
     }
     c->allocs.push_back(p);
     c->bytes += bytes;
@@ -556,14 +558,7 @@ void validate_nodes(const kglm_ctx* c, int m, const int32_t* in_ptr, const int32
 void push_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx, const int32_t* out_ptr,
                const int32_t* out_idx, const int32_t* warm_slot, const double* warm_B) {
     validate_nodes(c, m, in_ptr, in_idx, out_ptr, out_idx, warm_slot);
-    const size_t nnz_in = in_ptr[m], nnz_out = out_ptr[m];
-    const size_t need = std::max(nnz_in, nnz_out);
-    if (need > c->idx_cap) {
-        size_t cap = std::max(need, (size_t)c->mcap * (size_t)(c->k + 8));
-        c->d_in_idx = dalloc_t<int>(c, cap);
-        c->d_out_idx = dalloc_t<int>(c, cap);
-        c->idx_cap = cap;
-    }
+    const size_t nnz_in = in_ptr[m], nnz_out = out_ptr[m];   // <= m k and <= m p (validated)
     if (!c->d_warmB && warm_B) c->d_warmB = dalloc_t<double>(c, (size_t)c->mcap * c->p);
     const int* slot = warm_slot ? c->d_slot : nullptr;
     const double* wb = warm_B ? c->d_warmB : nullptr;
@@ -667,7 +662,254 @@ void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, 
     if (branch_j) memcpy(branch_j, c->h_jstar.data(), sizeof(int) * m);
 }
 
+// Device bytes kglm_create allocates for desc: the same allocations, in the
+// same order (the exact-splitting digits are skipped when they would pass the
+// budget), so that admission control can decide before any allocation.
+// Excluded: the buffers that kglm_push_nodes with warm_B and kglm_xtz
+// allocate on first use (one max_batch x p FP64 array each).
+size_t footprint(const kglm_desc& d) {
+    size_t est = 0;
+    auto add = [&](size_t b) { est += b == 0 ? 16 : b; };
+    const size_t n = (size_t)d.n, p = (size_t)d.p, mc = (size_t)d.max_batch, k = (size_t)d.k;
+    const bool f64 = d.prec == KGLM_FP64, tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32;
+    const size_t ws = f64 ? 8 : 4, W = (p + 31) / 32;
+    add(8 * n * p); add(8 * n * p); add(8 * n);
+    if (!f64) { add(4 * n * p); add(4 * n * p); add(4 * n); }
+    add(gemm_scratch_bytes(1)); add(4 * (size_t)gemm_scratch_counters(1));
+    if (!f64) { add(gemm_scratch_bytes(0)); add(4 * (size_t)gemm_scratch_counters(0)); }
+    bool tcerr = false;
+    if (tc) {
+        const size_t es = d.prec == KGLM_BF16 ? 2 : 4;
+        const size_t pK = (p + 7) / 8 * 8, nK = (n + 7) / 8 * 8;
+        add(n * pK * es); add(n * pK * es); add(p * nK * es);
+        add(mc * pK * es); add(mc * nK * es);
+        add(tc_scratch_bytes()); add(4 * (size_t)tc_scratch_counters());
+        add(4 * 4 * mc * p);   // gsplit_max = 4 slices of X^T R
+        add(4);
+        tcerr = true;
+    }
+    add(8 * p * p); add(8 * p);
+    if (!(d.lipschitz > 0)) { add(8 * p); add(8 * p); }
+    add(4 * mc * W); add(4 * mc * W); add(4 * mc); add(4 * mc);
+    add(mc * p * ws); add(mc * p * ws); add(mc * p * ws);
+    add(mc * n * std::max(ws, (size_t)4));
+    add(8 * mc); add(4 * mc); add(4 * mc);
+    add(8 * mc * n); add(8 * mc * p);
+    for (int t = 0; t < 7; ++t) add(8 * mc);
+    add(8 * mc * k); add(4 * mc * k); add(4 * mc); add(mc);
+    add(4 * (mc + 1)); add(4 * (mc + 1)); add(4 * mc); add(4 * mc); add(4 * mc); add(4);
+    const size_t slots = d.pool_slots > 0 ? (size_t)d.pool_slots : 4 * mc;
+    add(slots * p * ws);
+    add(4 * mc * k); add(4 * mc * p);
+    ExactPlan x{};
+    if (!f64 && exact_plan((int)n, 6, 7, &x)) {
+        const size_t K2 = (size_t)x.nd * x.npad;
+        const size_t need = 2 * K2 * (p + mc) + 8 * (p + mc) + 4 * (size_t)x.njobs * mc * p + 64;
+        if (d.hbm_budget <= 0 || (int64_t)(est + need) <= d.hbm_budget) {
+            add(2 * p * K2); add(8 * p); add(2 * mc * K2); add(8 * mc); add(4 * (size_t)x.njobs * mc * p);
+            if (!tcerr) add(4);
+        }
+    }
+    return est;
+}
+
+// The hybrid CPU-GPU loop of Fig. 1 on one context: best-bound host queue,
+// batches of up to `batch` open nodes evaluated on the device, incumbent from
+// the batched rounding and re-optimization, pruning and branching on j*.
+// Stops when the queue is empty, the time limit passes or *cancel is set
+// (checked between batches).
+struct SolveOut {
+    double opt = INFINITY, gap = INFINITY;
+    std::vector<int> support;
+    std::vector<double> beta;
+    int64_t nodes = 0, batches = 0;
+    bool cancelled = false;
+};
+
+void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
+                const std::atomic<int>* cancel, SolveOut& out) {
+    REQ(batch >= 1 && batch <= ctx->mcap, "batch must be in [1, max_batch]");
+    REQ(iters >= 1, "iters must be >= 1");
+    struct Open {
+        double lb;
+        int64_t id;
+        std::vector<int> J0, J1;
+        int slot;
+    };
+    struct Cmp {
+        bool operator()(const Open* a, const Open* b) const {
+            return a->lb > b->lb || (a->lb == b->lb && a->id > b->id);
+        }
+    };
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed = [&] {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    std::priority_queue<Open*, std::vector<Open*>, Cmp> open;
+    std::vector<int> slot_ref(ctx->pool_slots, 0), free_slots;
+    for (int s = ctx->pool_slots - 1; s >= 0; --s) free_slots.push_back(s);
+    auto release = [&](int s) {
+        if (s >= 0 && --slot_ref[s] == 0) free_slots.push_back(s);
+    };
+    int64_t next_id = 0, n_nodes = 0, n_batches = 0;
+    open.push(new Open{-INFINITY, next_id++, {}, {}, -1});
+    double ub = INFINITY;
+    std::vector<int> best_sup(ctx->k, -1);
+    std::vector<double> best_coef(ctx->k, 0.0);
+    const int k = ctx->k;
+    std::vector<int> in_ptr, in_idx, out_ptr, out_idx, wslot;
+    std::vector<double> lb(batch), ubc(batch), bre((size_t)batch * k);
+    std::vector<int> sup((size_t)batch * k), bj(batch);
+    std::vector<Open*> cur;
+    try {
+        while (!open.empty()) {
+            if (time_limit_s > 0 && elapsed() > time_limit_s) break;
+            if (cancel && cancel->load(std::memory_order_relaxed)) {
+                out.cancelled = true;
+                break;
+            }
+            cur.clear();
+            const double dl = delta_of(ctx, ub);
+            while (!open.empty() && (int)cur.size() < batch) {
+                Open* o = open.top();
+                open.pop();
+                if (o->lb >= ub - dl) {
+                    release(o->slot);
+                    delete o;
+                    continue;
+                }
+                cur.push_back(o);
+            }
+            if (cur.empty()) break;
+            const int m = (int)cur.size();
+            in_ptr.assign(1, 0);
+            out_ptr.assign(1, 0);
+            in_idx.clear();
+            out_idx.clear();
+            wslot.resize(m);
+            for (int b = 0; b < m; ++b) {
+                in_idx.insert(in_idx.end(), cur[b]->J1.begin(), cur[b]->J1.end());
+                out_idx.insert(out_idx.end(), cur[b]->J0.begin(), cur[b]->J0.end());
+                in_ptr.push_back((int)in_idx.size());
+                out_ptr.push_back((int)out_idx.size());
+                wslot[b] = cur[b]->slot;
+            }
+            push_impl(ctx, m, in_ptr.data(), in_idx.data(), out_ptr.data(), out_idx.data(), wslot.data(), nullptr);
+            ctx->ub_inc = ub;
+            evaluate_impl(ctx, iters, check_every);
+            evaluate_outputs(ctx, lb.data(), nullptr, ubc.data(), sup.data(), bre.data(), bj.data(), nullptr);
+            ctx->evaluated = true;
+            n_nodes += m;
+            ++n_batches;
+            for (int b = 0; b < m; ++b) {
+                release(cur[b]->slot);
+                if (ubc[b] < ub) {
+                    ub = ubc[b];
+                    std::copy(sup.begin() + (size_t)b * k, sup.begin() + (size_t)(b + 1) * k, best_sup.begin());
+                    std::copy(bre.begin() + (size_t)b * k, bre.begin() + (size_t)(b + 1) * k, best_coef.begin());
+                }
+            }
+            const double dl2 = delta_of(ctx, ub);
+            std::vector<int> rows, slots;
+            for (int b = 0; b < m; ++b) {
+                Open* o = cur[b];
+                const double lbb = std::max(lb[b], o->lb);
+                if (lbb >= ub - dl2 || bj[b] < 0 || ubc[b] - lbb <= dl2) {
+                    delete o;
+                    continue;
+                }
+                const int j = bj[b];
+                int s = -1;
+                if (!free_slots.empty()) {
+                    s = free_slots.back();
+                    free_slots.pop_back();
+                    slot_ref[s] = 2;
+                    rows.push_back(b);
+                    slots.push_back(s);
+                }
+                Open* c0 = new Open{lbb, next_id++, o->J0, o->J1, s};
+                c0->J0.push_back(j);
+                Open* c1 = new Open{lbb, next_id++, o->J0, o->J1, s};
+                c1->J1.push_back(j);
+                open.push(c0);
+                open.push(c1);
+                delete o;
+            }
+            if (!rows.empty()) {
+                CK(cudaMemcpyAsync(ctx->d_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, ctx->st));
+                CK(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, ctx->st));
+                {
+                    Scope sc(ctx, PH_SMALL, 1, 2.0 * (ctx->f64 ? 8 : 4) * (double)rows.size() * ctx->p);
+                    pool_store(ctx->st, (int)rows.size(), ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B,
+                               ctx->pool);
+                    check_launch();
+                }
+                sync(ctx);
+            }
+        }
+    } catch (...) {
+        while (!open.empty()) { delete open.top(); open.pop(); }
+        throw;
+    }
+    // the reduced-precision modes keep an upper bound of each incumbent's
+    // objective during the search; report the exact FP64 objective
+    if (!ctx->f64 && isfinite(ub)) {
+        std::vector<int> Sv;
+        std::vector<double> bv;
+        for (int r = 0; r < k; ++r)
+            if (best_sup[r] >= 0) { Sv.push_back(best_sup[r]); bv.push_back(best_coef[r]); }
+        const int ks = (int)Sv.size();
+        if (ks > 0) {
+            CK(cudaMemcpyAsync(ctx->d_rows, Sv.data(), sizeof(int) * ks, cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(ctx->beta_re, bv.data(), sizeof(double) * ks, cudaMemcpyHostToDevice, ctx->st));
+            objective64_launch(ctx->st, ctx->Xt64, ctx->y64, ctx->n, ctx->kind, ctx->lam2, ctx->d_rows,
+                               ctx->beta_re, ks, ctx->ub);
+            check_launch();
+            double exact = ub;
+            CK(cudaMemcpyAsync(&exact, ctx->ub, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            sync(ctx);
+            ub = exact;
+        }
+    }
+    double open_lb = INFINITY;
+    while (!open.empty()) {
+        open_lb = std::min(open_lb, open.top()->lb);
+        delete open.top();
+        open.pop();
+    }
+    const double glb = std::min(open_lb, ub);
+    out.opt = ub;
+    out.gap = isfinite(ub) ? (ub - glb) / fmax(1.0, fabs(ub)) : INFINITY;
+    out.nodes = n_nodes;
+    out.batches = n_batches;
+    out.support = best_sup;
+    out.beta.assign(ctx->p, 0.0);
+    for (int r = 0; r < k; ++r)
+        if (best_sup[r] >= 0) out.beta[best_sup[r]] = best_coef[r];
+}
+
 }  // namespace
+
+namespace kglm {
+
+size_t device_footprint(const kglm_desc& d) { return footprint(d); }
+
+kglm_status solve_cancellable(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
+                              const std::atomic<int>* cancel, SolveResult* r) {
+    if (!ctx || !r) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        SolveOut o;
+        solve_impl(ctx, batch, iters, check_every, time_limit_s, cancel, o);
+        r->opt = o.opt;
+        r->gap = o.gap;
+        r->support = o.support;
+        r->nodes = o.nodes;
+        r->batches = o.batches;
+        r->cancelled = o.cancelled;
+    });
+}
+
+}  // namespace kglm
 
 extern "C" {
 
@@ -684,7 +926,9 @@ void kglm_destroy(kglm_ctx* ctx) {
     destroy_graphs(ctx);
     for (auto& r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
-    for (void* p : ctx->allocs) cudaFree(p);
+    for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    cudaGetLastError();
     if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
 }
@@ -842,6 +1086,8 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->d_err = dalloc_t<int>(c, 1);
         c->pool_slots = d.pool_slots > 0 ? d.pool_slots : 4 * d.max_batch;
         c->pool = dalloc(c, (size_t)c->pool_slots * p * ws);
+        c->d_in_idx = dalloc_t<int>(c, mc * c->k);
+        c->d_out_idx = dalloc_t<int>(c, mc * p);
         // reduced-precision modes: digits of X for the exact certificate product
         // (6-bit digits, 7 per value), when the jobs and the HBM budget allow
         if (!c->f64 && exact_plan((int)n, 6, 7, &c->xplan)) {
@@ -1093,163 +1339,60 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
                        int64_t* batches) {
     if (!ctx) return KGLM_EINVAL;
     return guarded(ctx, [&] {
-        REQ(batch >= 1 && batch <= ctx->mcap, "batch must be in [1, max_batch]");
-        REQ(iters >= 1, "iters must be >= 1");
-        struct Open {
-            double lb;
-            int64_t id;
-            std::vector<int> J0, J1;
-            int slot;
-        };
-        struct Cmp {
-            bool operator()(const Open* a, const Open* b) const {
-                return a->lb > b->lb || (a->lb == b->lb && a->id > b->id);
-            }
-        };
-        const auto t0 = std::chrono::steady_clock::now();
-        auto elapsed = [&] {
-            return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        };
-        std::priority_queue<Open*, std::vector<Open*>, Cmp> open;
-        std::vector<int> slot_ref(ctx->pool_slots, 0), free_slots;
-        for (int s = ctx->pool_slots - 1; s >= 0; --s) free_slots.push_back(s);
-        auto release = [&](int s) {
-            if (s >= 0 && --slot_ref[s] == 0) free_slots.push_back(s);
-        };
-        int64_t next_id = 0, n_nodes = 0, n_batches = 0;
-        open.push(new Open{-INFINITY, next_id++, {}, {}, -1});
-        double ub = INFINITY;
-        std::vector<int> best_sup(ctx->k, -1);
-        std::vector<double> best_coef(ctx->k, 0.0);
-        const int k = ctx->k;
-        std::vector<int> in_ptr, in_idx, out_ptr, out_idx, wslot;
-        std::vector<double> lb(batch), ubc(batch), bre((size_t)batch * k);
-        std::vector<int> sup((size_t)batch * k), bj(batch);
-        std::vector<Open*> cur;
-        try {
-            while (!open.empty()) {
-                if (time_limit_s > 0 && elapsed() > time_limit_s) break;
-                cur.clear();
-                const double dl = delta_of(ctx, ub);
-                while (!open.empty() && (int)cur.size() < batch) {
-                    Open* o = open.top();
-                    open.pop();
-                    if (o->lb >= ub - dl) {
-                        release(o->slot);
-                        delete o;
-                        continue;
-                    }
-                    cur.push_back(o);
-                }
-                if (cur.empty()) break;
-                const int m = (int)cur.size();
-                in_ptr.assign(1, 0);
-                out_ptr.assign(1, 0);
-                in_idx.clear();
-                out_idx.clear();
-                wslot.resize(m);
-                for (int b = 0; b < m; ++b) {
-                    in_idx.insert(in_idx.end(), cur[b]->J1.begin(), cur[b]->J1.end());
-                    out_idx.insert(out_idx.end(), cur[b]->J0.begin(), cur[b]->J0.end());
-                    in_ptr.push_back((int)in_idx.size());
-                    out_ptr.push_back((int)out_idx.size());
-                    wslot[b] = cur[b]->slot;
-                }
-                push_impl(ctx, m, in_ptr.data(), in_idx.data(), out_ptr.data(), out_idx.data(), wslot.data(), nullptr);
-                ctx->ub_inc = ub;
-                evaluate_impl(ctx, iters, check_every);
-                evaluate_outputs(ctx, lb.data(), nullptr, ubc.data(), sup.data(), bre.data(), bj.data(), nullptr);
-                ctx->evaluated = true;
-                n_nodes += m;
-                ++n_batches;
-                for (int b = 0; b < m; ++b) {
-                    release(cur[b]->slot);
-                    if (ubc[b] < ub) {
-                        ub = ubc[b];
-                        std::copy(sup.begin() + (size_t)b * k, sup.begin() + (size_t)(b + 1) * k, best_sup.begin());
-                        std::copy(bre.begin() + (size_t)b * k, bre.begin() + (size_t)(b + 1) * k, best_coef.begin());
-                    }
-                }
-                const double dl2 = delta_of(ctx, ub);
-                std::vector<int> rows, slots;
-                for (int b = 0; b < m; ++b) {
-                    Open* o = cur[b];
-                    const double lbb = std::max(lb[b], o->lb);
-                    if (lbb >= ub - dl2 || bj[b] < 0 || ubc[b] - lbb <= dl2) {
-                        delete o;
-                        continue;
-                    }
-                    const int j = bj[b];
-                    int s = -1;
-                    if (!free_slots.empty()) {
-                        s = free_slots.back();
-                        free_slots.pop_back();
-                        slot_ref[s] = 2;
-                        rows.push_back(b);
-                        slots.push_back(s);
-                    }
-                    Open* c0 = new Open{lbb, next_id++, o->J0, o->J1, s};
-                    c0->J0.push_back(j);
-                    Open* c1 = new Open{lbb, next_id++, o->J0, o->J1, s};
-                    c1->J1.push_back(j);
-                    open.push(c0);
-                    open.push(c1);
-                    delete o;
-                }
-                if (!rows.empty()) {
-                    CK(cudaMemcpyAsync(ctx->d_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, ctx->st));
-                    CK(cudaMemcpyAsync(ctx->d_slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice, ctx->st));
-                    {
-                        Scope sc(ctx, PH_SMALL, 1, 2.0 * (ctx->f64 ? 8 : 4) * (double)rows.size() * ctx->p);
-                        pool_store(ctx->st, (int)rows.size(), ctx->p, ctx->f64, ctx->d_rows, ctx->d_slots, ctx->B,
-                                   ctx->pool);
-                        check_launch();
-                    }
-                    sync(ctx);
-                }
-            }
-        } catch (...) {
-            while (!open.empty()) { delete open.top(); open.pop(); }
-            throw;
-        }
-        // the reduced-precision modes keep an upper bound of each incumbent's
-        // objective during the search; report the exact FP64 objective
-        if (!ctx->f64 && isfinite(ub)) {
-            std::vector<int> Sv;
-            std::vector<double> bv;
-            for (int r = 0; r < k; ++r)
-                if (best_sup[r] >= 0) { Sv.push_back(best_sup[r]); bv.push_back(best_coef[r]); }
-            const int ks = (int)Sv.size();
-            if (ks > 0) {
-                CK(cudaMemcpyAsync(ctx->d_rows, Sv.data(), sizeof(int) * ks, cudaMemcpyHostToDevice, ctx->st));
-                CK(cudaMemcpyAsync(ctx->beta_re, bv.data(), sizeof(double) * ks, cudaMemcpyHostToDevice, ctx->st));
-                objective64_launch(ctx->st, ctx->Xt64, ctx->y64, ctx->n, ctx->kind, ctx->lam2, ctx->d_rows,
-                                   ctx->beta_re, ks, ctx->ub);
-                check_launch();
-                double exact = ub;
-                CK(cudaMemcpyAsync(&exact, ctx->ub, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-                sync(ctx);
-                ub = exact;
-            }
-        }
-        double open_lb = INFINITY;
-        while (!open.empty()) {
-            open_lb = std::min(open_lb, open.top()->lb);
-            delete open.top();
-            open.pop();
-        }
-        const double glb = std::min(open_lb, ub);
-        if (opt) *opt = ub;
-        if (gap) *gap = isfinite(ub) ? (ub - glb) / fmax(1.0, fabs(ub)) : INFINITY;
-        if (nodes) *nodes = n_nodes;
-        if (batches) *batches = n_batches;
-        if (opt_support) std::copy(best_sup.begin(), best_sup.end(), opt_support);
-        if (opt_beta) {
-            std::fill(opt_beta, opt_beta + ctx->p, 0.0);
-            for (int r = 0; r < k; ++r)
-                if (best_sup[r] >= 0) opt_beta[best_sup[r]] = best_coef[r];
-        }
+        SolveOut o;
+        solve_impl(ctx, batch, iters, check_every, time_limit_s, nullptr, o);
+        if (opt) *opt = o.opt;
+        if (gap) *gap = o.gap;
+        if (nodes) *nodes = o.nodes;
+        if (batches) *batches = o.batches;
+        if (opt_support) std::copy(o.support.begin(), o.support.end(), opt_support);
+        if (opt_beta) std::copy(o.beta.begin(), o.beta.end(), opt_beta);
     });
+}
+
+
+// Checks of kglm_create that need no data (sizes, ranges, enums).
+static kglm_status check_desc(const kglm_desc* d) {
+    if (!d) return KGLM_EINVAL;
+    if (!(d->n > 0 && d->p > 0 && d->n < (1LL << 31) && d->p < (1LL << 31))) return KGLM_EINVAL;
+    if (!(d->k >= 1 && d->k <= KGLM_MAX_K && d->k <= d->p)) return KGLM_EINVAL;
+    if (!(d->lambda2 > 0 && d->M > 0)) return KGLM_EINVAL;
+    if (d->loss != KGLM_LSQ && d->loss != KGLM_LOGISTIC) return KGLM_EINVAL;
+    if (d->prec < KGLM_FP64 || d->prec > KGLM_TF32) return KGLM_EINVAL;
+    if (d->max_batch < 1) return KGLM_EINVAL;
+    if (d->p > (d->prec == KGLM_FP64 ? 4096 : 8192)) return KGLM_EINVAL;
+    return KGLM_OK;
+}
+
+kglm_status kglm_estimate_bytes(const kglm_desc* desc, int64_t* bytes) {
+    if (!bytes) return KGLM_EINVAL;
+    const kglm_status st = check_desc(desc);
+    if (st != KGLM_OK) return st;
+    *bytes = (int64_t)footprint(*desc);
+    return KGLM_OK;
+}
+
+kglm_status kglm_device_bytes(const kglm_ctx* ctx, int64_t* bytes) {
+    if (!ctx || !bytes) return KGLM_EINVAL;
+    *bytes = (int64_t)ctx->bytes;
+    return KGLM_OK;
+}
+
+kglm_status kglm_suggest_batch(const kglm_desc* desc, int64_t budget, int32_t cap, int32_t* batch) {
+    if (!batch || budget <= 0 || cap < 1) return KGLM_EINVAL;
+    kglm_desc d = *desc;
+    d.max_batch = 1;
+    const kglm_status st = check_desc(&d);
+    if (st != KGLM_OK) return st;
+    if ((int64_t)footprint(d) > budget) return KGLM_ENOMEM;
+    int32_t best = 1;
+    for (int64_t m = 2; m <= cap && m <= (1 << 20); m *= 2) {
+        d.max_batch = (int32_t)m;
+        if ((int64_t)footprint(d) > budget) break;
+        best = (int32_t)m;
+    }
+    *batch = best;
+    return KGLM_OK;
 }
 
 }  // extern "C"

@@ -6,6 +6,11 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <vector>
+
+#include "kglm.h"
+
 namespace kglm {
 
 // Split-K scratch of the CUDA-core GEMMs: partial tiles and per-tile arrival
@@ -218,5 +223,18 @@ void check_update(cudaStream_t s, int m, const double* lb_now, const double* pri
                   double* primal_last, int* active, int* iters_done, int it, double ub_thr, double gap_rtol);
 void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count);
 void convert_to_f64(cudaStream_t s, const void* in, int is_f64, double* out, size_t count);
+
+// ---- host side shared by the C ABI and the serving loop (api.cu)
+// Device bytes kglm_create allocates for desc (see kglm_estimate_bytes).
+size_t device_footprint(const kglm_desc& d);
+struct SolveResult {
+    double opt = 0, gap = 0;
+    std::vector<int> support;
+    int64_t nodes = 0, batches = 0;
+    bool cancelled = false;
+};
+// kglm_solve that also stops (between batches) once *cancel is non-zero.
+kglm_status solve_cancellable(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
+                              const std::atomic<int>* cancel, SolveResult* r);
 
 }  // namespace kglm

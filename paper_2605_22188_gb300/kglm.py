@@ -62,6 +62,9 @@ _SIGS = {
     "kglm_xtr": (C.c_int, [P, C.c_int32, P, P]),
     "kglm_xtz": (C.c_int, [P, C.c_int32, P, P, P]),
     "kglm_xtr_noalloc_f32": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P]),
+    "kglm_estimate_bytes": (C.c_int, [C.POINTER(kglm_desc), I64]),
+    "kglm_device_bytes": (C.c_int, [P, I64]),
+    "kglm_suggest_batch": (C.c_int, [C.POINTER(kglm_desc), C.c_int64, C.c_int32, C.POINTER(C.c_int32)]),
 }
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
@@ -113,14 +116,45 @@ def kglm_version():
     return lib().kglm_version().decode()
 
 
+def make_desc(n, p, k, lambda2, M, loss, prec="fp64", max_batch=1024, lipschitz=0.0, gap_tol=0.0,
+              restart=True, pool_slots=0, hbm_budget=0):
+    return kglm_desc(n=int(n), p=int(p), k=int(k), loss=int(loss), prec=PREC.get(prec, prec),
+                     restart=int(bool(restart)), lambda2=float(lambda2), M=float(M), lipschitz=float(lipschitz),
+                     gap_tol=float(gap_tol), max_batch=int(max_batch), pool_slots=int(pool_slots),
+                     hbm_budget=int(hbm_budget))
+
+
+def kglm_estimate_bytes(desc):
+    """Device bytes kglm_create would allocate for a kglm_desc (host arithmetic only)."""
+    b = C.c_int64()
+    st = lib().kglm_estimate_bytes(C.byref(desc), C.byref(b))
+    if st != KGLM_OK:
+        raise KglmError(st, "kglm_estimate_bytes: desc rejected")
+    return b.value
+
+
+def kglm_device_bytes(ctx):
+    b = C.c_int64()
+    _check(lib().kglm_device_bytes(ctx, C.byref(b)), ctx)
+    return b.value
+
+
+def kglm_suggest_batch(desc, budget, cap=1 << 16):
+    """Largest power-of-two batch <= cap whose instance fits in `budget` device bytes (App. E.4)."""
+    m = C.c_int32()
+    st = lib().kglm_suggest_batch(C.byref(desc), int(budget), int(cap), C.byref(m))
+    if st != KGLM_OK:
+        raise KglmError(st, "kglm_suggest_batch: no batch fits %d bytes" % budget if st == KGLM_ENOMEM
+                        else "kglm_suggest_batch: bad arguments")
+    return m.value
+
+
 def kglm_create(X, y, k, lambda2, M, loss, prec="fp64", max_batch=1024, lipschitz=0.0, gap_tol=0.0,
                 restart=True, pool_slots=0, hbm_budget=0, stream=None):
     X = _f64(X)
     n, p = X.shape
     y = _f64(y, (n,))
-    d = kglm_desc(n=n, p=p, k=int(k), loss=int(loss), prec=PREC.get(prec, prec), restart=int(bool(restart)),
-                  lambda2=float(lambda2), M=float(M), lipschitz=float(lipschitz), gap_tol=float(gap_tol),
-                  max_batch=int(max_batch), pool_slots=int(pool_slots), hbm_budget=int(hbm_budget))
+    d = make_desc(n, p, k, lambda2, M, loss, prec, max_batch, lipschitz, gap_tol, restart, pool_slots, hbm_budget)
     out = P()
     st = lib().kglm_create(C.byref(d), _ptr(X, D), _ptr(y, D), P(stream) if stream else None, C.byref(out))
     _check(st, None)
@@ -286,6 +320,9 @@ class Engine:
 
     def branch(self, ub):
         return kglm_branch(self.ctx, self.m, ub)
+
+    def device_bytes(self):
+        return kglm_device_bytes(self.ctx)
 
     def solve(self, batch, iters, check_every=10, time_limit=0.0):
         return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit)

@@ -77,3 +77,39 @@ def test_null_context_calls(lib):
     assert lib.kglm_push_nodes(None, 1, None, None, None, None, None, None) == kglm.KGLM_EINVAL
     assert lib.kglm_evaluate(None, 1, 0, None, None, None, None, None, None, None) == kglm.KGLM_EINVAL
     lib.kglm_destroy(None)
+
+
+def test_estimate_bytes_grows_with_the_batch_and_counts_the_instance(lib):
+    """The footprint is host arithmetic: it needs no GPU.  It must grow with the
+    batch capacity and cover at least the FP64 copies of X and X^T and the
+    batch's m x n FP64 dual points."""
+    n, p = 2000, 200
+    prev = 0
+    for m in (1, 64, 1024, 4096):
+        for prec in ("fp64", "fp32", "bf16", "tf32"):
+            b = kglm.kglm_estimate_bytes(kglm.make_desc(n, p, 10, 1e-2, 2.0, kglm.LOGISTIC, prec, m))
+            assert b >= 2 * 8 * n * p + 8 * m * n
+        b64 = kglm.kglm_estimate_bytes(kglm.make_desc(n, p, 10, 1e-2, 2.0, kglm.LOGISTIC, "fp64", m))
+        assert b64 > prev
+        prev = b64
+
+
+def test_suggest_batch_is_the_largest_fitting_power_of_two(lib):
+    """App. E.4: the batch is the largest power of two whose instance fits the budget."""
+    d = kglm.make_desc(5000, 1000, 15, 1e-3, 2.0, kglm.LSQ, "bf16", 1)
+    for budget in (1 << 30, 1 << 32, 1 << 34):
+        m = kglm.kglm_suggest_batch(d, budget, cap=1 << 16)
+        assert m >= 1 and (m & (m - 1)) == 0
+        d.max_batch = m
+        assert kglm.kglm_estimate_bytes(d) <= budget
+        if m < (1 << 16):
+            d.max_batch = 2 * m
+            assert kglm.kglm_estimate_bytes(d) > budget
+        d.max_batch = 1
+    with pytest.raises(kglm.KglmError) as ei:
+        kglm.kglm_suggest_batch(d, 1 << 20)          # X alone needs 80 MB
+    assert ei.value.status == kglm.KGLM_ENOMEM
+    bad = kglm.make_desc(5000, 1000, 0, 1e-3, 2.0, kglm.LSQ, "bf16", 1)
+    with pytest.raises(kglm.KglmError) as ei:
+        kglm.kglm_estimate_bytes(bad)
+    assert ei.value.status == kglm.KGLM_EINVAL

@@ -1,0 +1,175 @@
+"""GPU parity at the full workload sizes, in the launch configuration bench.py times.
+
+The oracle cannot run thousands of nodes per test, so each case checks
+
+* on a sample of nodes (the special nodes of ``make_batch`` plus random ones):
+  the bound against the oracle's Psi_N at the GPU's own dual point (FP64
+  certificate arithmetic: never above it, within 1e-6 relative in the reduced
+  modes), the rounding support and branching index decided by the oracle on the
+  GPU's iterate (bit-exact), and the re-optimized objective against v(S) from
+  library routines (LAPACK / BVLS for least squares, L-BFGS-B for logistic);
+* on every node, properties that hold at any size: weak duality
+  LB_b <= UB_b = v(S_b) (S_b is consistent with node b, so v(S_b) bounds the
+  node's optimum, and the engine's UB is an upper estimate of v(S_b)),
+  LB_b <= Phi_b where the primal is finite, supports of size k with J1
+  inside and J0 outside, and j*_b free (or -1 exactly for leaves).
+
+Workloads (sizes and recipes of the engine's configurations):
+c2 logistic n=2000 p=200 k=10 m=1024 T=50 FP32 products (the bench line);
+c3 least squares n=5000 p=1000 k=15 rho=0.9 m=4096 T=50 BF16 products;
+c4 n=10000 p=2000 k=20 m=8192 T=50 BF16 products, both losses.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import node as on
+from oracle import reopt as ro
+from paper_2605_22188_gb300 import kglm, synth
+
+pytestmark = pytest.mark.gpu
+
+CERT_RTOL_REDUCED = 1e-6
+OBJ_RTOL_REDUCED = 2e-6
+
+
+def _v_exact(X, y, S, lam2, M, kind):
+    if kind == synth.LSQ:
+        return ro._v_lsq_exact(X, y, S, lam2, M)[0]
+    return ro._v_logistic_exact(X, y, S, lam2, M)[0]
+
+
+def _evaluate_like_bench(X, y, c, prec, m, T, csr):
+    """push_dev on a side stream, T FISTA iterations under CUDA graphs, as bench.py times them."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=prec, max_batch=m,
+                     stream=stream.cuda_stream) as eng:
+        t = [torch.from_numpy(a).to("cuda") for a in csr]
+        with torch.cuda.stream(stream):
+            eng.push_dev(m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(),
+                         int(csr[0][-1]), int(csr[2][-1]))
+            res = eng.evaluate(T)
+            # the same batch again: graph replay must give identical results
+            eng.push_dev(m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(),
+                         int(csr[0][-1]), int(csr[2][-1]))
+            res2 = eng.evaluate(T)
+            B, Z = eng.read_batch()
+        stream.synchronize()
+    for key in ("lb", "primal", "ub", "support", "branch_j"):
+        assert np.array_equal(res[key], res2[key]), key
+    return res, B, Z
+
+
+def _invariants(res, nodes, p, k):
+    lb, ub, primal = res["lb"], res["ub"], res["primal"]
+    assert np.all(np.isfinite(lb)) and np.all(np.isfinite(ub))
+    tol = 1e-12 * np.maximum(1.0, np.abs(ub))
+    assert np.all(lb <= ub + tol), "weak duality LB <= v(S_b) violated at %s" % np.where(lb > ub + tol)[0][:10]
+    fin = np.isfinite(primal)
+    assert np.all(lb[fin] <= primal[fin] + 1e-12 * np.maximum(1.0, np.abs(primal[fin])))
+    for b, (J0, J1) in enumerate(nodes):
+        S = [int(s) for s in res["support"][b] if s >= 0]
+        assert S == sorted(S) and len(set(S)) == len(S) <= k
+        assert set(J1) <= set(S) and not (set(J0) & set(S)), b
+        j = int(res["branch_j"][b])
+        leaf = (k - len(J1) == 0) or (p - len(J0) <= k)
+        if leaf:
+            assert j == -1, b
+        else:
+            assert 0 <= j < p and j not in J0 and j not in J1, b
+
+
+def _sampled(X, y, c, res, B, Z, nodes, sample, reduced, L=None, T=None):
+    worst = 0.0
+    for b in sample:
+        J0, J1 = nodes[b]
+        nd = on.Node(c["p"], c["k"], J0, J1)
+        psi = on.dual_value(X, y, Z[b], nd, c["lam2"], c["M"], c["kind"])
+        if reduced:
+            assert res["lb"][b] <= psi + 1e-12 * max(1.0, abs(psi)), (b, res["lb"][b], psi)
+            assert psi - res["lb"][b] <= CERT_RTOL_REDUCED * max(1.0, abs(psi)), (b, res["lb"][b], psi)
+        else:
+            assert abs(res["lb"][b] - psi) <= 1e-9 * max(1.0, abs(psi)), (b, res["lb"][b], psi)
+        S = on.round_support(B[b], nd)
+        assert [int(s) for s in res["support"][b] if s >= 0] == S, b
+        assert res["branch_j"][b] == on.branch_index(B[b], nd), b
+        v = _v_exact(X, y, S, c["lam2"], c["M"], c["kind"])
+        ub = res["ub"][b]
+        assert ub >= v - 1e-9 * max(1.0, abs(v)), (b, ub, v)
+        assert ub - v <= (OBJ_RTOL_REDUCED if reduced else 1e-9) * max(1.0, abs(v)), (b, ub, v)
+        if L is not None:
+            ref = on.solve_node(X, y, nd, c["lam2"], c["M"], c["kind"], L, T)
+            worst = max(worst, abs(res["lb"][b] - ref["lb"]) / max(1.0, abs(ref["lb"])))
+    return worst
+
+
+def _batch(c, m, seed):
+    rng = np.random.default_rng(seed)
+    p, k = c["p"], c["k"]
+    special = [([], []), ([], list(range(k))), (list(range(p - k + 1)), []),
+               (list(range(1, p - 2)), [0]), ([j for j in range(p) if j % 3], [0, 3])]
+    rest = synth.csr_to_sets(*synth.random_nodes(m - len(special), p, k, rng))
+    nodes = special + rest
+    return nodes, synth.sets_to_csr(nodes)
+
+
+def test_c2_logistic_bench_launch_configuration():
+    """The bench line's workload: 1024 nodes, T = 50, FP32 products, FP64 certificate."""
+    c, X, y, _ = synth.config_instance("c2_logistic_n2000_p200_k10", seed=0)
+    m, T = c["m"], 50
+    nodes, csr = _batch(c, m, 1000)
+    res, B, Z = _evaluate_like_bench(X, y, c, "fp32", m, T, csr)
+    _invariants(res, nodes, c["p"], c["k"])
+    L = on.lipschitz(X, c["kind"])
+    sample = list(range(5)) + [17, 256, 511, 777, 1023]
+    worst = _sampled(X, y, c, res, B, Z, nodes, sample, reduced=True, L=L, T=T)
+    print("c2 fp32 vs fp64 oracle after %d iterations: max rel LB difference %.3e" % (T, worst))
+    assert worst <= 1e-4
+
+
+def test_c2_fp64_products_match_oracle_iterates():
+    """FP64 products at the full c2 size: the bound after T iterations equals the
+    oracle's own FISTA run to 1e-9 on sampled nodes."""
+    c, X, y, _ = synth.config_instance("c2_logistic_n2000_p200_k10", seed=0)
+    m, T = c["m"], 50
+    nodes, csr = _batch(c, m, 1001)
+    L = on.lipschitz(X, c["kind"])
+    res, B, Z = _evaluate_like_bench(X, y, c, "fp64", m, T, csr)
+    _invariants(res, nodes, c["p"], c["k"])
+    for b in list(range(5)) + [100, 900]:
+        J0, J1 = nodes[b]
+        nd = on.Node(c["p"], c["k"], J0, J1)
+        ref = on.solve_node(X, y, nd, c["lam2"], c["M"], c["kind"], L, T)
+        assert abs(res["lb"][b] - ref["lb"]) <= 1e-9 * max(1.0, abs(ref["lb"])), (b, res["lb"][b], ref["lb"])
+        assert np.max(np.abs(B[b] - ref["beta"])) <= 1e-9 * max(1.0, np.max(np.abs(ref["beta"]))), b
+    _sampled(X, y, c, res, B, Z, nodes, [0, 1, 2, 3, 4, 100, 900], reduced=False)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_c2_tensor_core_modes(prec):
+    c, X, y, _ = synth.config_instance("c2_logistic_n2000_p200_k10", seed=0)
+    m, T = c["m"], 50
+    nodes, csr = _batch(c, m, 1002)
+    res, B, Z = _evaluate_like_bench(X, y, c, prec, m, T, csr)
+    _invariants(res, nodes, c["p"], c["k"])
+    _sampled(X, y, c, res, B, Z, nodes, [0, 1, 2, 3, 4, 333, 1020], reduced=True)
+
+
+def test_c3_lsq_bf16_full_batch():
+    c, X, y, _ = synth.config_instance("c3_lsq_n5000_p1000_k15", seed=0)
+    m, T = c["m"], 50
+    nodes, csr = _batch(c, m, 1003)
+    res, B, Z = _evaluate_like_bench(X, y, c, "bf16", m, T, csr)
+    _invariants(res, nodes, c["p"], c["k"])
+    _sampled(X, y, c, res, B, Z, nodes, [0, 1, 2, 3, 4, 2048, 4095], reduced=True)
+
+
+@pytest.mark.parametrize("kind", [synth.LSQ, synth.LOGISTIC])
+def test_c4_microbench_bf16_full_batch(kind):
+    c, X, y, _ = synth.config_instance("c4_micro_n10000_p2000_k20", seed=0, kind=kind)
+    m, T = c["m"], c["T"]
+    nodes, csr = _batch(c, m, 1004)
+    res, B, Z = _evaluate_like_bench(X, y, c, "bf16", m, T, csr)
+    _invariants(res, nodes, c["p"], c["k"])
+    _sampled(X, y, c, res, B, Z, nodes, [0, 1, 3, 4, 5000, 8191], reduced=True)
