@@ -258,6 +258,82 @@ kglm_status kglm_device_bytes(const kglm_ctx* ctx, int64_t* bytes);
  * does not fit; KGLM_EINVAL for bad arguments. */
 kglm_status kglm_suggest_batch(const kglm_desc* desc, int64_t budget, int32_t cap, int32_t* batch);
 
+/* ---- Serving loop: certified solves of many instances, admitted as they
+ * arrive (continuous batching at request granularity).  Each admitted
+ * request is a kglm_solve (the hybrid loop of Fig. 1) on its own context,
+ * stream and host worker thread; requests in flight share the GPU (their
+ * kernels run side by side on the SMs) and each one's host tree work
+ * overlaps the others' device work.  Admission is FIFO: the request at the
+ * head of the queue starts once a worker is free and its device footprint
+ * (kglm_estimate_bytes) fits in the budget the running requests leave; a
+ * request's memory returns to the budget when it finishes.  A request runs
+ * the same kernels in the same order as kglm_solve alone, so its result
+ * (objective, support, node count) does not depend on the other requests. */
+typedef struct kglm_server kglm_server;
+
+typedef struct {
+    int64_t hbm_budget;   /* device bytes all admitted requests may hold; 0: 80% of the free memory at creation */
+    int32_t max_active;   /* requests solved at once (worker threads and streams), 1..256 */
+    int32_t batch_cap;    /* cap of the automatic batch size (requests with max_batch 0); 0: 4096 */
+    int32_t iters;        /* FISTA iterations per node evaluation (kglm_solve's iters), >= 1 */
+    int32_t check_every;  /* certificate every check_every iterations (kglm_solve's), >= 0 */
+    double time_limit_s;  /* per request, counted from admission; <= 0: none */
+} kglm_server_desc;
+
+enum { KGLM_REQ_QUEUED = 0, KGLM_REQ_RUNNING = 1, KGLM_REQ_DONE = 2, KGLM_REQ_FAILED = 3, KGLM_REQ_CANCELLED = 4 };
+
+typedef struct {
+    int32_t state;                  /* KGLM_REQ_* */
+    int32_t status;                 /* kglm_status of the request (KGLM_OK unless FAILED) */
+    double opt;                     /* best objective found (certified when gap <= gap_tol) */
+    double gap;                     /* final relative gap; > 0 if the time limit stopped the search */
+    int32_t support[KGLM_MAX_K];    /* support of opt, ascending, -1 padded */
+    int64_t nodes, batches;         /* nodes evaluated, batches launched */
+    int64_t device_bytes;           /* admitted footprint */
+    int32_t batch;                  /* node-batch size used */
+    int32_t reserved;
+    double t_submit, t_admit, t_done;   /* seconds since server creation; -1 until reached */
+} kglm_request_info;
+
+typedef struct {
+    int64_t submitted, finished, queued;
+    int32_t active, peak_active;
+    int64_t bytes_in_use, peak_bytes, budget;
+    double elapsed_s;
+} kglm_server_stats_t;
+
+/* Start a server on the current CUDA device with max_active worker threads. */
+kglm_status kglm_server_create(const kglm_server_desc* desc, kglm_server** out);
+
+/* Queue an instance (the arguments of kglm_create; desc->hbm_budget is
+ * ignored, desc->max_batch 0 selects the App. E.4 batch for an even share of
+ * the budget, capped at batch_cap).  X and y are copied before the call
+ * returns.  *id identifies the request.  KGLM_ENOMEM if the instance needs
+ * more than the server's whole budget; KGLM_EINVAL for a desc kglm_create
+ * would reject on its sizes (data checks happen at admission and end the
+ * request as FAILED with the status of kglm_create). */
+kglm_status kglm_server_submit(kglm_server* s, const kglm_desc* desc, const double* X, const double* y,
+                               int64_t* id);
+
+/* Snapshot of a request (any state). */
+kglm_status kglm_server_info(kglm_server* s, int64_t id, kglm_request_info* info);
+
+/* Block until the request has finished (DONE, FAILED or CANCELLED), at most
+ * timeout_s seconds (<= 0: no limit; KGLM_ETIMEOUT when it runs out). */
+kglm_status kglm_server_wait(kglm_server* s, int64_t id, double timeout_s, kglm_request_info* info);
+
+/* Block until every submitted request has finished (timeout as above). */
+kglm_status kglm_server_drain(kglm_server* s, double timeout_s);
+
+kglm_status kglm_server_stats(kglm_server* s, kglm_server_stats_t* out);
+
+/* Message of the last rejected submission (valid until the next call on s). */
+const char* kglm_server_last_error(kglm_server* s);
+
+/* Stop the server: running requests stop at their next batch boundary
+ * (CANCELLED), queued ones are dropped; joins the workers and frees all. */
+void kglm_server_destroy(kglm_server* s);
+
 /* Message of the last failed call on ctx (never NULL). */
 const char* kglm_last_error(const kglm_ctx* ctx);
 

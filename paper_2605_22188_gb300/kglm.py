@@ -65,7 +65,34 @@ _SIGS = {
     "kglm_estimate_bytes": (C.c_int, [C.POINTER(kglm_desc), I64]),
     "kglm_device_bytes": (C.c_int, [P, I64]),
     "kglm_suggest_batch": (C.c_int, [C.POINTER(kglm_desc), C.c_int64, C.c_int32, C.POINTER(C.c_int32)]),
+    "kglm_server_create": (C.c_int, [C.c_void_p, C.POINTER(P)]),
+    "kglm_server_submit": (C.c_int, [P, C.POINTER(kglm_desc), D, D, I64]),
+    "kglm_server_info": (C.c_int, [P, C.c_int64, C.c_void_p]),
+    "kglm_server_wait": (C.c_int, [P, C.c_int64, C.c_double, C.c_void_p]),
+    "kglm_server_drain": (C.c_int, [P, C.c_double]),
+    "kglm_server_stats": (C.c_int, [P, C.c_void_p]),
+    "kglm_server_last_error": (C.c_char_p, [P]),
+    "kglm_server_destroy": (None, [P]),
 }
+class kglm_server_desc(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int32), ("batch_cap", C.c_int32),
+                ("iters", C.c_int32), ("check_every", C.c_int32), ("time_limit_s", C.c_double)]
+
+
+class kglm_request_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("opt", C.c_double), ("gap", C.c_double),
+                ("support", C.c_int32 * MAX_K), ("nodes", C.c_int64), ("batches", C.c_int64),
+                ("device_bytes", C.c_int64), ("batch", C.c_int32), ("reserved", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class kglm_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("finished", C.c_int64), ("queued", C.c_int64),
+                ("active", C.c_int32), ("peak_active", C.c_int32), ("bytes_in_use", C.c_int64),
+                ("peak_bytes", C.c_int64), ("budget", C.c_int64), ("elapsed_s", C.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
 
@@ -331,6 +358,82 @@ class Engine:
         if self.ctx:
             kglm_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving loop
+
+def _info_dict(i):
+    return dict(state=i.state, status=i.status, opt=i.opt, gap=i.gap,
+                support=[int(x) for x in i.support if x >= 0], nodes=i.nodes, batches=i.batches,
+                device_bytes=i.device_bytes, batch=i.batch, t_submit=i.t_submit, t_admit=i.t_admit,
+                t_done=i.t_done)
+
+
+class Server:
+    """kglm_server_*: certified solves of many instances admitted as they arrive."""
+
+    def __init__(self, max_active=8, hbm_budget=0, iters=200, check_every=10, time_limit_s=0.0, batch_cap=0):
+        d = kglm_server_desc(hbm_budget=int(hbm_budget), max_active=int(max_active), batch_cap=int(batch_cap),
+                             iters=int(iters), check_every=int(check_every), time_limit_s=float(time_limit_s))
+        out = P()
+        st = lib().kglm_server_create(C.byref(d), C.byref(out))
+        if st != KGLM_OK:
+            raise KglmError(st, "kglm_server_create failed")
+        self.s = out
+
+    def submit(self, X, y, k, lambda2, M, loss, prec="bf16", max_batch=0, lipschitz=0.0, gap_tol=0.0,
+               restart=True, pool_slots=0):
+        X = _f64(X)
+        n, p = X.shape
+        y = _f64(y, (n,))
+        d = make_desc(n, p, k, lambda2, M, loss, prec, 1, lipschitz, gap_tol, restart, pool_slots, 0)
+        d.max_batch = int(max_batch)
+        rid = C.c_int64()
+        st = lib().kglm_server_submit(self.s, C.byref(d), _ptr(X, D), _ptr(y, D), C.byref(rid))
+        if st != KGLM_OK:
+            raise KglmError(st, lib().kglm_server_last_error(self.s).decode())
+        return rid.value
+
+    def info(self, rid):
+        i = kglm_request_info()
+        st = lib().kglm_server_info(self.s, int(rid), C.byref(i))
+        if st != KGLM_OK:
+            raise KglmError(st, "unknown request %d" % rid)
+        return _info_dict(i)
+
+    def wait(self, rid, timeout=0.0):
+        i = kglm_request_info()
+        st = lib().kglm_server_wait(self.s, int(rid), float(timeout), C.byref(i))
+        if st != KGLM_OK:
+            raise KglmError(st, "wait for request %d" % rid)
+        return _info_dict(i)
+
+    def drain(self, timeout=0.0):
+        st = lib().kglm_server_drain(self.s, float(timeout))
+        if st != KGLM_OK:
+            raise KglmError(st, "drain")
+
+    def stats(self):
+        t = kglm_server_stats_t()
+        _check(lib().kglm_server_stats(self.s, C.byref(t)), None)
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def close(self):
+        if self.s:
+            lib().kglm_server_destroy(self.s)
+            self.s = None
 
     def __enter__(self):
         return self

@@ -122,3 +122,29 @@ def config_instance(name, seed=0, kind=None):
     X, y, b = instance(c["n"], c["p"], c["k"], kind, rho=c["rho"], snr=c["snr"], seed=seed)
     c["kind"] = kind
     return c, X, y, b
+
+
+def serving_specs(count=64, seed=0):
+    """Instance descriptions of the serving mix: loss uniform over {least squares,
+    logistic}, p log-uniform on [100, 2000], n log-uniform on [5p, 10p], k uniform
+    on {5..20}, Toeplitz rho in {0.5, 0.7, 0.9}, SNR in {3, 5}; lambda2 1e-3
+    (least squares) or 1e-2 (logistic), M = 2.  Each spec carries its own data
+    seed; instance(**spec) draws the data when the request is submitted."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        kind = LSQ if rng.random() < 0.5 else LOGISTIC
+        p = int(round(math.exp(rng.uniform(math.log(100), math.log(2000)))))
+        n = int(round(math.exp(rng.uniform(math.log(5 * p), math.log(10 * p)))))
+        k = int(rng.integers(5, 21))
+        rho = float(rng.choice([0.5, 0.7, 0.9]))
+        snr = float(rng.choice([3.0, 5.0]))
+        out.append(dict(n=n, p=p, k=k, kind=kind, rho=rho, snr=snr, seed=int(seed * 1000 + i),
+                        lam2=1e-3 if kind == LSQ else 1e-2, M=2.0))
+    return out
+
+
+def poisson_arrivals(count, rate, seed=0):
+    """Arrival times (seconds from 0) of a Poisson stream with `rate` requests per second."""
+    rng = np.random.default_rng(seed + 7919)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count)) if rate > 0 else np.zeros(count)

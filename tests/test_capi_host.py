@@ -113,3 +113,19 @@ def test_suggest_batch_is_the_largest_fitting_power_of_two(lib):
     with pytest.raises(kglm.KglmError) as ei:
         kglm.kglm_estimate_bytes(bad)
     assert ei.value.status == kglm.KGLM_EINVAL
+
+
+def test_server_rejects_bad_descriptions_before_touching_the_gpu(lib):
+    import ctypes as C
+    for kw in (dict(max_active=0), dict(max_active=1000), dict(iters=0), dict(check_every=-1),
+               dict(hbm_budget=-5), dict(batch_cap=-1)):
+        base = dict(hbm_budget=0, max_active=2, batch_cap=0, iters=10, check_every=0, time_limit_s=0.0)
+        base.update(kw)
+        d = kglm.kglm_server_desc(**base)
+        out = C.c_void_p()
+        assert lib.kglm_server_create(C.byref(d), C.byref(out)) == kglm.KGLM_EINVAL, kw
+        assert not out.value
+    # calls on a null server
+    assert lib.kglm_server_drain(None, 0.0) == kglm.KGLM_EINVAL
+    assert lib.kglm_server_info(None, 1, None) == kglm.KGLM_EINVAL
+    lib.kglm_server_destroy(None)

