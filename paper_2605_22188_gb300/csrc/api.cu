@@ -684,7 +684,7 @@ size_t footprint(const kglm_desc& d) {
         add(n * pK * es); add(n * pK * es); add(p * nK * es);
         add(mc * pK * es); add(mc * nK * es);
         add(tc_scratch_bytes()); add(4 * (size_t)tc_scratch_counters());
-        add(4 * 4 * mc * p);   // gsplit_max = 4 slices of X^T R
+        add(4 * (size_t)tc_split_cap((int)mc, (int)p) * mc * p);   // split slices of X^T R
         add(4);
         tcerr = true;
     }
@@ -1033,6 +1033,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->gtc.n_counters = tc_scratch_counters();
             c->gtc.counters = dalloc_t<int>(c, c->gtc.n_counters);
             CK(cudaMemsetAsync(c->gtc.counters, 0, sizeof(int) * c->gtc.n_counters, c->st));
+            c->gsplit_max = tc_split_cap((int)mc, (int)p);
             c->Gpart = dalloc_t<float>(c, (size_t)c->gsplit_max * mc * p);
             c->d_tcerr = dalloc_t<int>(c, 1);
             CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));

@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace kglm {
 
 constexpr int kLSQ = 0;
@@ -261,23 +263,30 @@ __device__ uint32_t group_topk_select(const K (&key)[E], uint32_t valid, int kth
     return gt | take;
 }
 
-// Warp tournament: the kth largest of the valid values of the warp, ties to
-// the smaller index (element e of lane l is index l + 32e), in kth rounds of a
-// warp-wide argmax over each lane's best untaken element.  Writes the
-// selection sorted (value descending) to sv/si (lane 0) and returns the
-// lane's bit mask of selected elements.  Values must be >= 0.
-template <int E, typename T>
-__device__ uint32_t warp_topk_tournament(const T (&val)[E], uint32_t valid, int kth, T* sv, int* si) {
+// Bit e of a per-thread element mask (E <= 64 elements per thread).
+template <int E>
+using ElemMask = typename std::conditional<(E > 32), unsigned long long, uint32_t>::type;
+template <typename Mk>
+__device__ __forceinline__ bool bit(Mk m, int e) { return (m >> e) & Mk(1); }
+
+// Warp tournament: the kth largest of |val| over the valid elements of the
+// warp, ties to the smaller index (element e of lane l is index l + 32e), in
+// kth rounds of a warp-wide argmax over each lane's best untaken element.
+// Writes the selection sorted (magnitude descending) to sv/si (lane 0) and
+// returns the lane's mask of selected elements.
+template <int E, typename T, typename Mk>
+__device__ Mk warp_topk_tournament(const T (&val)[E], Mk valid, int kth, T* sv, int* si) {
     const int lane = threadIdx.x & 31;
-    uint32_t taken = 0;
+    Mk taken = 0;
     for (int r = 0; r < kth; ++r) {
         T best = T(-1);
         int bidx = 0x7fffffff, be = -1;
 #pragma unroll
         for (int e = 0; e < E; ++e)
-            if (((valid & ~taken) >> e) & 1u) {
+            if (bit(valid & ~taken, e)) {
                 const int idx = lane + 32 * e;
-                if (val[e] > best || (val[e] == best && idx < bidx)) { best = val[e]; bidx = idx; be = e; }
+                const T x = abs(val[e]);
+                if (x > best || (x == best && idx < bidx)) { best = x; bidx = idx; be = e; }
             }
         T wv = best;
         int wi = bidx;
@@ -287,7 +296,7 @@ __device__ uint32_t warp_topk_tournament(const T (&val)[E], uint32_t valid, int 
             const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
             if (ov > wv || (ov == wv && oi < wi)) { wv = ov; wi = oi; }
         }
-        if (be >= 0 && bidx == wi) taken |= 1u << be;
+        if (be >= 0 && bidx == wi) taken |= Mk(1) << be;
         if (lane == 0) { sv[r] = wv; si[r] = wi; }
     }
     __syncwarp();

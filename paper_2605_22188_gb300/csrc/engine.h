@@ -77,6 +77,9 @@ int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, i
 // Sets the kernels' shared-memory attributes (call before any stream capture).
 int tc_prepare();
 int tc_tile_cols(int N);
+// Split-K slices of a TC_EPI_PARTIAL product with M x N output: enough units
+// to fill the SMs, at most 16.
+int tc_split_cap(int M, int N);
 int tc_tile_cols_wide(int N);   // 128-column tiles for N > 256 (more CTAs for a wide output)
 size_t tc_scratch_bytes();
 int tc_scratch_counters();

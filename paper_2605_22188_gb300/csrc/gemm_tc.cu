@@ -1,18 +1,29 @@
 // Tensor-core products of the BF16 and TF32 modes: S = X V (with the
-// loss/link fused) and G = X^T R of §4.2 Eq. (gradient_matrix_form), on the
-// fifth-generation tensor cores of sm_103a.
+// loss/link fused) and G = X^T R of §4.2 Eq. (gradient_matrix_form), and the
+// digit products of the exact certificate, on the fifth-generation tensor
+// cores of sm_103a.
 //
-// C[r][c] = sum_k A[r][k] B[c][k] with both operands K-contiguous.  One CTA
-// computes a 128 x BN tile (BN <= 256, a multiple of 16) of one K range:
+// C[r][c] = sum_k A[r][k] B[c][k] with both operands K-contiguous.  The
+// output is cut into 128 x BN tiles (BN <= 256, a multiple of 16) and,
+// optionally, into K ranges (split-K slices or the jobs of the certificate):
+// one work unit is one (tile, K range).  The kernel is persistent: one CTA per
+// SM walks the units u = blockIdx.x, blockIdx.x + gridDim.x, ... with
 //   warp 0, lane 0   TMA producer: 128-byte-swizzled K slices of A and B
-//                    (cp.async.bulk.tensor.2d) into a 4-stage ring;
+//                    (cp.async.bulk.tensor.2d) into a ring of stages;
 //   warp 1, lane 0   MMA issuer: tcgen05.mma.cta_group::1 (kind::f16 with BF16
-//                    operands, or kind::tf32), FP32 accumulator in tensor
-//                    memory; tcgen05.commit frees a stage / signals the tile;
-//   warps 0-7        epilogue: tcgen05.ld of the accumulator (warp w reads
-//                    TMEM lanes 32(w%4).. , i.e. tile rows, and every other
-//                    32-column chunk), then the link, a plain store or a
-//                    split-K partial.
+//                    operands, or kind::tf32) into one of two FP32
+//                    accumulators in tensor memory (512 columns), so that the
+//                    next unit's products run while the epilogue drains the
+//                    last one; tcgen05.commit frees a stage / publishes an
+//                    accumulator;
+//   warps 2-5        epilogue: tcgen05.ld of the accumulator (warp w reads
+//                    TMEM lanes 32(w%4).., the tile's rows), a 32 x 32
+//                    transpose through shared memory, then row-contiguous
+//                    stores of the link, the plain product, a split-K partial
+//                    or a slice of the partial products.
+// Units run row tiles fastest when B is the larger operand (its panel is
+// then reused by consecutive CTAs while A stays in L2) and column tiles
+// fastest otherwise.
 // The B operand can be given as two parts (hi + lo, both multiplied into the
 // same accumulator): the engine does this for X in S = X V, so that X enters
 // one of the two products of an iteration with ~16 (BF16) or ~22 (TF32) bits.
@@ -21,10 +32,12 @@
 // E^T E ~ n u^2 E[x^2]: a ridge shift comparable to lambda2 at n in the
 // thousands.  FP32 operands reach kind::tf32 rounded to nearest (the tensor
 // core would otherwise truncate them, a bias toward zero).
-// Split-K uses the scheme of the CUDA-core GEMM: partial tiles in scratch,
-// the last CTA of a tile (arrival counter) sums them in fixed order.
+// Split-K with the plain or link epilogue: partial tiles go to scratch and
+// the last epilogue warp to finish a 32-row slab of a tile (arrival counter
+// per slab) sums its partials in fixed order; no warp waits on another.
 // Every mbarrier wait is bounded; a wait that runs out sets an error flag,
-// the CTA still drains its MMAs and frees its tensor memory.
+// the roles stop, the MMA issuer drains its products and the producer its
+// copies before the tensor memory is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -39,14 +52,17 @@ namespace {
 constexpr int BM = 128;                 // rows per tile (one UMMA M = 128)
 constexpr int ROWB = 128;               // bytes of K per stage and row (one swizzle row)
 constexpr int MAXBN = 256;
-constexpr int NT = 256;                 // eight warps
+constexpr int NT = 192;                 // six warps: producer, MMA, four epilogue warps
 constexpr uint32_t STAGE_A = BM * ROWB;
 constexpr uint32_t STAGE_B = MAXBN * ROWB;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 512;     // two accumulators of up to 256 columns
+constexpr int TPAD = 36;                // transpose buffer row: 32 + 4 (16-byte rows, no 128-bit bank conflicts)
+constexpr int SMS = 152;
 // NB = 1: one B operand, four stages; NB = 2: B given as hi + lo parts
 // (both multiplied into the same accumulator), two stages.
 template <int NB> constexpr int stages() { return NB == 1 ? 4 : 2; }
-template <int NB> constexpr size_t smem_bytes() { return 1024 + stages<NB>() * (STAGE_A + NB * STAGE_B) + 256; }
+constexpr size_t kEpiBytes = 4 * 32 * TPAD * sizeof(float);
+template <int NB> constexpr size_t smem_bytes() { return 1024 + stages<NB>() * (STAGE_A + NB * STAGE_B) + kEpiBytes + 256; }
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // try_wait rounds before a wait gives up
 
 // ------------------------------------------------------------------ arguments and epilogues
@@ -54,7 +70,9 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;   // try_wait rounds before a wait giv
 struct TcArgs {
     int M, N;                 // output rows (A rows) and columns (B rows)
     int bn;                   // columns per tile, multiple of 16, <= MAXBN
-    int nkb, kb_per_split;    // K in 128-byte slices, slices per CTA
+    int mt, nt, nz;           // row tiles, column tiles, K ranges (splits or jobs)
+    int m_fast;               // units walk row tiles fastest
+    int nkb, kb_per_split;    // K in 128-byte slices, slices per split
     uint32_t idesc;           // instruction descriptor
     int epi;                  // TC_EPI_*
     int round_tf32;           // round FP32 link outputs to TF32 (nearest) for the next product
@@ -65,10 +83,10 @@ struct TcArgs {
     int ldo;
     const float* y;
     int loss;
-    float* part;
+    float* part;              // split-K partial tiles (nz > 1, epi != PARTIAL)
     int* counters;
     int* err;
-    int njobs;                // > 0: job z = blockIdx.z takes its own K ranges and slice
+    int njobs;                // > 0: K range z is job z (its own K offsets in A and B, and slice)
     TcJob jobs[kTcMaxJobs];
 };
 
@@ -84,48 +102,40 @@ __device__ __forceinline__ float dloss_fast(float s, float y, int kind) {
     return kind == kLSQ ? 2.0f * (s - y) : -y * __frcp_rn(1.0f + __expf(y * s));
 }
 
-// Writes columns c0 .. c0+31 of output row r (columns >= N are skipped); ys:
-// the tile's y values staged in shared memory (index c0 - n0 + j); zs: the
-// slice of a partial product.
-__device__ __forceinline__ void tc_epilogue(const TcArgs& a, int r, int c0, const float (&v)[32], const float* ys,
-                                            int zs) {
-    if (r >= a.M) return;
+// One output value v at (r, c) (r < M, c < N checked by the caller).
+__device__ __forceinline__ void tc_store(const TcArgs& a, int r, int c, float v, float yc, int zs) {
     if (a.epi == TC_EPI_PARTIAL) {
-        float* o = a.pout + (size_t)zs * a.pstride + (size_t)r * a.pld;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < a.N) o[c0 + j] = v[j];
+        a.pout[(size_t)zs * a.pstride + (size_t)r * a.pld + c] = v;
     } else if (a.epi == TC_EPI_STORE_F32) {
-        float* o = static_cast<float*>(a.out) + (size_t)r * a.ldo;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < a.N) o[c0 + j] = v[j];
+        static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = v;
     } else if (a.epi == TC_EPI_LINK_F32) {
-        float* o = static_cast<float*>(a.out) + (size_t)r * a.ldo;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < a.N) {
-                const float d = dloss_fast(v[j], ys[j], a.loss);
-                o[c0 + j] = a.round_tf32 ? tf32_rn(d) : d;
-            }
+        const float d = dloss_fast(v, yc, a.loss);
+        static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = a.round_tf32 ? tf32_rn(d) : d;
     } else {
-        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + (size_t)r * a.ldo;
-        if (c0 + 32 <= a.N && (a.ldo % 8) == 0) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                __nv_bfloat162 h[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    h[q] = __floats2bfloat162_rn(dloss_fast(v[j + 2 * q], ys[j + 2 * q], a.loss),
-                                                 dloss_fast(v[j + 2 * q + 1], ys[j + 2 * q + 1], a.loss));
-                *reinterpret_cast<uint4*>(o + c0 + j) = *reinterpret_cast<const uint4*>(h);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (c0 + j < a.N) o[c0 + j] = __float2bfloat16(dloss_fast(v[j], ys[j], a.loss));
-        }
+        static_cast<__nv_bfloat16*>(a.out)[(size_t)r * a.ldo + c] = __float2bfloat16(dloss_fast(v, yc, a.loss));
     }
+}
+
+// The unit's tile and K range.
+struct Unit {
+    int mtile, ntile, z, ka, kb, nloc, slice;
+};
+__device__ __forceinline__ Unit unit_of(const TcArgs& a, int u) {
+    Unit w;
+    const int tiles = a.mt * a.nt;
+    w.z = u / tiles;
+    const int t = u - w.z * tiles;
+    if (a.m_fast) { w.mtile = t % a.mt; w.ntile = t / a.mt; }
+    else          { w.ntile = t % a.nt; w.mtile = t / a.nt; }
+    if (a.njobs > 0) {
+        const TcJob& jb = a.jobs[w.z];
+        w.ka = jb.ka; w.kb = jb.kb; w.nloc = jb.nkb; w.slice = jb.slice;
+    } else {
+        w.ka = w.kb = w.z * a.kb_per_split;
+        w.nloc = max(0, min(a.nkb, w.ka + a.kb_per_split) - w.ka);
+        w.slice = w.z;
+    }
+    return w;
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -242,6 +252,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 
 // ------------------------------------------------------------------ the kernel
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 template <int KIND, int NB>
 __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB,
@@ -252,28 +266,27 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * STAGE_A;                    // stage s: B at s, B2 (NB = 2) at STAGES + s
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + NB * STAGES * STAGE_B);   // full[S], empty[S], accum
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-    __shared__ int s_last;
-    __shared__ float ys[MAXBN + 32];
+    float* sT = reinterpret_cast<float*>(sB + NB * STAGES * STAGE_B);              // 4 x 32 x TPAD
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sT + 4 * 32 * TPAD);
+    // bars: full[S], empty[S], tfull[2], tempty[2], drain
+    uint64_t* full = bars;
+    uint64_t* empty = bars + STAGES;
+    uint64_t* tfull = bars + 2 * STAGES;
+    uint64_t* tempty = bars + 2 * STAGES + 2;
+    uint64_t* drain = bars + 2 * STAGES + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    __shared__ int s_consumed;       // ring slices the MMA issuer consumed (producer drain at exit)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * a.bn;
-    // K slices of this CTA: a split of [0, nkb), or the job's own ranges of A and B
-    int ka0, kbb0, nloc, zs;
-    if (a.njobs > 0) {
-        const TcJob& jb = a.jobs[blockIdx.z];
-        ka0 = jb.ka; kbb0 = jb.kb; nloc = jb.nkb; zs = jb.slice;
-    } else {
-        ka0 = kbb0 = blockIdx.z * a.kb_per_split;
-        nloc = min(a.nkb, ka0 + a.kb_per_split) - ka0;
-        zs = blockIdx.z;
-    }
     constexpr int KE = KIND == 0 ? 64 : 32;          // elements per 128-byte row
     const uint32_t stage_bytes = STAGE_A + (uint32_t)NB * a.bn * ROWB;
+    const int units = a.mt * a.nt * a.nz;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), 1); }
+        for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 128); }
+        mbar_init(smem_u32(drain), 1);
+        s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -281,96 +294,198 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    int issued = 0;                  // producer: ring slices whose copies were started
 
-    if (warp == 0 && lane == 0) {
-        // producer
-        for (int i = 0; i < nloc; ++i) {
-            const int s = i % STAGES;
-            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1u, a.err)) break;
-            const uint32_t full = smem_u32(&bars[s]);
-            mbar_expect_tx(full, stage_bytes);
-            const int kxa = (ka0 + i) * KE, kxb = (kbb0 + i) * KE;
-            tma_load_2d(smem_u32(sA + s * STAGE_A), &tmA, kxa, m0, full);
-            tma_load_2d(smem_u32(sB + s * STAGE_B), &tmB, kxb, n0, full);
-            if (NB == 2) tma_load_2d(smem_u32(sB + (STAGES + s) * STAGE_B), &tmB2, kxb, n0, full);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int i = 0; i < nloc; ++i) {
-            const int s = i % STAGES;
-            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&bars[s]), ph, a.err)) break;
-            tc_fence_after();
-            const uint32_t aa = smem_u32(sA + s * STAGE_A), bb = smem_u32(sB + s * STAGE_B);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K each (per B part)
-                umma<KIND>(tmem, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                if (NB == 2) {
-                    const uint32_t b2 = smem_u32(sB + (STAGES + s) * STAGE_B);
-                    umma<KIND>(tmem, smem_desc(aa + kk * 32), smem_desc(b2 + kk * 32), a.idesc, 1u);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int g = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                const Unit w = unit_of(a, u);
+                const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
+                for (int i = 0; i < w.nloc; ++i, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.err)) { ok = false; break; }
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, stage_bytes);
+                    const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
+                    tma_load_2d(smem_u32(sA + s * STAGE_A), &tmA, kxa, m0, fb);
+                    tma_load_2d(smem_u32(sB + s * STAGE_B), &tmB, kxb, n0, fb);
+                    if (NB == 2) tma_load_2d(smem_u32(sB + (STAGES + s) * STAGE_B), &tmB2, kxb, n0, fb);
+                    issued = g + 1;
                 }
             }
-            umma_commit(smem_u32(&bars[STAGES + s]));   // stage s is free once these MMAs finish
         }
-        umma_commit(smem_u32(&bars[2 * STAGES]));       // the accumulator is complete (or drained)
-    }
-    __syncwarp();
-
-    // epilogue: all eight warps; warp w reads TMEM lanes 32*(w%4).. (tile rows)
-    // and the 32-column chunks of parity w/4
-    if (a.y != nullptr)
-        for (int c = threadIdx.x; c < a.bn + 32; c += NT) ys[c] = (n0 + c < a.N) ? a.y[n0 + c] : 0.f;
-    __syncthreads();
-    // warp-uniform: tcgen05.ld below is .sync.aligned
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[2 * STAGES]), 0u, a.err) && nloc > 0);
-    tc_fence_after();
-    const int quad = warp & 3, half = warp >> 2;
-    const int row = m0 + quad * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-    // split-K with the last-CTA reduction (TC_EPI_PARTIAL keeps every slice instead)
-    const bool split = gridDim.z > 1 && a.epi != TC_EPI_PARTIAL;
-    const int ntile = gridDim.x * gridDim.y;
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    if (ok) {
-        for (int c = half * 32; c < a.bn; c += 64) {
-            float v[32];
-            tmem_ld32(tl + (uint32_t)c, v);
-            if (!split) {
-                tc_epilogue(a, row, n0 + c, v, ys + c, zs);
-            } else {
-                float* my = a.part + (((size_t)blockIdx.z * ntile + tile) * BM + quad * 32 + lane) * MAXBN + c;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            int g = 0, li = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++li) {
+                const Unit w = unit_of(a, u);
+                const int b = li & 1;
+                const uint32_t use = (uint32_t)(li >> 1) & 1u;
+                if (!mbar_wait(smem_u32(&tempty[b]), use ^ 1u, a.err)) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * MAXBN);
+                for (int i = 0; i < w.nloc; ++i, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&full[s]), ph, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t aa = smem_u32(sA + s * STAGE_A), bb = smem_u32(sB + s * STAGE_B);
 #pragma unroll
-                for (int q = 0; q < 32; q += 4) *reinterpret_cast<float4*>(my + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                    for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K each (per B part)
+                        umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc,
+                                   (i > 0 || kk > 0) ? 1u : 0u);
+                        if (NB == 2) {
+                            const uint32_t b2 = smem_u32(sB + (STAGES + s) * STAGE_B);
+                            umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(b2 + kk * 32), a.idesc, 1u);
+                        }
+                    }
+                    umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
+                    s_consumed = g + 1;
+                }
+                umma_commit(smem_u32(&tfull[b]));       // the accumulator is complete (or abandoned)
             }
+            // every product issued so far has finished once this commit arrives
+            umma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0u, a.err);
         }
-    }
-    tc_fence_before();
-    if (split) {
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = (atomicAdd(&a.counters[tile], 1) == (int)gridDim.z - 1);
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            for (int c = half * 32; c < a.bn; c += 64) {
+    } else {
+        // epilogue: warps 2..5 cover the TMEM lane quadrants 2, 3, 0, 1
+        const int quad = warp & 3;
+        float* tb = sT + (warp - 2) * 32 * TPAD;
+        int li = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++li) {
+            const Unit w = unit_of(a, u);
+            const int b = li & 1;
+            const uint32_t use = (uint32_t)(li >> 1) & 1u;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[b]), use, a.err));
+            if (!ok) break;
+            tc_fence_after();
+            const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
+            const int rbase = m0 + quad * 32;             // this warp's 32 rows
+            const bool split = a.nz > 1 && a.epi != TC_EPI_PARTIAL;
+            const int tile = w.mtile * a.nt + w.ntile;
+            const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * MAXBN);
+            for (int c = 0; c < a.bn; c += 32) {
                 float v[32];
+                if (w.nloc > 0) {
+                    tmem_ld32(tl + (uint32_t)c, v);
+                } else {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = 0.f;
-                for (int s = 0; s < (int)gridDim.z; ++s) {
-                    const float* ps = a.part + (((size_t)s * ntile + tile) * BM + quad * 32 + lane) * MAXBN + c;
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                }
+                const int c0 = n0 + c;
+                if (!split && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16)) {
+                    // link on the row-per-lane values; y of column c0 + j from lane j
+                    const float yl = (c0 + lane < a.N) ? __ldg(a.y + c0 + lane) : 0.f;
 #pragma unroll
-                    for (int q = 0; q < 32; q += 4) {
-                        const float4 x = __ldcg(reinterpret_cast<const float4*>(ps + q));
-                        v[q] += x.x; v[q + 1] += x.y; v[q + 2] += x.z; v[q + 3] += x.w;
+                    for (int j = 0; j < 32; ++j) {
+                        const float d = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
+                        v[j] = (a.epi == TC_EPI_LINK_F32 && a.round_tf32) ? tf32_rn(d) : d;
                     }
                 }
-                tc_epilogue(a, row, n0 + c, v, ys + c, 0);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)                         // row lane, columns j..j+3
+                    *reinterpret_cast<float4*>(tb + lane * TPAD + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                __syncwarp();
+                if (split) {
+                    // 4 rows x 128 bytes per instruction
+                    float* pt = a.part + (((size_t)w.z * (a.mt * a.nt) + tile) * BM + quad * 32) * MAXBN + c;
+                    const int q = lane & 7, r0 = lane >> 3;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int r = r0 + 4 * i;
+                        *reinterpret_cast<float4*>(pt + (size_t)r * MAXBN + 4 * q) =
+                            *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * q);
+                    }
+                } else if (a.epi == TC_EPI_LINK_BF16) {
+                    // 8 rows x 64 bytes per instruction (8 BF16 per lane)
+                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out);
+                    const int q = lane & 3, r0 = lane >> 2;
+                    const bool vec = (a.ldo % 8) == 0 && c0 + 8 * q + 8 <= a.N;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = r0 + 8 * i, row = rbase + r;
+                        if (row >= a.M) continue;
+                        const float4 x0 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * q);
+                        const float4 x1 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * q + 4);
+                        __nv_bfloat16* dst = o + (size_t)row * a.ldo + c0 + 8 * q;
+                        if (vec) {
+                            __nv_bfloat162 h[4] = {__floats2bfloat162_rn(x0.x, x0.y), __floats2bfloat162_rn(x0.z, x0.w),
+                                                   __floats2bfloat162_rn(x1.x, x1.y), __floats2bfloat162_rn(x1.z, x1.w)};
+                            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+                        } else {
+                            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                            for (int t = 0; t < 8; ++t)
+                                if (c0 + 8 * q + t < a.N) dst[t] = __float2bfloat16(xs[t]);
+                        }
+                    }
+                } else {
+                    // FP32 outputs (product, link, partial slice): 4 rows x 128 bytes per instruction
+                    float* o;
+                    size_t ld;
+                    if (a.epi == TC_EPI_PARTIAL) { o = a.pout + (size_t)w.slice * a.pstride; ld = (size_t)a.pld; }
+                    else { o = static_cast<float*>(a.out); ld = (size_t)a.ldo; }
+                    const int q = lane & 7, r0 = lane >> 3;
+                    const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(o) % 16) == 0 && c0 + 4 * q + 4 <= a.N;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int r = r0 + 4 * i, row = rbase + r;
+                        if (row >= a.M) continue;
+                        const float4 x = *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * q);
+                        float* dst = o + (size_t)row * ld + c0 + 4 * q;
+                        if (vec) {
+                            *reinterpret_cast<float4*>(dst) = x;
+                        } else {
+                            const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                            for (int t = 0; t < 4; ++t)
+                                if (c0 + 4 * q + t < a.N) dst[t] = xs[t];
+                        }
+                    }
+                }
+                __syncwarp();
             }
-            if (threadIdx.x == 0) a.counters[tile] = 0;
+            // the accumulator may be overwritten by the unit after next
+            tc_fence_before();
+            mbar_arrive(smem_u32(&tempty[b]));
+            if (split) {
+                // per-warp arrival: the last of the nz units of this tile to finish
+                // this warp's 32 rows sums their partials (no warp waits on another)
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) last = atomicAdd(&a.counters[tile * 4 + quad], 1) == a.nz - 1;
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence();
+                    for (int c = 0; c < a.bn; c += 32) {
+                        const int col = n0 + c + lane;
+                        const float yc = (a.y != nullptr && col < a.N) ? __ldg(a.y + col) : 0.f;
+                        for (int r = 0; r < 32; ++r) {
+                            float acc = 0.f;
+                            for (int z = 0; z < a.nz; ++z)
+                                acc += __ldcg(a.part + (((size_t)z * (a.mt * a.nt) + tile) * BM + quad * 32 + r) * MAXBN + c + lane);
+                            if (col < a.N && rbase + r < a.M) tc_store(a, rbase + r, col, acc, yc, 0);
+                        }
+                    }
+                    if (lane == 0) a.counters[tile * 4 + quad] = 0;
+                }
+            }
         }
     }
     __syncthreads();
+    if (warp == 0 && lane == 0) {
+        // copies still in flight (a wait that ran out) land before the CTA exits
+        for (int g = s_consumed; g < issued; ++g)
+            mbar_wait(smem_u32(&full[g % STAGES]), (uint32_t)(g / STAGES) & 1u, a.err);
+    }
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
@@ -427,10 +542,17 @@ int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, i
 }
 
 int tc_tile_cols(int N) { return N >= MAXBN ? MAXBN : ((N + 15) / 16) * 16; }
+int tc_split_cap(int M, int N) {
+    const int tiles = ((M + BM - 1) / BM) * ((N + tc_tile_cols(N) - 1) / tc_tile_cols(N));
+    return std::max(1, std::min(16, (SMS + tiles - 1) / tiles));
+}
 int tc_tile_cols_wide(int N) { return N > MAXBN ? 128 : tc_tile_cols(N); }
 
-size_t tc_scratch_bytes() { return (size_t)3 * 152 * BM * MAXBN * sizeof(float); }
-int tc_scratch_counters() { return 3 * 152; }
+size_t tc_scratch_bytes() { return (size_t)3 * SMS * BM * MAXBN * sizeof(float); }
+int tc_scratch_counters() { return 4 * SMS; }   // one per 32-row slab of a tile
+
+// Persistent grid: one CTA per SM (at most one per unit).
+static int grid_of(int units) { return std::max(1, std::min(units, SMS)); }
 
 int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, const TcGemm& g,
             const GemmScratch* scr) {
@@ -444,20 +566,24 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     TcArgs a{};
     a.M = g.M; a.N = g.N; a.bn = g.bn;
     a.nkb = (g.K + KE - 1) / KE;
-    const int gx = (g.N + g.bn - 1) / g.bn, gy = (g.M + BM - 1) / BM;
-    const int tiles = gx * gy;
-    // split-K: at least 4 slices of K per CTA, at most one wave of CTAs
+    a.mt = (g.M + BM - 1) / BM;
+    a.nt = (g.N + g.bn - 1) / g.bn;
+    const int tiles = a.mt * a.nt;
+    // split-K: at least 4 slices of K per unit, until the units fill the SMs
     int splits = 1;
     if (g.epi == TC_EPI_PARTIAL) {
-        splits = std::max(1, std::min(g.max_splits, std::min((a.nkb + 3) / 4, std::max(1, 152 / tiles))));
-    } else if (tiles < 152 && scr && scr->part && scr->counters && scr->n_counters >= tiles) {
-        splits = std::min((a.nkb + 3) / 4, std::max(1, 152 / tiles));
+        splits = std::max(1, std::min(g.max_splits, std::min((a.nkb + 3) / 4, std::max(1, SMS / tiles))));
+    } else if (tiles < SMS && scr && scr->part && scr->counters && scr->n_counters >= 4 * tiles) {
+        splits = std::min((a.nkb + 3) / 4, std::max(1, SMS / tiles));
         const size_t need = (size_t)splits * tiles * BM * MAXBN * sizeof(float);
         if (need > scr->part_bytes) splits = (int)std::max<size_t>(1, scr->part_bytes / ((size_t)tiles * BM * MAXBN * sizeof(float)));
     }
     a.kb_per_split = (a.nkb + splits - 1) / splits;
     splits = (a.nkb + a.kb_per_split - 1) / a.kb_per_split;
+    a.nz = splits;
     if (g.splits_used) *g.splits_used = splits;
+    // reuse the larger operand's panels on consecutive units
+    a.m_fast = (size_t)g.N * (size_t)nb >= (size_t)g.M;
     a.pout = g.pout; a.pstride = g.pstride; a.pld = g.pld;
     // instruction descriptor: D F32 (bits 4-5 = 1), A/B format (bits 7-9, 10-12:
     // BF16 = 1 for kind::f16, TF32 = 2 for kind::tf32), K-major A and B, N>>3 at
@@ -472,7 +598,7 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const CUtensorMap& mb2 = *reinterpret_cast<const CUtensorMap*>((B2 ? B2 : &B)->bytes);
-    dim3 grid(gx, gy, splits);
+    const dim3 grid(grid_of(tiles * splits));
     if (g.kind == 0) {
         if (nb == 1) k_tc_gemm<0, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb2, a);
         else k_tc_gemm<0, 2><<<grid, NT, smem_bytes<2>(), s>>>(ma, mb, mb2, a);
@@ -490,6 +616,10 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     if (set_smem_attr<0, 1>()) return -5;
     TcArgs a{};
     a.M = M; a.N = N; a.bn = bn;
+    a.mt = (M + BM - 1) / BM;
+    a.nt = (N + bn - 1) / bn;
+    a.nz = njobs;
+    a.m_fast = N >= M;
     a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     a.epi = TC_EPI_PARTIAL;
     a.pout = pout; a.pstride = pstride; a.pld = pld;
@@ -498,7 +628,7 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     for (int j = 0; j < njobs; ++j) a.jobs[j] = jobs[j];
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
-    dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM, njobs);
+    const dim3 grid(grid_of(a.mt * a.nt * njobs));
     k_tc_gemm<0, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb, a);
     return 0;
 }

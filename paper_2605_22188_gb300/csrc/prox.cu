@@ -87,8 +87,12 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     const uint32_t* im = a.in_mask + (size_t)b * a.W;
     const uint32_t* om = a.out_mask + (size_t)b * a.W;
 
-    T u[E], vv[E], bo[E];
-    uint32_t valid = 0, fin = 0, fout = 0;
+    using Mk = ElemMask<E>;
+    // up to 16 elements per thread keep v and beta in registers; more re-read
+    // them (the same addresses, from L1/L2) when they are needed again
+    constexpr bool HOLD = E <= 16;
+    T u[E], vv[HOLD ? E : 1], bo[HOLD ? E : 1];
+    Mk valid = 0, fin = 0, fout = 0;
     // gradient: G, or the sum of its split slices (slice-outer so that the E
     // loads of a slice are in flight together; order of the sum fixed)
     T gsum[E];
@@ -113,50 +117,51 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int j = G::rank() + e * NT;
-        u[e] = vv[e] = bo[e] = T(0);
+        u[e] = T(0);
+        if constexpr (HOLD) vv[e] = bo[e] = T(0);
         if (j < p) {
-            valid |= 1u << e;
+            valid |= Mk(1) << e;
             const T v = V[base + j];
-            vv[e] = v;
-            bo[e] = Bm[base + j];
+            if constexpr (HOLD) {
+                vv[e] = v;
+                bo[e] = Bm[base + j];
+            }
             u[e] = v - eta * gsum[e];
-            if ((im[j >> 5] >> (j & 31)) & 1u) fin |= 1u << e;
-            else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= 1u << e;
+            if ((im[j >> 5] >> (j & 31)) & 1u) fin |= Mk(1) << e;
+            else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= Mk(1) << e;
         }
     }
-    const uint32_t ffree = valid & ~fin & ~fout;
+    const Mk ffree = valid & ~fin & ~fout;
     const int kb = a.kbar[b], pf = a.pf[b];
 
     T theta = T(0);
-    uint32_t top = 0;
+    Mk top = 0;
     if (kb > 0 && pf > kb) {
         T amax;
         if constexpr (NT == 32) {
             // one warp per node: tournament selection, already sorted
-            T mag[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) mag[e] = abs(u[e]);
-            top = warp_topk_tournament<E, T>(mag, ffree, kb, sh.sv, sh.si);
+            top = warp_topk_tournament<E, T, Mk>(u, ffree, kb, sh.sv, sh.si);
             T tmax = T(0);
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (((ffree & ~top) >> e) & 1u) tmax = max(tmax, mag[e]);
+                if (bit(ffree & ~top, e)) tmax = max(tmax, abs(u[e]));
             amax = G::max(tmax, sh.red);
         } else {
+            static_assert(E <= 32, "the CTA selection takes 32-bit element masks");
             K key[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) key[e] = mag_key(abs(u[e]));
-            top = group_topk_select<G, E, K>(key, ffree, kb, sh.sel, sh.ired);
+            top = group_topk_select<G, E, K>(key, (uint32_t)ffree, kb, sh.sel, sh.ired);
             if (G::rank() == 0) sh.topcnt = 0;
             G::sync();
             T tmax = T(0);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                if ((top >> e) & 1u) {
+                if (bit(top, e)) {
                     const int s = atomicAdd(&sh.topcnt, 1);
                     sh.topv[s] = abs(u[e]);
                     sh.topi[s] = G::rank() + e * NT;
-                } else if ((ffree >> e) & 1u) {
+                } else if (bit(ffree, e)) {
                     tmax = max(tmax, abs(u[e]));
                 }
             }
@@ -187,7 +192,7 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
                     T part[1] = {T(0)};
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        if (((ffree & ~top) >> e) & 1u) part[0] += max(abs(u[e]) - x, T(0));
+                        if (bit(ffree & ~top, e)) part[0] += max(abs(u[e]) - x, T(0));
                     for (int i = G::rank(); i < kb; i += NT)
                         if (sh.ep[i] < x) part[0] -= max(h - sh.sv[i], T(0));
                     G::template sum<1, T>(part, sh.red);
@@ -203,7 +208,7 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
                 T q[2] = {T(0), T(0)};
 #pragma unroll
                 for (int e = 0; e < E; ++e)
-                    if ((((ffree & ~top) >> e) & 1u) && abs(u[e]) > th) { q[0] += T(1); q[1] += abs(u[e]); }
+                    if (bit(ffree & ~top, e) && abs(u[e]) > th) { q[0] += T(1); q[1] += abs(u[e]); }
                 G::template sum<2, T>(q, sh.red);
                 T nl = q[0], Sl = q[1];
                 for (int it = 0; it < 4 * kMaxK + 64; ++it) {
@@ -212,7 +217,7 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
                     q[0] = q[1] = T(0);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        if ((((ffree & ~top) >> e) & 1u) && abs(u[e]) > tn) { q[0] += T(1); q[1] += abs(u[e]); }
+                        if (bit(ffree & ~top, e) && abs(u[e]) > tn) { q[0] += T(1); q[1] += abs(u[e]); }
                     G::template sum<2, T>(q, sh.red);
                     const bool done = (q[0] == nl);
                     th = tn;
@@ -230,24 +235,27 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         bn[e] = T(0);
-        if (!((valid >> e) & 1u)) continue;
+        if (!bit(valid, e)) continue;
         const T au = abs(u[e]);
         T mag = T(0);
-        if ((fout >> e) & 1u) {
+        if (bit(fout, e)) {
             mag = T(0);
-        } else if ((fin >> e) & 1u) {
+        } else if (bit(fin, e)) {
             mag = min(au / (T(1) + c), M);
         } else if (kb == 0) {
             mag = T(0);
         } else if (pf <= kb) {
             mag = min(au / (T(1) + c), M);
-        } else if ((top >> e) & 1u) {
+        } else if (bit(top, e)) {
             mag = max(min(min(au / (T(1) + c), M), au - theta), T(0));
         } else {
             mag = max(au - theta, T(0));
         }
         bn[e] = u[e] < T(0) ? -mag : mag;
-        dot[0] += (vv[e] - bn[e]) * (bn[e] - bo[e]);
+        T ve, be;
+        if constexpr (HOLD) { ve = vv[e]; be = bo[e]; }
+        else { const int j = G::rank() + e * NT; ve = V[base + j]; be = Bm[base + j]; }
+        dot[0] += (ve - bn[e]) * (bn[e] - be);
     }
     G::template sum<1, T>(dot, sh.red);
     if (G::rank() == 0) {                  // FISTA t update, once per node, in FP64
@@ -262,8 +270,11 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int j = G::rank() + e * NT;
-        if ((valid >> e) & 1u) {
-            const T vn = bn[e] + coef * (bn[e] - bo[e]);
+        if (bit(valid, e)) {
+            T be;
+            if constexpr (HOLD) be = bo[e];
+            else be = Bm[base + j];         // read before this thread overwrites it
+            const T vn = bn[e] + coef * (bn[e] - be);
             Bm[base + j] = bn[e];
             V[base + j] = vn;
             if (a.Vop != nullptr) store_operand(a.Vop, (size_t)b * a.op_ld + j, (float)vn, a.op_bf16);
