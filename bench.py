@@ -7,7 +7,11 @@ X^T*R, masked prox), the FP64 certificate, rounding, re-optimization,
 branching index, pruning and branching.  The workload is the k-sparse
 logistic regression instance n=2000, p=200, k=10, lambda2=1e-2, M=2 with
 node batches of 1024 random fixing patterns (|J1| ~ U{0..k},
-|J0| ~ U{0..p/2}), FP32 products and the FP64 certificate.
+|J0| ~ U{0..p/2}), FP32-accurate products and the FP64 certificate.  The
+products run on the tensor cores as the TF32 hi + lo split (each FP32 operand
+as two TF32 parts, hi*hi + hi*lo + lo*hi, FP32 accumulate; --prec tf32x3);
+the line also times the same steps with FP32 CUDA-core products and with FP64
+products, and the full certified solve of the instance (time to zero gap).
 
   value  nodes certified per second with the instance and the node batches
          already in device memory (kglm_push_nodes_dev);
@@ -48,6 +52,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Fallback peaks of the profiling recipe when MEASURED_PEAKS.json is absent.
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 SMS = 152
+# arithmetic type of the products per engine mode (tf32x3: FP32 values carried as TF32 hi + lo pairs)
+DTYPE = {"fp64": "f64", "fp32": "f32", "tf32x3": "f32", "bf16": "bf16", "tf32": "tf32"}
+PRODUCTS = {"fp64": "fp64 (CUDA cores)", "fp32": "fp32 (CUDA cores)",
+            "tf32x3": "fp32-accurate: TF32 hi+lo split, 3 tcgen05 products, FP32 accumulate",
+            "bf16": "bf16 tcgen05, FP32 accumulate", "tf32": "tf32 tcgen05, FP32 accumulate"}
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 partitions x 32)
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64, nominal
 
@@ -189,15 +198,18 @@ def roofline(stats, prec, pk, workload=WORKLOAD, nodes=1024):
     per_launch_s = s["ms"] / 1e3 / s["launches"]
     work = s["work"] / s["launches"]
     sm_max = pk.get("sm_max_mhz", 2070.0) * 1e6
-    if best in ("gemm_xv_link", "gemm_xtr") and prec in ("bf16", "tf32"):
+    if best in ("gemm_xv_link", "gemm_xtr") and prec in ("bf16", "tf32", "tf32x3"):
         # tensor-core products inside a long step: the sustained BF16 peak (TF32:
-        # times the nominal TF32/BF16 dense ratio 1.1/2.25)
+        # times the nominal TF32/BF16 dense ratio 1.1/2.25; the FP32-accurate
+        # TF32 hi + lo split issues three TF32 products per product: a third of that)
         base = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
-        peak = base if prec == "bf16" else base * 1.1 / 2.25
+        peak = {"bf16": base, "tf32": base * 1.1 / 2.25, "tf32x3": base * 1.1 / 2.25 / 3.0}[prec]
+        note = {"bf16": "BF16 sustained dense peak", "tf32": "TF32 sustained dense peak (BF16 x 1.1/2.25)",
+                "tf32x3": "FP32-accurate 3xTF32 peak (TF32 sustained / 3)"}[prec]
         achieved = work / per_launch_s / 1e12
         return {"kernel": best, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_for(best, workload, prec, nodes),
-                "peak_note": "%s sustained dense peak, %s" % (prec.upper(), pk["source"]),
+                "peak_note": "%s, %s" % (note, pk["source"]),
                 "launches": s["launches"], "avg_launch_us": per_launch_s * 1e6}
     if best in ("gemm_xv_link", "gemm_xtr", "cert_xb", "cert_xtzeta"):
         fp64 = prec == "fp64" or best == "cert_xtzeta"
@@ -356,18 +368,28 @@ def run_ours(args):
     h2d = 4 * (len(ip) + len(ii) + len(op) + len(oi))
     d2h = m * (8 * 3 + 4 * c["k"] + 8 * c["k"] + 4 + 4) + m      # lb, primal, ub, support, beta_re, j*, iters, pruned
 
-    # the same workload with FP64 products (the "mixed vs FP64" comparison of the metric)
+    # the same workload with FP64 products (the "mixed vs FP64" comparison of the
+    # metric) and, for the FP32-accurate split, with FP32 CUDA-core products
+    def other_mode(prec):
+        nonlocal eng
+        e2 = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=prec, max_batch=m,
+                         stream=stream.cuda_stream)
+        eng_keep, eng = eng, e2
+        try:
+            step_dev(0)
+            n2 = max(2, args.steps // 4)
+            dt2 = timed(step_dev, n2)
+        finally:
+            eng = eng_keep
+            e2.close()
+        return {"value": m * n2 / dt2, "unit": UNIT, "steps": n2, "products": PRODUCTS[prec]}
+
     fp64 = None
+    fp32cc = None
     if args.prec != "fp64" and not args.no_fp64:
-        e64 = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=m,
-                          stream=stream.cuda_stream)
-        eng_keep, eng = eng, e64
-        step_dev(0)
-        n64 = max(2, args.steps // 4)
-        dt64 = timed(step_dev, n64)
-        fp64 = {"value": m * n64 / dt64, "unit": UNIT, "steps": n64}
-        eng = eng_keep
-        e64.close()
+        fp64 = other_mode("fp64")
+        if args.prec == "tf32x3":
+            fp32cc = other_mode("fp32")
 
     ttz = None
     if not args.no_ttz:
@@ -380,11 +402,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
         "data": "synthetic",
         "config": {"workload": args.workload, "n": c["n"], "p": c["p"], "k": c["k"], "lambda2": c["lam2"],
                    "M": c["M"], "loss": "logistic" if c["kind"] == synth.LOGISTIC else "least_squares",
-                   "nodes_per_batch": m, "iters": T, "products": args.prec, "certificate": "fp64",
+                   "nodes_per_batch": m, "iters": T, "products": PRODUCTS[args.prec], "certificate": "fp64",
                    "masks": "|J1|~U{0..k}, |J0|~U{0..p/2}", "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": units_e / secs_e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -393,6 +415,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "fp64_products": fp64,
+        "fp32_cuda_core_products": fp32cc,
         "time_to_zero_gap": ttz,
         "phase_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stats.items() if v["ms"] > 0},
     }
@@ -430,6 +453,72 @@ def time_to_zero_gap(X, y, c, prec, stream, m):
     return out
 
 
+SERVING = "c5_serving_mix64"
+
+
+def run_serving(args):
+    """The serving mix: 64 instances (synth.serving_specs) arriving as a Poisson
+    stream, certified by the kglm_server loop with HBM-budgeted admission.
+    value = aggregate nodes evaluated per second over the makespan; latency =
+    time from submission to certified optimality (p50/p99 over the requests
+    that closed their gap within the per-request limit)."""
+    from paper_2605_22188_gb300 import kglm
+    rank, world, local = rank_info()
+    import torch
+    torch.cuda.set_device(local)
+    specs = synth.serving_specs(64, seed=rank)
+    arrivals = synth.poisson_arrivals(len(specs), args.rate, seed=rank)
+    data = []
+    for sp in specs:                       # drawn before the timed region
+        X, y, _ = synth.instance(sp["n"], sp["p"], sp["k"], sp["kind"], rho=sp["rho"], snr=sp["snr"], seed=sp["seed"])
+        data.append((X, y))
+    barrier()
+    srv = kglm.Server(max_active=args.max_active, hbm_budget=0, iters=200, check_every=10,
+                      time_limit_s=args.request_limit, batch_cap=4096)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        ids = []
+        for sp, (X, y), ta in zip(specs, data, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(X, y, sp["k"], sp["lam2"], sp["M"], sp["kind"], prec=args.prec, max_batch=0))
+        srv.drain()
+        wall = time.perf_counter() - t0
+    infos = [srv.info(r) for r in ids]
+    st = srv.stats()
+    srv.close()
+    nodes = sum(i["nodes"] for i in infos)
+    cert = [i for i in infos if i["state"] == kglm.REQ_DONE and i["gap"] <= 1e-6]
+    lat = sorted(i["t_done"] - i["t_submit"] for i in cert)
+    secs, units = reduce_max_sum(wall, float(nodes))
+    pct = lambda q: float(np.percentile(lat, q)) if lat else None
+    if rank != 0:
+        return
+    line = {
+        "metric": "aggregate node bounds/sec and time-to-certified-optimality p50/p99 (serving mix)",
+        "value": units / secs, "unit": "nodes/s", "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": SERVING, "requests": len(specs), "arrival_rate_per_s": args.rate,
+                   "max_active": args.max_active, "request_time_limit_s": args.request_limit,
+                   "products": args.prec, "certificate": "fp64", "iters": 200, "check_every": 10,
+                   "budget_bytes": st["budget"], "parallelism": "replicas" if world > 1 else "single"},
+        "latency_s": {"p50": pct(50), "p99": pct(99), "max": lat[-1] if lat else None, "unit": "s",
+                      "of": "requests certified within the limit"},
+        "certified": len(cert), "not_certified": len(infos) - len(cert),
+        "failed": sum(1 for i in infos if i["state"] == kglm.REQ_FAILED),
+        "worst_gap": max(i["gap"] for i in infos),
+        "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
+        "clocks": clk.summary(),
+        "requests": [{"n": sp["n"], "p": sp["p"], "k": sp["k"], "loss": "lsq" if sp["kind"] == synth.LSQ else "logistic",
+                      "rho": sp["rho"], "batch": i["batch"], "nodes": i["nodes"], "gap": i["gap"],
+                      "t_submit": round(i["t_submit"], 4), "t_admit": round(i["t_admit"], 4),
+                      "t_done": round(i["t_done"], 4)} for sp, i in zip(specs, infos)],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(X, y, c, T, args):
     """The oracle as it stands on the host cores, on a bounded sample of the workload's nodes."""
     from oracle import node as on
@@ -453,6 +542,10 @@ def run_reference(args):
     """The FP64 oracle timed on the host cores: same metric, bounded samples per step."""
     rank, world, _ = rank_info()
     if rank != 0:
+        return
+    if args.workload == SERVING:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed per node-bound workload; "
+                          "the serving mix has no oracle arm (its instances are certified by the engine)"}))
         return
     from oracle import node as on
     c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
@@ -490,11 +583,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "tf32"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "bf16", "tf32", "tf32x3"])
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--nodes", type=int, default=0, help="nodes per batch (0: the workload's)")
     ap.add_argument("--loss", default=None, choices=[None, "lsq", "logistic"],
@@ -504,6 +597,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ttz", action="store_true", help="skip the time-to-zero-gap solves")
+    ap.add_argument("--rate", type=float, default=4.0, help="serving mix: Poisson arrivals per second")
+    ap.add_argument("--max-active", type=int, default=8, help="serving mix: requests solved at once")
+    ap.add_argument("--request-limit", type=float, default=20.0, help="serving mix: seconds per request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank, world, local = rank_info()
@@ -518,6 +614,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args)
+        elif args.workload == SERVING:
+            run_serving(args)
         else:
             run_ours(args)
     finally:

@@ -63,7 +63,9 @@ typedef enum {
     KGLM_FP64 = 0,  /* FP64 products and prox */
     KGLM_FP32 = 1,  /* FP32 products (CUDA cores) and prox */
     KGLM_BF16 = 2,  /* BF16 tensor-core products, FP32 accumulate and prox */
-    KGLM_TF32 = 3   /* TF32 tensor-core products, FP32 accumulate and prox */
+    KGLM_TF32 = 3,  /* TF32 tensor-core products, FP32 accumulate and prox */
+    KGLM_TF32X3 = 4 /* FP32-accurate tensor-core products: every FP32 operand split into
+                       TF32 hi + lo, hi*hi + hi*lo + lo*hi, FP32 accumulate; FP32 prox */
 } kglm_prec;
 
 typedef struct {
@@ -154,7 +156,8 @@ kglm_status kglm_branch(kglm_ctx* ctx, double ub, int32_t* parent, int32_t* bran
                         int32_t* n_parents);
 
 /* Certify the instance with the built-in hybrid BnB loop of Fig. 1: best-bound
- * node queue on the host, batches of up to `batch` nodes evaluated with
+ * node queue on the host, batches of up to `batch` nodes (0: the autotuned
+ * batch, see kglm_autotune) evaluated with
  * `iters` iterations (certificate every `check_every`), incumbent from the
  * batched rounding and re-optimization, pruning and branching on j*.
  * time_limit_s <= 0 means none.  Outputs: *opt the certified objective,
@@ -239,6 +242,28 @@ kglm_status kglm_xtr_noalloc_f32(int32_t m, int32_t n, int32_t p, const float* R
 kglm_status kglm_stats_enable(kglm_ctx* ctx, int32_t enable);
 kglm_status kglm_stats_read(kglm_ctx* ctx, double* ms, int64_t* launches, double* work);
 const char* kglm_phase_name(int32_t phase);
+
+/* Autotuner (project-written; the paper picks the batch by memory, App. E.4,
+ * and shows throughput flattening with the batch size, Fig. 3).  Times node
+ * evaluations (iters FISTA iterations, certificate, re-optimization) of random
+ * fixing patterns (|J1| ~ U{0..k}, |J0| ~ U{0..p/2}; `seed`) on the context:
+ * in the tensor-core modes first the column tile of S = X V (64/128/256), then
+ * the column tile and split-K cap of G = X^T R, at the full batch; then every
+ * power-of-two batch size up to max_batch.  The context keeps the fastest
+ * tiles; the batch chosen is the smallest within 5% of the best node rate
+ * (kglm_solve with batch 0 uses it, tuning first with min(iters, 20) if
+ * needed).  Discards the pushed batch (push again before kglm_evaluate). */
+typedef struct {
+    int32_t batch;            /* chosen node-batch size */
+    int32_t link_tile_cols;   /* column tile of S = X V (tensor-core modes; 0 otherwise) */
+    int32_t grad_tile_cols;   /* column tile of G = X^T R (tensor-core modes; 0 otherwise) */
+    int32_t grad_split_cap;   /* split-K cap of G (tensor-core modes; 0 otherwise) */
+    int32_t timed;            /* configurations timed */
+    int32_t reserved;
+    double nodes_per_s;       /* node evaluations per second at the chosen batch */
+    double best_nodes_per_s;  /* the best rate over all batch sizes */
+} kglm_tune;
+kglm_status kglm_autotune(kglm_ctx* ctx, int32_t iters, uint64_t seed, kglm_tune* out);
 
 /* Device bytes kglm_create allocates for *desc (App. E.4 sizes the batch from
  * the memory per node; admission control needs the whole footprint before

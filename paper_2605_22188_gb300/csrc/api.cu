@@ -54,10 +54,13 @@ struct kglm_ctx {
     // tensor-core products (BF16 / TF32 modes): padded operand copies and TMA maps
     bool tc = false;
     int tc_kind = 0;              // 0: BF16 operands, 1: TF32
+    bool x3 = false;              // FP32-accurate split: TF32 hi + lo of every operand
     int pK = 0, nK = 0;           // operand row strides (multiples of 8 elements)
     void *Xop = nullptr, *Xop_lo = nullptr, *Xtop = nullptr, *Vop = nullptr, *Rop = nullptr;
-    TcMap mA1{}, mB1{}, mB1lo{}, mA2{}, mB2{};
+    float *Xtop_lo = nullptr, *Vop_lo = nullptr, *Rop_lo = nullptr;   // low parts (FP32-accurate mode)
+    TcMap mA1{}, mB1{}, mB1lo{}, mA2{}, mB2{}, mA1lo{}, mA2lo{}, mB2lo{};
     int bn1 = 0, bn2 = 0;
+    int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
     GemmScratch gtc{};
     int* d_tcerr = nullptr;
     float* Gpart = nullptr;       // split slices of X^T R (summed by the prox kernel)
@@ -353,6 +356,7 @@ void iterate(kglm_ctx* c) {
             g.kind = c->tc_kind; g.M = m; g.N = n; g.K = p; g.bn = c->bn1;
             g.epi = c->tc_kind == 0 ? TC_EPI_LINK_BF16 : TC_EPI_LINK_F32;
             g.out = c->Rop; g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
+            if (c->x3) { g.A2 = &c->mA1lo; g.out_lo = c->Rop_lo; }
             if (tc_gemm(c->st, c->mA1, c->mB1, &c->mB1lo, g, &c->gtc) != 0)
                 throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
             check_launch();
@@ -364,7 +368,9 @@ void iterate(kglm_ctx* c) {
             g.epi = TC_EPI_PARTIAL; g.err = c->d_tcerr;
             g.pout = c->Gpart; g.pstride = (size_t)c->mcap * p; g.pld = p;
             g.max_splits = c->gsplit_max; g.splits_used = &c->gsplits;
-            if (tc_gemm(c->st, c->mA2, c->mB2, nullptr, g, &c->gtc) != 0) throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+            if (c->x3) g.A2 = &c->mA2lo;
+            if (tc_gemm(c->st, c->mA2, c->mB2, c->x3 ? &c->mB2lo : nullptr, g, &c->gtc) != 0)
+                throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
             check_launch();
         }
     } else {
@@ -389,7 +395,7 @@ void iterate(kglm_ctx* c) {
         a.gsplits = c->gsplits;
         a.gstride = (size_t)c->mcap * p;
     }
-    a.Vop = c->Vop; a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
+    a.Vop = c->Vop; a.Vop_lo = c->Vop_lo; a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
@@ -589,7 +595,7 @@ void push_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx,
                                            (int)nnz_out, nullptr);
         check_launch();
         c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, slot, c->pool_slots, c->pool, wb,
-                                          c->out_mask, c->B, c->V, c->Vop, c->pK, c->tc_kind == 0, c->tmom, c->active);
+                                          c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK, c->tc_kind == 0, c->tmom, c->active);
         check_launch();
     }
     sync(c);   // host arrays may be pageable and reused by the caller
@@ -618,7 +624,7 @@ void push_dev_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_
                                               c->out_mask, warm_slot, c->pool_slots, c->d_err);
         check_launch();
         c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, warm_slot, c->pool_slots, c->pool, nullptr,
-                                          c->out_mask, c->B, c->V, c->Vop, c->pK, c->tc_kind == 0, c->tmom, c->active);
+                                          c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK, c->tc_kind == 0, c->tmom, c->active);
         check_launch();
     }
     {
@@ -671,7 +677,8 @@ size_t footprint(const kglm_desc& d) {
     size_t est = 0;
     auto add = [&](size_t b) { est += b == 0 ? 16 : b; };
     const size_t n = (size_t)d.n, p = (size_t)d.p, mc = (size_t)d.max_batch, k = (size_t)d.k;
-    const bool f64 = d.prec == KGLM_FP64, tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32;
+    const bool f64 = d.prec == KGLM_FP64, tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32 || d.prec == KGLM_TF32X3;
+    const bool x3 = d.prec == KGLM_TF32X3;
     const size_t ws = f64 ? 8 : 4, W = (p + 31) / 32;
     add(8 * n * p); add(8 * n * p); add(8 * n);
     if (!f64) { add(4 * n * p); add(4 * n * p); add(4 * n); }
@@ -682,7 +689,9 @@ size_t footprint(const kglm_desc& d) {
         const size_t es = d.prec == KGLM_BF16 ? 2 : 4;
         const size_t pK = (p + 7) / 8 * 8, nK = (n + 7) / 8 * 8;
         add(n * pK * es); add(n * pK * es); add(p * nK * es);
+        if (x3) add(4 * p * nK);
         add(mc * pK * es); add(mc * nK * es);
+        if (x3) { add(4 * mc * pK); add(4 * mc * nK); }
         add(tc_scratch_bytes()); add(4 * (size_t)tc_scratch_counters());
         add(4 * (size_t)tc_split_cap((int)mc, (int)p) * mc * p);   // split slices of X^T R
         add(4);
@@ -888,6 +897,146 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
         if (best_sup[r] >= 0) out.beta[best_sup[r]] = best_coef[r];
 }
 
+// ---- autotuner: tile shapes of the tensor-core products and the batch size
+
+// Column tiles of the products: rebuild the B operands' maps (box rows = tile).
+void set_tiles(kglm_ctx* c, int bn1, int bn2) {
+    const int ob = c->tc_kind == 0;
+    if (tc_make_map(&c->mB1, c->Xop, ob, c->n, c->p, c->pK, bn1) ||
+        tc_make_map(&c->mB1lo, c->Xop_lo, ob, c->n, c->p, c->pK, bn1) ||
+        tc_make_map(&c->mB2, c->Xtop, ob, c->p, c->n, c->nK, bn2) ||
+        (c->x3 && tc_make_map(&c->mB2lo, c->Xtop_lo, 0, c->p, c->n, c->nK, bn2)))
+        throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed while tuning the tiles"};
+    c->bn1 = bn1;
+    c->bn2 = bn2;
+    destroy_graphs(c);                     // captured launches hold the old maps
+}
+
+// Random fixing patterns for timing (|J1| ~ U{0..k}, |J0| ~ U{0..p/2}), from a
+// 64-bit linear congruential generator seeded by the caller.
+struct TuneNodes {
+    std::vector<int> in_ptr{0}, in_idx, out_ptr{0}, out_idx;
+};
+TuneNodes tune_nodes(int m, int p, int k, uint64_t seed) {
+    TuneNodes t;
+    uint64_t x = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto next = [&](uint32_t bound) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        return (uint32_t)((x >> 33) % bound);
+    };
+    std::vector<int> perm(p);
+    for (int b = 0; b < m; ++b) {
+        for (int j = 0; j < p; ++j) perm[j] = j;
+        const int n1 = (int)next((uint32_t)k + 1);
+        const int n0 = std::min((int)next((uint32_t)(p / 2) + 1), p - n1);
+        for (int i = 0; i < n1 + n0; ++i) std::swap(perm[i], perm[i + (int)next((uint32_t)(p - i))]);
+        std::sort(perm.begin(), perm.begin() + n1);
+        std::sort(perm.begin() + n1, perm.begin() + n1 + n0);
+        t.in_idx.insert(t.in_idx.end(), perm.begin(), perm.begin() + n1);
+        t.out_idx.insert(t.out_idx.end(), perm.begin() + n1, perm.begin() + n1 + n0);
+        t.in_ptr.push_back((int)t.in_idx.size());
+        t.out_ptr.push_back((int)t.out_idx.size());
+    }
+    return t;
+}
+
+// Device milliseconds of one node evaluation (iters iterations, certificate,
+// re-optimization) of the first m tuning nodes: best of `reps` runs after one
+// untimed run (graph capture).
+double time_eval(kglm_ctx* c, const TuneNodes& t, int m, int iters, int reps) {
+    std::vector<int> ip(t.in_ptr.begin(), t.in_ptr.begin() + m + 1), op(t.out_ptr.begin(), t.out_ptr.begin() + m + 1);
+    push_impl(c, m, ip.data(), t.in_idx.data(), op.data(), t.out_idx.data(), nullptr, nullptr);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = INFINITY;
+    try {
+        for (int r = 0; r <= reps; ++r) {
+            c->ub_inc = INFINITY;
+            CK(cudaEventRecord(e0, c->st));
+            evaluate_impl(c, iters, 0);
+            CK(cudaEventRecord(e1, c->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) best = std::min(best, (double)ms);
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
+    REQ(iters >= 1, "iters must be >= 1");
+    const int mc = c->mcap;
+    const TuneNodes t = tune_nodes(mc, c->p, c->k, seed);
+    int timed = 0;
+    kglm_tune r{};
+    if (c->tc) {
+        // coordinate descent at the full batch: the link product's column tile,
+        // then the gradient product's column tile and split cap
+        const int cap = c->gsplit_max;
+        std::vector<int> t1;
+        for (int bn : {64, 128, 256})
+            if (bn <= tc_tile_cols(c->n)) t1.push_back(bn);
+        if (t1.empty()) t1.push_back(tc_tile_cols(c->n));
+        std::vector<int> t2{tc_tile_cols(c->p)};
+        if (c->p > 128) t2.push_back(128);
+        if (c->p > 64) t2.push_back(64);
+        double best = INFINITY;
+        int b1 = c->bn1, b2 = c->bn2, bs = cap;
+        for (int bn : t1) {
+            set_tiles(c, bn, b2);
+            const double ms = time_eval(c, t, mc, iters, 2);
+            ++timed;
+            if (ms < best) { best = ms; b1 = bn; }
+        }
+        for (int bn : t2)
+            for (int sc = 1; sc <= cap; sc *= 2) {
+                set_tiles(c, b1, bn);
+                c->gsplit_max = sc;
+                const double ms = time_eval(c, t, mc, iters, 2);
+                ++timed;
+                if (ms < best) { best = ms; b2 = bn; bs = sc; }
+            }
+        set_tiles(c, b1, b2);
+        c->gsplit_max = bs;
+        r.link_tile_cols = b1;
+        r.grad_tile_cols = b2;
+        r.grad_split_cap = bs;
+    }
+    // batch size: node bounds per second at each power of two; the smallest
+    // within 5% of the best (larger batches evaluate nodes the search may
+    // never need, Fig. 3's plateau)
+    std::vector<std::pair<int, double>> rates;
+    for (int m = std::min(64, mc); m <= mc; m *= 2) {
+        const double ms = time_eval(c, t, m, iters, 1);
+        ++timed;
+        rates.push_back({m, m / (ms * 1e-3)});
+        if (m == mc) break;
+        if (m * 2 > mc && m != mc) {
+            const double ms2 = time_eval(c, t, mc, iters, 1);
+            ++timed;
+            rates.push_back({mc, mc / (ms2 * 1e-3)});
+            break;
+        }
+    }
+    double top = 0.0;
+    for (auto& q : rates) top = std::max(top, q.second);
+    for (auto& q : rates)
+        if (q.second >= 0.95 * top) { r.batch = q.first; r.nodes_per_s = q.second; break; }
+    r.best_nodes_per_s = top;
+    r.timed = timed;
+    c->tuned_batch = r.batch;
+    c->pushed = c->evaluated = false;
+    if (out) *out = r;
+}
+
 }  // namespace
 
 namespace kglm {
@@ -946,15 +1095,17 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         REQ(d.lambda2 > 0 && isfinite(d.lambda2), "lambda2 must be positive");
         REQ(d.M > 0 && isfinite(d.M), "M must be positive");
         REQ(d.loss == KGLM_LSQ || d.loss == KGLM_LOGISTIC, "unknown loss");
-        REQ(d.prec == KGLM_FP64 || d.prec == KGLM_FP32 || d.prec == KGLM_BF16 || d.prec == KGLM_TF32,
+        REQ(d.prec == KGLM_FP64 || d.prec == KGLM_FP32 || d.prec == KGLM_BF16 || d.prec == KGLM_TF32 ||
+                d.prec == KGLM_TF32X3,
             "unknown precision");
         REQ(d.max_batch >= 1, "max_batch must be >= 1");
         REQ(d.p <= (d.prec == KGLM_FP64 ? 4096 : 8192), "p above the prox kernel limit for this precision");
         c->d = d;
         c->n = (int)d.n; c->p = (int)d.p; c->k = d.k; c->kind = d.loss; c->prec = d.prec;
         c->f64 = d.prec == KGLM_FP64;
-        c->tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32;
+        c->tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32 || d.prec == KGLM_TF32X3;
         c->tc_kind = d.prec == KGLM_BF16 ? 0 : 1;
+        c->x3 = d.prec == KGLM_TF32X3;
         c->W = (c->p + 31) / 32;
         c->lam2 = d.lambda2; c->M = d.M;
         c->gap_tol = d.gap_tol > 0 ? d.gap_tol : 1e-6;
@@ -1011,14 +1162,21 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->Xop = dalloc(c, n * c->pK * es);
             c->Xop_lo = dalloc(c, n * c->pK * es);
             c->Xtop = dalloc(c, p * c->nK * es);
+            if (c->x3) c->Xtop_lo = dalloc_t<float>(c, p * c->nK);
             convert_pad(c->st, c->X64, (int)n, (int)p, (int)p, c->Xop, c->pK, ob, c->Xop_lo);
-            convert_pad(c->st, c->Xt64, (int)p, (int)n, (int)n, c->Xtop, c->nK, ob);
+            convert_pad(c->st, c->Xt64, (int)p, (int)n, (int)n, c->Xtop, c->nK, ob, c->Xtop_lo);
             check_launch();
             const size_t mc = (size_t)d.max_batch;
             c->Vop = dalloc(c, mc * c->pK * es);
             c->Rop = dalloc(c, mc * c->nK * es);
             CK(cudaMemsetAsync(c->Vop, 0, mc * c->pK * es, c->st));
             CK(cudaMemsetAsync(c->Rop, 0, mc * c->nK * es, c->st));
+            if (c->x3) {
+                c->Vop_lo = dalloc_t<float>(c, mc * c->pK);
+                c->Rop_lo = dalloc_t<float>(c, mc * c->nK);
+                CK(cudaMemsetAsync(c->Vop_lo, 0, mc * c->pK * 4, c->st));
+                CK(cudaMemsetAsync(c->Rop_lo, 0, mc * c->nK * 4, c->st));
+            }
             c->bn1 = tc_tile_cols_wide((int)n);
             c->bn2 = tc_tile_cols((int)p);
             if (tc_make_map(&c->mA1, c->Vop, ob, (int)mc, (int)p, c->pK, 128) ||
@@ -1027,6 +1185,10 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
                 tc_make_map(&c->mA2, c->Rop, ob, (int)mc, (int)n, c->nK, 128) ||
                 tc_make_map(&c->mB2, c->Xtop, ob, (int)p, (int)n, c->nK, c->bn2))
                 throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for an operand"};
+            if (c->x3 && (tc_make_map(&c->mA1lo, c->Vop_lo, 0, (int)mc, (int)p, c->pK, 128) ||
+                          tc_make_map(&c->mA2lo, c->Rop_lo, 0, (int)mc, (int)n, c->nK, 128) ||
+                          tc_make_map(&c->mB2lo, c->Xtop_lo, 0, (int)p, (int)n, c->nK, c->bn2)))
+                throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for a low-part operand"};
             if (tc_prepare() != 0) throw Fail{KGLM_ECUDA, "tensor-core kernels: shared memory attribute refused"};
             c->gtc.part_bytes = tc_scratch_bytes();
             c->gtc.part = dalloc(c, c->gtc.part_bytes);
@@ -1149,12 +1311,14 @@ kglm_status kglm_xtr(kglm_ctx* ctx, int32_t m, const void* R, void* G) {
         REQ(R && G, "R and G are required");
         Scope sc(ctx, PH_GEMM_GRAD, 1, 2.0 * ctx->n * (double)m * ctx->p);
         if (ctx->tc) {
-            convert_pad_f32(ctx->st, (const float*)R, m, ctx->n, ctx->Rop, ctx->nK, ctx->tc_kind == 0);
+            convert_pad_f32(ctx->st, (const float*)R, m, ctx->n, ctx->Rop, ctx->nK, ctx->tc_kind == 0, ctx->Rop_lo);
             check_launch();
             TcGemm g{};
             g.kind = ctx->tc_kind; g.M = m; g.N = ctx->p; g.K = ctx->n; g.bn = ctx->bn2;
             g.epi = TC_EPI_STORE_F32; g.out = G; g.ldo = ctx->p; g.err = ctx->d_tcerr;
-            if (tc_gemm(ctx->st, ctx->mA2, ctx->mB2, nullptr, g, &ctx->gtc) != 0) throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+            if (ctx->x3) g.A2 = &ctx->mA2lo;
+            if (tc_gemm(ctx->st, ctx->mA2, ctx->mB2, ctx->x3 ? &ctx->mB2lo : nullptr, g, &ctx->gtc) != 0)
+                throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
             check_launch();
             sync(ctx);
             check_tc_error(ctx);
@@ -1340,6 +1504,10 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
                        int64_t* batches) {
     if (!ctx) return KGLM_EINVAL;
     return guarded(ctx, [&] {
+        if (batch == 0) {
+            if (ctx->tuned_batch == 0) autotune_impl(ctx, std::min(iters, 20), 1, nullptr);
+            batch = ctx->tuned_batch;
+        }
         SolveOut o;
         solve_impl(ctx, batch, iters, check_every, time_limit_s, nullptr, o);
         if (opt) *opt = o.opt;
@@ -1359,7 +1527,7 @@ static kglm_status check_desc(const kglm_desc* d) {
     if (!(d->k >= 1 && d->k <= KGLM_MAX_K && d->k <= d->p)) return KGLM_EINVAL;
     if (!(d->lambda2 > 0 && d->M > 0)) return KGLM_EINVAL;
     if (d->loss != KGLM_LSQ && d->loss != KGLM_LOGISTIC) return KGLM_EINVAL;
-    if (d->prec < KGLM_FP64 || d->prec > KGLM_TF32) return KGLM_EINVAL;
+    if (d->prec < KGLM_FP64 || d->prec > KGLM_TF32X3) return KGLM_EINVAL;
     if (d->max_batch < 1) return KGLM_EINVAL;
     if (d->p > (d->prec == KGLM_FP64 ? 4096 : 8192)) return KGLM_EINVAL;
     return KGLM_OK;
@@ -1394,6 +1562,11 @@ kglm_status kglm_suggest_batch(const kglm_desc* desc, int64_t budget, int32_t ca
     }
     *batch = best;
     return KGLM_OK;
+}
+
+kglm_status kglm_autotune(kglm_ctx* ctx, int32_t iters, uint64_t seed, kglm_tune* out) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] { autotune_impl(ctx, iters, seed, out); });
 }
 
 }  // extern "C"

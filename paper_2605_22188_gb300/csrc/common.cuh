@@ -63,6 +63,17 @@ __device__ __forceinline__ void store_operand(void* base, size_t i, float v, int
     if (bf16) static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16(v);
     else static_cast<float*>(base)[i] = to_tf32(v);
 }
+// Operand copy of v for the tensor-core products; with lo != NULL (TF32 only)
+// also the TF32 low part v - hi, so that hi + lo carries v to ~22 bits.
+__device__ __forceinline__ void store_operand2(void* base, float* lo, size_t i, float v, int bf16) {
+    if (bf16) {
+        static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16(v);
+    } else {
+        const float h = to_tf32(v);
+        static_cast<float*>(base)[i] = h;
+        if (lo) lo[i] = to_tf32(v - h);
+    }
+}
 
 // ------------------------------------------------------------------ reductions
 

@@ -70,6 +70,8 @@ struct TcGemm {
     int pld;
     int max_splits;  // TC_EPI_PARTIAL: upper bound on the number of slices
     int* splits_used;
+    const TcMap* A2; // TF32 low part of A (out = (A + A2)(B + B2)^T less A2 B2^T); needs kind 1 and B2
+    float* out_lo;   // TC_EPI_LINK_F32: TF32 low part of each output (NULL: none)
 };
 // TMA map of a row-major rows x cols matrix (row stride ld elements) with
 // 128-byte boxes along cols and box_rows rows.  0 on success.
@@ -128,6 +130,7 @@ struct ProxArgs {
     void* V;              // extrapolated point v (in: v_k, out: v_{k+1})
     void* B;              // iterate beta (in: beta_k, out: beta_{k+1})
     void* Vop;            // optional copy of V for the tensor-core products (row stride op_ld)
+    float* Vop_lo;        // its TF32 low part (FP32-accurate mode), or NULL
     int op_ld;
     int op_bf16;          // 1: BF16, 0: FP32 rounded to TF32 (nearest)
     const uint32_t* in_mask;
@@ -209,14 +212,16 @@ int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out
                     const int* out_ptr, const uint32_t* in_mask, const uint32_t* out_mask, const int* slot,
                     int nslots, int* err);
 int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
-                const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, int op_ld,
+                const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, float* Vop_lo, int op_ld,
                 int op_bf16, double* tmom, int* active);
 // rows x cols FP64 (row stride ld_in) -> BF16 or TF32-in-FP32 with row stride ld_out, zero padded;
 // with lo != NULL also the low part bf16/tf32(x - hi) into lo.
 void convert_pad(cudaStream_t s, const double* in, int rows, int cols, int ld_in, void* out, int ld_out, int to_bf16,
                  void* lo = nullptr);
 // rows x cols FP32 (stride cols) -> BF16 or TF32-in-FP32 with row stride ld_out
-void convert_pad_f32(cudaStream_t s, const float* in, int rows, int cols, void* out, int ld_out, int to_bf16);
+// (with lo != NULL, TF32 only: also the low parts)
+void convert_pad_f32(cudaStream_t s, const float* in, int rows, int cols, void* out, int ld_out, int to_bf16,
+                     float* lo = nullptr);
 void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots,
                 const void* B, void* pool);
 // a8: pruned[b] = lb[b] >= thr ; alive[b] &= !pruned

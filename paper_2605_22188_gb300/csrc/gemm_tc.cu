@@ -32,6 +32,11 @@
 // E^T E ~ n u^2 E[x^2]: a ridge shift comparable to lambda2 at n in the
 // thousands.  FP32 operands reach kind::tf32 rounded to nearest (the tensor
 // core would otherwise truncate them, a bias toward zero).
+// With A also given as hi + lo (NA = 2, TF32 only) a K slice takes three
+// products, A_hi B_hi + A_hi B_lo + A_lo B_hi: each FP32 operand is carried to
+// ~22 bits and the dropped A_lo B_lo term is below 2^-22 of the product, so
+// the result has the accuracy of an FP32 product (the FP32-accurate mode);
+// its link epilogue writes R as the same hi + lo pair.
 // Split-K with the plain or link epilogue: partial tiles go to scratch and
 // the last epilogue warp to finish a 32-row slab of a tile (arrival counter
 // per slab) sums its partials in fixed order; no warp waits on another.
@@ -59,10 +64,12 @@ constexpr uint32_t TMEM_COLS = 512;     // two accumulators of up to 256 columns
 constexpr int TPAD = 36;                // transpose buffer row: 32 + 4 (16-byte rows, no 128-bit bank conflicts)
 constexpr int SMS = 152;
 // NB = 1: one B operand, four stages; NB = 2: B given as hi + lo parts
-// (both multiplied into the same accumulator), two stages.
-template <int NB> constexpr int stages() { return NB == 1 ? 4 : 2; }
+// (both multiplied into the same accumulator), two stages.  NA = 2: A also
+// as hi + lo (the FP32-accurate split: A_hi B_hi + A_hi B_lo + A_lo B_hi).
+template <int NB, int NA> constexpr int stages() { return NB == 1 && NA == 1 ? 4 : 2; }
 constexpr size_t kEpiBytes = 4 * 32 * TPAD * sizeof(float);
-template <int NB> constexpr size_t smem_bytes() { return 1024 + stages<NB>() * (STAGE_A + NB * STAGE_B) + kEpiBytes + 256; }
+template <int NB, int NA>
+constexpr size_t smem_bytes() { return 1024 + stages<NB, NA>() * (NA * STAGE_A + NB * STAGE_B) + kEpiBytes + 256; }
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // try_wait rounds before a wait gives up
 
 // ------------------------------------------------------------------ arguments and epilogues
@@ -80,6 +87,7 @@ struct TcArgs {
     size_t pstride;
     int pld;
     void* out;
+    float* out_lo;            // TC_EPI_LINK_F32: TF32 low part of each output (NULL: none)
     int ldo;
     const float* y;
     int loss;
@@ -110,7 +118,9 @@ __device__ __forceinline__ void tc_store(const TcArgs& a, int r, int c, float v,
         static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = v;
     } else if (a.epi == TC_EPI_LINK_F32) {
         const float d = dloss_fast(v, yc, a.loss);
-        static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = a.round_tf32 ? tf32_rn(d) : d;
+        const float h = a.round_tf32 ? tf32_rn(d) : d;
+        static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = h;
+        if (a.out_lo) a.out_lo[(size_t)r * a.ldo + c] = tf32_rn(d - h);
     } else {
         static_cast<__nv_bfloat16*>(a.out)[(size_t)r * a.ldo + c] = __float2bfloat16(dloss_fast(v, yc, a.loss));
     }
@@ -256,16 +266,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int KIND, int NB>
+template <int KIND, int NB, int NA>
 __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB,
                                                    const __grid_constant__ CUtensorMap tmB2,
+                                                   const __grid_constant__ CUtensorMap tmA2,
                                                    const __grid_constant__ TcArgs a) {
-    constexpr int STAGES = stages<NB>();
+    constexpr int STAGES = stages<NB, NA>();
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + STAGES * STAGE_A;                    // stage s: B at s, B2 (NB = 2) at STAGES + s
+    uint8_t* sA = smem;                                       // stage s: A at s, A2 (NA = 2) at STAGES + s
+    uint8_t* sB = smem + NA * STAGES * STAGE_A;               // stage s: B at s, B2 (NB = 2) at STAGES + s
     float* sT = reinterpret_cast<float*>(sB + NB * STAGES * STAGE_B);              // 4 x 32 x TPAD
     uint64_t* bars = reinterpret_cast<uint64_t*>(sT + 4 * 32 * TPAD);
     // bars: full[S], empty[S], tfull[2], tempty[2], drain
@@ -279,7 +290,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = KIND == 0 ? 64 : 32;          // elements per 128-byte row
-    const uint32_t stage_bytes = STAGE_A + (uint32_t)NB * a.bn * ROWB;
+    const uint32_t stage_bytes = (uint32_t)NA * STAGE_A + (uint32_t)NB * a.bn * ROWB;
     const int units = a.mt * a.nt * a.nz;
 
     if (threadIdx.x == 0) {
@@ -314,6 +325,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     tma_load_2d(smem_u32(sA + s * STAGE_A), &tmA, kxa, m0, fb);
                     tma_load_2d(smem_u32(sB + s * STAGE_B), &tmB, kxb, n0, fb);
                     if (NB == 2) tma_load_2d(smem_u32(sB + (STAGES + s) * STAGE_B), &tmB2, kxb, n0, fb);
+                    if (NA == 2) tma_load_2d(smem_u32(sA + (STAGES + s) * STAGE_A), &tmA2, kxa, m0, fb);
                     issued = g + 1;
                 }
             }
@@ -343,6 +355,10 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                         if (NB == 2) {
                             const uint32_t b2 = smem_u32(sB + (STAGES + s) * STAGE_B);
                             umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(b2 + kk * 32), a.idesc, 1u);
+                        }
+                        if (NA == 2) {
+                            const uint32_t a2 = smem_u32(sA + (STAGES + s) * STAGE_A);
+                            umma<KIND>(acc, smem_desc(a2 + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
                         }
                     }
                     umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
@@ -384,10 +400,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     // link on the row-per-lane values; y of column c0 + j from lane j
                     const float yl = (c0 + lane < a.N) ? __ldg(a.y + c0 + lane) : 0.f;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float d = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
-                        v[j] = (a.epi == TC_EPI_LINK_F32 && a.round_tf32) ? tf32_rn(d) : d;
-                    }
+                    for (int j = 0; j < 32; ++j) v[j] = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
                 }
 #pragma unroll
                 for (int j = 0; j < 32; j += 4)                         // row lane, columns j..j+3
@@ -432,21 +445,38 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     size_t ld;
                     if (a.epi == TC_EPI_PARTIAL) { o = a.pout + (size_t)w.slice * a.pstride; ld = (size_t)a.pld; }
                     else { o = static_cast<float*>(a.out); ld = (size_t)a.ldo; }
+                    const bool link = a.epi == TC_EPI_LINK_F32;
+                    const bool rnd = link && a.round_tf32;
+                    float* ol = link ? a.out_lo : nullptr;
                     const int q = lane & 7, r0 = lane >> 3;
-                    const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(o) % 16) == 0 && c0 + 4 * q + 4 <= a.N;
+                    const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(o) % 16) == 0 &&
+                                     (ol == nullptr || (reinterpret_cast<uintptr_t>(ol) % 16) == 0) && c0 + 4 * q + 4 <= a.N;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int r = r0 + 4 * i, row = rbase + r;
                         if (row >= a.M) continue;
                         const float4 x = *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * q);
+                        float xs[4] = {x.x, x.y, x.z, x.w}, ls[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (rnd) {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const float h = tf32_rn(xs[t]);
+                                ls[t] = tf32_rn(xs[t] - h);
+                                xs[t] = h;
+                            }
+                        }
                         float* dst = o + (size_t)row * ld + c0 + 4 * q;
+                        float* dlo = ol ? ol + (size_t)row * ld + c0 + 4 * q : nullptr;
                         if (vec) {
-                            *reinterpret_cast<float4*>(dst) = x;
+                            *reinterpret_cast<float4*>(dst) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+                            if (dlo) *reinterpret_cast<float4*>(dlo) = make_float4(ls[0], ls[1], ls[2], ls[3]);
                         } else {
-                            const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                             for (int t = 0; t < 4; ++t)
-                                if (c0 + 4 * q + t < a.N) dst[t] = xs[t];
+                                if (c0 + 4 * q + t < a.N) {
+                                    dst[t] = xs[t];
+                                    if (dlo) dlo[t] = ls[t];
+                                }
                         }
                     }
                 }
@@ -507,12 +537,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int KIND, int NB>
+template <int KIND, int NB, int NA>
 int set_smem_attr() {
     static int done = 0;
     if (!done) {
-        if (cudaFuncSetAttribute(k_tc_gemm<KIND, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<NB>()) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_tc_gemm<KIND, NB, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<NB, NA>()) != cudaSuccess)
             return -1;
         done = 1;
     }
@@ -522,7 +552,8 @@ int set_smem_attr() {
 }  // namespace
 
 int tc_prepare() {
-    return set_smem_attr<0, 1>() | set_smem_attr<0, 2>() | set_smem_attr<1, 1>() | set_smem_attr<1, 2>();
+    return set_smem_attr<0, 1, 1>() | set_smem_attr<0, 2, 1>() | set_smem_attr<1, 1, 1>() | set_smem_attr<1, 2, 1>() |
+           set_smem_attr<1, 2, 2>();
 }
 
 int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, int ld, int box_rows) {
@@ -558,9 +589,11 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
             const GemmScratch* scr) {
     if (g.M <= 0 || g.N <= 0) return 0;
     if (g.bn < 16 || g.bn > MAXBN || g.bn % 16 != 0) return -4;
-    const int nb = B2 ? 2 : 1;
-    const int rc = g.kind == 0 ? (nb == 1 ? set_smem_attr<0, 1>() : set_smem_attr<0, 2>())
-                               : (nb == 1 ? set_smem_attr<1, 1>() : set_smem_attr<1, 2>());
+    const int nb = B2 ? 2 : 1, na = g.A2 ? 2 : 1;
+    if (na == 2 && (g.kind != 1 || nb != 2)) return -6;     // the split is TF32 hi/lo on both sides
+    const int rc = na == 2 ? set_smem_attr<1, 2, 2>()
+                 : g.kind == 0 ? (nb == 1 ? set_smem_attr<0, 1, 1>() : set_smem_attr<0, 2, 1>())
+                               : (nb == 1 ? set_smem_attr<1, 1, 1>() : set_smem_attr<1, 2, 1>());
     if (rc) return -5;
     const int KE = g.kind == 0 ? 64 : 32;
     TcArgs a{};
@@ -590,7 +623,7 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     // bit 17, M>>4 at bit 24
     const uint32_t ab = g.kind == 0 ? 1u : 2u;
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(g.bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    a.epi = g.epi; a.out = g.out; a.ldo = g.ldo; a.y = g.y; a.loss = g.loss;
+    a.epi = g.epi; a.out = g.out; a.out_lo = g.out_lo; a.ldo = g.ldo; a.y = g.y; a.loss = g.loss;
     a.round_tf32 = g.kind == 1;
     a.part = splits > 1 ? static_cast<float*>(scr->part) : nullptr;
     a.counters = splits > 1 ? scr->counters : nullptr;
@@ -598,13 +631,16 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const CUtensorMap& mb2 = *reinterpret_cast<const CUtensorMap*>((B2 ? B2 : &B)->bytes);
+    const CUtensorMap& ma2 = *reinterpret_cast<const CUtensorMap*>((g.A2 ? g.A2 : &A)->bytes);
     const dim3 grid(grid_of(tiles * splits));
-    if (g.kind == 0) {
-        if (nb == 1) k_tc_gemm<0, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb2, a);
-        else k_tc_gemm<0, 2><<<grid, NT, smem_bytes<2>(), s>>>(ma, mb, mb2, a);
+    if (na == 2) {
+        k_tc_gemm<1, 2, 2><<<grid, NT, smem_bytes<2, 2>(), s>>>(ma, mb, mb2, ma2, a);
+    } else if (g.kind == 0) {
+        if (nb == 1) k_tc_gemm<0, 1, 1><<<grid, NT, smem_bytes<1, 1>(), s>>>(ma, mb, mb2, ma, a);
+        else k_tc_gemm<0, 2, 1><<<grid, NT, smem_bytes<2, 1>(), s>>>(ma, mb, mb2, ma, a);
     } else {
-        if (nb == 1) k_tc_gemm<1, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb2, a);
-        else k_tc_gemm<1, 2><<<grid, NT, smem_bytes<2>(), s>>>(ma, mb, mb2, a);
+        if (nb == 1) k_tc_gemm<1, 1, 1><<<grid, NT, smem_bytes<1, 1>(), s>>>(ma, mb, mb2, ma, a);
+        else k_tc_gemm<1, 2, 1><<<grid, NT, smem_bytes<2, 1>(), s>>>(ma, mb, mb2, ma, a);
     }
     return 0;
 }
@@ -613,7 +649,7 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
                  int njobs, float* pout, size_t pstride, int pld, int* err) {
     if (M <= 0 || N <= 0 || njobs <= 0) return 0;
     if (bn < 16 || bn > MAXBN || bn % 16 != 0 || njobs > kTcMaxJobs) return -4;
-    if (set_smem_attr<0, 1>()) return -5;
+    if (set_smem_attr<0, 1, 1>()) return -5;
     TcArgs a{};
     a.M = M; a.N = N; a.bn = bn;
     a.mt = (M + BM - 1) / BM;
@@ -629,7 +665,7 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const dim3 grid(grid_of(a.mt * a.nt * njobs));
-    k_tc_gemm<0, 1><<<grid, NT, smem_bytes<1>(), s>>>(ma, mb, mb, a);
+    k_tc_gemm<0, 1, 1><<<grid, NT, smem_bytes<1, 1>(), s>>>(ma, mb, mb, ma, a);
     return 0;
 }
 

@@ -67,7 +67,7 @@ __global__ void k_counts(int m, int p, int k, const int* in_ptr, const int* out_
 
 template <typename T>
 __global__ void k_warm(int m, int p, int W, const int* slot, int nslots, const T* pool, const double* warmB,
-                       const uint32_t* out_mask, T* B, T* V, void* Vop, int op_ld, int op_bf16) {
+                       const uint32_t* out_mask, T* B, T* V, void* Vop, float* Vop_lo, int op_ld, int op_bf16) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)m * p) return;
     const int b = (int)(t / p), j = (int)(t % p);
@@ -78,7 +78,7 @@ __global__ void k_warm(int m, int p, int W, const int* slot, int nslots, const T
     if ((out_mask[(size_t)b * W + (j >> 5)] >> (j & 31)) & 1u) w = T(0);
     B[t] = w;
     V[t] = w;
-    if (Vop) store_operand(Vop, (size_t)b * op_ld + j, (float)w, op_bf16);
+    if (Vop) store_operand2(Vop, Vop_lo, (size_t)b * op_ld + j, (float)w, op_bf16);
 }
 
 // hi = operand(x), lo = operand(x - hi) (x - hi is exact in FP64)
@@ -105,11 +105,12 @@ __global__ void k_convert_pad(const double* in, int rows, int cols, int ld_in, v
     }
 }
 
-__global__ void k_convert_pad_f32(const float* in, int rows, int cols, void* out, int ld_out, int to_bf16) {
+__global__ void k_convert_pad_f32(const float* in, int rows, int cols, void* out, int ld_out, int to_bf16,
+                                  float* lo) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)rows * ld_out) return;
     const int r = (int)(t / ld_out), c = (int)(t % ld_out);
-    store_operand(out, t, c < cols ? in[(size_t)r * cols + c] : 0.f, to_bf16);
+    store_operand2(out, lo, t, c < cols ? in[(size_t)r * cols + c] : 0.f, to_bf16);
 }
 
 __global__ void k_node_init(int m, double t0, double* tmom, int* active) {
@@ -190,15 +191,15 @@ int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out
 }
 
 int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
-                const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, int op_ld,
+                const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, float* Vop_lo, int op_ld,
                 int op_bf16, double* tmom, int* active) {
     const size_t n = (size_t)m * p;
     if (is_f64)
         k_warm<double><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const double*)pool, warmB, out_mask,
-                                                      (double*)B, (double*)V, Vop, op_ld, op_bf16);
+                                                      (double*)B, (double*)V, Vop, Vop_lo, op_ld, op_bf16);
     else
         k_warm<float><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const float*)pool, warmB, out_mask,
-                                                     (float*)B, (float*)V, Vop, op_ld, op_bf16);
+                                                     (float*)B, (float*)V, Vop, Vop_lo, op_ld, op_bf16);
     // t' = (1 + sqrt(5)) / 2: the FISTA t after t_0 = 1
     k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 0.5 * (1.0 + sqrt(5.0)), tmom, active);
     return 2;
@@ -210,9 +211,10 @@ void convert_pad(cudaStream_t s, const double* in, int rows, int cols, int ld_in
     if (n) k_convert_pad<<<blocks(n, 256), 256, 0, s>>>(in, rows, cols, ld_in, out, ld_out, to_bf16, lo);
 }
 
-void convert_pad_f32(cudaStream_t s, const float* in, int rows, int cols, void* out, int ld_out, int to_bf16) {
+void convert_pad_f32(cudaStream_t s, const float* in, int rows, int cols, void* out, int ld_out, int to_bf16,
+                     float* lo) {
     const size_t n = (size_t)rows * ld_out;
-    if (n) k_convert_pad_f32<<<blocks(n, 256), 256, 0, s>>>(in, rows, cols, out, ld_out, to_bf16);
+    if (n) k_convert_pad_f32<<<blocks(n, 256), 256, 0, s>>>(in, rows, cols, out, ld_out, to_bf16, lo);
 }
 
 void pool_store(cudaStream_t s, int count, int p, int is_f64, const int* rows, const int* slots, const void* B,

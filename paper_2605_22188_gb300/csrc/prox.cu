@@ -277,7 +277,7 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
             const T vn = bn[e] + coef * (bn[e] - be);
             Bm[base + j] = bn[e];
             V[base + j] = vn;
-            if (a.Vop != nullptr) store_operand(a.Vop, (size_t)b * a.op_ld + j, (float)vn, a.op_bf16);
+            if (a.Vop != nullptr) store_operand2(a.Vop, a.Vop_lo, (size_t)b * a.op_ld + j, (float)vn, a.op_bf16);
         }
     }
 }

@@ -15,8 +15,8 @@ from . import build as _build
 KGLM_OK, KGLM_EINVAL, KGLM_ENOMEM, KGLM_ECUDA, KGLM_ETIMEOUT, KGLM_ESTATE, KGLM_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENUMERIC"}
 LSQ, LOGISTIC = 0, 1
-FP64, FP32, BF16, TF32 = 0, 1, 2, 3
-PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "tf32": TF32}
+FP64, FP32, BF16, TF32, TF32X3 = 0, 1, 2, 3, 4
+PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "tf32": TF32, "tf32x3": TF32X3}
 MAX_K = 64
 
 
@@ -65,6 +65,7 @@ _SIGS = {
     "kglm_estimate_bytes": (C.c_int, [C.POINTER(kglm_desc), I64]),
     "kglm_device_bytes": (C.c_int, [P, I64]),
     "kglm_suggest_batch": (C.c_int, [C.POINTER(kglm_desc), C.c_int64, C.c_int32, C.POINTER(C.c_int32)]),
+    "kglm_autotune": (C.c_int, [P, C.c_int32, C.c_uint64, C.c_void_p]),
     "kglm_server_create": (C.c_int, [C.c_void_p, C.POINTER(P)]),
     "kglm_server_submit": (C.c_int, [P, C.POINTER(kglm_desc), D, D, I64]),
     "kglm_server_info": (C.c_int, [P, C.c_int64, C.c_void_p]),
@@ -93,6 +94,12 @@ class kglm_server_stats_t(C.Structure):
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
+
+
+class kglm_tune(C.Structure):
+    _fields_ = [("batch", C.c_int32), ("link_tile_cols", C.c_int32), ("grad_tile_cols", C.c_int32),
+                ("grad_split_cap", C.c_int32), ("timed", C.c_int32), ("reserved", C.c_int32),
+                ("nodes_per_s", C.c_double), ("best_nodes_per_s", C.c_double)]
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
 
@@ -298,6 +305,13 @@ def kglm_solve(ctx, k, p, batch, iters, check_every=10, time_limit=0.0):
                 nodes=nodes.value, batches=batches.value)
 
 
+def kglm_autotune(ctx, iters=20, seed=1):
+    """Tile shapes and batch size picked by timing (see kglm.h); returns the choice."""
+    t = kglm_tune()
+    _check(lib().kglm_autotune(ctx, int(iters), int(seed), C.byref(t)), ctx)
+    return {f: getattr(t, f) for f, _ in t._fields_ if f != "reserved"}
+
+
 def kglm_destroy(ctx):
     if ctx:
         lib().kglm_destroy(ctx)
@@ -350,6 +364,9 @@ class Engine:
 
     def device_bytes(self):
         return kglm_device_bytes(self.ctx)
+
+    def autotune(self, iters=20, seed=1):
+        return kglm_autotune(self.ctx, iters, seed)
 
     def solve(self, batch, iters, check_every=10, time_limit=0.0):
         return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit)

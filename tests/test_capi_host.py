@@ -52,6 +52,7 @@ def _inst(n=20, p=6):
     (dict(M=-1.0), "M must"),
     (dict(loss=5), "unknown loss"),
     (dict(max_batch=0), "max_batch"),
+    (dict(prec=5), "unknown precision"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, needle):
     X, y = _inst()

@@ -1,0 +1,59 @@
+"""The autotuner (kglm_autotune): tile shapes of the tensor-core products and the batch size.
+
+Its choices are valid (tiles from the candidate sets, a power-of-two batch
+within max_batch at >= 95% of the best rate it measured), and retiling changes
+no result beyond rounding: after tuning, the batch still matches the oracle's
+certificate at the GPU's own dual points and its rounding/branching decisions,
+and kglm_solve with the tuned batch (batch 0) still certifies the brute-force
+optimum.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import node as on
+from oracle import reopt as ro
+from paper_2605_22188_gb300 import kglm, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32x3", "fp32"])
+def test_autotune_choices_are_valid_and_results_unchanged(prec):
+    n, p, k, m = 1500, 300, 8, 512
+    X, y, _ = synth.instance(n, p, k, synth.LOGISTIC, rho=0.5, seed=31)
+    lam2, M, T = 1e-2, 2.0, 30
+    L = on.lipschitz(X, synth.LOGISTIC)
+    rng = np.random.default_rng(4)
+    nodes = synth.csr_to_sets(*synth.random_nodes(64, p, k, rng))
+    with kglm.Engine(X, y, k, lam2, M, synth.LOGISTIC, prec=prec, max_batch=m, lipschitz=L) as eng:
+        t = eng.autotune(iters=10, seed=3)
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(T)
+        B, Z = eng.read_batch()
+    assert 1 <= t["batch"] <= m and (t["batch"] & (t["batch"] - 1) == 0 or t["batch"] == m)
+    assert t["nodes_per_s"] >= 0.95 * t["best_nodes_per_s"] > 0
+    if prec in ("bf16", "tf32x3"):
+        assert t["link_tile_cols"] in (64, 128, 256)
+        assert t["grad_tile_cols"] in (64, 128, 256)
+        assert t["grad_split_cap"] in (1, 2, 4, 8, 16)
+    else:
+        assert t["link_tile_cols"] == t["grad_tile_cols"] == t["grad_split_cap"] == 0
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        psi = on.dual_value(X, y, Z[b], nd, lam2, M, synth.LOGISTIC)
+        assert res["lb"][b] <= psi + 1e-12 * max(1.0, abs(psi))
+        assert psi - res["lb"][b] <= 1e-6 * max(1.0, abs(psi))
+        assert [int(s) for s in res["support"][b] if s >= 0] == on.round_support(B[b], nd)
+        assert res["branch_j"][b] == on.branch_index(B[b], nd)
+
+
+def test_solve_with_the_tuned_batch_matches_brute_force():
+    X, y, _ = synth.instance(120, 16, 4, synth.LSQ, rho=0.8, snr=2.0, seed=13)
+    with kglm.Engine(X, y, 4, 1e-3, 2.0, synth.LSQ, prec="bf16", max_batch=256) as eng:
+        res = eng.solve(0, 300, 20)
+    top = ro.brute_force(X, y, 4, 1e-3, 2.0, synth.LSQ, top=2)
+    assert res["gap"] <= 1e-6
+    assert abs(res["opt"] - top[0][0]) <= 1e-6 * max(1.0, abs(top[0][0]))
+    if top[1][0] - top[0][0] > 1e-6 * abs(top[0][0]):
+        assert tuple(res["support"]) == tuple(top[0][1])

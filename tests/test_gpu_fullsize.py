@@ -114,17 +114,19 @@ def _batch(c, m, seed):
     return nodes, synth.sets_to_csr(nodes)
 
 
-def test_c2_logistic_bench_launch_configuration():
-    """The bench line's workload: 1024 nodes, T = 50, FP32 products, FP64 certificate."""
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_c2_logistic_bench_launch_configuration(prec):
+    """The bench line's workload: 1024 nodes, T = 50, FP32-accurate products (CUDA
+    cores, or the TF32 hi + lo split on the tensor cores), FP64 certificate."""
     c, X, y, _ = synth.config_instance("c2_logistic_n2000_p200_k10", seed=0)
     m, T = c["m"], 50
     nodes, csr = _batch(c, m, 1000)
-    res, B, Z = _evaluate_like_bench(X, y, c, "fp32", m, T, csr)
+    res, B, Z = _evaluate_like_bench(X, y, c, prec, m, T, csr)
     _invariants(res, nodes, c["p"], c["k"])
     L = on.lipschitz(X, c["kind"])
     sample = list(range(5)) + [17, 256, 511, 777, 1023]
     worst = _sampled(X, y, c, res, B, Z, nodes, sample, reduced=True, L=L, T=T)
-    print("c2 fp32 vs fp64 oracle after %d iterations: max rel LB difference %.3e" % (T, worst))
+    print("c2 %s vs fp64 oracle after %d iterations: max rel LB difference %.3e" % (prec, T, worst))
     assert worst <= 1e-4
 
 

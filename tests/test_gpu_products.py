@@ -9,11 +9,13 @@ pytestmark = pytest.mark.gpu
 
 
 SHAPES = [(1024, 2000, 200), (37, 301, 150), (1, 5, 3), (300, 4000, 130), (129, 700, 300)]
-# relative rounding of one operand: FP32 exact here; BF16 round-to-nearest 2^-8; TF32 (truncated) 2^-10
-OPERAND_U = {"fp32": 0.0, "bf16": 2.0 ** -8, "tf32": 2.0 ** -10}
+# relative rounding of one operand: FP32 exact here; BF16 round-to-nearest 2^-8; TF32 (truncated) 2^-10;
+# TF32 hi + lo split: each operand to 2^-22, the dropped lo*lo term 2^-22 of the product, and X taken
+# from FP64 (2^-24 from the FP32 copy of the reference): (1 + 2^-21)^2 - 1 > 3 2^-22 + 2^-24
+OPERAND_U = {"fp32": 0.0, "bf16": 2.0 ** -8, "tf32": 2.0 ** -10, "tf32x3": 2.0 ** -21}
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32", "tf32x3"])
 @pytest.mark.parametrize("m,n,p", SHAPES)
 def test_xtr_matches_fp64_product(prec, m, n, p):
     """|G - R X| <= ((1+u)^2 - 1 + n 2^-24) sum |r||x| with u the operand rounding of the mode."""
@@ -61,7 +63,7 @@ def _dual_rows(n, rng):
     return Z
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "tf32", "tf32x3"])
 def test_certificate_product_is_within_its_bound(prec):
     """kglm_xtz: |Q - Z X| <= Qerr entrywise against exact rational sums, and the
     bound of the reduced modes' exact-splitting product is tiny: at most
@@ -104,3 +106,29 @@ def test_certificate_product_exact_at_the_accumulator_limit(sign):
         d = abs(Q[b, j] - float(v))
         assert d <= E[b, j], (b, j, d, E[b, j])
         assert E[b, j] <= 1e-7, E[b, j]
+
+
+@pytest.mark.parametrize("m,n,p", [(1024, 2000, 200), (300, 4000, 130)])
+def test_fp32_accurate_split_is_as_close_to_fp64_as_fp32_products(m, n, p):
+    """The TF32 hi + lo products have the accuracy of FP32 products: against the
+    FP64 product of the same FP32 inputs, their worst relative error (scaled by
+    sum |r||x|) is within a small factor of the CUDA-core FP32 product's, and
+    far below the single TF32 product's."""
+    import torch
+    rng = np.random.default_rng(m + p)
+    X, y, _ = synth.instance(n, p, 3, synth.LSQ, seed=2)
+    X = X.astype(np.float32).astype(np.float64)           # exactly representable in FP32
+    R = rng.standard_normal((m, n)).astype(np.float32)
+    ref = R.astype(np.float64) @ X
+    scale = np.abs(R.astype(np.float64)) @ np.abs(X)
+    err = {}
+    for prec in ("fp32", "tf32", "tf32x3"):
+        with kglm.Engine(X, y, 3, 0.1, 2.0, synth.LSQ, prec=prec, max_batch=m) as eng:
+            Rd = torch.from_numpy(R).cuda()
+            Gd = torch.zeros((m, p), dtype=torch.float32, device="cuda")
+            kglm.kglm_xtr(eng.ctx, m, Rd.data_ptr(), Gd.data_ptr())
+            G = Gd.cpu().numpy().astype(np.float64)
+        err[prec] = float(np.max(np.abs(G - ref) / scale))
+    print("max |G - RX| / (|R||X|):", err)
+    assert err["tf32x3"] <= 4.0 * err["fp32"] + 2.0 ** -22
+    assert err["tf32x3"] * 100.0 <= err["tf32"]
