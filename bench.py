@@ -295,6 +295,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     eng = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=args.prec, max_batch=m,
                       stream=stream.cuda_stream)
+    tune = eng.autotune(iters=T, seed=1)    # tiles, split cap, launch mode of the products (setup, untimed)
     batches = make_batches(c, 8, m, seed=1000 + rank)
     dev = []
     for (ip, ii, op, oi) in batches:
@@ -411,6 +412,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": units_e / secs_e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "autotune": tune,
         "roofline": roofline(stats, args.prec, pk, args.workload, m),
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -454,6 +456,56 @@ def time_to_zero_gap(X, y, c, prec, stream, m):
 
 
 SERVING = "c5_serving_mix64"
+SWEEP = "sweep_batch_n1000_p1000_k10"
+
+
+def run_sweep(args):
+    """Node-evaluation throughput against the batch size (the paper's Fig. 3 setting:
+    n = p = 1000, rho = 0.9, k = 10, lambda2 = 1, M = 2; batch sizes 2^0..2^11 for
+    least squares and 2^7..2^16 for logistic).  Each point: the same random fixing
+    patterns, T iterations + certificate + re-optimization, device time by CUDA
+    events (best of 3 after one untimed run)."""
+    import torch
+    from paper_2605_22188_gb300 import kglm
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    out = {}
+    for kind, lo, hi in ((synth.LSQ, 0, 11), (synth.LOGISTIC, 7, 16)):
+        X, y, _ = synth.instance(1000, 1000, 10, kind, rho=0.9, snr=5.0, seed=0)
+        mmax = 1 << hi
+        rng = np.random.default_rng(5)
+        ip, ii, op, oi = synth.random_nodes(mmax, 1000, 10, rng)
+        stream = torch.cuda.Stream()
+        pts = []
+        with kglm.Engine(X, y, 10, 1.0, 2.0, kind, prec=args.prec, max_batch=mmax, stream=stream.cuda_stream) as eng:
+            for e in range(lo, hi + 1):
+                m = 1 << e
+                csr = (ip[:m + 1], ii[:ip[m]], op[:m + 1], oi[:op[m]])
+                eng.push(*csr)
+                best = None
+                for r in range(4):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(stream):
+                        a.record(stream)
+                        eng.evaluate(args.iters)
+                        b.record(stream)
+                    b.synchronize()
+                    if r > 0:
+                        ms = a.elapsed_time(b)
+                        best = ms if best is None else min(best, ms)
+                pts.append({"batch": m, "ms": round(best, 4), "nodes_per_s": m / (best * 1e-3)})
+        out["least_squares" if kind == synth.LSQ else "logistic"] = pts
+    top = {k: max(p["nodes_per_s"] for p in v) for k, v in out.items()}
+    line = {"metric": "node bounds/sec against batch size", "value": top["logistic"], "unit": "nodes/s",
+            "n_gpus": world, "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+            "config": {"workload": SWEEP, "n": 1000, "p": 1000, "k": 10, "lambda2": 1.0, "M": 2.0, "rho": 0.9,
+                       "iters": args.iters, "products": PRODUCTS[args.prec], "certificate": "fp64"},
+            "best": top, "points": out}
+    print(json.dumps(line), flush=True)
 
 
 def run_serving(args):
@@ -543,9 +595,9 @@ def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return
-    if args.workload == SERVING:
+    if args.workload in (SERVING, SWEEP):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed per node-bound workload; "
-                          "the serving mix has no oracle arm (its instances are certified by the engine)"}))
+                          "this workload has no oracle arm"}))
         return
     from oracle import node as on
     c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
@@ -616,6 +668,8 @@ def main():
             run_reference(args)
         elif args.workload == SERVING:
             run_serving(args)
+        elif args.workload == SWEEP:
+            run_sweep(args)
         else:
             run_ours(args)
     finally:

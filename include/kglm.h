@@ -249,8 +249,10 @@ const char* kglm_phase_name(int32_t phase);
  * fixing patterns (|J1| ~ U{0..k}, |J0| ~ U{0..p/2}; `seed`) on the context:
  * in the tensor-core modes first the column tile of S = X V (64/128/256), then
  * the column tile and split-K cap of G = X^T R, at the full batch; then every
- * power-of-two batch size up to max_batch.  The context keeps the fastest
- * tiles; the batch chosen is the smallest within 5% of the best node rate
+ * power-of-two batch size up to max_batch; programmatic dependent launch of
+ * the iteration kernels (each kernel's prologue overlapping the previous
+ * kernel) is timed on and off at the chosen tiles.  The context keeps the
+ * fastest configuration; the batch chosen is the smallest within 5% of the best node rate
  * (kglm_solve with batch 0 uses it, tuning first with min(iters, 20) if
  * needed).  Discards the pushed batch (push again before kglm_evaluate). */
 typedef struct {
@@ -259,11 +261,17 @@ typedef struct {
     int32_t grad_tile_cols;   /* column tile of G = X^T R (tensor-core modes; 0 otherwise) */
     int32_t grad_split_cap;   /* split-K cap of G (tensor-core modes; 0 otherwise) */
     int32_t timed;            /* configurations timed */
-    int32_t reserved;
+    int32_t pdl;              /* 1: iteration kernels use programmatic dependent launch */
     double nodes_per_s;       /* node evaluations per second at the chosen batch */
     double best_nodes_per_s;  /* the best rate over all batch sizes */
 } kglm_tune;
 kglm_status kglm_autotune(kglm_ctx* ctx, int32_t iters, uint64_t seed, kglm_tune* out);
+
+/* Set the tuning choices by hand (the fields of kglm_tune; a 0 tile, split cap
+ * or batch keeps the current value; `timed` and the rates are ignored).  The
+ * split cap may not exceed the slices allocated at creation.  pdl 0 launches
+ * the iteration kernels without programmatic dependent launch. */
+kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg);
 
 /* Device bytes kglm_create allocates for *desc (App. E.4 sizes the batch from
  * the memory per node; admission control needs the whole footprint before
@@ -282,6 +290,53 @@ kglm_status kglm_device_bytes(const kglm_ctx* ctx, int64_t* bytes);
  * scales with m) fits in `budget` device bytes.  KGLM_ENOMEM if even m = 1
  * does not fit; KGLM_EINVAL for bad arguments. */
 kglm_status kglm_suggest_batch(const kglm_desc* desc, int64_t budget, int32_t cap, int32_t* batch);
+
+/* ---- Rashomon-set collection (§4.5, App. G).
+ * The support-level Rashomon set is R = {S : |S| <= k, v(S) <= (1 + eps) Phi*}
+ * with v(S) the optimal objective on support S and Phi* the optimum of the
+ * problem.  The BnB loop of kglm_solve collects it by changing the pruning
+ * threshold: a node is pruned only when its bound exceeds
+ * tau = min((1 + eps) UB, v_(N)) (v_(N): the N-th best stored objective when
+ * max_models = N > 0), every re-optimized support with objective <= tau is
+ * stored, and nodes are branched until they hold one support (kbar = 0 or no
+ * free coordinate).  At completion UB = Phi* and the pool is the certified set
+ * (or its N best members). */
+
+/* Pool of supports in the layout of App. G: a trie whose non-root nodes carry
+ * one feature index (node 0 is the root; node v > 0 has parent[v] and
+ * label[v]); record m is a trie leaf whose root-to-leaf labels are its support
+ * in insertion order, its objective, and its coefficients c[o[m] .. o[m+1])
+ * in the order of those labels (o[0] = 0).  Host memory; one pool per
+ * collection. */
+typedef struct kglm_pool kglm_pool;
+kglm_status kglm_pool_create(int32_t p, kglm_pool** out);
+/* Adds a record (seq: len distinct indices in [0, p), insertion order; coef:
+ * len coefficients in the same order).  A support already held (as a set) is
+ * not added again: *record = -1 then. */
+kglm_status kglm_pool_insert(kglm_pool* pool, int32_t len, const int32_t* seq, const double* coef,
+                             double objective, int64_t* record);
+kglm_status kglm_pool_size(const kglm_pool* pool, int64_t* records, int64_t* trie_nodes, int64_t* coef_len);
+/* Copies the layout out (any pointer may be NULL): offsets records+1, coef
+ * coef_len, objective records, leaf records, parent and label trie_nodes. */
+kglm_status kglm_pool_read(const kglm_pool* pool, int64_t* offsets, double* coef, double* objective,
+                           int32_t* leaf, int32_t* parent, int32_t* label);
+/* Root-to-leaf labels of a record (at most k entries). */
+kglm_status kglm_pool_support(const kglm_pool* pool, int64_t record, int32_t* labels, int32_t* len);
+/* Keeps the records with objective <= threshold and, if keep_best > 0, the
+ * keep_best best of them (ties to the earlier record), in their order. */
+kglm_status kglm_pool_filter(kglm_pool* pool, double threshold, int64_t keep_best);
+void kglm_pool_destroy(kglm_pool* pool);
+
+/* Collect the Rashomon set of the instance into `pool` (cleared first; created
+ * with this instance's p).  batch, iters, check_every, time_limit_s as for
+ * kglm_solve; eps >= 0; max_models 0 for no cap.  In the reduced-precision
+ * modes the stored objectives are replaced by FP64 evaluations of the stored
+ * coefficients at the end and the pool is filtered at the final threshold.
+ * Outputs: *opt = Phi* (the incumbent), *nodes evaluated, *complete = 1 when
+ * the search finished (0 when the time limit stopped it). */
+kglm_status kglm_rashomon(kglm_ctx* ctx, double eps, int64_t max_models, int32_t batch, int32_t iters,
+                          int32_t check_every, double time_limit_s, kglm_pool* pool, double* opt, int64_t* nodes,
+                          int32_t* complete);
 
 /* ---- Serving loop: certified solves of many instances, admitted as they
  * arrive (continuous batching at request granularity).  Each admitted

@@ -142,3 +142,32 @@ def brute_force(X, y, k, lam2, M, kind, J0=(), J1=(), top=2):
         return exact[:top]
     out = sorted((_v_logistic_exact(X, y, list(S), lam2, M)[0], S) for S in sups)
     return out[:top]
+
+
+def rashomon_set(X, y, k, lam2, M, kind, eps, N=None):
+    """The support-level Rashomon set of §4.5 by its definition.
+
+    R_eps = { S : |S| <= k, v(S) <= (1 + eps) Phi* } with v(S) from library
+    routines (LAPACK / BVLS for least squares, L-BFGS-B for logistic) for every
+    support of size 0..k, and Phi* = min over them.  With N, the N best members
+    (the capped collection of §4.5).  Returns (Phi*, [(v, S)] ascending in v).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    p = X.shape[1]
+    vals = []
+    for size in range(0, k + 1):
+        for S in itertools.combinations(range(p), size):
+            if size == 0:
+                v = objective(X, y, np.zeros(p), lam2, kind)
+            elif kind == LSQ:
+                v = _v_lsq_exact(X, y, list(S), lam2, M)[0]
+            else:
+                v = _v_logistic_exact(X, y, list(S), lam2, M)[0]
+            vals.append((v, tuple(S)))
+    vals.sort()
+    phi = vals[0][0]
+    R = [(v, S) for v, S in vals if v <= (1.0 + eps) * phi]
+    if N is not None:
+        R = R[:N]
+    return phi, R

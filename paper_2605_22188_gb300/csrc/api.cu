@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "engine.h"
 #include "kglm.h"
+#include "pool.h"
 
 using namespace kglm;
 
@@ -61,6 +62,7 @@ struct kglm_ctx {
     TcMap mA1{}, mB1{}, mB1lo{}, mA2{}, mB2{}, mA1lo{}, mA2lo{}, mB2lo{};
     int bn1 = 0, bn2 = 0;
     int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
+    bool pdl = false;             // programmatic dependent launch inside the iteration graph (tuned)
     GemmScratch gtc{};
     int* d_tcerr = nullptr;
     float* Gpart = nullptr;       // split slices of X^T R (summed by the prox kernel)
@@ -357,6 +359,7 @@ void iterate(kglm_ctx* c) {
             g.epi = c->tc_kind == 0 ? TC_EPI_LINK_BF16 : TC_EPI_LINK_F32;
             g.out = c->Rop; g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
             if (c->x3) { g.A2 = &c->mA1lo; g.out_lo = c->Rop_lo; }
+            g.pdl = c->pdl && c->capturing && !c->stats_on;   // inside the iteration graph
             if (tc_gemm(c->st, c->mA1, c->mB1, &c->mB1lo, g, &c->gtc) != 0)
                 throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
             check_launch();
@@ -369,6 +372,7 @@ void iterate(kglm_ctx* c) {
             g.pout = c->Gpart; g.pstride = (size_t)c->mcap * p; g.pld = p;
             g.max_splits = c->gsplit_max; g.splits_used = &c->gsplits;
             if (c->x3) g.A2 = &c->mA2lo;
+            g.pdl = c->pdl && c->capturing && !c->stats_on;
             if (tc_gemm(c->st, c->mA2, c->mB2, c->x3 ? &c->mB2lo : nullptr, g, &c->gtc) != 0)
                 throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
             check_launch();
@@ -399,6 +403,7 @@ void iterate(kglm_ctx* c) {
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
+    a.pdl = c->pdl && c->tc && c->capturing && !c->stats_on;   // after a tensor-core product, inside the graph
     Scope sc(c, PH_PROX, 1, (c->f64 ? 8.0 : 4.0) * 5.0 * c->sum_pa);
     const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
     if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
@@ -706,7 +711,7 @@ size_t footprint(const kglm_desc& d) {
     add(8 * mc * n); add(8 * mc * p);
     for (int t = 0; t < 7; ++t) add(8 * mc);
     add(8 * mc * k); add(4 * mc * k); add(4 * mc); add(mc);
-    add(4 * (mc + 1)); add(4 * (mc + 1)); add(4 * mc); add(4 * mc); add(4 * mc); add(4);
+    add(4 * (mc + 1)); add(4 * (mc + 1)); add(4 * mc); add(4 * std::max(mc, k)); add(4 * mc); add(4);
     const size_t slots = d.pool_slots > 0 ? (size_t)d.pool_slots : 4 * mc;
     add(slots * p * ws);
     add(4 * mc * k); add(4 * mc * p);
@@ -733,10 +738,21 @@ struct SolveOut {
     std::vector<double> beta;
     int64_t nodes = 0, batches = 0;
     bool cancelled = false;
+    bool complete = false;       // the open queue was emptied
+};
+
+// Rashomon-set collection (§4.5): prune a node only when its bound exceeds
+// tau = min((1 + eps) UB, the cap-th best stored objective), keep every
+// re-optimized support whose objective is at most tau, and branch until a
+// node holds a single support (kbar = 0 or no free coordinate).
+struct RashomonOpts {
+    double eps = 0.0;
+    int64_t cap = 0;
+    kglm_pool* pool = nullptr;
 };
 
 void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
-                const std::atomic<int>* cancel, SolveOut& out) {
+                const std::atomic<int>* cancel, SolveOut& out, const RashomonOpts* rs = nullptr) {
     REQ(batch >= 1 && batch <= ctx->mcap, "batch must be in [1, max_batch]");
     REQ(iters >= 1, "iters must be >= 1");
     struct Open {
@@ -770,6 +786,17 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
     std::vector<double> lb(batch), ubc(batch), bre((size_t)batch * k);
     std::vector<int> sup((size_t)batch * k), bj(batch);
     std::vector<Open*> cur;
+    // the pruning threshold: the incumbent, or the Rashomon threshold tau
+    auto tau = [&]() {
+        double t = isfinite(ub) ? (1.0 + rs->eps) * ub : INFINITY;
+        if (rs->cap > 0) t = std::min(t, rs->pool->nth_best(rs->cap));
+        return t;
+    };
+    auto pruned = [&](double lbv) {
+        if (!rs) return lbv >= ub - delta_of(ctx, ub);
+        const double t = tau();
+        return lbv > t + delta_of(ctx, t);
+    };
     try {
         while (!open.empty()) {
             if (time_limit_s > 0 && elapsed() > time_limit_s) break;
@@ -782,7 +809,7 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
             while (!open.empty() && (int)cur.size() < batch) {
                 Open* o = open.top();
                 open.pop();
-                if (o->lb >= ub - dl) {
+                if (pruned(o->lb)) {
                     release(o->slot);
                     delete o;
                     continue;
@@ -804,7 +831,12 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
                 wslot[b] = cur[b]->slot;
             }
             push_impl(ctx, m, in_ptr.data(), in_idx.data(), out_ptr.data(), out_idx.data(), wslot.data(), nullptr);
-            ctx->ub_inc = ub;
+            if (rs) {
+                const double t = tau();
+                ctx->ub_inc = t + 2.0 * delta_of(ctx, t);   // stop iterating once the bound passes tau
+            } else {
+                ctx->ub_inc = ub;
+            }
             evaluate_impl(ctx, iters, check_every);
             evaluate_outputs(ctx, lb.data(), nullptr, ubc.data(), sup.data(), bre.data(), bj.data(), nullptr);
             ctx->evaluated = true;
@@ -818,16 +850,51 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
                     std::copy(bre.begin() + (size_t)b * k, bre.begin() + (size_t)(b + 1) * k, best_coef.begin());
                 }
             }
+            if (rs) {
+                // store the supports at or below tau: the node's own fixed-in features in
+                // branching order, then the rest of its rounded support ascending
+                const double t = tau();
+                for (int b = 0; b < m; ++b) {
+                    if (!(ubc[b] <= t)) continue;
+                    std::vector<int> seq(cur[b]->J1);
+                    std::vector<double> cf;
+                    for (int j : seq) {
+                        for (int r = 0; r < k; ++r)
+                            if (sup[(size_t)b * k + r] == j) cf.push_back(bre[(size_t)b * k + r]);
+                    }
+                    for (int r = 0; r < k; ++r) {
+                        const int j = sup[(size_t)b * k + r];
+                        if (j < 0 || std::find(cur[b]->J1.begin(), cur[b]->J1.end(), j) != cur[b]->J1.end()) continue;
+                        seq.push_back(j);
+                        cf.push_back(bre[(size_t)b * k + r]);
+                    }
+                    rs->pool->insert(seq, cf, ubc[b]);
+                }
+                rs->pool->filter(tau(), rs->cap);
+            }
             const double dl2 = delta_of(ctx, ub);
             std::vector<int> rows, slots;
             for (int b = 0; b < m; ++b) {
                 Open* o = cur[b];
                 const double lbb = std::max(lb[b], o->lb);
-                if (lbb >= ub - dl2 || bj[b] < 0 || ubc[b] - lbb <= dl2) {
+                int j = bj[b];
+                if (rs) {
+                    const int kb = k - (int)o->J1.size(), pf = ctx->p - (int)o->J0.size() - (int)o->J1.size();
+                    if (pruned(lbb) || kb == 0 || pf == 0) {
+                        delete o;
+                        continue;
+                    }
+                    if (j < 0) {   // every free coordinate fits: branch on the smallest
+                        std::vector<char> fixed(ctx->p, 0);
+                        for (int q : o->J0) fixed[q] = 1;
+                        for (int q : o->J1) fixed[q] = 1;
+                        j = 0;
+                        while (fixed[j]) ++j;
+                    }
+                } else if (lbb >= ub - dl2 || bj[b] < 0 || ubc[b] - lbb <= dl2) {
                     delete o;
                     continue;
                 }
-                const int j = bj[b];
                 int s = -1;
                 if (!free_slots.empty()) {
                     s = free_slots.back();
@@ -880,6 +947,29 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
             ub = exact;
         }
     }
+    if (rs && !ctx->f64 && !rs->pool->leaf.empty()) {
+        // the reduced modes store upper estimates of v(S): replace them by the FP64
+        // objective of each record's coefficients, then filter at the final tau
+        kglm_pool& q = *rs->pool;
+        std::vector<double> ex(q.leaf.size());
+        for (size_t r = 0; r < q.leaf.size(); ++r) {
+            const std::vector<int> Sv = q.path(q.leaf[r]);
+            const int ks = (int)Sv.size();
+            ex[r] = q.obj[r];
+            if (ks == 0) continue;
+            CK(cudaMemcpyAsync(ctx->d_rows, Sv.data(), sizeof(int) * ks, cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(ctx->beta_re, q.coef.data() + q.off[r], sizeof(double) * ks, cudaMemcpyHostToDevice,
+                               ctx->st));
+            objective64_launch(ctx->st, ctx->Xt64, ctx->y64, ctx->n, ctx->kind, ctx->lam2, ctx->d_rows,
+                               ctx->beta_re, ks, ctx->ub);
+            check_launch();
+            CK(cudaMemcpyAsync(&ex[r], ctx->ub, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            sync(ctx);
+        }
+        q.obj = ex;
+        q.filter(tau(), rs->cap);
+    }
+    out.complete = open.empty() && !out.cancelled;
     double open_lb = INFINITY;
     while (!open.empty()) {
         open_lb = std::min(open_lb, open.top()->lb);
@@ -992,7 +1082,7 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         int b1 = c->bn1, b2 = c->bn2, bs = cap;
         for (int bn : t1) {
             set_tiles(c, bn, b2);
-            const double ms = time_eval(c, t, mc, iters, 2);
+            const double ms = time_eval(c, t, mc, iters, 3);
             ++timed;
             if (ms < best) { best = ms; b1 = bn; }
         }
@@ -1000,16 +1090,31 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
             for (int sc = 1; sc <= cap; sc *= 2) {
                 set_tiles(c, b1, bn);
                 c->gsplit_max = sc;
-                const double ms = time_eval(c, t, mc, iters, 2);
+                const double ms = time_eval(c, t, mc, iters, 3);
                 ++timed;
                 if (ms < best) { best = ms; b2 = bn; bs = sc; }
             }
         set_tiles(c, b1, b2);
         c->gsplit_max = bs;
+        // programmatic dependent launch on or off at the chosen tiles
+        bool bp = c->pdl;
+        for (int on = 0; on <= 1; ++on) {
+            if ((bool)on == c->pdl) continue;
+            const bool keep = c->pdl;
+            c->pdl = on != 0;
+            destroy_graphs(c);
+            const double ms = time_eval(c, t, mc, iters, 3);
+            ++timed;
+            if (ms < best) { best = ms; bp = c->pdl; }
+            c->pdl = keep;
+        }
+        c->pdl = bp;
+        destroy_graphs(c);
         r.link_tile_cols = b1;
         r.grad_tile_cols = b2;
         r.grad_split_cap = bs;
     }
+    r.pdl = c->pdl ? 1 : 0;
     // batch size: node bounds per second at each power of two; the smallest
     // within 5% of the best (larger batches evaluate nodes the search may
     // never need, Fig. 3's plateau)
@@ -1244,7 +1349,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->d_in_ptr = dalloc_t<int>(c, mc + 1);
         c->d_out_ptr = dalloc_t<int>(c, mc + 1);
         c->d_slot = dalloc_t<int>(c, mc);
-        c->d_rows = dalloc_t<int>(c, mc);
+        c->d_rows = dalloc_t<int>(c, std::max(mc, (size_t)c->k));   // also a support's indices
         c->d_slots = dalloc_t<int>(c, mc);
         c->d_err = dalloc_t<int>(c, 1);
         c->pool_slots = d.pool_slots > 0 ? d.pool_slots : 4 * d.max_batch;
@@ -1567,6 +1672,56 @@ kglm_status kglm_suggest_batch(const kglm_desc* desc, int64_t budget, int32_t ca
 kglm_status kglm_autotune(kglm_ctx* ctx, int32_t iters, uint64_t seed, kglm_tune* out) {
     if (!ctx) return KGLM_EINVAL;
     return guarded(ctx, [&] { autotune_impl(ctx, iters, seed, out); });
+}
+
+kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg) {
+    if (!ctx || !cfg) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (cfg->batch != 0) {
+            REQ(cfg->batch >= 1 && cfg->batch <= ctx->mcap, "batch must be in [1, max_batch]");
+            ctx->tuned_batch = cfg->batch;
+        }
+        ctx->pdl = cfg->pdl != 0;
+        if (ctx->tc) {
+            const int b1 = cfg->link_tile_cols ? cfg->link_tile_cols : ctx->bn1;
+            const int b2 = cfg->grad_tile_cols ? cfg->grad_tile_cols : ctx->bn2;
+            REQ(b1 >= 16 && b1 <= 256 && b1 % 16 == 0 && b2 >= 16 && b2 <= 256 && b2 % 16 == 0,
+                "tile columns must be multiples of 16 in [16, 256]");
+            if (cfg->grad_split_cap != 0) {
+                REQ(cfg->grad_split_cap >= 1 && cfg->grad_split_cap <= tc_split_cap(ctx->mcap, ctx->p),
+                    "split cap must be in [1, the allocated slices]");
+                ctx->gsplit_max = cfg->grad_split_cap;
+            }
+            set_tiles(ctx, b1, b2);
+        }
+        destroy_graphs(ctx);
+    });
+}
+
+kglm_status kglm_rashomon(kglm_ctx* ctx, double eps, int64_t max_models, int32_t batch, int32_t iters,
+                          int32_t check_every, double time_limit_s, kglm_pool* pool, double* opt, int64_t* nodes,
+                          int32_t* complete) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(pool != nullptr && pool->p == ctx->p, "pool must be created for this instance's p");
+        REQ(eps >= 0.0 && isfinite(eps), "eps must be finite and >= 0");
+        REQ(max_models >= 0, "max_models must be >= 0");
+        if (batch == 0) {
+            if (ctx->tuned_batch == 0) autotune_impl(ctx, std::min(iters, 20), 1, nullptr);
+            batch = ctx->tuned_batch;
+        }
+        *pool = kglm_pool();
+        pool->p = ctx->p;
+        RashomonOpts rs;
+        rs.eps = eps;
+        rs.cap = max_models;
+        rs.pool = pool;
+        SolveOut o;
+        solve_impl(ctx, batch, iters, check_every, time_limit_s, nullptr, o, &rs);
+        if (opt) *opt = o.opt;
+        if (nodes) *nodes = o.nodes;
+        if (complete) *complete = o.complete ? 1 : 0;
+    });
 }
 
 }  // extern "C"

@@ -72,6 +72,7 @@ struct TcGemm {
     int* splits_used;
     const TcMap* A2; // TF32 low part of A (out = (A + A2)(B + B2)^T less A2 B2^T); needs kind 1 and B2
     float* out_lo;   // TC_EPI_LINK_F32: TF32 low part of each output (NULL: none)
+    int pdl;         // launch with programmatic stream serialization (prologue overlaps the previous kernel)
 };
 // TMA map of a row-major rows x cols matrix (row stride ld elements) with
 // 128-byte boxes along cols and box_rows rows.  0 on success.
@@ -141,6 +142,7 @@ struct ProxArgs {
     const int* active;    // 1 = iterate this node
     double eta, c, M;     // step, c = 2 eta lambda2 = 1/rho, box
     int restart;
+    int pdl;              // launch with programmatic stream serialization
 };
 // One FISTA step per node: u = v - eta*G, beta' = prox(u), restart, next v.
 int prox_fista_f64(cudaStream_t s, const ProxArgs& a);

@@ -59,17 +59,27 @@ constexpr int ROWB = 128;               // bytes of K per stage and row (one swi
 constexpr int MAXBN = 256;
 constexpr int NT = 192;                 // six warps: producer, MMA, four epilogue warps
 constexpr uint32_t STAGE_A = BM * ROWB;
-constexpr uint32_t STAGE_B = MAXBN * ROWB;
 constexpr uint32_t TMEM_COLS = 512;     // two accumulators of up to 256 columns
 constexpr int TPAD = 36;                // transpose buffer row: 32 + 4 (16-byte rows, no 128-bit bank conflicts)
 constexpr int SMS = 152;
-// NB = 1: one B operand, four stages; NB = 2: B given as hi + lo parts
-// (both multiplied into the same accumulator), two stages.  NA = 2: A also
-// as hi + lo (the FP32-accurate split: A_hi B_hi + A_hi B_lo + A_lo B_hi).
-template <int NB, int NA> constexpr int stages() { return NB == 1 && NA == 1 ? 4 : 2; }
+// A stage holds one K slice of every operand part: A (and A2 when NA = 2,
+// the FP32-accurate split A_hi B_hi + A_hi B_lo + A_lo B_hi), B (and B2 when
+// NB = 2, hi + lo).  The ring has as many stages as fit next to the epilogue
+// buffer for the launch's tile width (at most kMaxStages).
+constexpr int kMaxStages = 8;
 constexpr size_t kEpiBytes = 4 * 32 * TPAD * sizeof(float);
-template <int NB, int NA>
-constexpr size_t smem_bytes() { return 1024 + stages<NB, NA>() * (NA * STAGE_A + NB * STAGE_B) + kEpiBytes + 256; }
+constexpr size_t kSmemMax = 224 * 1024;                    // dynamic shared memory per CTA (static 1 KB on top)
+constexpr size_t kSmemFixed = 1024 + kEpiBytes + 256;      // alignment slack, epilogue, barriers
+__host__ __device__ constexpr uint32_t stage_stride(int na, int nb, int bn) {
+    return (uint32_t)na * STAGE_A + (uint32_t)nb * (uint32_t)bn * ROWB;   // a multiple of 2048
+}
+inline int ring_stages(int na, int nb, int bn) {
+    const size_t n = (kSmemMax - kSmemFixed) / stage_stride(na, nb, bn);
+    return (int)std::min<size_t>(n, kMaxStages);
+}
+inline size_t smem_for(int na, int nb, int bn) {
+    return kSmemFixed + (size_t)ring_stages(na, nb, bn) * stage_stride(na, nb, bn);
+}
 constexpr uint32_t WAIT_LIMIT = 1u << 22;   // try_wait rounds before a wait gives up
 
 // ------------------------------------------------------------------ arguments and epilogues
@@ -82,6 +92,7 @@ struct TcArgs {
     int nkb, kb_per_split;    // K in 128-byte slices, slices per split
     uint32_t idesc;           // instruction descriptor
     int epi;                  // TC_EPI_*
+    int stages;               // ring stages (<= kMaxStages)
     int round_tf32;           // round FP32 link outputs to TF32 (nearest) for the next product
     float* pout;              // TC_EPI_PARTIAL: slice z at pout + z * pstride, row stride pld
     size_t pstride;
@@ -262,6 +273,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 
 // ------------------------------------------------------------------ the kernel
 
+// Programmatic dependent launch: let the next kernel in the stream be scheduled
+// (its prologue overlaps this grid), and wait for the previous grid to have
+// completed with its memory visible.  Both are no-ops without the launch attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -272,20 +289,21 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                                                    const __grid_constant__ CUtensorMap tmB2,
                                                    const __grid_constant__ CUtensorMap tmA2,
                                                    const __grid_constant__ TcArgs a) {
-    constexpr int STAGES = stages<NB, NA>();
+    const int STAGES = a.stages;
+    const uint32_t SSTR = stage_stride(NA, NB, a.bn);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem;                                       // stage s: A at s, A2 (NA = 2) at STAGES + s
-    uint8_t* sB = smem + NA * STAGES * STAGE_A;               // stage s: B at s, B2 (NB = 2) at STAGES + s
-    float* sT = reinterpret_cast<float*>(sB + NB * STAGES * STAGE_B);              // 4 x 32 x TPAD
+    // stage s at smem + s SSTR: A, A2 (NA = 2), B, B2 (NB = 2); every part 1024-byte aligned
+    const uint32_t offB = (uint32_t)NA * STAGE_A, offB2 = offB + (uint32_t)a.bn * ROWB;
+    float* sT = reinterpret_cast<float*>(smem + (size_t)STAGES * SSTR);            // 4 x 32 x TPAD
     uint64_t* bars = reinterpret_cast<uint64_t*>(sT + 4 * 32 * TPAD);
     // bars: full[S], empty[S], tfull[2], tempty[2], drain
     uint64_t* full = bars;
-    uint64_t* empty = bars + STAGES;
-    uint64_t* tfull = bars + 2 * STAGES;
-    uint64_t* tempty = bars + 2 * STAGES + 2;
-    uint64_t* drain = bars + 2 * STAGES + 4;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    uint64_t* empty = bars + kMaxStages;
+    uint64_t* tfull = bars + 2 * kMaxStages;
+    uint64_t* tempty = bars + 2 * kMaxStages + 2;
+    uint64_t* drain = bars + 2 * kMaxStages + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 5);
     __shared__ int s_consumed;       // ring slices the MMA issuer consumed (producer drain at exit)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -293,6 +311,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     const uint32_t stage_bytes = (uint32_t)NA * STAGE_A + (uint32_t)NB * a.bn * ROWB;
     const int units = a.mt * a.nt * a.nz;
 
+    pdl_trigger();
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), 1); }
         for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 128); }
@@ -305,6 +324,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();                      // operands and outputs belong to the previous grid until it completes
     int issued = 0;                  // producer: ring slices whose copies were started
 
     if (warp == 0) {
@@ -322,10 +342,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     const uint32_t fb = smem_u32(&full[s]);
                     mbar_expect_tx(fb, stage_bytes);
                     const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
-                    tma_load_2d(smem_u32(sA + s * STAGE_A), &tmA, kxa, m0, fb);
-                    tma_load_2d(smem_u32(sB + s * STAGE_B), &tmB, kxb, n0, fb);
-                    if (NB == 2) tma_load_2d(smem_u32(sB + (STAGES + s) * STAGE_B), &tmB2, kxb, n0, fb);
-                    if (NA == 2) tma_load_2d(smem_u32(sA + (STAGES + s) * STAGE_A), &tmA2, kxa, m0, fb);
+                    uint8_t* sp = smem + (size_t)s * SSTR;
+                    tma_load_2d(smem_u32(sp), &tmA, kxa, m0, fb);
+                    if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), &tmA2, kxa, m0, fb);
+                    tma_load_2d(smem_u32(sp + offB), &tmB, kxb, n0, fb);
+                    if (NB == 2) tma_load_2d(smem_u32(sp + offB2), &tmB2, kxb, n0, fb);
                     issued = g + 1;
                 }
             }
@@ -347,19 +368,15 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
                     if (!mbar_wait(smem_u32(&full[s]), ph, a.err)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t aa = smem_u32(sA + s * STAGE_A), bb = smem_u32(sB + s * STAGE_B);
+                    const uint32_t aa = smem_u32(smem + (size_t)s * SSTR), bb = aa + offB;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K each (per B part)
                         umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc,
                                    (i > 0 || kk > 0) ? 1u : 0u);
-                        if (NB == 2) {
-                            const uint32_t b2 = smem_u32(sB + (STAGES + s) * STAGE_B);
-                            umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(b2 + kk * 32), a.idesc, 1u);
-                        }
-                        if (NA == 2) {
-                            const uint32_t a2 = smem_u32(sA + (STAGES + s) * STAGE_A);
-                            umma<KIND>(acc, smem_desc(a2 + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
-                        }
+                        if (NB == 2)
+                            umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(aa + offB2 + kk * 32), a.idesc, 1u);
+                        if (NA == 2)
+                            umma<KIND>(acc, smem_desc(aa + STAGE_A + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
                     }
                     umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
                     s_consumed = g + 1;
@@ -542,7 +559,7 @@ int set_smem_attr() {
     static int done = 0;
     if (!done) {
         if (cudaFuncSetAttribute(k_tc_gemm<KIND, NB, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<NB, NA>()) != cudaSuccess)
+                                 (int)kSmemMax) != cudaSuccess)
             return -1;
         done = 1;
     }
@@ -624,6 +641,8 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const uint32_t ab = g.kind == 0 ? 1u : 2u;
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(g.bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     a.epi = g.epi; a.out = g.out; a.out_lo = g.out_lo; a.ldo = g.ldo; a.y = g.y; a.loss = g.loss;
+    a.stages = ring_stages(na, nb, g.bn);
+    const size_t smem = smem_for(na, nb, g.bn);
     a.round_tf32 = g.kind == 1;
     a.part = splits > 1 ? static_cast<float*>(scr->part) : nullptr;
     a.counters = splits > 1 ? scr->counters : nullptr;
@@ -632,17 +651,23 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const CUtensorMap& mb2 = *reinterpret_cast<const CUtensorMap*>((B2 ? B2 : &B)->bytes);
     const CUtensorMap& ma2 = *reinterpret_cast<const CUtensorMap*>((g.A2 ? g.A2 : &A)->bytes);
-    const dim3 grid(grid_of(tiles * splits));
-    if (na == 2) {
-        k_tc_gemm<1, 2, 2><<<grid, NT, smem_bytes<2, 2>(), s>>>(ma, mb, mb2, ma2, a);
-    } else if (g.kind == 0) {
-        if (nb == 1) k_tc_gemm<0, 1, 1><<<grid, NT, smem_bytes<1, 1>(), s>>>(ma, mb, mb2, ma, a);
-        else k_tc_gemm<0, 2, 1><<<grid, NT, smem_bytes<2, 1>(), s>>>(ma, mb, mb2, ma, a);
-    } else {
-        if (nb == 1) k_tc_gemm<1, 1, 1><<<grid, NT, smem_bytes<1, 1>(), s>>>(ma, mb, mb2, ma, a);
-        else k_tc_gemm<1, 2, 1><<<grid, NT, smem_bytes<2, 1>(), s>>>(ma, mb, mb2, ma, a);
-    }
-    return 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid_of(tiles * splits));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g.pdl ? 1 : 0;
+    cudaError_t e;
+    if (na == 2) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 2>, ma, mb, mb2, ma2, a);
+    else if (g.kind == 0) e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1>, ma, mb, mb2, ma, a)
+                                      : cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 2, 1>, ma, mb, mb2, ma, a);
+    else e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 1, 1>, ma, mb, mb2, ma, a)
+                     : cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 1>, ma, mb, mb2, ma, a);
+    return e == cudaSuccess ? 0 : -7;
 }
 
 int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, int bn, const TcJob* jobs,
@@ -658,6 +683,7 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     a.m_fast = N >= M;
     a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     a.epi = TC_EPI_PARTIAL;
+    a.stages = ring_stages(1, 1, bn);
     a.pout = pout; a.pstride = pstride; a.pld = pld;
     a.err = err;
     a.njobs = njobs;
@@ -665,7 +691,7 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const dim3 grid(grid_of(a.mt * a.nt * njobs));
-    k_tc_gemm<0, 1, 1><<<grid, NT, smem_bytes<1, 1>(), s>>>(ma, mb, mb, ma, a);
+    k_tc_gemm<0, 1, 1><<<grid, NT, smem_for(1, 1, bn), s>>>(ma, mb, mb, ma, a);
     return 0;
 }
 

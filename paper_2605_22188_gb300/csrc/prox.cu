@@ -76,6 +76,10 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     const int grp = GPC == 1 ? 0 : (int)(threadIdx.x / 32);
     ProxShared<T>& sh = shared_all[grp];
     const int b = blockIdx.x * GPC + grp;
+    // programmatic dependent launch (no-ops without the launch attribute): let the
+    // next kernel start its prologue, then wait for the gradient's producer
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (b >= a.m) return;
     if (a.active != nullptr && a.active[b] == 0) return;
     const int p = a.p;
@@ -99,7 +103,26 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) gsum[e] = T(0);
     if (a.gsplits > 0) {
-        for (int q = 0; q < a.gsplits; ++q) {
+        // QB slices' loads in flight together; the sum keeps the slice order
+        constexpr int QB = E <= 8 ? 4 : 2;
+        int q = 0;
+        for (; q + QB <= a.gsplits; q += QB) {
+            float t[QB][E];
+#pragma unroll
+            for (int qq = 0; qq < QB; ++qq) {
+                const float* gp = a.Gpart + (size_t)(q + qq) * a.gstride + base;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int j = G::rank() + e * NT;
+                    t[qq][e] = j < p ? gp[j] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < QB; ++qq)
+#pragma unroll
+                for (int e = 0; e < E; ++e) gsum[e] += T(t[qq][e]);
+        }
+        for (; q < a.gsplits; ++q) {
             const float* gp = a.Gpart + (size_t)q * a.gstride + base;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -282,12 +305,26 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     }
 }
 
+template <typename T, typename Grp, int E, int GPC>
+void launch(cudaStream_t s, const ProxArgs& a, int grid, int block) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_prox_fista<T, Grp, E, GPC>, a);   // errors surface at the caller's check
+}
+
 template <typename T>
 int dispatch(cudaStream_t s, const ProxArgs& a) {
     const int p = a.p, m = a.m;
     if (m <= 0) return 0;
-#define KGLM_PROX(NT_, E_) k_prox_fista<T, CtaGroup<NT_>, E_, 1><<<m, NT_, 0, s>>>(a)
-#define KGLM_PROX_WARP(E_) k_prox_fista<T, WarpGroup, E_, 4><<<(m + 3) / 4, 128, 0, s>>>(a)
+#define KGLM_PROX(NT_, E_) launch<T, CtaGroup<NT_>, E_, 1>(s, a, m, NT_)
+#define KGLM_PROX_WARP(E_) launch<T, WarpGroup, E_, 4>(s, a, (m + 3) / 4, 128)
     // up to 512 coordinates: one warp per node, four nodes per CTA
     if (p <= 32) KGLM_PROX_WARP(1);
     else if (p <= 64) KGLM_PROX_WARP(2);

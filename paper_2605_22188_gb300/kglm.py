@@ -66,6 +66,16 @@ _SIGS = {
     "kglm_device_bytes": (C.c_int, [P, I64]),
     "kglm_suggest_batch": (C.c_int, [C.POINTER(kglm_desc), C.c_int64, C.c_int32, C.POINTER(C.c_int32)]),
     "kglm_autotune": (C.c_int, [P, C.c_int32, C.c_uint64, C.c_void_p]),
+    "kglm_configure": (C.c_int, [P, C.c_void_p]),
+    "kglm_pool_create": (C.c_int, [C.c_int32, C.POINTER(P)]),
+    "kglm_pool_insert": (C.c_int, [P, C.c_int32, I32, D, C.c_double, I64]),
+    "kglm_pool_size": (C.c_int, [P, I64, I64, I64]),
+    "kglm_pool_read": (C.c_int, [P, I64, D, D, I32, I32, I32]),
+    "kglm_pool_support": (C.c_int, [P, C.c_int64, I32, I32]),
+    "kglm_pool_filter": (C.c_int, [P, C.c_double, C.c_int64]),
+    "kglm_pool_destroy": (None, [P]),
+    "kglm_rashomon": (C.c_int, [P, C.c_double, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double, P, D, I64,
+                                C.POINTER(C.c_int32)]),
     "kglm_server_create": (C.c_int, [C.c_void_p, C.POINTER(P)]),
     "kglm_server_submit": (C.c_int, [P, C.POINTER(kglm_desc), D, D, I64]),
     "kglm_server_info": (C.c_int, [P, C.c_int64, C.c_void_p]),
@@ -98,7 +108,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 class kglm_tune(C.Structure):
     _fields_ = [("batch", C.c_int32), ("link_tile_cols", C.c_int32), ("grad_tile_cols", C.c_int32),
-                ("grad_split_cap", C.c_int32), ("timed", C.c_int32), ("reserved", C.c_int32),
+                ("grad_split_cap", C.c_int32), ("timed", C.c_int32), ("pdl", C.c_int32),
                 ("nodes_per_s", C.c_double), ("best_nodes_per_s", C.c_double)]
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
@@ -309,7 +319,14 @@ def kglm_autotune(ctx, iters=20, seed=1):
     """Tile shapes and batch size picked by timing (see kglm.h); returns the choice."""
     t = kglm_tune()
     _check(lib().kglm_autotune(ctx, int(iters), int(seed), C.byref(t)), ctx)
-    return {f: getattr(t, f) for f, _ in t._fields_ if f != "reserved"}
+    return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_cap=0, pdl=1):
+    """Set tile shapes, split cap, batch and programmatic dependent launch by hand."""
+    t = kglm_tune(batch=batch, link_tile_cols=link_tile_cols, grad_tile_cols=grad_tile_cols,
+                  grad_split_cap=grad_split_cap, pdl=pdl)
+    _check(lib().kglm_configure(ctx, C.byref(t)), ctx)
 
 
 def kglm_destroy(ctx):
@@ -367,6 +384,15 @@ class Engine:
 
     def autotune(self, iters=20, seed=1):
         return kglm_autotune(self.ctx, iters, seed)
+
+    def configure(self, **kw):
+        kglm_configure(self.ctx, **kw)
+
+    def rashomon(self, eps, max_models=0, batch=0, iters=200, check_every=10, time_limit=0.0):
+        """The support-level Rashomon set (§4.5) as a Pool plus (opt, nodes, complete)."""
+        pool = Pool(self.p)
+        info = kglm_rashomon(self.ctx, pool, eps, max_models, batch, iters, check_every, time_limit)
+        return pool, info
 
     def solve(self, batch, iters, check_every=10, time_limit=0.0):
         return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit)
@@ -463,3 +489,95 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ Rashomon pool (App. G layout)
+
+class Pool:
+    """kglm_pool_*: supports in a trie of included features, coefficients cut by offsets."""
+
+    def __init__(self, p):
+        out = P()
+        st = lib().kglm_pool_create(int(p), C.byref(out))
+        if st != KGLM_OK:
+            raise KglmError(st, "kglm_pool_create")
+        self.q = out
+        self.p = int(p)
+
+    def insert(self, seq, coef, objective):
+        seq = _i32(seq)
+        coef = _f64(coef)
+        r = C.c_int64()
+        st = lib().kglm_pool_insert(self.q, len(seq), _ptr(seq, I32), _ptr(coef, D), float(objective), C.byref(r))
+        if st != KGLM_OK:
+            raise KglmError(st, "kglm_pool_insert")
+        return r.value
+
+    def size(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        lib().kglm_pool_size(self.q, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    def read(self):
+        R, V, NC = self.size()
+        off = np.empty(R + 1, dtype=np.int64)
+        coef = np.empty(NC)
+        obj = np.empty(R)
+        leaf = np.empty(R, dtype=np.int32)
+        parent = np.empty(V, dtype=np.int32)
+        label = np.empty(V, dtype=np.int32)
+        st = lib().kglm_pool_read(self.q, _ptr(off, I64), _ptr(coef, D), _ptr(obj, D), _ptr(leaf, I32),
+                                  _ptr(parent, I32), _ptr(label, I32))
+        if st != KGLM_OK:
+            raise KglmError(st, "kglm_pool_read")
+        return dict(offsets=off, coef=coef, objective=obj, leaf=leaf, parent=parent, label=label)
+
+    def support(self, record):
+        buf = np.empty(max(self.p, 1), dtype=np.int32)
+        n = C.c_int32()
+        st = lib().kglm_pool_support(self.q, int(record), _ptr(buf, I32), C.byref(n))
+        if st != KGLM_OK:
+            raise KglmError(st, "kglm_pool_support")
+        return buf[:n.value].tolist()
+
+    def filter(self, threshold, keep_best=0):
+        st = lib().kglm_pool_filter(self.q, float(threshold), int(keep_best))
+        if st != KGLM_OK:
+            raise KglmError(st, "kglm_pool_filter")
+
+    def records(self):
+        """[(objective, support as a sorted tuple, coefficients in label order, labels)] in record order."""
+        d = self.read()
+        out = []
+        for r in range(len(d["leaf"])):
+            lab = self.support(r)
+            out.append((float(d["objective"][r]), tuple(sorted(lab)),
+                        d["coef"][d["offsets"][r]:d["offsets"][r + 1]].copy(), lab))
+        return out
+
+    def close(self):
+        if self.q:
+            lib().kglm_pool_destroy(self.q)
+            self.q = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kglm_rashomon(ctx, pool, eps, max_models=0, batch=0, iters=200, check_every=10, time_limit=0.0):
+    opt = C.c_double()
+    nodes = C.c_int64()
+    comp = C.c_int32()
+    st = lib().kglm_rashomon(ctx, float(eps), int(max_models), int(batch), int(iters), int(check_every),
+                             float(time_limit), pool.q, C.byref(opt), C.byref(nodes), C.byref(comp))
+    _check(st, ctx)
+    return dict(opt=opt.value, nodes=nodes.value, complete=bool(comp.value))

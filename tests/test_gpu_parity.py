@@ -310,3 +310,41 @@ def test_reopt_large_supports(k, kind, prec):
             assert rel(res["ub"][b], v) <= RTOL, (b, res["ub"][b], v)
         else:
             check_reduced_objective(res["ub"][b], v)
+
+
+@pytest.mark.parametrize("prec,p", [("fp64", 4096), ("fp32", 8192), ("bf16", 8192)])
+def test_largest_p_per_precision(prec, p):
+    """The widest instances each precision takes (the prox kernel's limit: 4096
+    features in FP64, 8192 otherwise): certificate at the GPU's own dual point,
+    rounding and branching on the GPU's iterate, and the re-optimized
+    objective, for special and random nodes with a ragged last word of masks."""
+    n, k = 300, 12
+    p = p - 3                                  # ragged: not a multiple of 32
+    X, y, _ = synth.instance(n, p, k, synth.LSQ, rho=0.5, snr=5.0, seed=77)
+    lam2, M, T = 1e-2, 2.0, 20
+    L = on.lipschitz(X, synth.LSQ)
+    rng = np.random.default_rng(78)
+    nodes = make_batch(p, k, 10, rng)
+    with kglm.Engine(X, y, k, lam2, M, synth.LSQ, prec=prec, max_batch=10, lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(T)
+        B, Z = eng.read_batch()
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        psi = on.dual_value(X, y, Z[b], nd, lam2, M, synth.LSQ)
+        if prec == "fp64":
+            assert rel(res["lb"][b], psi) <= RTOL, (b, res["lb"][b], psi)
+            ref = on.solve_node(X, y, nd, lam2, M, synth.LSQ, L, T)
+            assert rel(res["lb"][b], ref["lb"]) <= RTOL, (b, res["lb"][b], ref["lb"])
+        else:
+            check_reduced_certificate(res["lb"][b], psi)
+        S = on.round_support(B[b], nd)
+        assert [int(s) for s in res["support"][b] if s >= 0] == S, b
+        assert res["branch_j"][b] == on.branch_index(B[b], nd), b
+        _, v = ro.reopt(X, y, S, lam2, M, synth.LSQ, beta0=B[b])
+        if prec == "fp64":
+            assert rel(res["ub"][b], v) <= RTOL, (b, res["ub"][b], v)
+        else:
+            check_reduced_objective(res["ub"][b], v)
+    with pytest.raises(kglm.KglmError):
+        kglm.Engine(np.zeros((4, p + 4)), np.zeros(4), 2, 0.1, 2.0, synth.LSQ, prec=prec, max_batch=1)

@@ -364,3 +364,80 @@ def test_bnb_equals_brute_force_hard_lsq():
 def test_bnb_equals_brute_force_logistic():
     X, y, _ = synth.instance(60, 12, 3, ol.LOGISTIC, rho=0.7, seed=4)
     _check_bnb(X, y, 3, 0.05, 2.0, ol.LOGISTIC)
+
+
+# --------------------------------------------------------------------------
+# Rashomon set (§4.5): the brute-force definition, pinned by its properties
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_rashomon_set_definition(kind):
+    """Phi* equals the brute-force optimum; the set grows with eps; it is closed
+    under adding features up to size k (v is non-increasing under inclusion);
+    eps = 0 keeps exactly the minimizers; the capped set is a prefix."""
+    X, y, _ = synth.instance(40, 7, 3, kind, rho=0.6, snr=0.5, seed=8)
+    lam2, M = 0.05, 2.0
+    phi, R1 = ro.rashomon_set(X, y, 3, lam2, M, kind, 0.05)
+    best = ro.brute_force(X, y, 3, lam2, M, kind, top=1)[0]
+    assert abs(phi - best[0]) <= 1e-9 * max(1.0, abs(phi))
+    _, R0 = ro.rashomon_set(X, y, 3, lam2, M, kind, 0.0)
+    assert [S for _, S in R0] == [S for v, S in R1 if v <= phi]
+    _, R5 = ro.rashomon_set(X, y, 3, lam2, M, kind, 0.2)
+    s1, s5 = {S for _, S in R1}, {S for _, S in R5}
+    assert s1 <= s5 and len(s5) > len(s1)
+    vmap = {S: v for v, S in ro.rashomon_set(X, y, 3, lam2, M, kind, 10.0)[1]}
+    for S in s5:
+        for j in range(7):
+            if j not in S and len(S) < 3:
+                T = tuple(sorted(S + (j,)))
+                assert vmap[T] <= vmap[S] + 1e-9 * vmap[S]
+                assert T in s5
+    assert any(len(S) < 3 for S in s5)          # smaller supports belong to the set too
+    _, Rn = ro.rashomon_set(X, y, 3, lam2, M, kind, 0.2, N=4)
+    assert Rn == R5[:4]
+
+
+def test_appG_trie_layout_golden():
+    """The pool's trie-and-offset layout reproduces the worked example of App. G:
+    o = (0, 3, 6, 9, 11), the coefficient vector, shared prefixes (18, 2) and (18),
+    and supports recovered from the trie paths (through the C ABI, host only)."""
+    from paper_2605_22188_gb300 import kglm
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "appG_trie.txt")
+    recs, o, c, sets = [], None, None, []
+    for line in open(path):
+        if line.startswith("rec:"):
+            seq, cf = line[4:].split("|")
+            recs.append(([int(t) for t in seq.split()], [float(t) for t in cf.split()]))
+        elif line.startswith("o:"):
+            o = [int(t) for t in line[2:].split()]
+        elif line.startswith("c:"):
+            c = [float(t) for t in line[2:].split()]
+        elif line.startswith("S:"):
+            sets.append(tuple(sorted(int(t) for t in line[2:].split())))
+    with kglm.Pool(20) as pool:
+        for r, (seq, cf) in enumerate(recs):
+            assert pool.insert(seq, cf, objective=float(r)) == r
+        d = pool.read()
+        assert d["offsets"].tolist() == o
+        assert np.allclose(d["coef"], c, rtol=0, atol=0)
+        # root + {18, (18,2), (18,2,7), (18,2,11), (18,9), (18,9,3), 12, (12,4)}
+        assert len(d["parent"]) == 9
+        paths = [pool.support(r) for r in range(4)]
+        assert paths == [seq for seq, _ in recs]
+        assert [tuple(sorted(p)) for p in paths] == sets
+        # the first two records share the trie nodes of (18, 2); the first three share (18)
+        leaf = d["leaf"]
+        assert d["parent"][leaf[0]] == d["parent"][leaf[1]]
+        top = lambda v: v if d["parent"][v] == 0 else top(int(d["parent"][v]))
+        assert top(int(leaf[0])) == top(int(leaf[1])) == top(int(leaf[2])) != top(int(leaf[3]))
+        # record 2 (second) uses c[3:6] and the support {2, 11, 18}
+        recs2 = pool.records()
+        assert recs2[1][1] == (2, 11, 18) and np.allclose(recs2[1][2], [0.5, -1.0, 0.1])
+        # a support already held is not stored twice
+        assert pool.insert([7, 18, 2], [0.0, 0.0, 0.0], 9.0) == -1
+        # filtering keeps order and rebuilds the layout
+        pool.filter(2.5, keep_best=2)
+        d2 = pool.read()
+        assert d2["offsets"].tolist() == [0, 3, 6] and np.allclose(d2["coef"], c[:6])
+        assert len(d2["parent"]) == 5
