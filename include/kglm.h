@@ -251,7 +251,8 @@ const char* kglm_phase_name(int32_t phase);
  * the column tile and split-K cap of G = X^T R, at the full batch; then every
  * power-of-two batch size up to max_batch; programmatic dependent launch of
  * the iteration kernels (each kernel's prologue overlapping the previous
- * kernel) is timed on and off at the chosen tiles.  The context keeps the
+ * kernel) is timed on and off at the chosen tiles, then 1, 2 or 4 sub-batches
+ * (node ranges iterated side by side on forked streams, tensor-core modes).  The context keeps the
  * fastest configuration; the batch chosen is the smallest within 5% of the best node rate
  * (kglm_solve with batch 0 uses it, tuning first with min(iters, 20) if
  * needed).  Discards the pushed batch (push again before kglm_evaluate). */
@@ -262,13 +263,16 @@ typedef struct {
     int32_t grad_split_cap;   /* split-K cap of G (tensor-core modes; 0 otherwise) */
     int32_t timed;            /* configurations timed */
     int32_t pdl;              /* 1: iteration kernels use programmatic dependent launch */
+    int32_t sub_batches;      /* iteration loop split into this many node ranges on parallel streams */
+    int32_t reserved;
     double nodes_per_s;       /* node evaluations per second at the chosen batch */
     double best_nodes_per_s;  /* the best rate over all batch sizes */
 } kglm_tune;
 kglm_status kglm_autotune(kglm_ctx* ctx, int32_t iters, uint64_t seed, kglm_tune* out);
 
 /* Set the tuning choices by hand (the fields of kglm_tune; a 0 tile, split cap
- * or batch keeps the current value; `timed` and the rates are ignored).  The
+ * batch or sub_batches keeps the current value; `timed` and the rates are
+ * ignored).  The
  * split cap may not exceed the slices allocated at creation.  pdl 0 launches
  * the iteration kernels without programmatic dependent launch. */
 kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg);

@@ -63,6 +63,11 @@ struct kglm_ctx {
     int bn1 = 0, bn2 = 0;
     int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
     bool pdl = false;             // programmatic dependent launch inside the iteration graph (tuned)
+    // sub-batches of the iteration loop on forked streams (tensor-core modes, tuned)
+    static constexpr int kMaxSub = 4;
+    int nsub = 1;
+    cudaStream_t sub_st[kMaxSub] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxSub] = {};
     GemmScratch gtc{};
     int* d_tcerr = nullptr;
     float* Gpart = nullptr;       // split slices of X^T R (summed by the prox kernel)
@@ -77,7 +82,6 @@ struct kglm_ctx {
     TcMap mAz{}, mBx{};
     int bnx = 0;
     int gsplit_max = 4;
-    int gsplits = 0;
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
     std::vector<double> h_lb, h_ub;
@@ -100,7 +104,7 @@ struct kglm_ctx {
         double work[KGLM_NPHASE] = {};
         int64_t launches[KGLM_NPHASE] = {};
     };
-    std::map<std::tuple<int, int, int>, Graph> graphs;
+    std::map<std::tuple<int, int, int, int>, Graph> graphs;
     bool capturing = false;
     Graph* cap = nullptr;
 };
@@ -348,36 +352,73 @@ __global__ void k_filli(int m, int* x, int v) {
     if (b < m) x[b] = v;
 }
 
+// One FISTA iteration of batch rows [row0, row0 + mr) on stream st (tensor-core
+// modes): S = X V with the link, G = X^T R as split slices, the prox.  Rows of
+// different calls touch disjoint rows of every buffer, and the link product
+// takes no split-K scratch while sub-batches run side by side.
+void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
+    const int n = c->n, p = c->p;
+    const double share = c->m > 0 ? (double)mr / c->m : 1.0;
+    const double flops = 2.0 * n * c->sum_pa * share;
+    const size_t es = c->tc_kind == 0 ? 2 : 4;
+    const bool pdl = c->pdl && c->capturing && !c->stats_on;   // inside the iteration graph
+    {
+        Scope sc(c, PH_GEMM_LINK, 1, flops);
+        TcGemm g{};
+        g.kind = c->tc_kind; g.M = mr; g.N = n; g.K = p; g.bn = c->bn1;
+        g.arow0 = row0;
+        g.epi = c->tc_kind == 0 ? TC_EPI_LINK_BF16 : TC_EPI_LINK_F32;
+        g.out = static_cast<char*>(c->Rop) + (size_t)row0 * c->nK * es;
+        g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
+        if (c->x3) { g.A2 = &c->mA1lo; g.out_lo = c->Rop_lo + (size_t)row0 * c->nK; }
+        g.pdl = pdl;
+        if (tc_gemm(st, c->mA1, c->mB1, &c->mB1lo, g, sub ? nullptr : &c->gtc) != 0)
+            throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+        check_launch();
+    }
+    int splits = 0;
+    {
+        Scope sc(c, PH_GEMM_GRAD, 1, flops);
+        TcGemm g{};
+        g.kind = c->tc_kind; g.M = mr; g.N = p; g.K = n; g.bn = c->bn2;
+        g.arow0 = row0;
+        g.epi = TC_EPI_PARTIAL; g.err = c->d_tcerr;
+        g.pout = c->Gpart + (size_t)row0 * p; g.pstride = (size_t)c->mcap * p; g.pld = p;
+        g.max_splits = c->gsplit_max; g.splits_used = &splits;
+        if (c->x3) g.A2 = &c->mA2lo;
+        g.pdl = pdl;
+        if (tc_gemm(st, c->mA2, c->mB2, c->x3 ? &c->mB2lo : nullptr, g, &c->gtc) != 0)
+            throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
+        check_launch();
+    }
+    ProxArgs a{};
+    a.m = mr; a.p = p; a.W = c->W;
+    a.G = nullptr;
+    a.V = static_cast<float*>(c->V) + (size_t)row0 * p;
+    a.B = static_cast<float*>(c->B) + (size_t)row0 * p;
+    a.Gpart = c->Gpart + (size_t)row0 * p;
+    a.gsplits = splits;
+    a.gstride = (size_t)c->mcap * p;
+    a.Vop = static_cast<char*>(c->Vop) + (size_t)row0 * c->pK * es;
+    a.Vop_lo = c->Vop_lo ? c->Vop_lo + (size_t)row0 * c->pK : nullptr;
+    a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
+    a.in_mask = c->in_mask + (size_t)row0 * c->W; a.out_mask = c->out_mask + (size_t)row0 * c->W;
+    a.kbar = c->kbar + row0; a.pf = c->pf + row0;
+    a.tmom = c->tmom + row0; a.active = c->active + row0;
+    a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
+    a.pdl = pdl;
+    Scope sc(c, PH_PROX, 1, 4.0 * 5.0 * c->sum_pa * share);
+    if (prox_fista_f32(st, a) != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
+    check_launch();
+}
+
 void iterate(kglm_ctx* c) {
     const int m = c->m, n = c->n, p = c->p;
     const double flops = 2.0 * n * c->sum_pa;
     if (c->tc) {
-        {
-            Scope sc(c, PH_GEMM_LINK, 1, flops);
-            TcGemm g{};
-            g.kind = c->tc_kind; g.M = m; g.N = n; g.K = p; g.bn = c->bn1;
-            g.epi = c->tc_kind == 0 ? TC_EPI_LINK_BF16 : TC_EPI_LINK_F32;
-            g.out = c->Rop; g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
-            if (c->x3) { g.A2 = &c->mA1lo; g.out_lo = c->Rop_lo; }
-            g.pdl = c->pdl && c->capturing && !c->stats_on;   // inside the iteration graph
-            if (tc_gemm(c->st, c->mA1, c->mB1, &c->mB1lo, g, &c->gtc) != 0)
-                throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
-            check_launch();
-        }
-        {
-            Scope sc(c, PH_GEMM_GRAD, 1, flops);
-            TcGemm g{};
-            g.kind = c->tc_kind; g.M = m; g.N = p; g.K = n; g.bn = c->bn2;
-            g.epi = TC_EPI_PARTIAL; g.err = c->d_tcerr;
-            g.pout = c->Gpart; g.pstride = (size_t)c->mcap * p; g.pld = p;
-            g.max_splits = c->gsplit_max; g.splits_used = &c->gsplits;
-            if (c->x3) g.A2 = &c->mA2lo;
-            g.pdl = c->pdl && c->capturing && !c->stats_on;
-            if (tc_gemm(c->st, c->mA2, c->mB2, c->x3 ? &c->mB2lo : nullptr, g, &c->gtc) != 0)
-                throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
-            check_launch();
-        }
-    } else {
+        iterate_rows(c, c->st, 0, m, false);
+        return;
+    }
     {
         Scope sc(c, PH_GEMM_LINK, 1, flops);
         if (c->f64) gemm_link_f64(c->st, m, n, p, (const double*)c->V, c->X64, c->y64, c->kind, (double*)c->R, &c->gs64);
@@ -390,24 +431,46 @@ void iterate(kglm_ctx* c) {
         else gemm_nt_f32(c->st, m, p, n, (const float*)c->R, n, c->Xt32, n, (float*)c->G, p, &c->gs32);
         check_launch();
     }
-    }
     ProxArgs a{};
     a.m = m; a.p = p; a.W = c->W;
     a.G = c->G; a.V = c->V; a.B = c->B;
-    if (c->tc) {
-        a.Gpart = c->Gpart;
-        a.gsplits = c->gsplits;
-        a.gstride = (size_t)c->mcap * p;
-    }
-    a.Vop = c->Vop; a.Vop_lo = c->Vop_lo; a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
-    a.pdl = c->pdl && c->tc && c->capturing && !c->stats_on;   // after a tensor-core product, inside the graph
     Scope sc(c, PH_PROX, 1, (c->f64 ? 8.0 : 4.0) * 5.0 * c->sum_pa);
     const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
     if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
     check_launch();
+}
+
+// Sub-batches of the current batch: rows split into nsub parts (multiples of
+// 128 rows but the last), at most one per 128 rows.
+int sub_count(const kglm_ctx* c) {
+    if (!c->tc || c->stats_on || c->nsub <= 1) return 1;
+    return std::max(1, std::min(c->nsub, c->m / 128));
+}
+
+// `count` iterations; with sub-batches, forked onto the sub-streams and joined
+// back onto the context's stream (inside a graph capture this is one graph
+// with parallel branches).
+void iterate_many(kglm_ctx* c, int count) {
+    const int ns = sub_count(c);
+    if (ns == 1) {
+        for (int i = 0; i < count; ++i) iterate(c);
+        return;
+    }
+    const int per = ((c->m + ns - 1) / ns + 127) / 128 * 128;
+    CK(cudaEventRecord(c->ev_fork, c->st));
+    for (int q = 0; q < ns; ++q) CK(cudaStreamWaitEvent(c->sub_st[q], c->ev_fork, 0));
+    for (int i = 0; i < count; ++i)
+        for (int q = 0; q < ns; ++q) {
+            const int r0 = q * per, mr = std::min(c->m, r0 + per) - r0;
+            if (mr > 0) iterate_rows(c, c->sub_st[q], r0, mr, true);
+        }
+    for (int q = 0; q < ns; ++q) {
+        CK(cudaEventRecord(c->ev_join[q], c->sub_st[q]));
+        CK(cudaStreamWaitEvent(c->st, c->ev_join[q], 0));
+    }
 }
 
 void destroy_graphs(kglm_ctx* c) {
@@ -426,7 +489,7 @@ void run_iters(kglm_ctx* c, int count) {
         for (int i = 0; i < count; ++i) iterate(c);   // the legacy streams cannot be captured
         return;
     }
-    const auto key = std::make_tuple(c->m, count, c->stats_on ? 1 : 0);
+    const auto key = std::make_tuple(c->m, count, c->stats_on ? 1 : 0, sub_count(c));
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         if (c->graphs.size() >= 16) destroy_graphs(c);
@@ -436,7 +499,7 @@ void run_iters(kglm_ctx* c, int count) {
         c->capturing = true;
         c->cap = &g;
         try {
-            for (int i = 0; i < count; ++i) iterate(c);
+            iterate_many(c, count);
         } catch (...) {
             c->capturing = false;
             cudaStreamEndCapture(c->st, &graph);
@@ -1110,11 +1173,24 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         }
         c->pdl = bp;
         destroy_graphs(c);
+        // sub-batches of the iteration loop side by side on forked streams
+        int bsub = c->nsub;
+        for (int ns : {1, 2, 4}) {
+            if (ns == c->nsub || mc < 128 * ns) continue;
+            const int keep = c->nsub;
+            c->nsub = ns;
+            const double ms = time_eval(c, t, mc, iters, 3);
+            ++timed;
+            if (ms < best) { best = ms; bsub = ns; }
+            c->nsub = keep;
+        }
+        c->nsub = bsub;
         r.link_tile_cols = b1;
         r.grad_tile_cols = b2;
         r.grad_split_cap = bs;
     }
     r.pdl = c->pdl ? 1 : 0;
+    r.sub_batches = c->nsub;
     // batch size: node bounds per second at each power of two; the smallest
     // within 5% of the best (larger batches evaluate nodes the search may
     // never need, Fig. 3's plateau)
@@ -1183,6 +1259,11 @@ void kglm_destroy(kglm_ctx* ctx) {
     for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     cudaGetLastError();
+    for (int q = 0; q < kglm_ctx::kMaxSub; ++q) {
+        if (ctx->sub_st[q]) cudaStreamDestroy(ctx->sub_st[q]);
+        if (ctx->ev_join[q]) cudaEventDestroy(ctx->ev_join[q]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
 }
@@ -1304,6 +1385,11 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->Gpart = dalloc_t<float>(c, (size_t)c->gsplit_max * mc * p);
             c->d_tcerr = dalloc_t<int>(c, 1);
             CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));
+            for (int q = 0; q < kglm_ctx::kMaxSub; ++q) {
+                CK(cudaStreamCreateWithFlags(&c->sub_st[q], cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming));
+            }
+            CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         }
         c->gram = dalloc_t<double>(c, p * p);
         c->Xty = dalloc_t<double>(c, p);
@@ -1682,6 +1768,10 @@ kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg) {
             ctx->tuned_batch = cfg->batch;
         }
         ctx->pdl = cfg->pdl != 0;
+        if (cfg->sub_batches != 0) {
+            REQ(cfg->sub_batches >= 1 && cfg->sub_batches <= kglm_ctx::kMaxSub, "sub_batches must be in [1, 4]");
+            ctx->nsub = cfg->sub_batches;
+        }
         if (ctx->tc) {
             const int b1 = cfg->link_tile_cols ? cfg->link_tile_cols : ctx->bn1;
             const int b2 = cfg->grad_tile_cols ? cfg->grad_tile_cols : ctx->bn2;

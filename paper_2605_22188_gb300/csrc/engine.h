@@ -73,6 +73,7 @@ struct TcGemm {
     const TcMap* A2; // TF32 low part of A (out = (A + A2)(B + B2)^T less A2 B2^T); needs kind 1 and B2
     float* out_lo;   // TC_EPI_LINK_F32: TF32 low part of each output (NULL: none)
     int pdl;         // launch with programmatic stream serialization (prologue overlaps the previous kernel)
+    int arow0;       // first row of A used (rows arow0 .. arow0 + M); outputs are indexed from row 0
 };
 // TMA map of a row-major rows x cols matrix (row stride ld elements) with
 // 128-byte boxes along cols and box_rows rows.  0 on success.

@@ -86,6 +86,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;   // try_wait rounds before a wait giv
 
 struct TcArgs {
     int M, N;                 // output rows (A rows) and columns (B rows)
+    int arow0;                // first A row (a sub-batch of the A operand's rows)
     int bn;                   // columns per tile, multiple of 16, <= MAXBN
     int mt, nt, nz;           // row tiles, column tiles, K ranges (splits or jobs)
     int m_fast;               // units walk row tiles fastest
@@ -343,8 +344,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     mbar_expect_tx(fb, stage_bytes);
                     const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
                     uint8_t* sp = smem + (size_t)s * SSTR;
-                    tma_load_2d(smem_u32(sp), &tmA, kxa, m0, fb);
-                    if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), &tmA2, kxa, m0, fb);
+                    tma_load_2d(smem_u32(sp), &tmA, kxa, a.arow0 + m0, fb);
+                    if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), &tmA2, kxa, a.arow0 + m0, fb);
                     tma_load_2d(smem_u32(sp + offB), &tmB, kxb, n0, fb);
                     if (NB == 2) tma_load_2d(smem_u32(sp + offB2), &tmB2, kxb, n0, fb);
                     issued = g + 1;
@@ -615,6 +616,7 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const int KE = g.kind == 0 ? 64 : 32;
     TcArgs a{};
     a.M = g.M; a.N = g.N; a.bn = g.bn;
+    a.arow0 = g.arow0;
     a.nkb = (g.K + KE - 1) / KE;
     a.mt = (g.M + BM - 1) / BM;
     a.nt = (g.N + g.bn - 1) / g.bn;

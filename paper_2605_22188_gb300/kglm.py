@@ -109,6 +109,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 class kglm_tune(C.Structure):
     _fields_ = [("batch", C.c_int32), ("link_tile_cols", C.c_int32), ("grad_tile_cols", C.c_int32),
                 ("grad_split_cap", C.c_int32), ("timed", C.c_int32), ("pdl", C.c_int32),
+                ("sub_batches", C.c_int32), ("reserved", C.c_int32),
                 ("nodes_per_s", C.c_double), ("best_nodes_per_s", C.c_double)]
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
@@ -319,13 +320,13 @@ def kglm_autotune(ctx, iters=20, seed=1):
     """Tile shapes and batch size picked by timing (see kglm.h); returns the choice."""
     t = kglm_tune()
     _check(lib().kglm_autotune(ctx, int(iters), int(seed), C.byref(t)), ctx)
-    return {f: getattr(t, f) for f, _ in t._fields_}
+    return {f: getattr(t, f) for f, _ in t._fields_ if f != "reserved"}
 
 
-def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_cap=0, pdl=1):
-    """Set tile shapes, split cap, batch and programmatic dependent launch by hand."""
+def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_cap=0, pdl=0, sub_batches=0):
+    """Set tile shapes, split cap, batch, launch mode and sub-batches by hand."""
     t = kglm_tune(batch=batch, link_tile_cols=link_tile_cols, grad_tile_cols=grad_tile_cols,
-                  grad_split_cap=grad_split_cap, pdl=pdl)
+                  grad_split_cap=grad_split_cap, pdl=pdl, sub_batches=sub_batches)
     _check(lib().kglm_configure(ctx, C.byref(t)), ctx)
 
 

@@ -57,3 +57,36 @@ def test_solve_with_the_tuned_batch_matches_brute_force():
     assert abs(res["opt"] - top[0][0]) <= 1e-6 * max(1.0, abs(top[0][0]))
     if top[1][0] - top[0][0] > 1e-6 * abs(top[0][0]):
         assert tuple(res["support"]) == tuple(top[0][1])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32x3"])
+def test_sub_batches_give_the_same_results(prec):
+    """Iterating node ranges side by side on forked streams changes no result
+    beyond summation order.  With one split-K slice of X^T R the BF16 run has
+    the same summation order in every product, so bounds, iterates, supports
+    and branching indices are identical for 1, 2 and 4 sub-batches (ragged last
+    range included).  In the TF32 split at this shape the whole-batch link
+    product takes split-K (few tiles) while sub-batches do not, so its FP32
+    sums are ordered differently: bounds agree to 1e-6 and iterates to 1e-5."""
+    n, p, k, m = 900, 150, 6, 600
+    X, y, _ = synth.instance(n, p, k, synth.LOGISTIC, rho=0.5, seed=41)
+    rng = np.random.default_rng(6)
+    csr = synth.random_nodes(m, p, k, rng)
+    out = []
+    with kglm.Engine(X, y, k, 1e-2, 2.0, synth.LOGISTIC, prec=prec, max_batch=m) as eng:
+        for ns in (1, 2, 4):
+            eng.configure(grad_split_cap=1, sub_batches=ns)
+            eng.push(*csr)
+            res = eng.evaluate(25)
+            B, _ = eng.read_batch(zeta=False)
+            out.append((res, B))
+    r0, B0 = out[0]
+    for res, B in out[1:]:
+        if prec == "bf16":
+            assert np.array_equal(B, B0)
+            for key in ("lb", "ub", "support", "branch_j"):
+                assert np.array_equal(res[key], r0[key]), key
+        else:
+            assert np.max(np.abs(B - B0)) <= 1e-5 * max(1.0, np.max(np.abs(B0)))
+            for key in ("lb", "ub"):
+                assert np.all(np.abs(res[key] - r0[key]) <= 1e-6 * np.maximum(1.0, np.abs(r0[key]))), key
