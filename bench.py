@@ -295,7 +295,16 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     eng = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=args.prec, max_batch=m,
                       stream=stream.cuda_stream)
-    tune = eng.autotune(iters=T, seed=1)    # tiles, split cap, launch mode of the products (setup, untimed)
+    if args.tiles:
+        # a fixed configuration (e.g. the tuned one) instead of tuning: link tile, gradient
+        # tile, split cap, sub-batches
+        l1, g2, cap, ns = (int(v) for v in args.tiles.split(","))
+        eng.configure(link_tile_cols=l1, grad_tile_cols=g2, grad_split_cap=cap, sub_batches=ns)
+        tune = {"fixed": args.tiles}
+    elif args.no_autotune:
+        tune = None
+    else:
+        tune = eng.autotune(iters=T, seed=1)    # tiles, split cap, launch mode of the products (setup, untimed)
     batches = make_batches(c, 8, m, seed=1000 + rank)
     dev = []
     for (ip, ii, op, oi) in batches:
@@ -565,6 +574,7 @@ def run_serving(args):
         "clocks": clk.summary(),
         "requests": [{"n": sp["n"], "p": sp["p"], "k": sp["k"], "loss": "lsq" if sp["kind"] == synth.LSQ else "logistic",
                       "rho": sp["rho"], "batch": i["batch"], "nodes": i["nodes"], "gap": i["gap"],
+                      "status": i["status"], "state": i["state"], "message": i["message"],
                       "t_submit": round(i["t_submit"], 4), "t_admit": round(i["t_admit"], 4),
                       "t_done": round(i["t_done"], 4)} for sp, i in zip(specs, infos)],
     }
@@ -649,8 +659,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ttz", action="store_true", help="skip the time-to-zero-gap solves")
-    ap.add_argument("--rate", type=float, default=4.0, help="serving mix: Poisson arrivals per second")
-    ap.add_argument("--max-active", type=int, default=8, help="serving mix: requests solved at once")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles (profiling runs)")
+    ap.add_argument("--tiles", default="", help="fixed tiles instead of tuning: link,grad,split_cap,sub_batches")
+    ap.add_argument("--rate", type=float, default=2.0, help="serving mix: Poisson arrivals per second")
+    ap.add_argument("--max-active", type=int, default=16, help="serving mix: requests solved at once")
     ap.add_argument("--request-limit", type=float, default=20.0, help="serving mix: seconds per request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -252,7 +252,8 @@ const char* kglm_phase_name(int32_t phase);
  * power-of-two batch size up to max_batch; programmatic dependent launch of
  * the iteration kernels (each kernel's prologue overlapping the previous
  * kernel) is timed on and off at the chosen tiles, then 1, 2 or 4 sub-batches
- * (node ranges iterated side by side on forked streams, tensor-core modes).  The context keeps the
+ * (node ranges iterated side by side on forked streams, tensor-core modes),
+ * and for p > 512 in the FP32-type modes the prox's threads per node.  The context keeps the
  * fastest configuration; the batch chosen is the smallest within 5% of the best node rate
  * (kglm_solve with batch 0 uses it, tuning first with min(iters, 20) if
  * needed).  Discards the pushed batch (push again before kglm_evaluate). */
@@ -264,7 +265,7 @@ typedef struct {
     int32_t timed;            /* configurations timed */
     int32_t pdl;              /* 1: iteration kernels use programmatic dependent launch */
     int32_t sub_batches;      /* iteration loop split into this many node ranges on parallel streams */
-    int32_t reserved;
+    int32_t prox_threads;     /* threads per node of the prox for p > 512 in the FP32-type modes (0: default) */
     double nodes_per_s;       /* node evaluations per second at the chosen batch */
     double best_nodes_per_s;  /* the best rate over all batch sizes */
 } kglm_tune;
@@ -377,6 +378,7 @@ typedef struct {
     int32_t batch;                  /* node-batch size used */
     int32_t reserved;
     double t_submit, t_admit, t_done;   /* seconds since server creation; -1 until reached */
+    char message[128];              /* FAILED: the failing call's message (kglm_last_error) */
 } kglm_request_info;
 
 typedef struct {
@@ -417,6 +419,16 @@ const char* kglm_server_last_error(kglm_server* s);
 /* Stop the server: running requests stop at their next batch boundary
  * (CANCELLED), queued ones are dropped; joins the workers and frees all. */
 void kglm_server_destroy(kglm_server* s);
+
+/* Self-test of the device-wait timeout path (failure detection without a GPU
+ * fault; the paper has no counterpart).  Every wait in the engine's kernels
+ * (the tensor-core pipelines' mbarriers) is bounded: when it runs out the
+ * kernel sets an error flag, drains its own work and returns, and the call
+ * that launched it returns KGLM_ETIMEOUT with the context still usable.  This
+ * call launches one kernel whose wait is on an mbarrier nothing arrives on,
+ * bounded by `rounds` try_wait rounds, and returns KGLM_ETIMEOUT when the
+ * timeout was detected and reported (KGLM_ECUDA if it was not). */
+kglm_status kglm_selftest_timeout(kglm_ctx* ctx, int32_t rounds);
 
 /* Message of the last failed call on ctx (never NULL). */
 const char* kglm_last_error(const kglm_ctx* ctx);

@@ -66,6 +66,7 @@ struct kglm_ctx {
     // sub-batches of the iteration loop on forked streams (tensor-core modes, tuned)
     static constexpr int kMaxSub = 4;
     int nsub = 1;
+    int prox_threads = 0;         // FP32 CTA prox: threads per node (0: default; tuned)
     cudaStream_t sub_st[kMaxSub] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxSub] = {};
     GemmScratch gtc{};
@@ -407,6 +408,7 @@ void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
     a.tmom = c->tmom + row0; a.active = c->active + row0;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
     a.pdl = pdl;
+    a.threads = c->prox_threads;
     Scope sc(c, PH_PROX, 1, 4.0 * 5.0 * c->sum_pa * share);
     if (prox_fista_f32(st, a) != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
     check_launch();
@@ -437,6 +439,7 @@ void iterate(kglm_ctx* c) {
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
+    a.threads = c->prox_threads;
     Scope sc(c, PH_PROX, 1, (c->f64 ? 8.0 : 4.0) * 5.0 * c->sum_pa);
     const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
     if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
@@ -1191,6 +1194,25 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
     }
     r.pdl = c->pdl ? 1 : 0;
     r.sub_batches = c->nsub;
+    // threads per node of the prox (FP32 working type, p > 512)
+    if (!c->f64) {
+        int opts[3];
+        const int no = prox_thread_options(c->p, opts);
+        if (no > 1) {
+            double best = INFINITY;
+            int bt = c->prox_threads;
+            for (int q = 0; q < no; ++q) {
+                c->prox_threads = opts[q];
+                destroy_graphs(c);
+                const double ms = time_eval(c, t, mc, iters, 3);
+                ++timed;
+                if (ms < best) { best = ms; bt = opts[q]; }
+            }
+            c->prox_threads = bt;
+            destroy_graphs(c);
+        }
+    }
+    r.prox_threads = c->prox_threads;
     // batch size: node bounds per second at each power of two; the smallest
     // within 5% of the best (larger batches evaluate nodes the search may
     // never need, Fig. 3's plateau)
@@ -1768,6 +1790,14 @@ kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg) {
             ctx->tuned_batch = cfg->batch;
         }
         ctx->pdl = cfg->pdl != 0;
+        if (cfg->prox_threads != 0) {
+            int opts[3];
+            const int no = prox_thread_options(ctx->p, opts);
+            bool ok = false;
+            for (int q = 0; q < no; ++q) ok |= opts[q] == cfg->prox_threads;
+            REQ(ok && !ctx->f64, "prox_threads is not an option for this p and precision");
+            ctx->prox_threads = cfg->prox_threads;
+        }
         if (cfg->sub_batches != 0) {
             REQ(cfg->sub_batches >= 1 && cfg->sub_batches <= kglm_ctx::kMaxSub, "sub_batches must be in [1, 4]");
             ctx->nsub = cfg->sub_batches;
@@ -1811,6 +1841,24 @@ kglm_status kglm_rashomon(kglm_ctx* ctx, double eps, int64_t max_models, int32_t
         if (opt) *opt = o.opt;
         if (nodes) *nodes = o.nodes;
         if (complete) *complete = o.complete ? 1 : 0;
+    });
+}
+
+kglm_status kglm_selftest_timeout(kglm_ctx* ctx, int32_t rounds) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(rounds >= 1, "rounds must be >= 1");
+        int* flag = ctx->d_tcerr ? ctx->d_tcerr : ctx->d_err;
+        CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->st));
+        wait_probe(ctx->st, (uint32_t)rounds, flag);
+        check_launch();
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        sync(ctx);
+        CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->st));
+        sync(ctx);
+        if (h & 8) throw Fail{KGLM_ETIMEOUT, "self-test: the bounded device wait ran out and reported it"};
+        throw Fail{KGLM_ECUDA, "self-test: the bounded device wait did not report its timeout"};
     });
 }
 

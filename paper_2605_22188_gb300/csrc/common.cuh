@@ -177,12 +177,19 @@ struct SelectShared {
     unsigned hist[256];
     int digit;
     unsigned above;
+    unsigned bincnt;                  // elements in the chosen bin
+    int ncand;                        // early exit: candidates gathered
+    int need;
+    unsigned long long thr;
+    unsigned long long ckey[64];
 };
 
 // Radix select over the CTA: the kth (1-based) largest key among the elements
 // whose bit is set in `valid`.  Returns the key and `need`, the number of
 // elements equal to it that belong to the kth largest.  Requires 1 <= kth <=
-// number of valid elements.
+// number of valid elements.  Once the bin holding the kth key has at most 64
+// elements, they are gathered to shared memory and ranked there by one warp
+// (the remaining 8-bit passes would only split that bin further).
 template <typename G, int E, typename K>
 __device__ void group_kth_largest(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
                                   K& thr, int& need) {
@@ -220,15 +227,47 @@ __device__ void group_kth_largest(const K (&key)[E], uint32_t valid, int kth, Se
                 unsigned acc = above;
 #pragma unroll
                 for (int q = 7; q >= 0; --q) {
-                    if (acc + c[q] >= (unsigned)rem) { sh.digit = l * 8 + q; sh.above = acc; break; }
+                    if (acc + c[q] >= (unsigned)rem) {
+                        sh.digit = l * 8 + q;
+                        sh.above = acc;
+                        sh.bincnt = c[q];
+                        break;
+                    }
                     acc += c[q];
                 }
             }
+            if (l == 0) sh.ncand = 0;
         }
         G::sync();
         rem -= (int)sh.above;
         prefix |= K(sh.digit) << shift;
         pmask |= K(255) << shift;
+        if (shift > 0 && sh.bincnt <= 64u) {
+            // gather the bin's elements, then rank them in one warp
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (((valid >> e) & 1u) && (key[e] & pmask) == prefix) sh.ckey[atomicAdd(&sh.ncand, 1)] = key[e];
+            G::sync();
+            if (G::rank() < 32) {
+                const int nc = sh.ncand, l = G::rank();
+                for (int i = l; i < nc; i += 32) {
+                    const unsigned long long ki = sh.ckey[i];
+                    int gt = 0, eq = 0;
+                    for (int j = 0; j < nc; ++j) {
+                        gt += sh.ckey[j] > ki;
+                        eq += sh.ckey[j] == ki;
+                    }
+                    if (gt <= rem - 1 && rem - 1 < gt + eq) {   // ki is the rem-th largest
+                        sh.thr = ki;
+                        sh.need = rem - gt;
+                    }
+                }
+            }
+            G::sync();
+            thr = K(sh.thr);
+            need = sh.need;
+            return;
+        }
     }
     G::sync();
     thr = prefix;

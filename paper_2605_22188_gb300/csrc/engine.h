@@ -80,6 +80,8 @@ struct TcGemm {
 int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, int ld, int box_rows);
 // Sets the kernels' shared-memory attributes (call before any stream capture).
 int tc_prepare();
+// A bounded wait on an mbarrier nothing arrives on (rounds try_wait rounds); sets bit 8 of *err.
+void wait_probe(cudaStream_t s, uint32_t rounds, int* err);
 int tc_tile_cols(int N);
 // Split-K slices of a TC_EPI_PARTIAL product with M x N output: enough units
 // to fill the SMs, at most 16.
@@ -144,10 +146,14 @@ struct ProxArgs {
     double eta, c, M;     // step, c = 2 eta lambda2 = 1/rho, box
     int restart;
     int pdl;              // launch with programmatic stream serialization
+    int threads;          // FP32, p > 512: threads per node (0: 8 coordinates per thread)
 };
 // One FISTA step per node: u = v - eta*G, beta' = prox(u), restart, next v.
 int prox_fista_f64(cudaStream_t s, const ProxArgs& a);
 int prox_fista_f32(cudaStream_t s, const ProxArgs& a);
+// Candidate threads-per-node values of the FP32 CTA kernels for p (0 = default
+// first); returns the count written to out (at most 3).
+int prox_thread_options(int p, int* out);
 
 struct CertArgs {
     int m, n, p, W, k, kind;

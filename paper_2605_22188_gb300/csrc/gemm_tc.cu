@@ -540,6 +540,23 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     }
 }
 
+// A wait that nothing ends: one thread waits on an mbarrier no thread arrives
+// on, for `rounds` try_wait rounds, then reports the timeout through the same
+// flag as the products' waits (bit 8).  Checks the timeout path end to end.
+__global__ void k_wait_probe(uint32_t rounds, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        for (uint32_t i = 0; i < rounds && !ok; ++i) ok = mbar_try_wait(smem_u32(&bar), 0u);
+        if (!ok) atomicOr(err, 8);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -568,6 +585,8 @@ int set_smem_attr() {
 }
 
 }  // namespace
+
+void wait_probe(cudaStream_t s, uint32_t rounds, int* err) { k_wait_probe<<<1, 32, 0, s>>>(rounds, err); }
 
 int tc_prepare() {
     return set_smem_attr<0, 1, 1>() | set_smem_attr<0, 2, 1>() | set_smem_attr<1, 1, 1>() | set_smem_attr<1, 2, 1>() |

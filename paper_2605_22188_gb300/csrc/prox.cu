@@ -36,10 +36,12 @@ template <typename T> struct KeyOf;
 template <> struct KeyOf<float> { using type = uint32_t; };
 template <> struct KeyOf<double> { using type = unsigned long long; };
 
-template <typename T>
+template <typename T, int NW>
 struct ProxShared {
     SelectShared sel;
     T red[2 * 32];
+    T fred[kMaxK * NW];   // CTA groups: per-warp tail sums at every breakpoint of the piece search
+    int fpos[kMaxK];      // and f > 0 at each breakpoint
     int ired[32];
     int topcnt;
     T topv[kMaxK];
@@ -72,9 +74,10 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     using G = Grp;
     using K = typename KeyOf<T>::type;
     constexpr int NT = G::N;
-    __shared__ ProxShared<T> shared_all[GPC];
+    constexpr int NWG = NT / 32;
+    __shared__ ProxShared<T, NWG> shared_all[GPC];
     const int grp = GPC == 1 ? 0 : (int)(threadIdx.x / 32);
-    ProxShared<T>& sh = shared_all[grp];
+    ProxShared<T, NWG>& sh = shared_all[grp];
     const int b = blockIdx.x * GPC + grp;
     // programmatic dependent launch (no-ops without the launch attribute): let the
     // next kernel start its prologue, then wait for the gradient's producer
@@ -202,31 +205,58 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
             if (emin >= amax) {
                 theta = amax;                      // no violation: nothing pools
             } else {
-                int cnt = 0;                       // entry points below amax
-                for (int i = G::rank(); i < kb; i += NT) cnt += sh.ep[i] < amax;
-                const int r = G::count(cnt, sh.ired);
+                int r = 0;                         // entry points below amax (from shared memory)
+                for (int i = 0; i < kb; ++i) r += sh.ep[i] < amax;
                 auto xval = [&](int i) -> T { return i == 0 ? T(0) : (i <= r ? sh.ep[kb - i] : amax); };
                 int lo = 0, hi = r + 1;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    const T x = xval(mid);
-                    const T h = x + min(x / c, M);
-                    // f(x) = sum_tail (|u| - x)^+ - sum_{top, p(t) < x} (h(x) - t)
-                    T part[1] = {T(0)};
+                if constexpr (NT == 32) {
+                    // one warp: binary search, each probe a shuffle reduction
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        const T x = xval(mid);
+                        const T h = x + min(x / c, M);
+                        // f(x) = sum_tail (|u| - x)^+ - sum_{top, p(t) < x} (h(x) - t)
+                        T part[1] = {T(0)};
 #pragma unroll
-                    for (int e = 0; e < E; ++e)
-                        if (bit(ffree & ~top, e)) part[0] += max(abs(u[e]) - x, T(0));
-                    for (int i = G::rank(); i < kb; i += NT)
-                        if (sh.ep[i] < x) part[0] -= max(h - sh.sv[i], T(0));
-                    G::template sum<1, T>(part, sh.red);
-                    if (part[0] > T(0)) lo = mid; else hi = mid;
+                        for (int e = 0; e < E; ++e)
+                            if (bit(ffree & ~top, e)) part[0] += max(abs(u[e]) - x, T(0));
+                        for (int i = G::rank(); i < kb; i += NT)
+                            if (sh.ep[i] < x) part[0] -= max(h - sh.sv[i], T(0));
+                        G::template sum<1, T>(part, sh.red);
+                        if (part[0] > T(0)) lo = mid; else hi = mid;
+                    }
+                } else {
+                    // a CTA: f at every breakpoint x_1..x_r in one pass (per-warp tail
+                    // sums, then one thread per breakpoint), f decreasing: lo = #{f > 0}
+                    const int w = (int)(threadIdx.x >> 5), ln = (int)(threadIdx.x & 31);
+                    for (int i = 1; i <= r; ++i) {
+                        const T x = xval(i);
+                        T part = T(0);
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if (bit(ffree & ~top, e)) part += max(abs(u[e]) - x, T(0));
+                        part = warp_sum(part);
+                        if (ln == 0) sh.fred[(i - 1) * NWG + w] = part;
+                    }
+                    G::sync();
+                    for (int i = G::rank() + 1; i <= r; i += NT) {
+                        const T x = xval(i);
+                        const T h = x + min(x / c, M);
+                        T f = T(0);
+                        for (int q = 0; q < NWG; ++q) f += sh.fred[(i - 1) * NWG + q];
+                        for (int j = 0; j < kb; ++j)
+                            if (sh.ep[j] < x) f -= max(h - sh.sv[j], T(0));
+                        sh.fpos[i - 1] = f > T(0);
+                    }
+                    G::sync();
+                    for (int i = 0; i < r; ++i) lo += sh.fpos[i];
+                    hi = lo + 1;
                 }
                 const T xlo = xval(lo), xhi = xval(hi);
-                T ns[2] = {T(0), T(0)};
-                for (int i = G::rank(); i < kb; i += NT)
-                    if (sh.ep[i] <= xlo) { ns[0] += T(1); ns[1] += sh.sv[i]; }
-                G::template sum<2, T>(ns, sh.red);
-                const T nt = ns[0], St = ns[1];
+                // the block's top part: entries whose entry point is at most xlo (from shared memory)
+                T nt = T(0), St = T(0);
+                for (int i = 0; i < kb; ++i)
+                    if (sh.ep[i] <= xlo) { nt += T(1); St += sh.sv[i]; }
                 T th = xlo;
                 T q[2] = {T(0), T(0)};
 #pragma unroll
@@ -319,6 +349,9 @@ void launch(cudaStream_t s, const ProxArgs& a, int grid, int block) {
     cudaLaunchKernelEx(&cfg, k_prox_fista<T, Grp, E, GPC>, a);   // errors surface at the caller's check
 }
 
+// Threads per node for the CTA kernels: the default splits a node's
+// coordinates 8 per thread; a.threads (FP32, tuned) trades threads for more
+// coordinates per thread so that more nodes are in flight per SM.
 template <typename T>
 int dispatch(cudaStream_t s, const ProxArgs& a) {
     const int p = a.p, m = a.m;
@@ -331,11 +364,32 @@ int dispatch(cudaStream_t s, const ProxArgs& a) {
     else if (p <= 128) KGLM_PROX_WARP(4);
     else if (p <= 256) KGLM_PROX_WARP(8);
     else if (p <= 512) KGLM_PROX_WARP(16);
-    else if (p <= 1024) KGLM_PROX(128, 8);
-    else if (p <= 2048) KGLM_PROX(256, 8);
-    else if (p <= 4096) KGLM_PROX(512, 8);
-    else if (sizeof(T) == 4 && p <= 8192) KGLM_PROX(512, 16);
-    else return -1;
+    else if constexpr (sizeof(T) == 4) {
+        const int t = a.threads;
+        if (p <= 1024) {
+            if (t == 64) KGLM_PROX(64, 16);
+            else if (t == 32) KGLM_PROX(32, 32);
+            else KGLM_PROX(128, 8);
+        } else if (p <= 2048) {
+            if (t == 128) KGLM_PROX(128, 16);
+            else if (t == 64) KGLM_PROX(64, 32);
+            else KGLM_PROX(256, 8);
+        } else if (p <= 4096) {
+            if (t == 256) KGLM_PROX(256, 16);
+            else if (t == 128) KGLM_PROX(128, 32);
+            else KGLM_PROX(512, 8);
+        } else if (p <= 8192) {
+            if (t == 256) KGLM_PROX(256, 32);
+            else KGLM_PROX(512, 16);
+        } else {
+            return -1;
+        }
+    } else {
+        if (p <= 1024) KGLM_PROX(128, 8);
+        else if (p <= 2048) KGLM_PROX(256, 8);
+        else if (p <= 4096) KGLM_PROX(512, 8);
+        else return -1;
+    }
 #undef KGLM_PROX
 #undef KGLM_PROX_WARP
     return 0;
@@ -344,6 +398,15 @@ int dispatch(cudaStream_t s, const ProxArgs& a) {
 }  // namespace
 
 int prox_fista_f64(cudaStream_t s, const ProxArgs& a) { return dispatch<double>(s, a); }
+int prox_thread_options(int p, int* out) {
+    int n = 0;
+    out[n++] = 0;
+    if (p > 512 && p <= 1024) { out[n++] = 64; out[n++] = 32; }
+    else if (p > 1024 && p <= 2048) { out[n++] = 128; out[n++] = 64; }
+    else if (p > 2048 && p <= 4096) { out[n++] = 256; out[n++] = 128; }
+    else if (p > 4096 && p <= 8192) { out[n++] = 256; }
+    return n;
+}
 int prox_fista_f32(cudaStream_t s, const ProxArgs& a) { return dispatch<float>(s, a); }
 
 }  // namespace kglm

@@ -12,6 +12,7 @@
 // the same deterministic kernels in the same order as kglm_solve alone, so
 // its result does not depend on the mix.
 #include <math.h>
+#include <stdio.h>
 
 #include <algorithm>
 #include <atomic>
@@ -71,9 +72,11 @@ kglm_request_info run_request(kglm_server* s, Req* r, kglm_request_info in) {
     d.hbm_budget = in.device_bytes + 65536;   // the admitted share (plus rounding of small arrays)
     kglm_ctx* ctx = nullptr;
     kglm_status st = kglm_create(&d, r->X.data(), r->y.data(), nullptr, &ctx);
+    const char* msg = st == KGLM_OK ? "" : kglm_last_error(nullptr);
     if (st == KGLM_OK) {
         SolveResult res;
         st = solve_cancellable(ctx, d.max_batch, s->d.iters, s->d.check_every, s->d.time_limit_s, &s->cancel, &res);
+        if (st != KGLM_OK) msg = kglm_last_error(ctx);
         if (st == KGLM_OK) {
             in.opt = res.opt;
             in.gap = res.gap;
@@ -82,7 +85,10 @@ kglm_request_info run_request(kglm_server* s, Req* r, kglm_request_info in) {
             for (int t = 0; t < KGLM_MAX_K; ++t) in.support[t] = t < (int)res.support.size() ? res.support[t] : -1;
             in.state = res.cancelled ? KGLM_REQ_CANCELLED : KGLM_REQ_DONE;
         }
+        if (st != KGLM_OK) snprintf(in.message, sizeof(in.message), "%s", msg);
         kglm_destroy(ctx);
+    } else {
+        snprintf(in.message, sizeof(in.message), "%s", msg);
     }
     if (st != KGLM_OK) in.state = KGLM_REQ_FAILED;
     in.status = st;
@@ -219,6 +225,7 @@ kglm_status kglm_server_submit(kglm_server* s, const kglm_desc* desc, const doub
     r->info.batch = d.max_batch;
     r->info.t_admit = -1;
     r->info.t_done = -1;
+    r->info.message[0] = 0;
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (s->stopping) {

@@ -67,6 +67,7 @@ _SIGS = {
     "kglm_suggest_batch": (C.c_int, [C.POINTER(kglm_desc), C.c_int64, C.c_int32, C.POINTER(C.c_int32)]),
     "kglm_autotune": (C.c_int, [P, C.c_int32, C.c_uint64, C.c_void_p]),
     "kglm_configure": (C.c_int, [P, C.c_void_p]),
+    "kglm_selftest_timeout": (C.c_int, [P, C.c_int32]),
     "kglm_pool_create": (C.c_int, [C.c_int32, C.POINTER(P)]),
     "kglm_pool_insert": (C.c_int, [P, C.c_int32, I32, D, C.c_double, I64]),
     "kglm_pool_size": (C.c_int, [P, I64, I64, I64]),
@@ -94,7 +95,8 @@ class kglm_request_info(C.Structure):
     _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("opt", C.c_double), ("gap", C.c_double),
                 ("support", C.c_int32 * MAX_K), ("nodes", C.c_int64), ("batches", C.c_int64),
                 ("device_bytes", C.c_int64), ("batch", C.c_int32), ("reserved", C.c_int32),
-                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("message", C.c_char * 128)]
 
 
 class kglm_server_stats_t(C.Structure):
@@ -109,7 +111,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 class kglm_tune(C.Structure):
     _fields_ = [("batch", C.c_int32), ("link_tile_cols", C.c_int32), ("grad_tile_cols", C.c_int32),
                 ("grad_split_cap", C.c_int32), ("timed", C.c_int32), ("pdl", C.c_int32),
-                ("sub_batches", C.c_int32), ("reserved", C.c_int32),
+                ("sub_batches", C.c_int32), ("prox_threads", C.c_int32),
                 ("nodes_per_s", C.c_double), ("best_nodes_per_s", C.c_double)]
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
@@ -320,14 +322,20 @@ def kglm_autotune(ctx, iters=20, seed=1):
     """Tile shapes and batch size picked by timing (see kglm.h); returns the choice."""
     t = kglm_tune()
     _check(lib().kglm_autotune(ctx, int(iters), int(seed), C.byref(t)), ctx)
-    return {f: getattr(t, f) for f, _ in t._fields_ if f != "reserved"}
+    return {f: getattr(t, f) for f, _ in t._fields_}
 
 
-def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_cap=0, pdl=0, sub_batches=0):
-    """Set tile shapes, split cap, batch, launch mode and sub-batches by hand."""
+def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_cap=0, pdl=0, sub_batches=0,
+                   prox_threads=0):
+    """Set tile shapes, split cap, batch, launch mode, sub-batches and prox threads by hand."""
     t = kglm_tune(batch=batch, link_tile_cols=link_tile_cols, grad_tile_cols=grad_tile_cols,
-                  grad_split_cap=grad_split_cap, pdl=pdl, sub_batches=sub_batches)
+                  grad_split_cap=grad_split_cap, pdl=pdl, sub_batches=sub_batches, prox_threads=prox_threads)
     _check(lib().kglm_configure(ctx, C.byref(t)), ctx)
+
+
+def kglm_selftest_timeout(ctx, rounds=10000):
+    """Runs a bounded device wait that nothing ends; returns the status (KGLM_ETIMEOUT expected)."""
+    return lib().kglm_selftest_timeout(ctx, int(rounds))
 
 
 def kglm_destroy(ctx):
@@ -422,7 +430,7 @@ def _info_dict(i):
     return dict(state=i.state, status=i.status, opt=i.opt, gap=i.gap,
                 support=[int(x) for x in i.support if x >= 0], nodes=i.nodes, batches=i.batches,
                 device_bytes=i.device_bytes, batch=i.batch, t_submit=i.t_submit, t_admit=i.t_admit,
-                t_done=i.t_done)
+                t_done=i.t_done, message=i.message.decode(errors="replace"))
 
 
 class Server:

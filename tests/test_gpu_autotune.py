@@ -90,3 +90,35 @@ def test_sub_batches_give_the_same_results(prec):
             assert np.max(np.abs(B - B0)) <= 1e-5 * max(1.0, np.max(np.abs(B0)))
             for key in ("lb", "ub"):
                 assert np.all(np.abs(res[key] - r0[key]) <= 1e-6 * np.maximum(1.0, np.abs(r0[key]))), key
+
+
+@pytest.mark.parametrize("p,opts", [(1000, (0, 64, 32)), (2000, (0, 128, 64))])
+def test_prox_thread_options_agree(p, opts):
+    """The prox kernels with fewer threads per node (more coordinates each) compute
+    the same step: the certificate at the GPU's own dual point and the
+    rounding/branching decisions match the oracle for every option, and with the
+    FP32-accurate products (no BF16 rounding to amplify the FP32 reduction-order
+    differences of the kernels) the bounds agree across options to 1e-3."""
+    n, k, m = 700, 8, 40
+    X, y, _ = synth.instance(n, p, k, synth.LSQ, rho=0.5, snr=5.0, seed=p)
+    lam2, M = 1e-2, 2.0
+    rng = np.random.default_rng(p + 1)
+    nodes = synth.csr_to_sets(*synth.random_nodes(m, p, k, rng))
+    nodes[0] = ([], [])
+    lbs = []
+    with kglm.Engine(X, y, k, lam2, M, synth.LSQ, prec="tf32x3", max_batch=m) as eng:
+        for t in opts:
+            eng.configure(prox_threads=t) if t else eng.configure()
+            eng.push(*synth.sets_to_csr(nodes))
+            res = eng.evaluate(20)
+            B, Z = eng.read_batch()
+            for b, (J0, J1) in enumerate(nodes):
+                nd = on.Node(p, k, J0, J1)
+                psi = on.dual_value(X, y, Z[b], nd, lam2, M, synth.LSQ)
+                assert res["lb"][b] <= psi + 1e-12 * max(1.0, abs(psi))
+                assert psi - res["lb"][b] <= 1e-6 * max(1.0, abs(psi))
+                assert [int(s) for s in res["support"][b] if s >= 0] == on.round_support(B[b], nd)
+                assert res["branch_j"][b] == on.branch_index(B[b], nd)
+            lbs.append(res["lb"])
+    for lb in lbs[1:]:
+        assert np.all(np.abs(lb - lbs[0]) <= 1e-3 * np.maximum(1.0, np.abs(lbs[0])))
