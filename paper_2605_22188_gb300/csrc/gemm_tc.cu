@@ -313,6 +313,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     const int units = a.mt * a.nt * a.nz;
 
     pdl_trigger();
+    if (threadIdx.x == 32) {
+        // descriptors of the operand maps into the TMA unit's cache before the first copy
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+        if (NB == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB2)) : "memory");
+        if (NA == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
+    }
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), 1); }
         for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 128); }
@@ -397,6 +404,15 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             const Unit w = unit_of(a, u);
             const int b = li & 1;
             const uint32_t use = (uint32_t)(li >> 1) & 1u;
+            // the link's y of this unit's columns (lane l holds column 32 c + l), loaded
+            // before the wait so that the epilogue does not wait on them per chunk
+            float ypre[MAXBN / 32];
+            const bool linky = a.y != nullptr && a.nz == 1 && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16);
+#pragma unroll
+            for (int q = 0; q < MAXBN / 32; ++q) {
+                const int col = w.ntile * a.bn + 32 * q + lane;
+                ypre[q] = (linky && 32 * q < a.bn && col < a.N) ? __ldg(a.y + col) : 0.f;
+            }
             const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[b]), use, a.err));
             if (!ok) break;
             tc_fence_after();
@@ -416,7 +432,10 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                 const int c0 = n0 + c;
                 if (!split && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16)) {
                     // link on the row-per-lane values; y of column c0 + j from lane j
-                    const float yl = (c0 + lane < a.N) ? __ldg(a.y + c0 + lane) : 0.f;
+                    float yl = 0.f;
+#pragma unroll
+                    for (int q = 0; q < MAXBN / 32; ++q)
+                        if (32 * q == c) yl = ypre[q];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
                 }
