@@ -45,7 +45,7 @@ __host__ __device__ inline PairMap pair_map(int ks) {
     pm.nb = (ks + 3) / 4;
     pm.nbp = pm.nb * (pm.nb + 1) / 2;
     pm.ss = 1;
-    while (pm.ss < 32 && 2 * pm.ss * pm.nbp <= NT) pm.ss *= 2;
+    while (pm.ss < 32 && 2 * pm.ss * pm.nbp <= NT) pm.ss *= 2;   // largest power of two with ss * nbp <= NT
     return pm;
 }
 
