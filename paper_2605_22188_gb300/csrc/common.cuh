@@ -328,6 +328,28 @@ template <int E, typename T, typename Mk>
 __device__ Mk warp_topk_tournament(const T (&val)[E], Mk valid, int kth, T* sv, int* si) {
     const int lane = threadIdx.x & 31;
     Mk taken = 0;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the bits of a non-negative float order like the value, so a round is
+        // two warp reductions (redux.sync): the largest magnitude, then the smallest
+        // index holding it.  A lane with nothing left offers key 0 with an index
+        // above every coordinate, so it never wins against a valid element.
+        for (int r = 0; r < kth; ++r) {
+            unsigned bkey = 0u, bidx = 0x7fffffffu;
+            int be = -1;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (bit(valid & ~taken, e)) {
+                    const unsigned k = __float_as_uint(fabsf(val[e]));
+                    if (be < 0 || k > bkey) { bkey = k; bidx = (unsigned)(lane + 32 * e); be = e; }
+                }
+            const unsigned wk = __reduce_max_sync(0xffffffffu, bkey);
+            const unsigned wi = __reduce_min_sync(0xffffffffu, bkey == wk ? bidx : 0x7fffffffu);
+            if (be >= 0 && bidx == wi) taken |= Mk(1) << be;
+            if (lane == 0) { sv[r] = __uint_as_float(wk); si[r] = (int)wi; }
+        }
+        __syncwarp();
+        return taken;
+    }
     for (int r = 0; r < kth; ++r) {
         T best = T(-1);
         int bidx = 0x7fffffff, be = -1;

@@ -116,10 +116,13 @@ __device__ __forceinline__ float tf32_rn(float x) {
     return __uint_as_float(r);
 }
 
-// Loss derivative for operands that are rounded to BF16/TF32 next: fast
-// exponential and reciprocal (relative error far below the operand rounding).
+// Loss derivative for operands that are rounded to BF16/TF32 (or split into
+// TF32 hi + lo) next: fast exponential and approximate division, a few ulp of
+// FP32, below the 2^-22 of the split.  Both are branch-free, so the 32 values
+// of a chunk are evaluated interleaved (a correctly rounded reciprocal
+// serialises them).  1 + e^{ys} = inf gives -0, the limit.
 __device__ __forceinline__ float dloss_fast(float s, float y, int kind) {
-    return kind == kLSQ ? 2.0f * (s - y) : -y * __frcp_rn(1.0f + __expf(y * s));
+    return kind == kLSQ ? 2.0f * (s - y) : __fdividef(-y, 1.0f + __expf(y * s));
 }
 
 // One output value v at (r, c) (r < M, c < N checked by the caller).
@@ -329,6 +332,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     }
     if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
     tc_fence_before();
+    __syncwarp();                    // whole warps at the CTA barrier (lane 0 of warp 0 ran the setup)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
@@ -547,6 +551,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             }
         }
     }
+    // reconverge the role warps (one lane each ran the producer / MMA loop) so
+    // that the barrier holds every thread until the epilogue warps are done
+    __syncwarp();
     __syncthreads();
     if (warp == 0 && lane == 0) {
         // copies still in flight (a wait that ran out) land before the CTA exits

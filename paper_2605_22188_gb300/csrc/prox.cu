@@ -100,6 +100,29 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     constexpr bool HOLD = E <= 16;
     T u[E], vv[HOLD ? E : 1], bo[HOLD ? E : 1];
     Mk valid = 0, fin = 0, fout = 0;
+    // A warp per node loads its momentum t, V, beta and fixing bits before the
+    // gradient, so that these loads overlap the gradient's (a CTA per node loads
+    // them after it: holding them across the gradient loads costs registers, and
+    // registers bound how many node CTAs an SM holds).
+    constexpr bool EARLY = std::is_same<Grp, WarpGroup>::value;
+    const double tprev = (EARLY && G::rank() == 0) ? a.tmom[b] : 0.0;
+    auto load_node = [&](int e) {
+        const int j = G::rank() + e * NT;
+        if constexpr (HOLD) vv[e] = bo[e] = T(0);
+        if (j < p) {
+            valid |= Mk(1) << e;
+            if constexpr (HOLD) {
+                vv[e] = V[base + j];
+                bo[e] = Bm[base + j];
+            }
+            if ((im[j >> 5] >> (j & 31)) & 1u) fin |= Mk(1) << e;
+            else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= Mk(1) << e;
+        }
+    };
+    if constexpr (EARLY) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) load_node(e);
+    }
     // gradient: G, or the sum of its split slices (slice-outer so that the E
     // loads of a slice are in flight together; order of the sum fixed)
     T gsum[E];
@@ -107,7 +130,7 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     for (int e = 0; e < E; ++e) gsum[e] = T(0);
     if (a.gsplits > 0) {
         // QB slices' loads in flight together; the sum keeps the slice order
-        constexpr int QB = E <= 8 ? 4 : 2;
+        constexpr int QB = E <= 8 ? (EARLY ? 8 : 4) : 2;   // a warp per node: more slices in flight
         int q = 0;
         for (; q + QB <= a.gsplits; q += QB) {
             float t[QB][E];
@@ -142,22 +165,26 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int j = G::rank() + e * NT;
+        if constexpr (!EARLY) load_node(e);
         u[e] = T(0);
-        if constexpr (HOLD) vv[e] = bo[e] = T(0);
-        if (j < p) {
-            valid |= Mk(1) << e;
-            const T v = V[base + j];
-            if constexpr (HOLD) {
-                vv[e] = v;
-                bo[e] = Bm[base + j];
-            }
+        if (bit(valid, e)) {
+            T v;
+            if constexpr (HOLD) v = vv[e];
+            else v = V[base + G::rank() + e * NT];
             u[e] = v - eta * gsum[e];
-            if ((im[j >> 5] >> (j & 31)) & 1u) fin |= Mk(1) << e;
-            else if ((om[j >> 5] >> (j & 31)) & 1u) fout |= Mk(1) << e;
         }
     }
     const Mk ffree = valid & ~fin & ~fout;
+    // FISTA t update (FP64), both outcomes of the restart test: without a restart
+    // t' = (1 + sqrt(1 + 4 t^2)) / 2 and coefficient (t - 1) / t'; with one, t = 1,
+    // so t' = (1 + sqrt 5) / 2 and coefficient 0.  The test picks one at the end;
+    // a warp per node computes them here, off the end of its critical path.
+    double t_keep = 0.0, c_keep = 0.0;
+    auto t_candidates = [&](double tp) {
+        t_keep = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tp * tp));
+        c_keep = (tp - 1.0) / t_keep;
+    };
+    if (EARLY && G::rank() == 0) t_candidates(tprev);
     const int kb = a.kbar[b], pf = a.pf[b];
 
     T theta = T(0);
@@ -312,11 +339,10 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     }
     G::template sum<1, T>(dot, sh.red);
     if (G::rank() == 0) {                  // FISTA t update, once per node, in FP64
-        const double tp = a.tmom[b];
-        const double tk1 = (a.restart && dot[0] > T(0)) ? 1.0 : tp;
-        const double tpp = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk1 * tk1));
-        sh.coef = T((tk1 - 1.0) / tpp);
-        a.tmom[b] = tpp;
+        if constexpr (!EARLY) t_candidates(a.tmom[b]);
+        const bool rs = a.restart && dot[0] > T(0);
+        sh.coef = rs ? T(0) : T(c_keep);
+        a.tmom[b] = rs ? 0.5 * (1.0 + sqrt(5.0)) : t_keep;
     }
     G::sync();
     const T coef = sh.coef;
