@@ -16,11 +16,12 @@
 //                    next unit's products run while the epilogue drains the
 //                    last one; tcgen05.commit frees a stage / publishes an
 //                    accumulator;
-//   warps 2-5        epilogue: tcgen05.ld of the accumulator (warp w reads
-//                    TMEM lanes 32(w%4).., the tile's rows), a 32 x 32
-//                    transpose through shared memory, then row-contiguous
-//                    stores of the link, the plain product, a split-K partial
-//                    or a slice of the partial products.
+//   warps 2-9        epilogue: tcgen05.ld of the accumulator (warp w reads
+//                    TMEM lanes 32(w%4).., the tile's rows, and every other
+//                    16-column chunk, so two warps share each sub-partition),
+//                    a 32 x 16 transpose through shared memory, then
+//                    row-contiguous stores of the link, the plain product, a
+//                    split-K partial or a slice of the partial products.
 // Units run row tiles fastest when B is the larger operand (its panel is
 // then reused by consecutive CTAs while A stays in L2) and column tiles
 // fastest otherwise.
@@ -38,8 +39,9 @@
 // the result has the accuracy of an FP32 product (the FP32-accurate mode);
 // its link epilogue writes R as the same hi + lo pair.
 // Split-K with the plain or link epilogue: partial tiles go to scratch and
-// the last epilogue warp to finish a 32-row slab of a tile (arrival counter
-// per slab) sums its partials in fixed order; no warp waits on another.
+// the last epilogue warp to finish a 32-row slab and column half of a tile
+// (an arrival counter for each) sums its partials in fixed order; no warp
+// waits on another.
 // Every mbarrier wait is bounded; a wait that runs out sets an error flag,
 // the roles stop, the MMA issuer drains its products and the producer its
 // copies before the tensor memory is freed.
@@ -57,17 +59,18 @@ namespace {
 constexpr int BM = 128;                 // rows per tile (one UMMA M = 128)
 constexpr int ROWB = 128;               // bytes of K per stage and row (one swizzle row)
 constexpr int MAXBN = 256;
-constexpr int NT = 192;                 // six warps: producer, MMA, four epilogue warps
+constexpr int NT = 320;                 // ten warps: producer, MMA, eight epilogue warps
+constexpr int EPI_WARPS = 8;
 constexpr uint32_t STAGE_A = BM * ROWB;
 constexpr uint32_t TMEM_COLS = 512;     // two accumulators of up to 256 columns
-constexpr int TPAD = 36;                // transpose buffer row: 32 + 4 (16-byte rows, no 128-bit bank conflicts)
+constexpr int TPAD = 20;                // transpose buffer row: 16 + 4 (16-byte rows, no 128-bit bank conflicts on write)
 constexpr int SMS = 152;
 // A stage holds one K slice of every operand part: A (and A2 when NA = 2,
 // the FP32-accurate split A_hi B_hi + A_hi B_lo + A_lo B_hi), B (and B2 when
 // NB = 2, hi + lo).  The ring has as many stages as fit next to the epilogue
 // buffer for the launch's tile width (at most kMaxStages).
 constexpr int kMaxStages = 8;
-constexpr size_t kEpiBytes = 4 * 32 * TPAD * sizeof(float);
+constexpr size_t kEpiBytes = EPI_WARPS * 32 * TPAD * sizeof(float);
 constexpr size_t kSmemMax = 224 * 1024;                    // dynamic shared memory per CTA (static 1 KB on top)
 constexpr size_t kSmemFixed = 1024 + kEpiBytes + 256;      // alignment slack, epilogue, barriers
 __host__ __device__ constexpr uint32_t stage_stride(int na, int nb, int bn) {
@@ -244,22 +247,19 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     // stage s at smem + s SSTR: A, A2 (NA = 2), B, B2 (NB = 2); every part 1024-byte aligned
     const uint32_t offB = (uint32_t)NA * STAGE_A, offB2 = offB + (uint32_t)a.bn * ROWB;
     float* sT = reinterpret_cast<float*>(smem + (size_t)STAGES * SSTR);            // 4 x 32 x TPAD
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sT + 4 * 32 * TPAD);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sT + EPI_WARPS * 32 * TPAD);
     // bars: full[S], empty[S], tfull[2], tempty[2], drain
     uint64_t* full = bars;
     uint64_t* empty = bars + kMaxStages;
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     }
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), 1); }
-        for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 128); }
+        for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 32 * EPI_WARPS); }
         mbar_init(smem_u32(drain), 1);
         s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -400,22 +400,28 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             mbar_wait(smem_u32(drain), 0u, a.err);
         }
     } else {
-        // epilogue: warps 2..5 cover the TMEM lane quadrants 2, 3, 0, 1
+        // epilogue: warps 2..9; warp w reads the TMEM lane quadrant w % 4 (the
+        // tile's rows 32 (w % 4) ..) and every other 16-column chunk of the tile,
+        // starting at chunk h = (w - 2) / 4, so that two warps per SM
+        // sub-partition overlap one's link arithmetic with the other's stores
         const int quad = warp & 3;
+        const int h = (warp - 2) >> 2;
         float* tb = sT + (warp - 2) * 32 * TPAD;
         int li = 0;
         for (int u = blockIdx.x; u < units; u += gridDim.x, ++li) {
             const Unit w = unit_of(a, u);
             const int b = li & 1;
             const uint32_t use = (uint32_t)(li >> 1) & 1u;
-            // the link's y of this unit's columns (lane l holds column 32 c + l), loaded
-            // before the wait so that the epilogue does not wait on them per chunk
+            // the link's y of this warp's columns (lane l < 16 holds column c + l of
+            // its chunk q at c = 16 h + 32 q), loaded before the wait so that the
+            // epilogue does not wait on them per chunk
             float ypre[MAXBN / 32];
             const bool linky = a.y != nullptr && a.nz == 1 && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16);
 #pragma unroll
             for (int q = 0; q < MAXBN / 32; ++q) {
-                const int col = w.ntile * a.bn + 32 * q + lane;
-                ypre[q] = (linky && 32 * q < a.bn && col < a.N) ? __ldg(a.y + col) : 0.f;
+                const int cc = 16 * h + 32 * q + (lane & 15);
+                const int col = w.ntile * a.bn + cc;
+                ypre[q] = (linky && cc < a.bn && col < a.N) ? __ldg(a.y + col) : 0.f;
             }
             const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[b]), use, a.err));
             if (!ok) break;
@@ -425,63 +431,64 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             const bool split = a.nz > 1 && a.epi != TC_EPI_PARTIAL;
             const int tile = w.mtile * a.nt + w.ntile;
             const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * MAXBN);
-            for (int c = 0; c < a.bn; c += 32) {
-                float v[32];
+#pragma unroll 1
+            for (int c = 16 * h, q = 0; c < a.bn; c += 32, ++q) {
+                float v[16];
                 if (w.nloc > 0) {
-                    tmem_ld32(tl + (uint32_t)c, v);
+                    tmem_ld16(tl + (uint32_t)c, v);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
                 }
                 const int c0 = n0 + c;
                 if (!split && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16)) {
                     // link on the row-per-lane values; y of column c0 + j from lane j
                     float yl = 0.f;
 #pragma unroll
-                    for (int q = 0; q < MAXBN / 32; ++q)
-                        if (32 * q == c) yl = ypre[q];
+                    for (int t = 0; t < MAXBN / 32; ++t)
+                        if (t == q) yl = ypre[t];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
+                    for (int j = 0; j < 16; ++j) v[j] = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
                 }
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)                         // row lane, columns j..j+3
+                for (int j = 0; j < 16; j += 4)                         // row lane, columns j..j+3
                     *reinterpret_cast<float4*>(tb + lane * TPAD + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 __syncwarp();
                 if (split) {
-                    // 4 rows x 128 bytes per instruction
+                    // 8 rows x 64 bytes per instruction
                     float* pt = a.part + (((size_t)w.z * (a.mt * a.nt) + tile) * BM + quad * 32) * MAXBN + c;
-                    const int q = lane & 7, r0 = lane >> 3;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = r0 + 4 * i;
-                        *reinterpret_cast<float4*>(pt + (size_t)r * MAXBN + 4 * q) =
-                            *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * q);
-                    }
-                } else if (a.epi == TC_EPI_LINK_BF16) {
-                    // 8 rows x 64 bytes per instruction (8 BF16 per lane)
-                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out);
-                    const int q = lane & 3, r0 = lane >> 2;
-                    const bool vec = (a.ldo % 8) == 0 && c0 + 8 * q + 8 <= a.N;
+                    const int qq = lane & 3, r0 = lane >> 2;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int r = r0 + 8 * i, row = rbase + r;
+                        const int r = r0 + 8 * i;
+                        *reinterpret_cast<float4*>(pt + (size_t)r * MAXBN + 4 * qq) =
+                            *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * qq);
+                    }
+                } else if (a.epi == TC_EPI_LINK_BF16) {
+                    // 16 rows x 32 bytes per instruction (8 BF16 per lane)
+                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out);
+                    const int qq = lane & 1, r0 = lane >> 1;
+                    const bool vec = (a.ldo % 8) == 0 && c0 + 8 * qq + 8 <= a.N;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int r = r0 + 16 * i, row = rbase + r;
                         if (row >= a.M) continue;
-                        const float4 x0 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * q);
-                        const float4 x1 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * q + 4);
-                        __nv_bfloat16* dst = o + (size_t)row * a.ldo + c0 + 8 * q;
+                        const float4 x0 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * qq);
+                        const float4 x1 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * qq + 4);
+                        __nv_bfloat16* dst = o + (size_t)row * a.ldo + c0 + 8 * qq;
                         if (vec) {
-                            __nv_bfloat162 h[4] = {__floats2bfloat162_rn(x0.x, x0.y), __floats2bfloat162_rn(x0.z, x0.w),
-                                                   __floats2bfloat162_rn(x1.x, x1.y), __floats2bfloat162_rn(x1.z, x1.w)};
-                            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+                            __nv_bfloat162 hh[4] = {__floats2bfloat162_rn(x0.x, x0.y), __floats2bfloat162_rn(x0.z, x0.w),
+                                                    __floats2bfloat162_rn(x1.x, x1.y), __floats2bfloat162_rn(x1.z, x1.w)};
+                            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(hh);
                         } else {
                             const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
                             for (int t = 0; t < 8; ++t)
-                                if (c0 + 8 * q + t < a.N) dst[t] = __float2bfloat16(xs[t]);
+                                if (c0 + 8 * qq + t < a.N) dst[t] = __float2bfloat16(xs[t]);
                         }
                     }
                 } else {
-                    // FP32 outputs (product, link, partial slice): 4 rows x 128 bytes per instruction
+                    // FP32 outputs (product, link, partial slice): 8 rows x 64 bytes per instruction
                     float* o;
                     size_t ld;
                     if (a.epi == TC_EPI_PARTIAL) { o = a.pout + (size_t)w.slice * a.pstride; ld = (size_t)a.pld; }
@@ -489,32 +496,32 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     const bool link = a.epi == TC_EPI_LINK_F32;
                     const bool rnd = link && a.round_tf32;
                     float* ol = link ? a.out_lo : nullptr;
-                    const int q = lane & 7, r0 = lane >> 3;
+                    const int qq = lane & 3, r0 = lane >> 2;
                     const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(o) % 16) == 0 &&
-                                     (ol == nullptr || (reinterpret_cast<uintptr_t>(ol) % 16) == 0) && c0 + 4 * q + 4 <= a.N;
+                                     (ol == nullptr || (reinterpret_cast<uintptr_t>(ol) % 16) == 0) && c0 + 4 * qq + 4 <= a.N;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = r0 + 4 * i, row = rbase + r;
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = r0 + 8 * i, row = rbase + r;
                         if (row >= a.M) continue;
-                        const float4 x = *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * q);
+                        const float4 x = *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * qq);
                         float xs[4] = {x.x, x.y, x.z, x.w}, ls[4] = {0.f, 0.f, 0.f, 0.f};
                         if (rnd) {
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
-                                const float h = tf32_rn(xs[t]);
-                                ls[t] = tf32_rn(xs[t] - h);
-                                xs[t] = h;
+                                const float hi = tf32_rn(xs[t]);
+                                ls[t] = tf32_rn(xs[t] - hi);
+                                xs[t] = hi;
                             }
                         }
-                        float* dst = o + (size_t)row * ld + c0 + 4 * q;
-                        float* dlo = ol ? ol + (size_t)row * ld + c0 + 4 * q : nullptr;
+                        float* dst = o + (size_t)row * ld + c0 + 4 * qq;
+                        float* dlo = ol ? ol + (size_t)row * ld + c0 + 4 * qq : nullptr;
                         if (vec) {
                             *reinterpret_cast<float4*>(dst) = make_float4(xs[0], xs[1], xs[2], xs[3]);
                             if (dlo) *reinterpret_cast<float4*>(dlo) = make_float4(ls[0], ls[1], ls[2], ls[3]);
                         } else {
 #pragma unroll
                             for (int t = 0; t < 4; ++t)
-                                if (c0 + 4 * q + t < a.N) {
+                                if (c0 + 4 * qq + t < a.N) {
                                     dst[t] = xs[t];
                                     if (dlo) dlo[t] = ls[t];
                                 }
@@ -528,25 +535,31 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             mbar_arrive(smem_u32(&tempty[b]));
             if (split) {
                 // per-warp arrival: the last of the nz units of this tile to finish
-                // this warp's 32 rows sums their partials (no warp waits on another)
+                // this warp's 32 rows and chunks sums their partials (no warp waits
+                // on another)
                 __threadfence();
                 __syncwarp();
+                const int slab = (tile * 4 + quad) * 2 + h;
                 int last = 0;
-                if (lane == 0) last = atomicAdd(&a.counters[tile * 4 + quad], 1) == a.nz - 1;
+                if (lane == 0) last = atomicAdd(&a.counters[slab], 1) == a.nz - 1;
                 last = __shfl_sync(0xffffffffu, last, 0);
                 if (last) {
                     __threadfence();
-                    for (int c = 0; c < a.bn; c += 32) {
-                        const int col = n0 + c + lane;
-                        const float yc = (a.y != nullptr && col < a.N) ? __ldg(a.y + col) : 0.f;
+                    // lanes 0-15 take chunk c, lanes 16-31 chunk c + 32 (this warp's next)
+                    for (int c = 16 * h; c < a.bn; c += 64) {
+                        const int cc = c + (lane < 16 ? lane : 16 + lane);
+                        const int col = n0 + cc;
+                        const bool in = cc < a.bn && col < a.N;
+                        const float yc = (in && a.y != nullptr) ? __ldg(a.y + col) : 0.f;
                         for (int r = 0; r < 32; ++r) {
                             float acc = 0.f;
-                            for (int z = 0; z < a.nz; ++z)
-                                acc += __ldcg(a.part + (((size_t)z * (a.mt * a.nt) + tile) * BM + quad * 32 + r) * MAXBN + c + lane);
-                            if (col < a.N && rbase + r < a.M) tc_store(a, rbase + r, col, acc, yc, 0);
+                            if (in)
+                                for (int z = 0; z < a.nz; ++z)
+                                    acc += __ldcg(a.part + (((size_t)z * (a.mt * a.nt) + tile) * BM + quad * 32 + r) * MAXBN + cc);
+                            if (in && rbase + r < a.M) tc_store(a, rbase + r, col, acc, yc, 0);
                         }
                     }
-                    if (lane == 0) a.counters[tile * 4 + quad] = 0;
+                    if (lane == 0) a.counters[slab] = 0;
                 }
             }
         }
@@ -643,7 +656,7 @@ int tc_split_cap(int M, int N) {
 int tc_tile_cols_wide(int N) { return N > MAXBN ? 128 : tc_tile_cols(N); }
 
 size_t tc_scratch_bytes() { return (size_t)3 * SMS * BM * MAXBN * sizeof(float); }
-int tc_scratch_counters() { return 4 * SMS; }   // one per 32-row slab of a tile
+int tc_scratch_counters() { return 8 * SMS; }   // one per 32-row slab and column half of a tile
 
 // Persistent grid: one CTA per SM (at most one per unit).
 static int grid_of(int units) { return std::max(1, std::min(units, SMS)); }
@@ -670,7 +683,7 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     int splits = 1;
     if (g.epi == TC_EPI_PARTIAL) {
         splits = std::max(1, std::min(g.max_splits, std::min((a.nkb + 3) / 4, std::max(1, SMS / tiles))));
-    } else if (tiles < SMS && scr && scr->part && scr->counters && scr->n_counters >= 4 * tiles) {
+    } else if (tiles < SMS && scr && scr->part && scr->counters && scr->n_counters >= 8 * tiles) {
         splits = std::min((a.nkb + 3) / 4, std::max(1, SMS / tiles));
         const size_t need = (size_t)splits * tiles * BM * MAXBN * sizeof(float);
         if (need > scr->part_bytes) splits = (int)std::max<size_t>(1, scr->part_bytes / ((size_t)tiles * BM * MAXBN * sizeof(float)));
