@@ -265,7 +265,8 @@ typedef struct {
     int32_t timed;            /* configurations timed */
     int32_t pdl;              /* 1: iteration kernels use programmatic dependent launch */
     int32_t sub_batches;      /* iteration loop split into this many node ranges on parallel streams */
-    int32_t prox_threads;     /* threads per node of the prox for p > 512 in the FP32-type modes (0: default) */
+    int32_t prox_threads;     /* threads per node of the prox for p > 512 in the FP32-type modes (0: default;
+                                 32: one warp per node, p <= 2048) */
     double nodes_per_s;       /* node evaluations per second at the chosen batch */
     double best_nodes_per_s;  /* the best rate over all batch sizes */
 } kglm_tune;

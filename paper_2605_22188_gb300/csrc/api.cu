@@ -1196,7 +1196,7 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
     r.sub_batches = c->nsub;
     // threads per node of the prox (FP32 working type, p > 512)
     if (!c->f64) {
-        int opts[3];
+        int opts[4];
         const int no = prox_thread_options(c->p, opts);
         if (no > 1) {
             double best = INFINITY;
@@ -1791,7 +1791,7 @@ kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg) {
         }
         ctx->pdl = cfg->pdl != 0;
         if (cfg->prox_threads != 0) {
-            int opts[3];
+            int opts[4];
             const int no = prox_thread_options(ctx->p, opts);
             bool ok = false;
             for (int q = 0; q < no; ++q) ok |= opts[q] == cfg->prox_threads;

@@ -375,6 +375,71 @@ __device__ Mk warp_topk_tournament(const T (&val)[E], Mk valid, int kth, T* sv, 
     return taken;
 }
 
+// FP32 warp selection by candidates: tau = the kth largest of the 32 lane
+// maxima (kth lanes each hold an element >= tau, so at least kth elements
+// qualify); when at most 64 elements are >= tau they are ranked in shared
+// memory (cbuf, 64 entries: key above, complemented index below, so that the
+// order of the packed words is magnitude descending, index ascending),
+// otherwise the tournament runs.  Same result, order and tie rule as the
+// tournament; writes sv/si (kth entries) and returns the lane's mask.
+template <int E, typename Mk>
+__device__ Mk warp_topk_candidates(const float (&val)[E], Mk valid, int kth, float* sv, int* si,
+                                   unsigned long long* cbuf) {
+    const int lane = threadIdx.x & 31;
+    if (kth > 32) return warp_topk_tournament<E, float, Mk>(val, valid, kth, sv, si);
+    // keys are recomputed where needed (one instruction) rather than held
+    auto key = [&](int e) { return __float_as_uint(fabsf(val[e])); };
+    unsigned lm = 0u;   // an empty lane offers 0, at or below every valid key
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (bit(valid, e)) lm = max(lm, key(e));
+    // bitonic sort of the lane maxima, ascending over the lanes
+    unsigned x = lm;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned o = __shfl_xor_sync(0xffffffffu, x, j);
+            x = (((lane & j) == 0) == ((lane & k) == 0)) ? min(x, o) : max(x, o);
+        }
+    const unsigned tau = __shfl_sync(0xffffffffu, x, 32 - kth);
+    int cnt = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) cnt += (bit(valid, e) && key(e) >= tau) ? 1 : 0;
+    const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    if (total > 64) return warp_topk_tournament<E, float, Mk>(val, valid, kth, sv, si);
+    int incl = cnt;   // inclusive prefix over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int pos = incl - cnt;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (bit(valid, e) && key(e) >= tau)
+            cbuf[pos++] = ((unsigned long long)key(e) << 32) | (unsigned long long)(0xffffffffu - (unsigned)(lane + 32 * e));
+    __syncwarp();
+    for (int i = lane; i < total; i += 32) {
+        const unsigned long long ci = cbuf[i];
+        int r = 0;
+        for (int t = 0; t < total; ++t) r += cbuf[t] > ci;
+        if (r < kth) {
+            sv[r] = __uint_as_float((unsigned)(ci >> 32));
+            si[r] = (int)(0xffffffffu - (unsigned)ci);
+        }
+    }
+    __syncwarp();
+    const unsigned thk = __float_as_uint(sv[kth - 1]);
+    const int thi = si[kth - 1];
+    Mk sel = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (bit(valid, e) && (key(e) > thk || (key(e) == thk && lane + 32 * e <= thi))) sel |= Mk(1) << e;
+    __syncwarp();
+    return sel;
+}
+
 template <int NT, int E, typename K>
 __device__ uint32_t block_topk_select(const K (&key)[E], uint32_t valid, int kth, SelectShared& sh,
                                       int* ired) {

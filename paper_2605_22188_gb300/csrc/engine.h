@@ -151,8 +151,8 @@ struct ProxArgs {
 // One FISTA step per node: u = v - eta*G, beta' = prox(u), restart, next v.
 int prox_fista_f64(cudaStream_t s, const ProxArgs& a);
 int prox_fista_f32(cudaStream_t s, const ProxArgs& a);
-// Candidate threads-per-node values of the FP32 CTA kernels for p (0 = default
-// first); returns the count written to out (at most 3).
+// Candidate threads-per-node values of the FP32 prox for p (0 = default first,
+// 32 = one warp per node); returns the count written to out (at most 4).
 int prox_thread_options(int p, int* out);
 
 struct CertArgs {

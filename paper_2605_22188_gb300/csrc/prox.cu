@@ -69,8 +69,14 @@ __device__ __forceinline__ T model_root(T nt, T St, T nl, T Sl, T c, T M) {
 }
 
 // One node per group (a CTA of NT threads, or a warp with GPC groups per CTA).
+// A warp per node with 32 or more elements per lane is capped at 128 registers
+// (four 128-thread CTAs per SM): its nodes are independent, so nodes in flight
+// per SM is what hides their latency.
+template <typename Grp, int E>
+constexpr int prox_min_blocks() { return (std::is_same<Grp, WarpGroup>::value && E >= 32) ? 4 : 1; }
+
 template <typename T, typename Grp, int E, int GPC>
-__global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
+__global__ __launch_bounds__(Grp::N * GPC, prox_min_blocks<Grp, E>()) void k_prox_fista(ProxArgs a) {
     using G = Grp;
     using K = typename KeyOf<T>::type;
     constexpr int NT = G::N;
@@ -130,7 +136,7 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     for (int e = 0; e < E; ++e) gsum[e] = T(0);
     if (a.gsplits > 0) {
         // QB slices' loads in flight together; the sum keeps the slice order
-        constexpr int QB = E <= 8 ? (EARLY ? 8 : 4) : 2;   // a warp per node: more slices in flight
+        constexpr int QB = E <= 8 ? (EARLY ? 8 : 4) : (E <= 16 ? 2 : 1);   // a warp per node: more slices in flight
         int q = 0;
         for (; q + QB <= a.gsplits; q += QB) {
             float t[QB][E];
@@ -192,8 +198,9 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
     if (kb > 0 && pf > kb) {
         T amax;
         if constexpr (NT == 32) {
-            // one warp per node: tournament selection, already sorted
-            top = warp_topk_tournament<E, T, Mk>(u, ffree, kb, sh.sv, sh.si);
+            // one warp per node: selection by candidates (FP32) or tournament, already sorted
+            if constexpr (sizeof(T) == 4) top = warp_topk_candidates<E, Mk>(u, ffree, kb, sh.sv, sh.si, sh.sel.ckey);
+            else top = warp_topk_tournament<E, T, Mk>(u, ffree, kb, sh.sv, sh.si);
             T tmax = T(0);
 #pragma unroll
             for (int e = 0; e < E; ++e)
@@ -310,12 +317,9 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
         }
     }
 
-    T bn[E];
-    T dot[1] = {T(0)};
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        bn[e] = T(0);
-        if (!bit(valid, e)) continue;
+    // the new beta_j; with more than 16 elements per thread it is recomputed in
+    // the store loop instead of held (registers bound the nodes in flight)
+    auto beta_new = [&](int e) -> T {
         const T au = abs(u[e]);
         T mag = T(0);
         if (bit(fout, e)) {
@@ -331,11 +335,21 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
         } else {
             mag = max(au - theta, T(0));
         }
-        bn[e] = u[e] < T(0) ? -mag : mag;
+        return u[e] < T(0) ? -mag : mag;
+    };
+    constexpr bool KEEP = E <= 16;
+    T bn[KEEP ? E : 1];
+    T dot[1] = {T(0)};
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if constexpr (KEEP) bn[e] = T(0);
+        if (!bit(valid, e)) continue;
+        const T bv = beta_new(e);
+        if constexpr (KEEP) bn[e] = bv;
         T ve, be;
         if constexpr (HOLD) { ve = vv[e]; be = bo[e]; }
         else { const int j = G::rank() + e * NT; ve = V[base + j]; be = Bm[base + j]; }
-        dot[0] += (ve - bn[e]) * (bn[e] - be);
+        dot[0] += (ve - bv) * (bv - be);
     }
     G::template sum<1, T>(dot, sh.red);
     if (G::rank() == 0) {                  // FISTA t update, once per node, in FP64
@@ -353,8 +367,11 @@ __global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) {
             T be;
             if constexpr (HOLD) be = bo[e];
             else be = Bm[base + j];         // read before this thread overwrites it
-            const T vn = bn[e] + coef * (bn[e] - be);
-            Bm[base + j] = bn[e];
+            T bv;
+            if constexpr (KEEP) bv = bn[e];
+            else bv = beta_new(e);
+            const T vn = bv + coef * (bv - be);
+            Bm[base + j] = bv;
             V[base + j] = vn;
             if (a.Vop != nullptr) store_operand2(a.Vop, a.Vop_lo, (size_t)b * a.op_ld + j, (float)vn, a.op_bf16);
         }
@@ -394,11 +411,12 @@ int dispatch(cudaStream_t s, const ProxArgs& a) {
         const int t = a.threads;
         if (p <= 1024) {
             if (t == 64) KGLM_PROX(64, 16);
-            else if (t == 32) KGLM_PROX(32, 32);
+            else if (t == 32) KGLM_PROX_WARP(32);
             else KGLM_PROX(128, 8);
         } else if (p <= 2048) {
             if (t == 128) KGLM_PROX(128, 16);
             else if (t == 64) KGLM_PROX(64, 32);
+            else if (t == 32) KGLM_PROX_WARP(64);
             else KGLM_PROX(256, 8);
         } else if (p <= 4096) {
             if (t == 256) KGLM_PROX(256, 16);
@@ -428,7 +446,7 @@ int prox_thread_options(int p, int* out) {
     int n = 0;
     out[n++] = 0;
     if (p > 512 && p <= 1024) { out[n++] = 64; out[n++] = 32; }
-    else if (p > 1024 && p <= 2048) { out[n++] = 128; out[n++] = 64; }
+    else if (p > 1024 && p <= 2048) { out[n++] = 128; out[n++] = 64; out[n++] = 32; }
     else if (p > 2048 && p <= 4096) { out[n++] = 256; out[n++] = 128; }
     else if (p > 4096 && p <= 8192) { out[n++] = 256; }
     return n;
