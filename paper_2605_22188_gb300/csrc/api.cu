@@ -1141,6 +1141,19 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         for (int bn : {64, 128, 256})
             if (bn <= tc_tile_cols(c->n)) t1.push_back(bn);
         if (t1.empty()) t1.push_back(tc_tile_cols(c->n));
+        // plus the narrowest tiles whose units (node tiles x sample tiles) fill one
+        // and two waves of the persistent grid, one CTA per SM
+        int sms = 0, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int mt = (mc + 127) / 128;
+        for (int waves : {1, 2}) {
+            for (int bn = 16; bn <= tc_tile_cols(c->n); bn += 16)
+                if (mt * ((c->n + bn - 1) / bn) <= waves * sms) {
+                    if (std::find(t1.begin(), t1.end(), bn) == t1.end()) t1.push_back(bn);
+                    break;
+                }
+        }
         std::vector<int> t2{tc_tile_cols(c->p)};
         if (c->p > 128) t2.push_back(128);
         if (c->p > 64) t2.push_back(64);

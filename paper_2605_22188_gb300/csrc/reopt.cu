@@ -457,6 +457,9 @@ __global__ __launch_bounds__(NT, sizeof(TI) == 4 ? 4 : 1) void k_reopt(ReoptArgs
     // addition give l~ within 2^-22 + 2^-23 + 2^-24 < 2^-21 relative of l(tf)
     // [the relative error of E passes to log1p(E) damped, since
     // d log1p(E)/dE * E <= log1p(E)]: margin 2^-21 l~ + 2^-125 per sample.
+    // The margin and l~ + margin are formed in FP32 rounded upward (|t| <=
+    // |tf| / (1 - 2^-24), so 2^-23 |t| <= 2^-23 |tf| (1 + 2^-22)); only the
+    // predictor and the running sum take FP64 operations, the slow pipe here.
     double part = 0.0;
     const bool fast = sizeof(TI) == 4 && a.kind == kLOGISTIC;
     for (int i = tid; i < a.n; i += NT) {
@@ -466,8 +469,10 @@ __global__ __launch_bounds__(NT, sizeof(TI) == 4 ? 4 : 1) void k_reopt(ReoptArgs
             const double t = a.y[i] * s;
             const float tf = (float)t;
             const float l = fmaxf(-tf, 0.f) + log1pf(expf(-fabsf(tf)));
-            const double slope = tf > 1.f ? fmin(1.0, (double)expf(1.f - tf) * (1.0 + 0x1p-20)) : 1.0;
-            part += (double)l + (ldexp(fabs(t), -23) * slope + ldexp((double)l, -21) + 0x1p-125);
+            const float slope = tf > 1.f ? fminf(1.f, __fmul_ru(expf(1.f - tf), 1.f + 0x1p-20f)) : 1.f;
+            const float m1 = __fmul_ru(__fmul_ru(fabsf(tf), 0x1p-23f * (1.f + 0x1p-22f)), slope);
+            const float mg = __fadd_ru(__fadd_ru(m1, l * 0x1p-21f), 0x1p-125f);
+            part += (double)__fadd_ru(l, mg);
         } else {
             part += loss64(s, a.y[i], a.kind);
         }
