@@ -69,14 +69,8 @@ __device__ __forceinline__ T model_root(T nt, T St, T nl, T Sl, T c, T M) {
 }
 
 // One node per group (a CTA of NT threads, or a warp with GPC groups per CTA).
-// A warp per node with 32 or more elements per lane is capped at 128 registers
-// (four 128-thread CTAs per SM): its nodes are independent, so nodes in flight
-// per SM is what hides their latency.
-template <typename Grp, int E>
-constexpr int prox_min_blocks() { return (std::is_same<Grp, WarpGroup>::value && E >= 32) ? 4 : 1; }
-
 template <typename T, typename Grp, int E, int GPC>
-__global__ __launch_bounds__(Grp::N * GPC, prox_min_blocks<Grp, E>()) void k_prox_fista(ProxArgs a) {
+__device__ __forceinline__ void prox_node(const ProxArgs& a) {
     using G = Grp;
     using K = typename KeyOf<T>::type;
     constexpr int NT = G::N;
@@ -379,6 +373,15 @@ __global__ __launch_bounds__(Grp::N * GPC, prox_min_blocks<Grp, E>()) void k_pro
 }
 
 template <typename T, typename Grp, int E, int GPC>
+__global__ __launch_bounds__(Grp::N * GPC) void k_prox_fista(ProxArgs a) { prox_node<T, Grp, E, GPC>(a); }
+
+// A warp per node with 32 or more elements per lane, capped at 128 registers
+// (four 128-thread CTAs per SM): its nodes are independent, so nodes in flight
+// per SM is what hides their latency.
+template <typename T, int E>
+__global__ __launch_bounds__(128, 4) void k_prox_fista_wide(ProxArgs a) { prox_node<T, WarpGroup, E, 4>(a); }
+
+template <typename T, typename Grp, int E, int GPC>
 void launch(cudaStream_t s, const ProxArgs& a, int grid, int block) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
@@ -389,7 +392,9 @@ void launch(cudaStream_t s, const ProxArgs& a, int grid, int block) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = a.pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_prox_fista<T, Grp, E, GPC>, a);   // errors surface at the caller's check
+    // errors surface at the caller's check
+    if constexpr (std::is_same<Grp, WarpGroup>::value && E >= 32) cudaLaunchKernelEx(&cfg, k_prox_fista_wide<T, E>, a);
+    else cudaLaunchKernelEx(&cfg, k_prox_fista<T, Grp, E, GPC>, a);
 }
 
 // Threads per node for the CTA kernels: the default splits a node's

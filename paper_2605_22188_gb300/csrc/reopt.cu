@@ -116,10 +116,18 @@ __device__ Dyn<TI> carve(unsigned char* base, int k) {
     return d;
 }
 
+// Sum over the CTA, returned in thread 0 (the only reader); the other threads
+// skip the final FP64 additions.  Same order as block_sum.
 __device__ double block_total(double v, double* red) {
-    double a[1] = {v};
-    block_sum<NT, 1, double>(a, red);
-    return a[0];
+    constexpr int NW = NT / 32;
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NW; ++w) s += red[w];
+    return s;
 }
 
 __device__ __forceinline__ float softplus_t(float t) { return t > 0.f ? t + log1pf(expf(-t)) : log1pf(expf(t)); }
@@ -281,10 +289,12 @@ __device__ void evaluate(const ReoptArgs& a, RS& sh, const Dyn<TI>& dy, const do
             }
         }
     }
-    double ridge = 0.0;
-    for (int r = 0; r < ks; ++r) ridge += vec[r] * vec[r];
-    const double f = block_total((double)floss, sh.red) + a.lam2 * ridge;
-    if (tid == 0) sh.f[buf] = f;
+    const double fl = block_total((double)floss, sh.red);
+    if (tid == 0) {                // the ridge term once (FP64 is the slow pipe), same sum as before
+        double ridge = 0.0;
+        for (int r = 0; r < ks; ++r) ridge += vec[r] * vec[r];
+        sh.f[buf] = fl + a.lam2 * ridge;
+    }
     __syncthreads();
 }
 
