@@ -86,6 +86,23 @@ struct kglm_ctx {
     // host mirror of the evaluated batch
     std::vector<int> h_kbar, h_pf, h_jstar;
     std::vector<double> h_lb, h_ub;
+    // pinned staging of the per-batch results read back to the host (asynchronous
+    // copies; pageable destinations would stage and serialise each one)
+    unsigned char* pin = nullptr;
+    size_t pin_m = 0;   // max_batch rounded up to 8
+    template <typename T>
+    T* pinned(size_t off) { return reinterpret_cast<T*>(pin + off); }
+    size_t off_lb() const { return 0; }
+    size_t off_ub() const { return 8 * pin_m; }
+    size_t off_primal() const { return 16 * pin_m; }
+    size_t off_beta() const { return 24 * pin_m; }
+    size_t off_jstar() const { return 24 * pin_m + 8 * pin_m * (size_t)k; }
+    size_t off_iters() const { return off_jstar() + 4 * pin_m; }
+    size_t off_support() const { return off_iters() + 4 * pin_m; }
+    size_t off_err() const { return off_support() + 4 * pin_m * (size_t)k; }
+    size_t off_kbar() const { return off_err() + 16; }
+    size_t off_pf() const { return off_kbar() + 4 * pin_m; }
+    size_t pin_bytes() const { return off_pf() + 4 * pin_m; }
     double sum_pa = 0.0;   // sum over the batch of p - |J0(b)|
     // per-phase device timers and launch counters
     struct Rec {
@@ -700,11 +717,14 @@ void push_dev_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_
     }
     {
         Scope sc(c, PH_COPY, 0, 4.0 + 8.0 * m);
-        CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaMemcpyAsync(hk.data(), c->kbar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaMemcpyAsync(hp.data(), c->pf, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_err()), c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_kbar()), c->kbar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_pf()), c->pf, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
     }
     sync(c);
+    herr = *c->pinned<int>(c->off_err());
+    memcpy(hk.data(), c->pinned<int>(c->off_kbar()), sizeof(int) * m);
+    memcpy(hp.data(), c->pinned<int>(c->off_pf()), sizeof(int) * m);
     if (herr) throw Fail{KGLM_EINVAL, std::string("device checks of the pushed batch failed (") +
                                           ((herr & 1) ? "index out of range " : "") +
                                           ((herr & 2) ? "bad offsets, |J1| > k, repeat or J0/J1 overlap " : "") +
@@ -725,14 +745,26 @@ void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, 
     c->h_jstar.resize(m);
     Scope sc(c, PH_COPY, 0, (double)m * (20.0 + (primal ? 8 : 0) + (support ? 4.0 * c->k : 0) +
                                          (beta_re ? 8.0 * c->k : 0) + (iters_done ? 4 : 0)));
-    CK(cudaMemcpyAsync(c->h_lb.data(), c->lb_best, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(c->h_ub.data(), c->ub, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(c->h_jstar.data(), c->jstar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
-    if (primal) CK(cudaMemcpyAsync(primal, c->primal_now, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
-    if (support) CK(cudaMemcpyAsync(support, c->support, sizeof(int) * (size_t)m * c->k, cudaMemcpyDeviceToHost, c->st));
-    if (beta_re) CK(cudaMemcpyAsync(beta_re, c->beta_re, sizeof(double) * (size_t)m * c->k, cudaMemcpyDeviceToHost, c->st));
-    if (iters_done) CK(cudaMemcpyAsync(iters_done, c->iters_done, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+    const size_t mk = (size_t)m * c->k;
+    CK(cudaMemcpyAsync(c->pinned<double>(c->off_lb()), c->lb_best, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->pinned<double>(c->off_ub()), c->ub, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->pinned<int>(c->off_jstar()), c->jstar, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+    if (primal)
+        CK(cudaMemcpyAsync(c->pinned<double>(c->off_primal()), c->primal_now, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st));
+    if (support)
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_support()), c->support, sizeof(int) * mk, cudaMemcpyDeviceToHost, c->st));
+    if (beta_re)
+        CK(cudaMemcpyAsync(c->pinned<double>(c->off_beta()), c->beta_re, sizeof(double) * mk, cudaMemcpyDeviceToHost, c->st));
+    if (iters_done)
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_iters()), c->iters_done, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
     sync(c);
+    memcpy(c->h_lb.data(), c->pinned<double>(c->off_lb()), sizeof(double) * m);
+    memcpy(c->h_ub.data(), c->pinned<double>(c->off_ub()), sizeof(double) * m);
+    memcpy(c->h_jstar.data(), c->pinned<int>(c->off_jstar()), sizeof(int) * m);
+    if (primal) memcpy(primal, c->pinned<double>(c->off_primal()), sizeof(double) * m);
+    if (support) memcpy(support, c->pinned<int>(c->off_support()), sizeof(int) * mk);
+    if (beta_re) memcpy(beta_re, c->pinned<double>(c->off_beta()), sizeof(double) * mk);
+    if (iters_done) memcpy(iters_done, c->pinned<int>(c->off_iters()), sizeof(int) * m);
     harvest(c);
     if (lb) memcpy(lb, c->h_lb.data(), sizeof(double) * m);
     if (ub_cand) memcpy(ub_cand, c->h_ub.data(), sizeof(double) * m);
@@ -1299,6 +1331,7 @@ void kglm_destroy(kglm_ctx* ctx) {
         if (ctx->ev_join[q]) cudaEventDestroy(ctx->ev_join[q]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
 }
@@ -1442,6 +1475,12 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         // node batch
         const size_t mc = (size_t)d.max_batch;
         c->mcap = d.max_batch;
+        c->pin_m = (mc + 7) / 8 * 8;
+        if (cudaHostAlloc((void**)&c->pin, c->pin_bytes(), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            c->pin = nullptr;
+            throw Fail{KGLM_ENOMEM, "pinned host staging of the batch results refused"};
+        }
         const size_t ws = c->f64 ? sizeof(double) : sizeof(float);
         c->in_mask = dalloc_t<uint32_t>(c, mc * c->W);
         c->out_mask = dalloc_t<uint32_t>(c, mc * c->W);

@@ -546,17 +546,26 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                 if (last) {
                     __threadfence();
                     // lanes 0-15 take chunk c, lanes 16-31 chunk c + 32 (this warp's next)
+                    // eight rows at a time, so that their partial loads are in flight
+                    // together (each sum still runs over z = 0.. in order)
                     for (int c = 16 * h; c < a.bn; c += 64) {
                         const int cc = c + (lane < 16 ? lane : 16 + lane);
                         const int col = n0 + cc;
                         const bool in = cc < a.bn && col < a.N;
                         const float yc = (in && a.y != nullptr) ? __ldg(a.y + col) : 0.f;
-                        for (int r = 0; r < 32; ++r) {
-                            float acc = 0.f;
+                        for (int r0 = 0; r0 < 32; r0 += 8) {
+                            float acc[8];
+#pragma unroll
+                            for (int rr = 0; rr < 8; ++rr) acc[rr] = 0.f;
                             if (in)
-                                for (int z = 0; z < a.nz; ++z)
-                                    acc += __ldcg(a.part + (((size_t)z * (a.mt * a.nt) + tile) * BM + quad * 32 + r) * MAXBN + cc);
-                            if (in && rbase + r < a.M) tc_store(a, rbase + r, col, acc, yc, 0);
+                                for (int z = 0; z < a.nz; ++z) {
+                                    const float* pz = a.part + (((size_t)z * (a.mt * a.nt) + tile) * BM + quad * 32 + r0) * MAXBN + cc;
+#pragma unroll
+                                    for (int rr = 0; rr < 8; ++rr) acc[rr] += __ldcg(pz + (size_t)rr * MAXBN);
+                                }
+#pragma unroll
+                            for (int rr = 0; rr < 8; ++rr)
+                                if (in && rbase + r0 + rr < a.M) tc_store(a, rbase + r0 + rr, col, acc[rr], yc, 0);
                         }
                     }
                     if (lane == 0) a.counters[slab] = 0;
