@@ -93,7 +93,7 @@ def test_sub_batches_give_the_same_results(prec):
                 assert np.all(np.abs(res[key] - r0[key]) <= 1e-6 * np.maximum(1.0, np.abs(r0[key]))), key
 
 
-@pytest.mark.parametrize("p,opts", [(1000, (0, 64, 32)), (2000, (0, 128, 64))])
+@pytest.mark.parametrize("p,opts", [(1000, (0, 64, 32)), (2000, (0, 128, 64, 32))])
 def test_prox_thread_options_agree(p, opts):
     """The prox kernels with fewer threads per node (more coordinates each) compute
     the same step: the certificate at the GPU's own dual point and the

@@ -348,3 +348,36 @@ def test_largest_p_per_precision(prec, p):
             check_reduced_objective(res["ub"][b], v)
     with pytest.raises(kglm.KglmError):
         kglm.Engine(np.zeros((4, p + 4)), np.zeros(4), 2, 0.1, 2.0, synth.LSQ, prec=prec, max_batch=1)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("p", [64, 1024])
+def test_exact_ties_go_to_the_smaller_index(p, prec):
+    """Duplicated columns (x_{2i} = x_{2i+1}) make the two coordinates of a pair
+    tie exactly in every product and prox step, so the iterate keeps the pairs
+    equal; the rounding support and the branching index must then take the
+    smaller index of a tied pair (reading 7), as the oracle does on the same
+    iterate.  The prox selection covers both kernels: a warp per node (p = 64)
+    and a CTA per node (p = 1024).  The bound is checked as a certificate at the
+    GPU's own dual point (X^T X is singular here, so reduced-precision
+    trajectories drift from the FP64 one faster than on the other instances)."""
+    n, k, T, lam2, M = 300, 4, 30, 1e-2, 2.0
+    rng = np.random.default_rng(7)
+    X = np.ascontiguousarray(np.repeat(synth.design(n, p // 2, 0.3, rng), 2, axis=1))
+    bstar = np.zeros(p)
+    bstar[[0, 2 * (p // 8), 2 * (p // 4) + 2, p - 2]] = [1.0, -1.0, 1.0, -1.0]
+    y = X @ bstar + 0.3 * rng.standard_normal(n)
+    L = on.lipschitz(X, synth.LSQ)
+    nodes = [([], [])] + synth.csr_to_sets(*synth.random_nodes(15, p, k, rng, max_out=p // 4, max_in=2))
+    with kglm.Engine(X, y, k, lam2, M, synth.LSQ, prec=prec, max_batch=len(nodes), lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes))
+        res = eng.evaluate(T)
+        B, Z = eng.read_batch()
+    assert np.array_equal(B[0][::2], B[0][1::2]), "the root's iterate should keep the duplicated pairs equal"
+    for b, (J0, J1) in enumerate(nodes):
+        nd = on.Node(p, k, J0, J1)
+        assert [int(s) for s in res["support"][b] if s >= 0] == on.round_support(B[b], nd), b
+        assert res["branch_j"][b] == on.branch_index(B[b], nd), b
+        psi = on.dual_value(X, y, Z[b], nd, lam2, M, synth.LSQ)
+        assert res["lb"][b] <= psi + 1e-12 * max(1.0, abs(psi)), (b, res["lb"][b], psi)
+        assert psi - res["lb"][b] <= 1e-6 * max(1.0, abs(psi)), (b, res["lb"][b], psi)
