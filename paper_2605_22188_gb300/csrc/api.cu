@@ -1169,23 +1169,10 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         // coordinate descent at the full batch: the link product's column tile,
         // then the gradient product's column tile and split cap
         const int cap = c->gsplit_max;
+        // link tile: every width from 32 columns (multiples of 16) up to the sample count
         std::vector<int> t1;
-        for (int bn : {64, 128, 256})
-            if (bn <= tc_tile_cols(c->n)) t1.push_back(bn);
+        for (int bn = 32; bn <= tc_tile_cols(c->n); bn += 16) t1.push_back(bn);
         if (t1.empty()) t1.push_back(tc_tile_cols(c->n));
-        // plus the narrowest tiles whose units (node tiles x sample tiles) fill one
-        // and two waves of the persistent grid, one CTA per SM
-        int sms = 0, dev = 0;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int mt = (mc + 127) / 128;
-        for (int waves : {1, 2}) {
-            for (int bn = 16; bn <= tc_tile_cols(c->n); bn += 16)
-                if (mt * ((c->n + bn - 1) / bn) <= waves * sms) {
-                    if (std::find(t1.begin(), t1.end(), bn) == t1.end()) t1.push_back(bn);
-                    break;
-                }
-        }
         std::vector<int> t2{tc_tile_cols(c->p)};
         if (c->p > 128) t2.push_back(128);
         if (c->p > 64) t2.push_back(64);
@@ -1205,6 +1192,15 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
                 ++timed;
                 if (ms < best) { best = ms; b2 = bn; bs = sc; }
             }
+        // the other gradient widths (multiples of 16 from 64) at the best split cap
+        for (int bn = 64; bn <= tc_tile_cols(c->p); bn += 16) {
+            if (std::find(t2.begin(), t2.end(), bn) != t2.end()) continue;
+            set_tiles(c, b1, bn);
+            c->gsplit_max = bs;
+            const double ms = time_eval(c, t, mc, iters, 3);
+            ++timed;
+            if (ms < best) { best = ms; b2 = bn; }
+        }
         set_tiles(c, b1, b2);
         c->gsplit_max = bs;
         // programmatic dependent launch on or off at the chosen tiles
