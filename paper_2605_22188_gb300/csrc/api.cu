@@ -60,6 +60,10 @@ struct kglm_ctx {
     void *Xop = nullptr, *Xop_lo = nullptr, *Xtop = nullptr, *Vop = nullptr, *Rop = nullptr;
     float *Xtop_lo = nullptr, *Vop_lo = nullptr, *Rop_lo = nullptr;   // low parts (FP32-accurate mode)
     TcMap mA1{}, mB1{}, mB1lo{}, mA2{}, mB2{}, mA1lo{}, mA2lo{}, mB2lo{};
+    // FP32-accurate mode: beta as a TF32 hi + lo operand for the certificate's X beta
+    float *Bop = nullptr, *Bop_lo = nullptr;
+    TcMap mAb{}, mAblo{};
+    bool tc_check_pending = false;   // the tensor-core error flag is on its way to the pinned staging
     int bn1 = 0, bn2 = 0;
     int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
     bool pdl = false;             // programmatic dependent launch inside the iteration graph (tuned)
@@ -100,6 +104,7 @@ struct kglm_ctx {
     size_t off_iters() const { return off_jstar() + 4 * pin_m; }
     size_t off_support() const { return off_iters() + 4 * pin_m; }
     size_t off_err() const { return off_support() + 4 * pin_m * (size_t)k; }
+    size_t off_tcerr() const { return off_err() + 8; }
     size_t off_kbar() const { return off_err() + 16; }
     size_t off_pf() const { return off_kbar() + 4 * pin_m; }
     size_t pin_bytes() const { return off_pf() + 4 * pin_m; }
@@ -336,8 +341,21 @@ void certify(kglm_ctx* c) {
     const double ws = c->f64 ? 8.0 : 4.0;
     {
         Scope sc(c, PH_CERT_XB, 1, 2.0 * n * c->sum_pa);
-        if (c->f64) gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n, &c->gs64);
-        else gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n, &c->gs32);
+        if (c->f64) {
+            gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n, &c->gs64);
+        } else if (c->x3) {
+            // FP32-accurate mode: the same TF32 hi + lo split as S = X V, beta in place of V
+            convert_pad_f32(c->st, (const float*)c->B, m, p, c->Bop, c->pK, 0, c->Bop_lo);
+            check_launch();
+            TcGemm g{};
+            g.kind = 1; g.M = m; g.N = n; g.K = p; g.bn = c->bn1;
+            g.epi = TC_EPI_STORE_F32; g.out = c->R; g.ldo = n; g.err = c->d_tcerr;
+            g.A2 = &c->mAblo;
+            if (tc_gemm(c->st, c->mAb, c->mB1, &c->mB1lo, g, &c->gtc) != 0)
+                throw Fail{KGLM_ECUDA, "tensor-core launch failed (certificate X beta)"};
+        } else {
+            gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n, &c->gs32);
+        }
         check_launch();
     }
     {
@@ -608,7 +626,22 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
         if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
         check_launch();
     }
-    if (c->tc || c->cexact) check_tc_error(c);
+    if (c->tc || c->cexact) {
+        // read back with the results (one synchronisation), checked by finish_tc_check
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_tcerr()), c->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        c->tc_check_pending = true;
+    }
+}
+
+// After a synchronisation that follows evaluate_impl: the tensor-core error flag
+// it sent to the pinned staging.
+void finish_tc_check(kglm_ctx* c) {
+    if (!c->tc_check_pending) return;
+    c->tc_check_pending = false;
+    if (*c->pinned<int>(c->off_tcerr())) {
+        CK(cudaMemsetAsync(c->d_tcerr, 0, sizeof(int), c->st));
+        throw Fail{KGLM_ETIMEOUT, "a tensor-core product's pipeline wait ran out"};
+    }
 }
 
 // A tensor-core product whose mbarrier wait ran out leaves a flag (the kernel
@@ -758,6 +791,7 @@ void evaluate_outputs(kglm_ctx* c, double* lb, double* primal, double* ub_cand, 
     if (iters_done)
         CK(cudaMemcpyAsync(c->pinned<int>(c->off_iters()), c->iters_done, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
     sync(c);
+    finish_tc_check(c);
     memcpy(c->h_lb.data(), c->pinned<double>(c->off_lb()), sizeof(double) * m);
     memcpy(c->h_ub.data(), c->pinned<double>(c->off_ub()), sizeof(double) * m);
     memcpy(c->h_jstar.data(), c->pinned<int>(c->off_jstar()), sizeof(int) * m);
@@ -794,7 +828,7 @@ size_t footprint(const kglm_desc& d) {
         add(n * pK * es); add(n * pK * es); add(p * nK * es);
         if (x3) add(4 * p * nK);
         add(mc * pK * es); add(mc * nK * es);
-        if (x3) { add(4 * mc * pK); add(4 * mc * nK); }
+        if (x3) { add(4 * mc * pK); add(4 * mc * nK); add(4 * mc * pK); add(4 * mc * pK); }
         add(tc_scratch_bytes()); add(4 * (size_t)tc_scratch_counters());
         add(4 * (size_t)tc_split_cap((int)mc, (int)p) * mc * p);   // split slices of X^T R
         add(4);
@@ -1145,6 +1179,7 @@ double time_eval(kglm_ctx* c, const TuneNodes& t, int m, int iters, int reps) {
             evaluate_impl(c, iters, 0);
             CK(cudaEventRecord(e1, c->st));
             CK(cudaEventSynchronize(e1));
+            finish_tc_check(c);
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (r > 0) best = std::min(best, (double)ms);
@@ -1426,6 +1461,8 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
                 c->Rop_lo = dalloc_t<float>(c, mc * c->nK);
                 CK(cudaMemsetAsync(c->Vop_lo, 0, mc * c->pK * 4, c->st));
                 CK(cudaMemsetAsync(c->Rop_lo, 0, mc * c->nK * 4, c->st));
+                c->Bop = dalloc_t<float>(c, mc * c->pK);
+                c->Bop_lo = dalloc_t<float>(c, mc * c->pK);
             }
             c->bn1 = tc_tile_cols_wide((int)n);
             c->bn2 = tc_tile_cols((int)p);
@@ -1437,6 +1474,8 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
                 throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for an operand"};
             if (c->x3 && (tc_make_map(&c->mA1lo, c->Vop_lo, 0, (int)mc, (int)p, c->pK, 128) ||
                           tc_make_map(&c->mA2lo, c->Rop_lo, 0, (int)mc, (int)n, c->nK, 128) ||
+                          tc_make_map(&c->mAb, c->Bop, 0, (int)mc, (int)p, c->pK, 128) ||
+                          tc_make_map(&c->mAblo, c->Bop_lo, 0, (int)mc, (int)p, c->pK, 128) ||
                           tc_make_map(&c->mB2lo, c->Xtop_lo, 0, (int)p, (int)n, c->nK, c->bn2)))
                 throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for a low-part operand"};
             if (tc_prepare() != 0) throw Fail{KGLM_ECUDA, "tensor-core kernels: shared memory attribute refused"};

@@ -36,7 +36,9 @@ constexpr double kFeasRtol = 1e-12;
 //   |t1 - a ln a| <= (2^-23 + 2^-24)|a ln a|             <= 2^-22 |t1|,
 //   |t2 - (1-a) ln(1-a)| <= (2^-22 + 2 * 2^-24)|...|     <= 2^-21 |t2|,
 // so each term carries the margin 2^-22|t1| + 2^-21|t2| + 2^-125 (the last
-// for denormal products), and terms plus margins are summed in FP64.
+// for denormal products); a term plus its margin is formed in FP32 rounded
+// upward (never below the exact sum of the same parts) and the terms are
+// summed in FP64.
 template <int NT>
 __global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
     __shared__ double red[2 * (NT / 32)];
@@ -63,8 +65,10 @@ __global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
             float t1 = 0.f, t2 = 0.f;
             if (sg > 0.f) t1 = sg * logf(sg);
             if (sg < 1.f) t2 = (1.0f - sg) * log1pf(-sg);
-            acc[1] += (double)t1 + (double)t2 +
-                      (ldexp(fabs((double)t1), -22) + ldexp(fabs((double)t2), -21) + 0x1p-125);
+            // margin and sum in FP32 rounded upward (an upper bound, as the FP64 sum of the
+            // same terms was), so that only the running sum uses the slow FP64 pipe
+            const float mg = __fadd_ru(__fadd_ru(fabsf(t1) * 0x1p-22f, fabsf(t2) * 0x1p-21f), 0x1p-125f);
+            acc[1] += (double)__fadd_ru(__fadd_ru(t1, t2), mg);
         }
     }
     block_sum<NT, 2, double>(acc, red);
