@@ -622,14 +622,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 template <int KIND, int NB, int NA>
 int set_smem_attr() {
-    static int done = 0;
-    if (!done) {
-        if (cudaFuncSetAttribute(k_tc_gemm<KIND, NB, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemMax) != cudaSuccess)
-            return -1;
-        done = 1;
-    }
-    return 0;
+    // once per process (thread-safe static initialisation: serving contexts launch from several threads)
+    static const int rc = cudaFuncSetAttribute(k_tc_gemm<KIND, NB, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kSmemMax) == cudaSuccess ? 0 : -1;
+    return rc;
 }
 
 }  // namespace

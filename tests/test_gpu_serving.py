@@ -132,3 +132,33 @@ def test_destroy_stops_running_requests_at_a_batch_boundary():
     srv.close()
     assert time.perf_counter() - t0 < 30.0
     assert ids
+
+
+def test_contexts_with_different_k_evaluate_concurrently():
+    """Two contexts whose re-optimization needs different shared memory (k = 3 and
+    k = 40) evaluate node batches from two host threads at once.  A per-launch
+    shared-memory opt-in sized to one context's k could be lowered by the other
+    between its setting and its launch ("too many resources requested"); the
+    opt-in is now set once to the largest need."""
+    import threading
+    errors = []
+
+    def run(k, seed):
+        try:
+            X, y, _ = synth.instance(600, 120, min(k, 10), synth.LOGISTIC, rho=0.5, seed=seed)
+            rng = np.random.default_rng(seed)
+            csr = synth.random_nodes(256, 120, k, rng)
+            with kglm.Engine(X, y, k, 1e-2, 2.0, synth.LOGISTIC, prec="bf16", max_batch=256) as eng:
+                for _ in range(25):
+                    eng.push(*csr)
+                    res = eng.evaluate(10)
+                    assert np.all(np.isfinite(res["ub"]))
+        except Exception as e:   # reported to the main thread
+            errors.append(repr(e))
+
+    ts = [threading.Thread(target=run, args=(3, 1)), threading.Thread(target=run, args=(40, 2))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
