@@ -26,7 +26,7 @@
 // group of lanes that is summed by shuffles.  Every line-search trial is a
 // full evaluation (f, g, H), so an accepted step needs no further pass.  The
 // returned v(S) is recomputed in a final FP64 pass over the samples.
-#include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "engine.h"
@@ -529,27 +529,22 @@ size_t reopt_smem_bytes(int k) {
     return a > b ? a : b;
 }
 
-// The dynamic shared memory opt-in of k_reopt<TI>, set once per process to the
-// largest need over every supported k.  (Set per launch to that launch's need,
-// a concurrent context with a smaller k could lower it between another
+// The dynamic shared memory opt-in of k_reopt<TI> is set to each launch's need
+// and the launch is issued under the same lock.  (Without the lock, a
+// concurrent context with a smaller k could lower the opt-in between another
 // context's setting and its launch, which then failed with "too many resources
-// requested".)  The opt-in is a ceiling: occupancy follows each launch's size.
-template <typename TI>
-bool reopt_optin() {
-    static const bool ok = [] {
-        size_t mx = 0;
-        for (int k = 1; k <= kMaxK; ++k) mx = std::max(mx, dyn_bytes<TI>(k, true));
-        return cudaFuncSetAttribute(k_reopt<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx) == cudaSuccess;
-    }();
-    return ok;
-}
+// requested".)
+static std::mutex g_reopt_launch_mu;
 
 int reopt_launch(cudaStream_t s, const ReoptArgs& a) {
     if (a.m <= 0) return 0;
     const bool f32 = a.kind == kLOGISTIC && a.Xt32 != nullptr && a.y32 != nullptr;
     const size_t smem = f32 ? dyn_bytes<float>(a.k, true) : dyn_bytes<double>(a.k, a.kind == kLOGISTIC);
     // the opt-in covers static + dynamic shared memory above the 48 KB default
-    if (!(f32 ? reopt_optin<float>() : reopt_optin<double>())) return -1;
+    std::lock_guard<std::mutex> lock(g_reopt_launch_mu);
+    if (cudaFuncSetAttribute(f32 ? k_reopt<float> : k_reopt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return -1;
     if (f32) k_reopt<float><<<a.m, NT, smem, s>>>(a);
     else k_reopt<double><<<a.m, NT, smem, s>>>(a);
     return 0;

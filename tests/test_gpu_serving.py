@@ -139,7 +139,7 @@ def test_contexts_with_different_k_evaluate_concurrently():
     k = 40) evaluate node batches from two host threads at once.  A per-launch
     shared-memory opt-in sized to one context's k could be lowered by the other
     between its setting and its launch ("too many resources requested"); the
-    opt-in is now set once to the largest need."""
+    setting and the launch now happen under one lock."""
     import threading
     errors = []
 
