@@ -163,7 +163,8 @@ PHASE_KERNEL_SOURCES = {
     "prox_fista": ["paper_2605_22188_gb300/csrc/prox.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
     "cert_xtzeta": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu",
                     "paper_2605_22188_gb300/csrc/cert_exact.cu"],
-    "cert_xb": ["paper_2605_22188_gb300/csrc/gemm_simt.cu"],
+    "cert_xb": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu",
+                "paper_2605_22188_gb300/csrc/layout.cu"],
     "cert_bound": ["paper_2605_22188_gb300/csrc/cert.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
     "cert_dual_point": ["paper_2605_22188_gb300/csrc/cert.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
     "reopt": ["paper_2605_22188_gb300/csrc/reopt.cu"],
