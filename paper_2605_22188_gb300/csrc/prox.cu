@@ -1,5 +1,7 @@
 // Masked proximal step of §3 Eq. (pgd_step_vector_form) for a batch of nodes,
-// fused with the FISTA extrapolation and gradient restart.  One CTA per node.
+// fused with the FISTA extrapolation and gradient restart.  One warp per node
+// up to 512 coordinates (four nodes per CTA; a tuned option up to 2048), one
+// CTA per node above.
 //
 // For node N with step eta, c = 2*eta*lambda2 = 1/rho and u = v - eta*G:
 //   J0:  beta_j = 0
@@ -17,7 +19,8 @@
 //   f(x) = sum_tail (|u_j| - x)^+ - sum_top (h(x) - |u_j|)^+ = 0,
 //   h(x) = x + min(x/c, M),
 // a strictly decreasing function.  Instead of the padded column sort of §4.2
-// (Fig. 2) the kernel selects the kbar largest free magnitudes (radix select),
+// (Fig. 2) the kernel selects the kbar largest free magnitudes (a CTA by radix
+// select, a warp by candidates above the kbar-th largest lane maximum),
 // sorts only those, finds the piece of f between consecutive top entry points
 // p(|u_j|) that holds the root (binary search), and solves the piece by Newton
 // steps from its left end: f is convex there, so the steps never pass the

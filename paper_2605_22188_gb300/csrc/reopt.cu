@@ -25,7 +25,9 @@
 // on and above the diagonal, each block's samples split over a power-of-two
 // group of lanes that is summed by shuffles.  Every line-search trial is a
 // full evaluation (f, g, H), so an accepted step needs no further pass.  The
-// returned v(S) is recomputed in a final FP64 pass over the samples.
+// returned v(S) is recomputed in a final pass over the samples: FP64 in the
+// FP64 mode; in the others an FP64 predictor with the logistic loss and its
+// rigorous rounding margin in FP32 (rounded upward), an upper bound of v(S).
 #include <mutex>
 
 #include "common.cuh"
