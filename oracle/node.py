@@ -177,24 +177,26 @@ def g_node(beta, node, M):
         return g + 0.5 * float(np.sum(b * b))
     bs = np.sort(b)[::-1]                          # |beta_pi(1)| >= ... >= |beta_pi(pf)|
     tail = np.cumsum(bs[::-1])[::-1]               # tail[r] = sum_{r' >= r} bs[r'] (0-based)
-    for s in range(kbar):                          # s = number of capped coordinates
-        tau = tail[s] / (kbar - s)
-        upper = np.inf if s == 0 else bs[s - 1]
-        lower = bs[s]
-        if upper >= tau >= lower:
-            # z = 1 on the first s, z = |beta|/tau after: sum_{r>s} beta^2/z = tau * sum_{r>s} |beta|
-            return g + 0.5 * (float(np.sum(bs[:s] ** 2)) + tau * float(tail[s]))
-    # no consistent s: only reachable through rounding at a breakpoint; take the
-    # s whose consistency violation is smallest.
-    best, best_val = None, np.inf
+    s, tau = _capped_count(bs, tail, kbar)
+    # z = 1 on the first s, z = |beta|/tau after: sum_{r>s} beta^2/z = tau * sum_{r>s} |beta|
+    return g + 0.5 * (float(np.sum(bs[:s] ** 2)) + tau * float(tail[s]))
+
+
+def _capped_count(bs, tail, kbar):
+    """The s of Theorem 4.1 (coordinates with z_j = 1) and tau = tail[s] / (kbar - s).
+
+    s is the smallest index in [0, kbar) with tau_s >= |beta|_(s+1); then also
+    tau_s < |beta|_(s) (for s > 0, tau_{s-1} < |beta|_(s) is equivalent to
+    tau_s < |beta|_(s)), so |beta|_(s) > tau >= |beta|_(s+1) as the theorem
+    requires.  s = kbar - 1 always qualifies (tail[kbar-1] >= bs[kbar-1], also
+    in floating point, where adding non-negative terms never decreases a sum),
+    so the search needs no fallback.
+    """
     for s in range(kbar):
         tau = tail[s] / (kbar - s)
-        upper = np.inf if s == 0 else bs[s - 1]
-        viol = max(0.0, tau - upper) + max(0.0, bs[s] - tau)
-        if viol < best_val:
-            best, best_val = s, viol
-    tau = tail[best] / (kbar - best)
-    return g + 0.5 * (float(np.sum(bs[:best] ** 2)) + tau * float(tail[best]))
+        if tau >= bs[s]:
+            return s, tau
+    raise ArithmeticError("unreachable: tail[kbar-1] >= bs[kbar-1]")
 
 
 def z_recover(beta, node, M):
@@ -215,14 +217,9 @@ def z_recover(beta, node, M):
     order = np.argsort(-b, kind="stable")
     bs = b[order]
     tail = np.cumsum(bs[::-1])[::-1]
-    for s in range(kbar):
-        tau = tail[s] / (kbar - s)
-        upper = np.inf if s == 0 else bs[s - 1]
-        if upper >= tau >= bs[s]:
-            zz = np.where(np.arange(bs.size) < s, 1.0, bs / tau)
-            z[Jf[order]] = zz
-            return z
-    raise ArithmeticError("no consistent s in Theorem 4.1")
+    s, tau = _capped_count(bs, tail, kbar)
+    z[Jf[order]] = np.where(np.arange(bs.size) < s, 1.0, bs / tau)
+    return z
 
 
 def g_conj_node(q, node, M):
@@ -280,12 +277,16 @@ def solve_node(X, y, node, lam2, M, kind, L, T, beta0=None, restart=True,
                check_every=0, ub=np.inf, delta=0.0, gap_rtol=0.0):
     """T iterations of FISTA on Phi_N (§3 Eq. (node_composite)) from beta0.
 
-    Iteration (t_0 = 1, beta_{-1} = beta_0):
+    FISTA in the indexing of Beck and Teboulle (2009): y_1 = x_0 = beta0,
+    t_1 = 1, and for k = 1, 2, ...
+        x_k     = prox_node(y_k - eta * X^T dl(X y_k, y))   (§3 Eq. (pgd_step_vector_form))
         t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
-        v       = beta_k + ((t_k - 1) / t_{k+1}) (beta_k - beta_{k-1})
-        u       = v - eta * X^T dl(X v, y)
-        beta_{k+1} = prox_node(u)                    (§3 Eq. (pgd_step_vector_form))
-        if restart and <v - beta_{k+1}, beta_{k+1} - beta_k> > 0:  t_{k+1} = 1
+        y_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1})
+    so the first two proximal steps take no momentum.  Gradient restart
+    (O'Donoghue and Candes 2015) with the proximal gradient mapping in place
+    of the gradient: if <y_k - x_k, x_k - x_{k-1}> > 0 the method starts over
+    from x_k, i.e. y_{k+1} = x_k and t_{k+1} = 1 (the step after it then takes
+    no momentum either).
     With check_every > 0 the certificate is evaluated every check_every
     iterations; the loop stops once LB >= ub - delta or Phi - LB <=
     gap_rtol * max(1, |Phi|).  The returned LB is the best certificate seen
@@ -301,20 +302,21 @@ def solve_node(X, y, node, lam2, M, kind, L, T, beta0=None, restart=True,
     beta = np.zeros(p) if beta0 is None else np.array(beta0, dtype=np.float64)
     if node.J0:
         beta[np.array(node.J0)] = 0.0
-    beta_old = beta.copy()
-    t = 1.0
+    beta_old = beta.copy()     # x_{k-1}
+    yk = beta.copy()           # y_k
+    t = 1.0                    # t_k
     best_lb = -np.inf
     primal = np.inf
     it = 0
     while it < T:
+        grad = X.T @ dloss(X @ yk, y, kind)
+        beta_new = prox_node(yk - eta * grad, node, rho, M)        # x_k
         t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
-        v = beta + ((t - 1.0) / t_new) * (beta - beta_old)
-        grad = X.T @ dloss(X @ v, y, kind)
-        u = v - eta * grad
-        beta_new = prox_node(u, node, rho, M)
-        if restart and float(np.dot(v - beta_new, beta_new - beta)) > 0.0:
-            t_new = 1.0
-        beta_old, beta, t = beta, beta_new, t_new
+        if restart and float(np.dot(yk - beta_new, beta_new - beta)) > 0.0:
+            y_next, t_new = beta_new.copy(), 1.0
+        else:
+            y_next = beta_new + ((t - 1.0) / t_new) * (beta_new - beta)
+        beta, yk, t = beta_new, y_next, t_new
         it += 1
         if check_every > 0 and it % check_every == 0 and it < T:
             lb, primal = certify(X, y, beta, node, lam2, M, kind)

@@ -28,7 +28,8 @@ def reopt(X, y, S, lam2, M, kind, beta0=None, tol=1e-12, max_iter=200000):
     Step 1/L_S with L_S the Lipschitz constant of the gradient of
     F(X_S b) + lambda2 ||b||^2.  Stops when the gradient-mapping norm
     L_S * ||b - P(b - grad/L_S)|| <= tol * max(1, ||grad at the start||);
-    gradient restart as in the node solver.  Returns (beta in R^p, v(S)).
+    FISTA indexing and gradient restart as in the node solver.  Returns
+    (beta in R^p, v(S)).
     """
     X = np.asarray(X, dtype=np.float64)
     p = X.shape[1]
@@ -45,15 +46,16 @@ def reopt(X, y, S, lam2, M, kind, beta0=None, tol=1e-12, max_iter=200000):
 
     g0 = np.linalg.norm(grad(b))
     stop = tol * max(1.0, g0)
-    b_old = b.copy()
+    v = b.copy()
     t = 1.0
     for _ in range(max_iter):
-        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
-        v = b + ((t - 1.0) / t_new) * (b - b_old)
         b_new = np.clip(v - grad(v) / LS, -M, M)
+        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
         if float(np.dot(v - b_new, b_new - b)) > 0.0:
-            t_new = 1.0
-        b_old, b, t = b, b_new, t_new
+            v, t_new = b_new.copy(), 1.0
+        else:
+            v = b_new + ((t - 1.0) / t_new) * (b_new - b)
+        b, t = b_new, t_new
         gm = LS * np.linalg.norm(b - np.clip(b - grad(b) / LS, -M, M))
         if gm <= stop:
             break
