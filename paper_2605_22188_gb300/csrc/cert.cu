@@ -238,27 +238,18 @@ __global__ __launch_bounds__(NT) void k_cert_bound(const __grid_constant__ CertA
         else if (total / M > kb * (1.0 + kFeasRtol)) gf = INFINITY;
         else if (nnz <= kb) gf = 0.5 * sumsq;
         else {
-            gf = -1.0;
+            // s = the smallest index with tau_s >= |beta|_(s+1); then |beta|_(s) > tau_s
+            // too, as Theorem 4.1 requires.  s = kbar - 1 qualifies in exact
+            // arithmetic; it is also taken if rounding in total - pre says otherwise.
             double pre = 0.0, presq = 0.0;
-            int best = 0;
-            double bestv = INFINITY;
-            for (int s = 0; s < kb; ++s) {
-                const double tail = total - pre;
-                const double tau = tail / (kb - s);
-                const double upper = s == 0 ? INFINITY : sh.sv[s - 1];
-                const double lower = sh.sv[s];
-                if (upper >= tau && tau >= lower) { gf = 0.5 * (presq + tau * tail); break; }
-                const double viol = fmax(0.0, tau - upper) + fmax(0.0, lower - tau);
-                if (viol < bestv) { bestv = viol; best = s; }
+            int s = 0;
+            for (; s < kb - 1; ++s) {
+                if ((total - pre) / (kb - s) >= sh.sv[s]) break;
                 pre += sh.sv[s];
                 presq += sh.sv[s] * sh.sv[s];
             }
-            if (gf < 0.0) {
-                double pre2 = 0.0, presq2 = 0.0;
-                for (int s = 0; s < best; ++s) { pre2 += sh.sv[s]; presq2 += sh.sv[s] * sh.sv[s]; }
-                const double tail = total - pre2;
-                gf = 0.5 * (presq2 + tail / (kb - best) * tail);
-            }
+            const double tail = total - pre;
+            gf = 0.5 * (presq + tail / (kb - s) * tail);
         }
         sh.gfree = gf;
     }

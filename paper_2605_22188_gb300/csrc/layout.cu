@@ -200,8 +200,8 @@ int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot
     else
         k_warm<float><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const float*)pool, warmB, out_mask,
                                                      (float*)B, (float*)V, Vop, Vop_lo, op_ld, op_bf16);
-    // t' = (1 + sqrt(5)) / 2: the FISTA t after t_0 = 1
-    k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 0.5 * (1.0 + sqrt(5.0)), tmom, active);
+    // t_1 = 1 (Beck and Teboulle): the first extrapolation, after x_1, takes no momentum
+    k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 1.0, tmom, active);
     return 2;
 }
 

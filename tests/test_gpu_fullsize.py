@@ -39,11 +39,13 @@ def _v_exact(X, y, S, lam2, M, kind):
     return ro._v_logistic_exact(X, y, S, lam2, M)[0]
 
 
-def _evaluate_like_bench(X, y, c, prec, m, T, csr):
-    """push_dev on a side stream, T FISTA iterations under CUDA graphs, as bench.py times them."""
+def _evaluate_like_bench(X, y, c, prec, m, T, csr, L=0.0):
+    """push_dev on a side stream, T FISTA iterations under CUDA graphs, as bench.py times them.
+    L: the step's Lipschitz constant (0: the engine's own estimate, as the bench runs;
+    trajectory comparisons pass the oracle's value so that both sides take one step size)."""
     torch = pytest.importorskip("torch")
     stream = torch.cuda.Stream()
-    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=prec, max_batch=m,
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=prec, max_batch=m, lipschitz=L,
                      stream=stream.cuda_stream) as eng:
         t = [torch.from_numpy(a).to("cuda") for a in csr]
         with torch.cuda.stream(stream):
@@ -140,7 +142,7 @@ def test_c2_fp64_products_match_oracle_iterates():
     m, T = c["m"], 50
     nodes, csr = _batch(c, m, 1001)
     L = on.lipschitz(X, c["kind"])
-    res, B, Z = _evaluate_like_bench(X, y, c, "fp64", m, T, csr)
+    res, B, Z = _evaluate_like_bench(X, y, c, "fp64", m, T, csr, L=L)
     _invariants(res, nodes, c["p"], c["k"])
     for b in list(range(5)) + [100, 900]:
         J0, J1 = nodes[b]

@@ -2,8 +2,11 @@
 
 Tolerances (written here, derived from the arithmetic):
 * FP64 path: iterates, bounds, primal values and re-optimized objectives
-  agree with the oracle to 1e-9 relative (summation order is the only
-  difference; FISTA is non-expansive so it does not amplify it);
+  agree with the oracle to 1e-9 relative.  Summation order is the only
+  difference; the proximal-gradient step is non-expansive, the momentum step
+  is not, so the rounding differences can grow over the iterations, but at
+  these sizes and T <= 60 they stay far below 1e-9 (at the full c2 size and
+  T = 50 the iterates are compared at 1e-7, test_gpu_fullsize.py);
 * FP64 path: the GPU bound equals the oracle's Psi_N evaluated at the GPU's
   own dual point to 1e-9 relative (the certificate arithmetic is FP64);
 * reduced-precision paths: the GPU bound never exceeds Psi_N at its own dual
