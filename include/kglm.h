@@ -220,11 +220,14 @@ kglm_status kglm_xtz(kglm_ctx* ctx, int32_t m, const double* Z, double* Q, doubl
  * The call only enqueues work on `stream` (G is ready when the stream
  * reaches it).  The first call on a device, with that device current, looks
  * up the array's device address and clears the counters; make that first
- * call before any stream capture.  All calls share the one array, which
+ * call before any stream capture (a first call on a capturing stream returns
+ * KGLM_EINVAL and changes nothing).  All calls share the one array, which
  * keeps the last call's partial tiles (the counters return to 0 after each
  * call): calls that overlap on the GPU, on any streams, race.  Errors:
- * KGLM_EINVAL for bad sizes or pointers, KGLM_ECUDA for a failed CUDA call;
- * no message is recorded (there is no context). */
+ * KGLM_EINVAL for bad sizes or pointers, KGLM_ECUDA for a failed CUDA call,
+ * and also, without launching, when an error from earlier work on the calling
+ * thread is still pending (it is left for its owner to read); no message is
+ * recorded (there is no context). */
 #define KGLM_XTR_NOALLOC_SCRATCH_FLOATS (4u << 20)
 #define KGLM_XTR_NOALLOC_MAX_TILES 256
 kglm_status kglm_xtr_noalloc_f32(int32_t m, int32_t n, int32_t p, const float* R, const float* Xt,

@@ -324,8 +324,9 @@ void launch_clamped(cudaStream_t s, int R, int C, int K, const T* A, int lda, co
 
 template <typename T>
 int ctas_per_sm() {
-    static int cached = 0;
-    if (cached == 0) {
+    // computed once per process (a function-local static initialiser is
+    // thread-safe; calls may come from several host threads at once)
+    static const int cached = [] {
         using TL = Tile<T>;
         constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
         int n = 0;
@@ -335,8 +336,8 @@ int ctas_per_sm() {
             cudaGetLastError();
             n = 2;
         }
-        cached = n;
-    }
+        return n;
+    }();
     return cached;
 }
 

@@ -35,8 +35,8 @@ DeviceScratch g_dev[kMaxDevices];
 extern "C" kglm_status kglm_xtr_noalloc_f32(int32_t m, int32_t n, int32_t p, const float* R, const float* Xt,
                                              float* G, void* stream) {
     if (m < 1 || n < 1 || p < 1 || !R || !Xt || !G) return KGLM_EINVAL;
-    const int64_t tiles = (int64_t)((m + kglm::gemm_tile_rows_f32() - 1) / kglm::gemm_tile_rows_f32()) *
-                          ((p + kglm::gemm_tile_cols_f32() - 1) / kglm::gemm_tile_cols_f32());
+    const int64_t tr = kglm::gemm_tile_rows_f32(), tc = kglm::gemm_tile_cols_f32();
+    const int64_t tiles = (((int64_t)m + tr - 1) / tr) * (((int64_t)p + tc - 1) / tc);
     if (tiles > KGLM_XTR_NOALLOC_MAX_TILES) return KGLM_EINVAL;   // beyond the fixed scratch
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -44,12 +44,22 @@ extern "C" kglm_status kglm_xtr_noalloc_f32(int32_t m, int32_t n, int32_t p, con
         return KGLM_ECUDA;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // an error left pending by earlier work on this thread is not this call's:
+    // report it without clearing it and without launching
+    if (cudaPeekAtLastError() != cudaSuccess) return KGLM_ECUDA;
     DeviceScratch ds;
     {
         std::lock_guard<std::mutex> lock(g_mu);
         if (g_dev[dev].part == nullptr) {
             // first call on this device: device addresses of the file-scope
-            // arrays (host code only holds stand-ins for them), counters to 0
+            // arrays (host code only holds stand-ins for them), counters to 0.
+            // Not under stream capture: the set-up must run, not be recorded.
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+                cudaGetLastError();
+                return KGLM_ECUDA;
+            }
+            if (cap != cudaStreamCaptureStatusNone) return KGLM_EINVAL;
             float* part = nullptr;
             int* counters = nullptr;
             if (cudaGetSymbolAddress((void**)&part, g_xtr_part) != cudaSuccess ||

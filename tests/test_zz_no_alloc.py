@@ -38,6 +38,12 @@ def test_noalloc_matches_kglm_xtr_on_two_calls():
             a, b = G_ref.cpu().numpy().astype(np.float64), G_new.cpu().numpy().astype(np.float64)
             assert np.all(np.isfinite(b))
             assert np.all(np.abs(a - b) <= 2 * _bound(R, X, n)), "call %d" % call
+        # nothing is allocated: device free memory is unchanged across further calls
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            kglm.kglm_xtr_noalloc_f32(m, n, p, Rd.data_ptr(), Xt.data_ptr(), G_new.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_ragged_sizes_and_limit():
