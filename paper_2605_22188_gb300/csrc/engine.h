@@ -154,6 +154,12 @@ int prox_fista_f32(cudaStream_t s, const ProxArgs& a);
 // Candidate threads-per-node values of the FP32 prox for p (0 = default first,
 // 32 = one warp per node); returns the count written to out (at most 4).
 int prox_thread_options(int p, int* out);
+// The FP32 prox as a persistent kernel, a warp streaming nodes through shared
+// memory (prox_stream.cu); the default for 512 < p <= kStreamMaxP where at
+// least six warps' rows fit in an SM's shared memory.  Returns 0 when
+// launched, 1 when p is outside its range (no launch), -1 on a CUDA error.
+constexpr int kStreamMaxP = 4096;
+int prox_stream_f32(cudaStream_t s, const ProxArgs& a);
 
 struct CertArgs {
     int m, n, p, W, k, kind;

@@ -1,7 +1,8 @@
 // Masked proximal step of §3 Eq. (pgd_step_vector_form) for a batch of nodes,
 // fused with the FISTA extrapolation and gradient restart.  One warp per node
 // up to 512 coordinates (four nodes per CTA; a tuned option up to 2048), one
-// CTA per node above.
+// CTA per node above.  In FP32 with 512 < p <= 4096 the default is the
+// persistent kernel of prox_stream.cu (the kernels here remain tuned options).
 //
 // For node N with step eta, c = 2*eta*lambda2 = 1/rho and u = v - eta*G:
 //   J0:  beta_j = 0
@@ -178,10 +179,12 @@ __device__ __forceinline__ void prox_node(const ProxArgs& a) {
         }
     }
     const Mk ffree = valid & ~fin & ~fout;
-    // FISTA t update (FP64), both outcomes of the restart test: without a restart
-    // t' = (1 + sqrt(1 + 4 t^2)) / 2 and coefficient (t - 1) / t'; with one, t = 1,
-    // so t' = (1 + sqrt 5) / 2 and coefficient 0.  The test picks one at the end;
-    // a warp per node computes them here, off the end of its critical path.
+    // FISTA t update (FP64; tmom holds t_k of the iterate x_k this step makes,
+    // t_1 = 1): without a restart t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 and
+    // v_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1}); a restart starts over
+    // from x_k (v_{k+1} = x_k, t_{k+1} = 1, so the next coefficient is 0 too).
+    // The test picks one at the end; a warp per node computes the candidates
+    // here, off the end of its critical path.
     double t_keep = 0.0, c_keep = 0.0;
     auto t_candidates = [&](double tp) {
         t_keep = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tp * tp));
@@ -353,7 +356,7 @@ __device__ __forceinline__ void prox_node(const ProxArgs& a) {
         if constexpr (!EARLY) t_candidates(a.tmom[b]);
         const bool rs = a.restart && dot[0] > T(0);
         sh.coef = rs ? T(0) : T(c_keep);
-        a.tmom[b] = rs ? 0.5 * (1.0 + sqrt(5.0)) : t_keep;
+        a.tmom[b] = rs ? 1.0 : t_keep;      // restart: start over from this iterate, t = 1
     }
     G::sync();
     const T coef = sh.coef;
@@ -417,6 +420,10 @@ int dispatch(cudaStream_t s, const ProxArgs& a) {
     else if (p <= 512) KGLM_PROX_WARP(16);
     else if constexpr (sizeof(T) == 4) {
         const int t = a.threads;
+        if (t == 0 && p <= kStreamMaxP) {           // persistent, a warp streams nodes
+            const int rc = prox_stream_f32(s, a);
+            if (rc <= 0) return rc;                 // 1: too few warps fit; the kernels below
+        }
         if (p <= 1024) {
             if (t == 64) KGLM_PROX(64, 16);
             else if (t == 32) KGLM_PROX_WARP(32);

@@ -1,0 +1,516 @@
+// Masked proximal step of §3 Eq. (pgd_step_vector_form) with the FISTA
+// extrapolation and gradient restart, for FP32 batches with 512 < p <= 4096:
+// a persistent kernel in which every warp streams nodes, one at a time, through
+// its own slice of shared memory.
+//
+// The step is the one of prox.cu (Algorithm 1 of App. B as top-kbar selection
+// plus one pooled block with threshold theta, in the scale of u):
+//   J0: beta = 0;  J1: beta = sign(u) min(|u|/(1+c), M);
+//   top (kbar largest free |u|): sign(u) max(min(|u|/(1+c), M, |u| - theta), 0);
+//   tail (other free):           sign(u) max(|u| - theta, 0);
+//   theta = the root of f(x) = sum_tail (|u|-x)^+ - sum_top (h(x)-|u|)^+,
+//   h(x) = x + min(x/c, M), or max tail |u| when no entry point lies below it.
+// What differs is the schedule.  The CTA-per-node kernel holds a node's
+// coordinates in registers and spends most of its time in barrier-separated
+// phases with three nodes per SM, so HBM idles.  Here a warp copies the node's
+// rows of G (or its first split slice), V and beta into shared memory with
+// asynchronous 16-byte copies (one round trip per node, no registers held),
+// and every later pass runs on shared memory with warp shuffles only, so that
+// an SM keeps several nodes in flight and their copies overlap the others'
+// passes.  Global memory sees each input once and each output once.
+//
+// Per node (one warp):
+//  A. copy G, V, beta and the two fixing-mask rows; u = v - eta G replaces G
+//     (J0 and J1 entries set to 0, so that every later pass sees only free
+//     coordinates: 0 never exceeds a non-negative threshold, and the passes
+//     need neither masks nor branches); J1 entries go to a short list
+//     (index, u); each lane keeps its two largest free |u|.
+//  B. tau = the kbar-th largest of the 64 lane top-two values (so at least
+//     kbar free coordinates have |u| >= tau); the free |u| >= tau are gathered
+//     (at most kCandCap) as keys (|u| bits, complemented index) and ranked:
+//     the kbar best are the top set (ties to the smaller index), the next one
+//     is the largest tail value.  If more than kCandCap qualify, kbar rounds
+//     of a warp argmax over shared memory select the top set instead.
+//  C. the top coordinates are set to 0 too; theta on the piece of f between
+//     top entry points that holds the root (the last piece is tested first:
+//     with small c every entry point is tiny and the root lies above all of
+//     them; else a binary search), then Newton steps from the piece's left end
+//     (f is convex there), each a pass over the tail in shared memory.
+//  D. beta in shared memory (tail formula, 0 for the other entries, then the
+//     top and J1 lists scattered in); one pass writes beta and
+//     v' = beta + ((t-1)/t')(beta - beta_old) (and the tensor-core operand
+//     copy of v') while summing the restart test <v - beta, beta - beta_old>;
+//     if the test fires, v' = beta is written again (rare).
+#include <float.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace kglm {
+namespace {
+
+constexpr int kCandCap = 128;
+constexpr int kSMs = 152;
+constexpr int kStreamMaxWarps = 16;
+constexpr int kStreamMinWarps = 6;      // below this the CTA-per-node kernel is used
+constexpr size_t kSmemPerSM = 227 * 1024;
+
+struct WarpHdr {
+    unsigned long long cand[kCandCap];
+    float sv[kMaxK];     // top magnitudes, descending
+    float tu[kMaxK];     // their u (signed)
+    int si[kMaxK];       // their coordinates (-1: an empty slot)
+    float ep[kMaxK];     // entry points p(sv[i]), descending
+    float j1u[kMaxK];
+    int j1i[kMaxK];
+    int ncand, nj1;
+    float amax;
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+// a row of p floats padded to a multiple of 4 (the padding stays 0)
+__host__ __device__ inline size_t row_bytes(int p) { return align16((size_t)p * sizeof(float)); }
+__host__ __device__ inline size_t mask_bytes(int W) { return align16((size_t)W * sizeof(uint32_t)); }
+// per warp: header, two mask rows, then the u (G), v and beta rows
+__host__ __device__ inline size_t warp_bytes(int p, int W) {
+    return align16(sizeof(WarpHdr)) + 2 * mask_bytes(W) + 3 * row_bytes(p);
+}
+
+__device__ __forceinline__ float entry_pt(float a, float c, float M) {
+    return a <= (1.f + c) * M ? a * c / (1.f + c) : a - M;
+}
+__device__ __forceinline__ float model_root_f(float nt, float St, float nl, float Sl, float c, float M) {
+    const float xa = c * (St + Sl) / (nt * (1.f + c) + c * nl);
+    if (xa <= c * M) return xa;
+    return (St + Sl - nt * M) / (nt + nl);
+}
+__device__ __forceinline__ float sgn_mag(float u, float mag) { return u < 0.f ? -mag : mag; }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Bitonic sort (ascending) of 64 keys held two per lane (element 2*lane + s).
+__device__ __forceinline__ void sort64(uint32_t& k0, uint32_t& k1, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 1) {
+                const int g = 2 * lane;                  // pair (g, g+1) in this lane
+                const bool asc = (g & k) == 0;
+                const uint32_t lo = min(k0, k1), hi = max(k0, k1);
+                k0 = asc ? lo : hi;
+                k1 = asc ? hi : lo;
+            } else {
+                const int lj = j >> 1;                   // partner lane
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    uint32_t& x = s ? k1 : k0;
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, x, lj);
+                    const int g = 2 * lane + s;
+                    const bool asc = (g & k) == 0, lower = (g & j) == 0;
+                    x = (asc == lower) ? min(x, o) : max(x, o);
+                }
+            }
+        }
+    }
+}
+
+// Tensor-core operand copy of 4 consecutive values of v' (index i, a multiple of 4).
+__device__ __forceinline__ void store_operand4(void* base, float* lo, size_t i, float4 v, int bf16) {
+    if (bf16) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&h0);
+        w.y = *reinterpret_cast<uint32_t*>(&h1);
+        *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(base) + i) = w;
+    } else {
+        const float4 hi = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+        *reinterpret_cast<float4*>(static_cast<float*>(base) + i) = hi;
+        if (lo)
+            *reinterpret_cast<float4*>(lo + i) =
+                make_float4(to_tf32(v.x - hi.x), to_tf32(v.y - hi.y), to_tf32(v.z - hi.z), to_tf32(v.w - hi.w));
+    }
+}
+
+// Sum over the tail of (|u| - x)^+, four independent partial sums per lane.
+__device__ __forceinline__ float tail_excess(const float4* su4, int p4, int lane, float x) {
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+    for (int q = lane; q < p4; q += 32) {
+        const float4 s = su4[q];
+        f0 += fmaxf(fabsf(s.x) - x, 0.f);
+        f1 += fmaxf(fabsf(s.y) - x, 0.f);
+        f2 += fmaxf(fabsf(s.z) - x, 0.f);
+        f3 += fmaxf(fabsf(s.w) - x, 0.f);
+    }
+    return (f0 + f1) + (f2 + f3);
+}
+
+// Count and sum of the tail above x (entries at 0 never count for x >= 0).
+__device__ __forceinline__ void tail_above(const float4* su4, int p4, int lane, float x, float& cnt, float& sum) {
+    float n0 = 0.f, n1 = 0.f, s0 = 0.f, s1 = 0.f;
+    for (int q = lane; q < p4; q += 32) {
+        const float4 s = su4[q];
+        const float a0 = fabsf(s.x), a1 = fabsf(s.y), a2 = fabsf(s.z), a3 = fabsf(s.w);
+        n0 += (a0 > x ? 1.f : 0.f) + (a2 > x ? 1.f : 0.f);
+        n1 += (a1 > x ? 1.f : 0.f) + (a3 > x ? 1.f : 0.f);
+        s0 += (a0 > x ? a0 : 0.f) + (a2 > x ? a2 : 0.f);
+        s1 += (a1 > x ? a1 : 0.f) + (a3 > x ? a3 : 0.f);
+    }
+    cnt = warp_sum(n0 + n1);
+    sum = warp_sum(s0 + s1);
+}
+
+// VEC = 4: 16-byte copies and stores (p a multiple of 4, 16-byte aligned rows);
+// VEC = 1: 4-byte ones.  Shared-memory passes use 16-byte accesses either way
+// (the padded rows).
+template <int VEC>
+__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int p = a.p, p4 = (p + 3) >> 2, W = a.W;
+    unsigned char* wbase = smem + (size_t)warp * warp_bytes(p, W);
+    WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
+    uint32_t* smi = reinterpret_cast<uint32_t*>(wbase + align16(sizeof(WarpHdr)));
+    uint32_t* smo = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(smi) + mask_bytes(W));
+    float* su = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smo) + mask_bytes(W));
+    float* sv = su + row_bytes(p) / sizeof(float);
+    float* sb = sv + row_bytes(p) / sizeof(float);
+    float4* su4 = reinterpret_cast<float4*>(su);
+    for (int j = p + lane; j < 4 * p4; j += 32) su[j] = sv[j] = sb[j] = 0.f;   // padding: 0 for good
+    const float eta = (float)a.eta, c = (float)a.c, M = (float)a.M, c1 = 1.f + c;
+    const int nq = p / VEC;
+
+    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) {
+        if (a.active != nullptr && a.active[b] == 0) continue;
+        const size_t base = (size_t)b * p;
+        float* __restrict__ V = static_cast<float*>(a.V) + base;
+        float* __restrict__ Bm = static_cast<float*>(a.B) + base;
+        const float* G0 = a.gsplits == 0 ? static_cast<const float*>(a.G) + base : a.Gpart + base;
+        const int kb = a.kbar[b], pf = a.pf[b];
+        const double tprev = lane == 0 ? a.tmom[b] : 0.0;
+
+        // ---- A. rows to shared memory in one round trip
+        for (int q = lane; q < W; q += 32) {
+            cp_async4(smi + q, a.in_mask + (size_t)b * W + q);
+            cp_async4(smo + q, a.out_mask + (size_t)b * W + q);
+        }
+        for (int q = lane; q < nq; q += 32) {
+            if constexpr (VEC == 4) {
+                cp_async16(su + 4 * q, G0 + 4 * q);
+                cp_async16(sv + 4 * q, V + 4 * q);
+                cp_async16(sb + 4 * q, Bm + 4 * q);
+            } else {
+                cp_async4(su + q, G0 + q);
+                cp_async4(sv + q, V + q);
+                cp_async4(sb + q, Bm + q);
+            }
+        }
+        if (lane == 0) { h.nj1 = 0; h.ncand = 0; }
+        cp_async_wait_all();
+        __syncwarp();
+        // u = v - eta G (split slices after the first are added from global memory, in order)
+        float t1 = 0.f, t2 = 0.f;
+        for (int q = lane; q < p4; q += 32) {
+            float4 g = su4[q];
+            const float4 v = reinterpret_cast<const float4*>(sv)[q];
+            const int j0 = 4 * q;
+            for (int s = 1; s < a.gsplits; ++s) {
+                const float* gs = a.Gpart + (size_t)s * a.gstride + base;
+                g.x += gs[j0];
+                if (j0 + 1 < p) g.y += gs[j0 + 1];
+                if (j0 + 2 < p) g.z += gs[j0 + 2];
+                if (j0 + 3 < p) g.w += gs[j0 + 3];
+            }
+            const uint32_t wi = smi[j0 >> 5] >> (j0 & 31), wo = smo[j0 >> 5] >> (j0 & 31);
+            const float uu[4] = {v.x - eta * g.x, v.y - eta * g.y, v.z - eta * g.z, v.w - eta * g.w};
+            float o[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool inb = j0 + t < p, in = inb && ((wi >> t) & 1u), fr = inb && !(((wi | wo) >> t) & 1u);
+                if (in) {                              // J1: at most k per node
+                    const int qq = atomicAdd(&h.nj1, 1);
+                    h.j1i[qq] = j0 + t;
+                    h.j1u[qq] = uu[t];
+                }
+                const float au = fr ? fabsf(uu[t]) : 0.f;
+                t2 = fmaxf(t2, fminf(t1, au));
+                t1 = fmaxf(t1, au);
+                o[t] = fr ? uu[t] : 0.f;
+            }
+            su4[q] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        __syncwarp();
+
+        // ---- B. top-kbar selection over the free coordinates
+        float theta = 0.f;
+        int ntop = 0;
+        if (kb > 0 && pf > kb) {
+            ntop = kb;
+            uint32_t k0 = __float_as_uint(t1), k1 = __float_as_uint(t2);
+            sort64(k0, k1, lane);
+            const int pos = 64 - kb;                           // kb-th largest of 64 (kb <= kMaxK = 64)
+            const uint32_t ka = __shfl_sync(0xffffffffu, k0, pos >> 1), kbk = __shfl_sync(0xffffffffu, k1, pos >> 1);
+            const uint32_t tau = max((pos & 1) ? kbk : ka, 1u);
+            float lo_max = 0.f;
+            for (int q = lane; q < p4; q += 32) {
+                const float4 s4 = su4[q];
+                const float e[4] = {fabsf(s4.x), fabsf(s4.y), fabsf(s4.z), fabsf(s4.w)};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t key = __float_as_uint(e[t]);
+                    if (key >= tau) {
+                        const int qq = atomicAdd(&h.ncand, 1);
+                        if (qq < kCandCap)
+                            h.cand[qq] = ((unsigned long long)key << 32) | (0xffffffffu - (uint32_t)(4 * q + t));
+                    } else {
+                        lo_max = fmaxf(lo_max, e[t]);
+                    }
+                }
+            }
+            // a top slot stays empty (si -1, value 0) only if fewer than kbar free
+            // |u| are positive; an empty slot stands for a zero entry
+            for (int i = lane; i < kb; i += 32) { h.si[i] = -1; h.sv[i] = 0.f; }
+            __syncwarp();
+            const int total = h.ncand;
+            const float amax_lo = warp_max(lo_max);
+            if (total <= kCandCap) {
+                for (int i = lane; i < total; i += 32) {
+                    const unsigned long long ci = h.cand[i];
+                    int r = 0;
+                    for (int t = 0; t < total; ++t) r += h.cand[t] > ci;
+                    const float val = __uint_as_float((uint32_t)(ci >> 32));
+                    if (r < kb) {
+                        h.sv[r] = val;
+                        h.si[r] = (int)(0xffffffffu - (uint32_t)ci);
+                    } else if (r == kb) {
+                        h.amax = val;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0 && total <= kb) h.amax = amax_lo;
+            } else {
+                // too many ties near tau: kb rounds of a warp argmax below the last winner
+                unsigned long long last = ~0ull;
+                for (int r = 0; r <= kb; ++r) {
+                    unsigned long long best = 0ull;
+                    for (int q = lane; q < p4; q += 32) {
+                        const float4 s4 = su4[q];
+                        const float e[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const unsigned long long pk = ((unsigned long long)__float_as_uint(fabsf(e[t])) << 32) |
+                                                          (0xffffffffu - (uint32_t)(4 * q + t));
+                            if (pk < last && pk > best) best = pk;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, o);
+                        best = x > best ? x : best;
+                    }
+                    last = best;
+                    if (lane == 0) {
+                        const int j = (int)(0xffffffffu - (uint32_t)best);
+                        if (r < kb) {
+                            if (best != 0ull && j < p) {
+                                h.sv[r] = __uint_as_float((uint32_t)(best >> 32));
+                                h.si[r] = j;
+                            }
+                        } else {
+                            h.amax = best ? __uint_as_float((uint32_t)(best >> 32)) : 0.f;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // ---- C. the top set leaves the tail (set to 0), then the pooled block's threshold
+            for (int i = lane; i < kb; i += 32) {
+                const int j = h.si[i];
+                h.tu[i] = (unsigned)j < (unsigned)p ? su[j] : 0.f;
+                h.ep[i] = entry_pt(h.sv[i], c, M);
+            }
+            __syncwarp();
+            for (int i = lane; i < kb; i += 32)
+                if ((unsigned)h.si[i] < (unsigned)p) su[h.si[i]] = 0.f;
+            __syncwarp();
+            const float amax = h.amax;
+            if (amax > 0.f) {
+                const float emin = h.ep[kb - 1];
+                if (emin >= amax) {
+                    theta = amax;                          // nothing pools
+                } else {
+                    int r = 0;
+                    for (int i = 0; i < kb; ++i) r += h.ep[i] < amax;
+                    auto xval = [&](int i) -> float { return i == 0 ? 0.f : (i <= r ? h.ep[kb - i] : amax); };
+                    auto f_at = [&](int i) -> float {   // f at breakpoint i (one pass)
+                        const float x = xval(i);
+                        const float hx = x + fminf(x / c, M);
+                        float f = tail_excess(su4, p4, lane, x);
+                        if (lane < kb && h.ep[lane] < x) f -= fmaxf(hx - h.sv[lane], 0.f);
+                        if (lane + 32 < kb && h.ep[lane + 32] < x) f -= fmaxf(hx - h.sv[lane + 32], 0.f);
+                        return warp_sum(f);
+                    };
+                    int lo = 0, hi = r + 1;
+                    if (r > 0 && f_at(r) > 0.f) lo = r;        // the last piece holds the root
+                    else hi = r;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (f_at(mid) > 0.f) lo = mid; else hi = mid;
+                    }
+                    const float xlo = xval(lo), xhi = xval(hi);
+                    float nt = 0.f, St = 0.f;
+                    for (int i = 0; i < kb; ++i)
+                        if (h.ep[i] <= xlo) { nt += 1.f; St += h.sv[i]; }
+                    float th = xlo, nl, Sl;
+                    tail_above(su4, p4, lane, th, nl, Sl);
+                    for (int it = 0; it < 4 * kMaxK + 64; ++it) {
+                        float tn = model_root_f(nt, St, nl, Sl, c, M);
+                        tn = fminf(fmaxf(tn, th), xhi);
+                        float q0, q1;
+                        tail_above(su4, p4, lane, tn, q0, q1);
+                        const bool done = q0 == nl;
+                        th = tn;
+                        nl = q0;
+                        Sl = q1;
+                        if (done) break;
+                    }
+                    theta = th;
+                }
+            }
+        }
+
+        // ---- D. beta in shared memory, then the fused write / restart pass
+        const bool ridge = kb > 0 && pf <= kb;      // every free coordinate fits the budget
+        for (int q = lane; q < p4; q += 32) {
+            const float4 s4 = su4[q];
+            auto bf = [&](float u) -> float {
+                const float au = fabsf(u);
+                const float mag = kb == 0 ? 0.f : (ridge ? fminf(au / c1, M) : fmaxf(au - theta, 0.f));
+                return sgn_mag(u, mag);
+            };
+            su4[q] = make_float4(bf(s4.x), bf(s4.y), bf(s4.z), bf(s4.w));
+        }
+        __syncwarp();
+        for (int i = lane; i < ntop; i += 32) {       // top first: a J1 entry never loses to an empty slot
+            const int j = h.si[i];
+            if ((unsigned)j >= (unsigned)p) continue;
+            const float u = h.tu[i], au = fabsf(u);
+            su[j] = sgn_mag(u, fmaxf(fminf(fminf(au / c1, M), au - theta), 0.f));
+        }
+        __syncwarp();
+        const int nj1 = h.nj1;
+        for (int i = lane; i < nj1; i += 32) {
+            const float u = h.j1u[i];
+            su[h.j1i[i]] = sgn_mag(u, fminf(fabsf(u) / c1, M));
+        }
+        __syncwarp();
+        double t_keep = 0.0, c_keep = 0.0;
+        if (lane == 0) {
+            t_keep = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tprev * tprev));
+            c_keep = (tprev - 1.0) / t_keep;
+        }
+        const float coef = (float)__shfl_sync(0xffffffffu, c_keep, 0);
+        float d0 = 0.f, d1 = 0.f;
+        const size_t ob = (size_t)b * a.op_ld;
+        for (int q = lane; q < nq; q += 32) {
+            if constexpr (VEC == 4) {
+                const float4 v = reinterpret_cast<const float4*>(sv)[q];
+                const float4 bo = reinterpret_cast<const float4*>(sb)[q];
+                const float4 bn = su4[q];
+                d0 += (v.x - bn.x) * (bn.x - bo.x) + (v.z - bn.z) * (bn.z - bo.z);
+                d1 += (v.y - bn.y) * (bn.y - bo.y) + (v.w - bn.w) * (bn.w - bo.w);
+                const float4 vn = make_float4(bn.x + coef * (bn.x - bo.x), bn.y + coef * (bn.y - bo.y),
+                                              bn.z + coef * (bn.z - bo.z), bn.w + coef * (bn.w - bo.w));
+                reinterpret_cast<float4*>(Bm)[q] = bn;
+                reinterpret_cast<float4*>(V)[q] = vn;
+                if (a.Vop != nullptr) store_operand4(a.Vop, a.Vop_lo, ob + 4 * q, vn, a.op_bf16);
+            } else {
+                const float v = sv[q], bo = sb[q], bn = su[q];
+                d0 += (v - bn) * (bn - bo);
+                const float vn = bn + coef * (bn - bo);
+                Bm[q] = bn;
+                V[q] = vn;
+                if (a.Vop != nullptr) store_operand2(a.Vop, a.Vop_lo, ob + q, vn, a.op_bf16);
+            }
+        }
+        const float dot = warp_sum(d0 + d1);
+        const bool rs = a.restart && dot > 0.f;
+        if (lane == 0) a.tmom[b] = rs ? 1.0 : t_keep;   // restart: start over from beta, t = 1
+        if (rs) {
+            // momentum off: v' = beta
+            for (int j = lane; j < p; j += 32) {
+                const float bn = su[j];
+                V[j] = bn;
+                if (a.Vop != nullptr) store_operand2(a.Vop, a.Vop_lo, ob + j, bn, a.op_bf16);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int VEC>
+int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
+    const size_t smem = (size_t)wpc * warp_bytes(a.p, a.W);
+    auto kern = k_prox_stream<VEC>;
+    {
+        // set once per kernel to the SM's whole shared memory, so that no launch
+        // ever finds the opt-in below its need
+        static std::mutex mu;
+        static bool opted = false;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!opted) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPerSM) != cudaSuccess)
+                return -1;
+            opted = true;
+        }
+    }
+    const int grid = std::max(1, std::min(kSMs, (a.m + wpc - 1) / wpc));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * wpc);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, a);   // errors surface at the caller's check
+    return 0;
+}
+
+}  // namespace
+
+int prox_stream_warps(int p, int W) {
+    return (int)std::min<size_t>(kStreamMaxWarps, kSmemPerSM / warp_bytes(p, W));
+}
+
+int prox_stream_f32(cudaStream_t s, const ProxArgs& a) {
+    if (a.m <= 0) return 0;
+    const int wpc = prox_stream_warps(a.p, a.W);
+    if (a.p > kStreamMaxP || wpc < kStreamMinWarps) return 1;     // not this kernel's range
+    const bool vec = (a.p % 4 == 0) && ((uintptr_t)a.V % 16 == 0) && ((uintptr_t)a.B % 16 == 0) &&
+                     (a.Vop == nullptr || (a.op_ld % 4 == 0 && (uintptr_t)a.Vop % 16 == 0 &&
+                                           (a.Vop_lo == nullptr || (uintptr_t)a.Vop_lo % 16 == 0))) &&
+                     (a.gsplits == 0 ? ((uintptr_t)a.G % 16 == 0)
+                                     : ((uintptr_t)a.Gpart % 16 == 0 && a.gstride % 4 == 0));
+    return vec ? launch_stream<4>(s, a, wpc) : launch_stream<1>(s, a, wpc);
+}
+
+}  // namespace kglm

@@ -6,9 +6,12 @@ warp per node by candidates above the kbar-th largest lane maximum (or the
 kbar-round tournament when kbar > 32 or too many candidates qualify), and a
 CTA per node by radix select.  These tests compare its output beta element by
 element with the oracle's prox_node (Algorithm 1, App. B, in FP64), across
-feature counts that reach each path: p = 64 and 512 (a warp per node), 1000,
-2000 and 8189 (a CTA per node, every prox_threads option, including a warp
-per node up to 2048).
+feature counts that reach each path: p = 64 and 512 (a warp per node), 600,
+1000, 1001 and 2000 (the persistent kernel that streams nodes through shared
+memory by default, with 16-byte copies when p is a multiple of 4 and 4-byte
+ones at 1001; every prox_threads option selects one of the CTA-per-node or
+warp-per-node kernels instead), 4093 and 8189 (a CTA per node: too few rows
+of the persistent kernel fit in shared memory).
 
 First step (exact products).  With X on a coarse dyadic grid (entries k/4,
 |k| <= 2), a warm start beta0 on the grid 2^-6 inside the box, y on the grid
@@ -136,8 +139,9 @@ def _options(p):
     return [0, 256]
 
 
-CASES = [(64, 12, False), (64, 40, True), (512, 20, False), (512, 40, False), (1000, 15, True),
-         (2000, 20, False), (2000, 40, False), (8189, 20, False)]
+CASES = [(64, 12, False), (64, 40, True), (512, 20, False), (512, 40, False), (600, 10, False),
+         (1000, 15, True), (1001, 30, False), (2000, 20, False), (2000, 40, False), (4093, 30, False),
+         (8189, 20, False)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
