@@ -56,6 +56,12 @@ struct kglm_ctx {
     bool tc = false;
     int tc_kind = 0;              // 0: BF16 operands, 1: TF32
     bool x3 = false;              // FP32-accurate split: TF32 hi + lo of every operand
+    // X as hi + lo in S = X V (TF32 modes).  In the BF16 mode X is rounded once:
+    // there V and R are rounded to BF16 as well, and their rounding sets the
+    // bound's accuracy (the bound after 50 or 300 iterations moves by the same
+    // ~1e-3 relative with or without X's low part), so the low part would only
+    // double the product's tensor work.
+    bool xlo = false;
     int pK = 0, nK = 0;           // operand row strides (multiples of 8 elements)
     void *Xop = nullptr, *Xop_lo = nullptr, *Xtop = nullptr, *Vop = nullptr, *Rop = nullptr;
     float *Xtop_lo = nullptr, *Vop_lo = nullptr, *Rop_lo = nullptr;   // low parts (FP32-accurate mode)
@@ -63,6 +69,11 @@ struct kglm_ctx {
     // FP32-accurate mode: beta as a TF32 hi + lo operand for the certificate's X beta
     float *Bop = nullptr, *Bop_lo = nullptr;
     TcMap mAb{}, mAblo{};
+    // BF16 mode: X as TF32 hi + lo for the certificate's X beta on the tensor
+    // cores (FP32-accurate, as in the FP32-accurate mode; the iterations keep BF16)
+    float *Xc = nullptr, *Xc_lo = nullptr;
+    TcMap mXc{}, mXclo{};
+    int bnc = 0;
     bool tc_check_pending = false;   // the tensor-core error flag is on its way to the pinned staging
     int bn1 = 0, bn2 = 0;
     int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
@@ -343,15 +354,18 @@ void certify(kglm_ctx* c) {
         Scope sc(c, PH_CERT_XB, 1, 2.0 * n * c->sum_pa);
         if (c->f64) {
             gemm_nt_f64(c->st, m, n, p, (const double*)c->B, p, c->X64, p, (double*)c->R, n, &c->gs64);
-        } else if (c->x3) {
-            // FP32-accurate mode: the same TF32 hi + lo split as S = X V, beta in place of V
+        } else if (c->tc) {
+            // tensor-core modes: X beta as the TF32 hi + lo split (hi hi + hi lo + lo hi,
+            // FP32 accumulate; FP32-accurate), with the TF32 modes' own X hi + lo operands
+            // and, in the BF16 mode, the TF32 copies of X kept for this product
             convert_pad_f32(c->st, (const float*)c->B, m, p, c->Bop, c->pK, 0, c->Bop_lo);
             check_launch();
+            const bool own = c->tc_kind == 0;
             TcGemm g{};
-            g.kind = 1; g.M = m; g.N = n; g.K = p; g.bn = c->bn1;
+            g.kind = 1; g.M = m; g.N = n; g.K = p; g.bn = own ? c->bnc : c->bn1;
             g.epi = TC_EPI_STORE_F32; g.out = c->R; g.ldo = n; g.err = c->d_tcerr;
             g.A2 = &c->mAblo;
-            if (tc_gemm(c->st, c->mAb, c->mB1, &c->mB1lo, g, &c->gtc) != 0)
+            if (tc_gemm(c->st, c->mAb, own ? c->mXc : c->mB1, own ? &c->mXclo : &c->mB1lo, g, &c->gtc) != 0)
                 throw Fail{KGLM_ECUDA, "tensor-core launch failed (certificate X beta)"};
         } else {
             gemm_nt_f32(c->st, m, n, p, (const float*)c->B, p, c->X32, p, (float*)c->R, n, &c->gs32);
@@ -408,7 +422,7 @@ void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
         g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
         if (c->x3) { g.A2 = &c->mA1lo; g.out_lo = c->Rop_lo + (size_t)row0 * c->nK; }
         g.pdl = pdl;
-        if (tc_gemm(st, c->mA1, c->mB1, &c->mB1lo, g, sub ? nullptr : &c->gtc) != 0)
+        if (tc_gemm(st, c->mA1, c->mB1, c->xlo ? &c->mB1lo : nullptr, g, sub ? nullptr : &c->gtc) != 0)
             throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
         check_launch();
     }
@@ -825,10 +839,12 @@ size_t footprint(const kglm_desc& d) {
     if (tc) {
         const size_t es = d.prec == KGLM_BF16 ? 2 : 4;
         const size_t pK = (p + 7) / 8 * 8, nK = (n + 7) / 8 * 8;
-        add(n * pK * es); add(n * pK * es); add(p * nK * es);
+        add(n * pK * es); if (d.prec != KGLM_BF16) add(n * pK * es); add(p * nK * es);
         if (x3) add(4 * p * nK);
         add(mc * pK * es); add(mc * nK * es);
-        if (x3) { add(4 * mc * pK); add(4 * mc * nK); add(4 * mc * pK); add(4 * mc * pK); }
+        if (x3) { add(4 * mc * pK); add(4 * mc * nK); }
+        add(4 * mc * pK); add(4 * mc * pK);                              // beta hi + lo (certificate)
+        if (d.prec == KGLM_BF16) { add(4 * n * pK); add(4 * n * pK); }  // X as TF32 hi + lo (certificate)
         add(tc_scratch_bytes()); add(4 * (size_t)tc_scratch_counters());
         add(4 * (size_t)tc_split_cap((int)mc, (int)p) * mc * p);   // split slices of X^T R
         add(4);
@@ -1125,7 +1141,7 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
 void set_tiles(kglm_ctx* c, int bn1, int bn2) {
     const int ob = c->tc_kind == 0;
     if (tc_make_map(&c->mB1, c->Xop, ob, c->n, c->p, c->pK, bn1) ||
-        tc_make_map(&c->mB1lo, c->Xop_lo, ob, c->n, c->p, c->pK, bn1) ||
+        (c->xlo && tc_make_map(&c->mB1lo, c->Xop_lo, ob, c->n, c->p, c->pK, bn1)) ||
         tc_make_map(&c->mB2, c->Xtop, ob, c->p, c->n, c->nK, bn2) ||
         (c->x3 && tc_make_map(&c->mB2lo, c->Xtop_lo, 0, c->p, c->n, c->nK, bn2)))
         throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed while tuning the tiles"};
@@ -1391,6 +1407,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->tc = d.prec == KGLM_BF16 || d.prec == KGLM_TF32 || d.prec == KGLM_TF32X3;
         c->tc_kind = d.prec == KGLM_BF16 ? 0 : 1;
         c->x3 = d.prec == KGLM_TF32X3;
+        c->xlo = d.prec == KGLM_TF32 || d.prec == KGLM_TF32X3;
         c->W = (c->p + 31) / 32;
         c->lam2 = d.lambda2; c->M = d.M;
         c->gap_tol = d.gap_tol > 0 ? d.gap_tol : 1e-6;
@@ -1445,7 +1462,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->pK = (int)((p + 7) / 8 * 8);
             c->nK = (int)((n + 7) / 8 * 8);
             c->Xop = dalloc(c, n * c->pK * es);
-            c->Xop_lo = dalloc(c, n * c->pK * es);
+            if (c->xlo) c->Xop_lo = dalloc(c, n * c->pK * es);
             c->Xtop = dalloc(c, p * c->nK * es);
             if (c->x3) c->Xtop_lo = dalloc_t<float>(c, p * c->nK);
             convert_pad(c->st, c->X64, (int)n, (int)p, (int)p, c->Xop, c->pK, ob, c->Xop_lo);
@@ -1461,21 +1478,32 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
                 c->Rop_lo = dalloc_t<float>(c, mc * c->nK);
                 CK(cudaMemsetAsync(c->Vop_lo, 0, mc * c->pK * 4, c->st));
                 CK(cudaMemsetAsync(c->Rop_lo, 0, mc * c->nK * 4, c->st));
-                c->Bop = dalloc_t<float>(c, mc * c->pK);
-                c->Bop_lo = dalloc_t<float>(c, mc * c->pK);
             }
+            c->Bop = dalloc_t<float>(c, mc * c->pK);
+            c->Bop_lo = dalloc_t<float>(c, mc * c->pK);
+            if (c->tc_kind == 0) {
+                c->Xc = dalloc_t<float>(c, n * c->pK);
+                c->Xc_lo = dalloc_t<float>(c, n * c->pK);
+                convert_pad(c->st, c->X64, (int)n, (int)p, (int)p, c->Xc, c->pK, 0, c->Xc_lo);
+                check_launch();
+                c->bnc = tc_tile_cols_wide((int)n);
+                if (tc_make_map(&c->mXc, c->Xc, 0, (int)n, (int)p, c->pK, c->bnc) ||
+                    tc_make_map(&c->mXclo, c->Xc_lo, 0, (int)n, (int)p, c->pK, c->bnc))
+                    throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for the certificate's X"};
+            }
+            if (tc_make_map(&c->mAb, c->Bop, 0, (int)mc, (int)p, c->pK, 128) ||
+                tc_make_map(&c->mAblo, c->Bop_lo, 0, (int)mc, (int)p, c->pK, 128))
+                throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for the certificate's beta"};
             c->bn1 = tc_tile_cols_wide((int)n);
             c->bn2 = tc_tile_cols((int)p);
             if (tc_make_map(&c->mA1, c->Vop, ob, (int)mc, (int)p, c->pK, 128) ||
                 tc_make_map(&c->mB1, c->Xop, ob, (int)n, (int)p, c->pK, c->bn1) ||
-                tc_make_map(&c->mB1lo, c->Xop_lo, ob, (int)n, (int)p, c->pK, c->bn1) ||
+                (c->xlo && tc_make_map(&c->mB1lo, c->Xop_lo, ob, (int)n, (int)p, c->pK, c->bn1)) ||
                 tc_make_map(&c->mA2, c->Rop, ob, (int)mc, (int)n, c->nK, 128) ||
                 tc_make_map(&c->mB2, c->Xtop, ob, (int)p, (int)n, c->nK, c->bn2))
                 throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for an operand"};
             if (c->x3 && (tc_make_map(&c->mA1lo, c->Vop_lo, 0, (int)mc, (int)p, c->pK, 128) ||
                           tc_make_map(&c->mA2lo, c->Rop_lo, 0, (int)mc, (int)n, c->nK, 128) ||
-                          tc_make_map(&c->mAb, c->Bop, 0, (int)mc, (int)p, c->pK, 128) ||
-                          tc_make_map(&c->mAblo, c->Bop_lo, 0, (int)mc, (int)p, c->pK, 128) ||
                           tc_make_map(&c->mB2lo, c->Xtop_lo, 0, (int)p, (int)n, c->nK, c->bn2)))
                 throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for a low-part operand"};
             if (tc_prepare() != 0) throw Fail{KGLM_ECUDA, "tensor-core kernels: shared memory attribute refused"};
