@@ -4,20 +4,28 @@
 A step is one pass of the whole hot path over one node batch: layout of the
 batch's fixing masks, `iters` FISTA iterations (X*V with the fused link,
 X^T*R, masked prox), the FP64 certificate, rounding, re-optimization,
-branching index, pruning and branching.  The workload is the k-sparse
-logistic regression instance n=2000, p=200, k=10, lambda2=1e-2, M=2 with
-node batches of 1024 random fixing patterns (|J1| ~ U{0..k},
-|J0| ~ U{0..p/2}), FP32-accurate products and the FP64 certificate.  The
-products run on the tensor cores as the TF32 hi + lo split (each FP32 operand
-as two TF32 parts, hi*hi + hi*lo + lo*hi, FP32 accumulate; --prec tf32x3);
-the line also times the same steps with FP32 CUDA-core products and with FP64
-products, and the full certified solve of the instance (time to zero gap).
+branching index, pruning and branching.
+
+Headline workload: the node-bound microbenchmark, X 10000 x 2000 (Toeplitz
+rho = 0.5, columns standardized), k = 20, lambda2 = 1e-3, M = 2, least
+squares, 8192 nodes per batch with random fixing patterns (|J1| ~ U{0..k},
+|J0| ~ U{0..p/2}), T = 50 iterations, BF16 tensor-core products with FP32
+accumulate and the FP64 certificate (the largest single-GPU configuration).
 
   value  nodes certified per second with the instance and the node batches
          already in device memory (kglm_push_nodes_dev);
   e2e    the same through kglm_push_nodes from pinned host buffers, the
          host->device copy of the batch and the device->host read of the
          per-node results inside each timed step.
+
+Extra keys of the default run (untimed for the headline, each measured on
+its own): the same workload with logistic loss, with FP32-accurate and with
+FP64 products; the error of the BF16 bounds against the FP64 oracle on
+sampled nodes; the time to zero gap of a full certified solve of the hard
+correlated least-squares instance (n = 5000, p = 1000, rho = 0.9) in BF16
+and in FP64; the logistic n = 2000, p = 200 line with FP32-accurate
+products; the serving mix (p50/p99 time to certified optimality); the
+batch-size sweep at the paper's Fig. 3 setting.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run, one rank per GPU, each rank evaluating its own
@@ -45,7 +53,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2605_22188_gb300 import synth  # noqa: E402
 
-WORKLOAD = "c2_logistic_n2000_p200_k10"
+WORKLOAD = "c4_micro_n10000_p2000_k20"
 METRIC = "certified node bounds/sec"
 UNIT = "nodes/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -160,7 +168,8 @@ PHASE_KERNEL_SOURCES = {
     "gemm_xv_link": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu",
                      "paper_2605_22188_gb300/csrc/common.cuh"],
     "gemm_xtr": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu"],
-    "prox_fista": ["paper_2605_22188_gb300/csrc/prox.cu", "paper_2605_22188_gb300/csrc/common.cuh"],
+    "prox_fista": ["paper_2605_22188_gb300/csrc/prox.cu", "paper_2605_22188_gb300/csrc/prox_stream.cu",
+                   "paper_2605_22188_gb300/csrc/common.cuh"],
     "cert_xtzeta": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu",
                     "paper_2605_22188_gb300/csrc/cert_exact.cu"],
     "cert_xb": ["paper_2605_22188_gb300/csrc/gemm_simt.cu", "paper_2605_22188_gb300/csrc/gemm_tc.cu",
@@ -186,7 +195,7 @@ def traffic_for(phase, workload, prec, nodes):
     return e.get("dram_bytes_per_launch")
 
 
-def roofline(stats, prec, pk, workload=WORKLOAD, nodes=1024):
+def roofline(stats, prec, pk, workload=WORKLOAD, nodes=8192):
     """Achieved rate of the phase with the largest device time, against its peak."""
     best = None
     for name, s in stats.items():
@@ -205,12 +214,14 @@ def roofline(stats, prec, pk, workload=WORKLOAD, nodes=1024):
         # TF32 hi + lo split issues three TF32 products per product: a third of that)
         base = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
         peak = {"bf16": base, "tf32": base * 1.1 / 2.25, "tf32x3": base * 1.1 / 2.25 / 3.0}[prec]
-        note = {"bf16": "BF16 sustained dense peak", "tf32": "TF32 sustained dense peak (BF16 x 1.1/2.25)",
-                "tf32x3": "FP32-accurate 3xTF32 peak (TF32 sustained / 3)"}[prec]
+        src = pk["source"]
+        note = {"bf16": "BF16 sustained dense peak (%s)" % src,
+                "tf32": "TF32: BF16 sustained (%s) x nominal TF32/BF16 ratio 1.1/2.25" % src,
+                "tf32x3": "FP32-accurate 3xTF32: BF16 sustained (%s) x 1.1/2.25 / 3" % src}[prec]
         achieved = work / per_launch_s / 1e12
         return {"kernel": best, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_for(best, workload, prec, nodes),
-                "peak_note": "%s, %s" % (note, pk["source"]),
+                "peak_note": note,
                 "launches": s["launches"], "avg_launch_us": per_launch_s * 1e6}
     if best in ("gemm_xv_link", "gemm_xtr", "cert_xb", "cert_xtzeta"):
         fp64 = prec == "fp64" or best == "cert_xtzeta"
@@ -245,28 +256,38 @@ def _oracle_node(args):
     """One node through the oracle: T FISTA iterations, certificate, rounding, re-opt, branch index."""
     from oracle import node as on
     from oracle import reopt as ro
-    J0, J1, T = args
+    J0, J1, T, full = args
     s = _ORACLE_STATE
     c = s["c"]
     nd = on.Node(c["p"], c["k"], J0, J1)
     r = on.solve_node(s["X"], s["y"], nd, c["lam2"], c["M"], c["kind"], s["L"], T)
-    S = on.round_support(r["beta"], nd)
-    ro.reopt(s["X"], s["y"], S, c["lam2"], c["M"], c["kind"], beta0=r["beta"])
-    on.branch_index(r["beta"], nd)
+    if full:
+        S = on.round_support(r["beta"], nd)
+        ro.reopt(s["X"], s["y"], S, c["lam2"], c["M"], c["kind"], beta0=r["beta"])
+        on.branch_index(r["beta"], nd)
     return r["lb"]
 
 
-def oracle_pool(X, y, c, L, cores):
+def oracle_pool(X, y, c, cores):
+    from oracle import node as on
+    L = on.lipschitz(X, c["kind"])
     ctx = mp.get_context("spawn")
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     return ctx.Pool(cores, initializer=_oracle_init, initargs=(X, y, c, L))
 
 
-def oracle_rate(pool, nodes, T, cores):
+def oracle_run(pool, nodes, T, full=True):
     t0 = time.perf_counter()
-    pool.map(_oracle_node, [(J0, J1, T) for J0, J1 in nodes], chunksize=1)
-    dt = time.perf_counter() - t0
-    return len(nodes) / dt, dt
+    lbs = pool.map(_oracle_node, [(J0, J1, T, full) for J0, J1 in nodes], chunksize=1)
+    return lbs, time.perf_counter() - t0
+
+
+def workload_config(name, c, m, T, world):
+    """The workload (identical in both arms): what is evaluated, not how."""
+    return {"workload": name, "n": c["n"], "p": c["p"], "k": c["k"], "lambda2": c["lam2"], "M": c["M"],
+            "loss": "logistic" if c["kind"] == synth.LOGISTIC else "least_squares", "nodes_per_batch": m,
+            "iters": T, "masks": "|J1|~U{0..k}, |J0|~U{0..p/2}",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 # ------------------------------------------------------------------ the engine arm
@@ -280,188 +301,274 @@ def make_batches(c, nb, m, seed):
     return [synth.random_nodes(m, c["p"], c["k"], rng) for _ in range(nb)]
 
 
-def run_ours(args):
-    import torch
-    from paper_2605_22188_gb300 import kglm
-    rank, world, local = rank_info()
-    torch.cuda.set_device(local)
-    c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
-    m, T = args.nodes or c.get("m", 1024), args.iters
-    pk = peaks()
+class Arm:
+    """One workload on the engine: its instance, device-resident and pinned node batches,
+    and the timed step (push + evaluate + prune + branch)."""
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(X, y, c, T, args)      # spawn pool before the first CUDA call
+    def __init__(self, name, prec, m, T, stream, kind=None, tune="auto", seed=1000):
+        import torch
+        from paper_2605_22188_gb300 import kglm
+        self.torch = torch
+        self.c, self.X, self.y, _ = synth.config_instance(name, seed=0, kind=kind)
+        self.name, self.prec, self.m, self.T, self.stream = name, prec, m, T, stream
+        c = self.c
+        self.eng = kglm.Engine(self.X, self.y, c["k"], c["lam2"], c["M"], c["kind"], prec=prec, max_batch=m,
+                               stream=stream.cuda_stream)
+        if isinstance(tune, str) and tune == "auto":
+            self.tune = self.eng.autotune(iters=T, seed=1)   # tiles, split cap, launch mode (setup, untimed)
+            self.tune["batch"] = m
+        elif isinstance(tune, dict):
+            cfg = {k: tune[k] for k in ("link_tile_cols", "grad_tile_cols", "grad_split_cap", "sub_batches", "pdl",
+                                        "prox_threads") if k in tune}
+            self.eng.configure(**cfg)
+            self.tune = dict(tune, fixed=True)
+        else:
+            self.tune = None
+        self.batches = make_batches(c, 8, m, seed=seed)
+        self.dev = []
+        for (ip, ii, op, oi) in self.batches:
+            t = [torch.from_numpy(a).to("cuda") for a in (ip, ii, op, oi)]
+            self.dev.append((t, int(ip[-1]), int(op[-1])))
+        self.pinned = [tuple(torch.from_numpy(a).pin_memory().numpy() for a in bt) for bt in self.batches]
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.ub = math.inf
 
-    stream = torch.cuda.Stream()
-    eng = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=args.prec, max_batch=m,
-                      stream=stream.cuda_stream)
-    if args.tiles:
-        # a fixed configuration (e.g. the tuned one) instead of tuning: link tile, gradient
-        # tile, split cap, sub-batches
-        l1, g2, cap, ns = (int(v) for v in args.tiles.split(","))
-        eng.configure(link_tile_cols=l1, grad_tile_cols=g2, grad_split_cap=cap, sub_batches=ns)
-        tune = {"fixed": args.tiles}
-    elif args.no_autotune:
-        tune = None
-    else:
-        tune = eng.autotune(iters=T, seed=1)    # tiles, split cap, launch mode of the products (setup, untimed)
-    batches = make_batches(c, 8, m, seed=1000 + rank)
-    dev = []
-    for (ip, ii, op, oi) in batches:
-        t = [torch.from_numpy(a).to("cuda") for a in (ip, ii, op, oi)]
-        dev.append((t, int(ip[-1]), int(op[-1])))
-    pinned = [tuple(torch.from_numpy(a).pin_memory().numpy() for a in bt) for bt in batches]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def step_dev(i):
-        t, nin, nout = dev[i % len(dev)]
-        eng.push_dev(m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(), nin, nout)
-        res = eng.evaluate(T)
-        eng.prune(ub)
-        eng.branch(ub)
+    def step_dev(self, i):
+        t, nin, nout = self.dev[i % len(self.dev)]
+        self.eng.push_dev(self.m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(), nin, nout)
+        res = self.eng.evaluate(self.T)
+        self.eng.prune(self.ub)
+        self.eng.branch(self.ub)
         return res
 
-    def step_host(i):
-        eng.push(*pinned[i % len(pinned)])
-        res = eng.evaluate(T)
-        eng.prune(ub)
-        eng.branch(ub)
+    def step_host(self, i):
+        self.eng.push(*self.pinned[i % len(self.pinned)])
+        res = self.eng.evaluate(self.T)
+        self.eng.prune(self.ub)
+        self.eng.branch(self.ub)
         return res
 
-    def timed(fn, steps):
+    def timed(self, fn, steps):
+        """Device time of `steps` steps (CUDA events on the engine's stream), L2 flushed between steps."""
+        torch = self.torch
         total = 0.0
-        with torch.cuda.stream(stream):
+        with torch.cuda.stream(self.stream):
             for i in range(steps):
-                flush.zero_()
+                self.flush.zero_()
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
+                a.record(self.stream)
                 fn(i)
-                b.record(stream)
+                b.record(self.stream)
                 b.synchronize()
                 total += a.elapsed_time(b) / 1e3
         return total
 
-    ub = math.inf
-    for i in range(max(args.warmup, 3)):
-        r = step_dev(i)
-        ub = min(ub, float(np.min(r["ub"])))
-    torch.cuda.synchronize()
+    def warm(self, n):
+        for i in range(n):
+            r = self.step_dev(i)
+            self.ub = min(self.ub, float(np.min(r["ub"])))
+        self.torch.cuda.synchronize()
+
+    def rate(self, steps):
+        """Nodes per second over `steps` device-resident steps, with the per-phase
+        breakdown and the roofline from a second, event-instrumented pass."""
+        dt = self.timed(self.step_dev, steps)
+        self.eng.stats_enable(True)
+        self.timed(self.step_dev, steps)
+        st = self.eng.stats()
+        self.eng.stats_enable(False)
+        return {"value": self.m * steps / dt, "unit": UNIT, "steps": steps, "ms_per_step": dt / steps * 1e3,
+                "nodes_per_batch": self.m, "products": PRODUCTS[self.prec],
+                "phase_ms_per_step": {k: round(v["ms"] / steps, 4) for k, v in st.items() if v["ms"] > 0},
+                "roofline": roofline(st, self.prec, peaks(), self.name, self.m)}
+
+    def close(self):
+        self.eng.close()
+
+
+def guarded(label, fn):
+    """Run one extra measurement; a failure is recorded in its key instead of ending the run."""
+    t0 = time.perf_counter()
+    try:
+        out = fn()
+    except Exception as e:  # noqa: BLE001 - reported in the line
+        out = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+    if isinstance(out, dict):
+        out["wall_s"] = round(time.perf_counter() - t0, 2)
+    print("[bench] %s done in %.1f s" % (label, time.perf_counter() - t0), file=sys.stderr, flush=True)
+    return out
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    c0 = synth.CONFIGS[args.workload]
+    m = args.nodes or c0.get("m", 1024)
+    T = args.iters or c0.get("T", 50)
+    extras = args.extras and rank == 0 and world == 1 and args.workload == WORKLOAD
+
+    pool, cores, cpu = None, os.cpu_count() or 1, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
+        pool = oracle_pool(X, y, c, cores)              # spawn pool before the first CUDA call
+        cpu = cpu_baseline(pool, c, T, cores, args)
+
+    stream = torch.cuda.Stream()
+    tune = "auto"
+    if args.tiles:
+        l1, g2, cap, ns = (int(v) for v in args.tiles.split(","))
+        tune = {"link_tile_cols": l1, "grad_tile_cols": g2, "grad_split_cap": cap, "sub_batches": ns}
+    elif args.no_autotune:
+        tune = None
+    arm = Arm(args.workload, args.prec, m, T, stream, kind=loss_kind(args), tune=tune, seed=1000 + rank)
+    c = arm.c
+    arm.warm(max(args.warmup, 3))
 
     # timed region: the bare step (kernel launches are counted, no timing events)
-    eng.stats_enable(False)
+    arm.eng.stats_enable(False)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        dt = timed(step_dev, args.steps)
+        dt = arm.timed(arm.step_dev, args.steps)
     torch.cuda.synchronize()
     barrier()
-    launches = sum(s["launches"] for s in eng.stats().values())
+    launches = sum(s["launches"] for s in arm.eng.stats().values())
     secs, units = reduce_max_sum(dt, float(m * args.steps))
     value = units / secs
     # the same steps again with CUDA events around every kernel on the engine's
     # stream (per-phase device time for the roofline; events inside the CUDA
     # graph of the iterations cost a few microseconds each, so they stay out of
     # the timed region above)
-    eng.stats_enable(True)
-    timed(step_dev, args.steps)
-    stats = eng.stats()
-    eng.stats_enable(False)
+    arm.eng.stats_enable(True)
+    arm.timed(arm.step_dev, args.steps)
+    stats = arm.eng.stats()
+    arm.eng.stats_enable(False)
 
     # end to end from pinned host buffers
     for i in range(2):
-        step_host(i)
+        arm.step_host(i)
     barrier()
-    dt_e2e = timed(step_host, args.steps)
+    dt_e2e = arm.timed(arm.step_host, args.steps)
     secs_e, units_e = reduce_max_sum(dt_e2e, float(m * args.steps))
-    ip, ii, op, oi = batches[0]
+    ip, ii, op, oi = arm.batches[0]
     h2d = 4 * (len(ip) + len(ii) + len(op) + len(oi))
     d2h = m * (8 * 3 + 4 * c["k"] + 8 * c["k"] + 4 + 4) + m      # lb, primal, ub, support, beta_re, j*, iters, pruned
-
-    # the same workload with FP64 products (the "mixed vs FP64" comparison of the
-    # metric) and, for the FP32-accurate split, with FP32 CUDA-core products
-    def other_mode(prec):
-        nonlocal eng
-        e2 = kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=prec, max_batch=m,
-                         stream=stream.cuda_stream)
-        eng_keep, eng = eng, e2
-        try:
-            step_dev(0)
-            n2 = max(2, args.steps // 4)
-            dt2 = timed(step_dev, n2)
-        finally:
-            eng = eng_keep
-            e2.close()
-        return {"value": m * n2 / dt2, "unit": UNIT, "steps": n2, "products": PRODUCTS[prec]}
-
-    fp64 = None
-    fp32cc = None
-    if args.prec != "fp64" and not args.no_fp64:
-        fp64 = other_mode("fp64")
-        if args.prec == "tf32x3":
-            fp32cc = other_mode("fp32")
-
-    ttz = None
-    if not args.no_ttz:
-        ttz = time_to_zero_gap(X, y, c, args.prec, stream, m)
-
-    if rank != 0:
-        eng.close()
-        return
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
-        "data": "synthetic",
-        "config": {"workload": args.workload, "n": c["n"], "p": c["p"], "k": c["k"], "lambda2": c["lam2"],
-                   "M": c["M"], "loss": "logistic" if c["kind"] == synth.LOGISTIC else "least_squares",
-                   "nodes_per_batch": m, "iters": T, "products": PRODUCTS[args.prec], "certificate": "fp64",
-                   "masks": "|J1|~U{0..k}, |J0|~U{0..p/2}", "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+        "config": workload_config(args.workload, c, m, T, world),
+        "impl_config": {"products": PRODUCTS[args.prec], "certificate": "fp64",
+                        "l2": "flushed between steps (256 MiB write)", "autotune": arm.tune},
         "e2e": {"value": units_e / secs_e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "autotune": tune,
-        "roofline": roofline(stats, args.prec, pk, args.workload, m),
+        "roofline": roofline(stats, args.prec, peaks(), args.workload, m),
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "fp64_products": fp64,
-        "fp32_cuda_core_products": fp32cc,
-        "time_to_zero_gap": ttz,
         "phase_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stats.items() if v["ms"] > 0},
     }
-    if fp64:
-        line["mixed_over_fp64"] = value / fp64["value"]
-    print(json.dumps(line), flush=True)
-    eng.close()
+    if extras:
+        line["bf16_bound_error_vs_fp64_oracle"] = guarded("bound error", lambda: bound_error(arm, pool, cores))
+        tuned = arm.tune if isinstance(arm.tune, dict) else None
+        arm.close()
+        line["logistic"] = guarded("logistic", lambda: other_arm(args.workload, args.prec, m, T, stream,
+                                                                 synth.LOGISTIC, tuned, args))
+        line["fp32_accurate_products"] = guarded("tf32x3", lambda: other_arm(args.workload, "tf32x3", m, T, stream,
+                                                                             None, None, args))
+        line["fp64_products"] = guarded("fp64", lambda: other_arm(args.workload, "fp64", 256, T, stream, None, None,
+                                                                  args, steps=2))
+        if isinstance(line["fp64_products"], dict) and "value" in line["fp64_products"]:
+            line["mixed_over_fp64"] = value / line["fp64_products"]["value"]
+        line["time_to_zero_gap"] = guarded("time to zero gap", lambda: time_to_zero_gap(
+            "c3_lsq_n5000_p1000_k15", "bf16", stream, 4096))
+        line["c2"] = guarded("c2", lambda: c2_line(stream, args))
+        line["serving"] = guarded("serving", lambda: serving_summary(args))
+        line["batch_sweep"] = guarded("sweep", lambda: sweep_summary(args))
+    else:
+        arm.close()
+    if pool is not None:
+        pool.close()
+        pool.join()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
-def time_to_zero_gap(X, y, c, prec, stream, m):
+def other_arm(name, prec, m, T, stream, kind, tune, args, steps=None):
+    """The same workload in another precision or loss: a shorter timed run on its own engine."""
+    arm = Arm(name, prec, m, T, stream, kind=kind, tune=tune if tune else None, seed=2000)
+    try:
+        arm.warm(2)
+        out = arm.rate(steps or max(3, args.steps // 4))
+        out["loss"] = "logistic" if arm.c["kind"] == synth.LOGISTIC else "least_squares"
+        return out
+    finally:
+        arm.close()
+
+
+def bound_error(arm, pool, cores):
+    """The BF16 bounds of one batch against the FP64 oracle's after the same T (the
+    oracle's FISTA from the same start), on nodes sampled across the batch: per-node
+    relative difference (LB_oracle - LB_gpu) / max(1, |LB_oracle|)."""
+    if pool is None:
+        return {"skipped": "no oracle pool (--no-cpu-baseline)"}
+    from paper_2605_22188_gb300 import kglm  # noqa: F401
+    arm.eng.push(*arm.batches[0])
+    res = arm.eng.evaluate(arm.T)
+    nodes = synth.csr_to_sets(*arm.batches[0])
+    idx = sorted(set(np.linspace(0, arm.m - 1, min(cores, arm.m)).astype(int).tolist()))
+    ref, dt = oracle_run(pool, [nodes[i] for i in idx], arm.T, full=False)
+    rel = [(r - float(res["lb"][i])) / max(1.0, abs(r)) for i, r in zip(idx, ref)]
+    return {"nodes": len(idx), "iters": arm.T, "median_rel": float(np.median(rel)), "max_abs_rel": float(np.max(np.abs(rel))),
+            "min_rel": float(np.min(rel)), "per_node": [round(v, 8) for v in rel], "node_index": idx,
+            "note": "positive = the GPU bound is below the oracle's (same T, same start); both are valid bounds"}
+
+
+def time_to_zero_gap(name, prec, stream, m):
     """Wall time of a full certified solve (kglm_solve, the hybrid loop of Fig. 1) of the
-    workload's instance in the bench precision and with FP64 products.  Each solve runs
-    once untimed (CUDA-graph capture) and once timed; both must close the gap and agree
+    instance in the mixed precision and with FP64 products.  Each solve runs once
+    untimed (CUDA-graph capture) and once timed; both must close the gap and agree
     on the support."""
     from paper_2605_22188_gb300 import kglm
-    out = {"batch": m, "iters": 200, "check_every": 10}
+    c, X, y, _ = synth.config_instance(name, seed=0)
+    out = {"workload": name, "batch": m, "iters": 200, "check_every": 10}
     sols = {}
-    for label, pr in (("mixed", prec), ("fp64", "fp64")):
+    for label, pr, limit in (("mixed", prec, 120.0), ("fp64", "fp64", 240.0)):
         with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec=pr, max_batch=m,
                          stream=stream.cuda_stream) as e:
-            e.solve(m, 200, 10, 600.0)
+            e.solve(m, 200, 10, limit)
             stream.synchronize()
             t0 = time.perf_counter()
-            r = e.solve(m, 200, 10, 600.0)
+            r = e.solve(m, 200, 10, limit)
             dt = time.perf_counter() - t0
         sols[label] = r
         out[label + "_s"] = dt
         out[label + "_nodes"] = r["nodes"]
         out[label + "_gap"] = r["gap"]
         out[label + "_opt"] = r["opt"]
-    out["mixed_products"] = prec
+    out["mixed_products"] = PRODUCTS[prec]
     out["support"] = sols["mixed"]["support"]
     out["support_equal"] = sols["mixed"]["support"] == sols["fp64"]["support"]
     out["fp64_over_mixed_time"] = out["fp64_s"] / out["mixed_s"]
+    return out
+
+
+def c2_line(stream, args):
+    """The logistic n = 2000, p = 200, k = 10 workload (1024 nodes, T = 50) with
+    FP32-accurate products: device-resident and end-to-end rates, and FP64 products."""
+    arm = Arm("c2_logistic_n2000_p200_k10", "tf32x3", 1024, 50, stream, tune="auto", seed=3000)
+    try:
+        arm.warm(3)
+        out = arm.rate(max(10, args.steps))
+        dt = arm.timed(arm.step_host, max(10, args.steps))
+        out["e2e_value"] = arm.m * max(10, args.steps) / dt
+    finally:
+        arm.close()
+    f = other_arm("c2_logistic_n2000_p200_k10", "fp64", 1024, 50, stream, None, None, args, steps=3)
+    out["fp64_products_value"] = f["value"]
+    out["mixed_over_fp64"] = out["value"] / f["value"]
     return out
 
 
@@ -469,56 +576,66 @@ SERVING = "c5_serving_mix64"
 SWEEP = "sweep_batch_n1000_p1000_k10"
 
 
-def run_sweep(args):
-    """Node-evaluation throughput against the batch size (the paper's Fig. 3 setting:
-    n = p = 1000, rho = 0.9, k = 10, lambda2 = 1, M = 2; batch sizes 2^0..2^11 for
-    least squares and 2^7..2^16 for logistic).  Each point: the same random fixing
-    patterns, T iterations + certificate + re-optimization, device time by CUDA
-    events (best of 3 after one untimed run)."""
+def sweep_summary(args):
+    """Node-evaluation throughput against the batch size at the paper's Fig. 3 setting
+    (n = p = 1000, rho = 0.9, k = 10, lambda2 = 1, M = 2): least squares 2^0..2^15,
+    logistic 2^7..2^16.  Each point: the same random fixing patterns, T iterations +
+    certificate + re-optimization, device time by CUDA events (best of 3 after one
+    untimed run).  The plateau batch is the smallest reaching 95% of the best rate."""
     import torch
     from paper_2605_22188_gb300 import kglm
-    rank, world, local = rank_info()
-    torch.cuda.set_device(local)
-    if rank != 0:
-        return
-    out = {}
-    for kind, lo, hi in ((synth.LSQ, 0, 11), (synth.LOGISTIC, 7, 16)):
+    out = {"n": 1000, "p": 1000, "k": 10, "lambda2": 1.0, "M": 2.0, "rho": 0.9, "iters": args.sweep_iters,
+           "products": PRODUCTS["bf16"]}
+    for kind, lo, hi in ((synth.LSQ, 0, 15), (synth.LOGISTIC, 7, 16)):
         X, y, _ = synth.instance(1000, 1000, 10, kind, rho=0.9, snr=5.0, seed=0)
         mmax = 1 << hi
         rng = np.random.default_rng(5)
         ip, ii, op, oi = synth.random_nodes(mmax, 1000, 10, rng)
         stream = torch.cuda.Stream()
         pts = []
-        with kglm.Engine(X, y, 10, 1.0, 2.0, kind, prec=args.prec, max_batch=mmax, stream=stream.cuda_stream) as eng:
+        with kglm.Engine(X, y, 10, 1.0, 2.0, kind, prec="bf16", max_batch=mmax, stream=stream.cuda_stream) as eng:
             for e in range(lo, hi + 1):
-                m = 1 << e
-                csr = (ip[:m + 1], ii[:ip[m]], op[:m + 1], oi[:op[m]])
-                eng.push(*csr)
+                mb = 1 << e
+                eng.push(ip[:mb + 1], ii[:ip[mb]], op[:mb + 1], oi[:op[mb]])
                 best = None
                 for r in range(4):
                     a = torch.cuda.Event(enable_timing=True)
                     b = torch.cuda.Event(enable_timing=True)
                     with torch.cuda.stream(stream):
                         a.record(stream)
-                        eng.evaluate(args.iters)
+                        eng.evaluate(args.sweep_iters)
                         b.record(stream)
                     b.synchronize()
                     if r > 0:
                         ms = a.elapsed_time(b)
                         best = ms if best is None else min(best, ms)
-                pts.append({"batch": m, "ms": round(best, 4), "nodes_per_s": m / (best * 1e-3)})
-        out["least_squares" if kind == synth.LSQ else "logistic"] = pts
-    top = {k: max(p["nodes_per_s"] for p in v) for k, v in out.items()}
-    line = {"metric": "node bounds/sec against batch size", "value": top["logistic"], "unit": "nodes/s",
-            "n_gpus": world, "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+                pts.append({"batch": mb, "ms": round(best, 4), "nodes_per_s": mb / (best * 1e-3)})
+        top = max(p["nodes_per_s"] for p in pts)
+        plateau = min(p["batch"] for p in pts if p["nodes_per_s"] >= 0.95 * top)
+        key = "least_squares" if kind == synth.LSQ else "logistic"
+        out[key] = {"points": pts, "best_nodes_per_s": top, "plateau_batch": plateau,
+                    "plateau_log2": int(round(math.log2(plateau))),
+                    "paper_plateau_log2": 10 if kind == synth.LSQ else 15}
+    return out
+
+
+def run_sweep(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    out = sweep_summary(args)
+    line = {"metric": "node bounds/sec against batch size", "value": out["logistic"]["best_nodes_per_s"],
+            "unit": "nodes/s", "n_gpus": world, "steps": 3, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE["bf16"], "data": "synthetic",
             "config": {"workload": SWEEP, "n": 1000, "p": 1000, "k": 10, "lambda2": 1.0, "M": 2.0, "rho": 0.9,
-                       "iters": args.iters, "products": PRODUCTS[args.prec], "certificate": "fp64"},
-            "best": top, "points": out}
+                       "iters": args.sweep_iters},
+            "sweep": out}
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
+def serving_summary(args):
     """The serving mix: 64 instances (synth.serving_specs) arriving as a Poisson
     stream, certified by the kglm_server loop with HBM-budgeted admission.
     value = aggregate nodes evaluated per second over the makespan; latency =
@@ -526,25 +643,23 @@ def run_serving(args):
     that closed their gap within the per-request limit)."""
     from paper_2605_22188_gb300 import kglm
     rank, world, local = rank_info()
-    import torch
-    torch.cuda.set_device(local)
     specs = synth.serving_specs(64, seed=rank)
     arrivals = synth.poisson_arrivals(len(specs), args.rate, seed=rank)
     data = []
     for sp in specs:                       # drawn before the timed region
         X, y, _ = synth.instance(sp["n"], sp["p"], sp["k"], sp["kind"], rho=sp["rho"], snr=sp["snr"], seed=sp["seed"])
         data.append((X, y))
-    barrier()
     srv = kglm.Server(max_active=args.max_active, hbm_budget=0, iters=200, check_every=10,
                       time_limit_s=args.request_limit, batch_cap=4096)
-    with ClockSampler(local) as clk:
+    local_clk = ClockSampler(local)
+    with local_clk as clk:
         t0 = time.perf_counter()
         ids = []
         for sp, (X, y), ta in zip(specs, data, arrivals):
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            ids.append(srv.submit(X, y, sp["k"], sp["lam2"], sp["M"], sp["kind"], prec=args.prec, max_batch=0))
+            ids.append(srv.submit(X, y, sp["k"], sp["lam2"], sp["M"], sp["kind"], prec=args.serve_prec, max_batch=0))
         srv.drain()
         wall = time.perf_counter() - t0
     infos = [srv.info(r) for r in ids]
@@ -553,56 +668,63 @@ def run_serving(args):
     nodes = sum(i["nodes"] for i in infos)
     cert = [i for i in infos if i["state"] == kglm.REQ_DONE and i["gap"] <= 1e-6]
     lat = sorted(i["t_done"] - i["t_submit"] for i in cert)
-    secs, units = reduce_max_sum(wall, float(nodes))
     pct = lambda q: float(np.percentile(lat, q)) if lat else None
+    return {
+        "value": nodes / wall, "unit": "nodes/s", "wall_s": wall, "requests": len(specs),
+        "arrival_rate_per_s": args.rate, "max_active": args.max_active, "request_time_limit_s": args.request_limit,
+        "products": args.serve_prec, "budget_bytes": st["budget"],
+        "latency_s": {"p50": pct(50), "p99": pct(99), "max": lat[-1] if lat else None,
+                      "of": "requests certified within the limit"},
+        "certified": len(cert), "not_certified": len(infos) - len(cert),
+        "failed": sum(1 for i in infos if i["state"] == kglm.REQ_FAILED),
+        "worst_gap": max(i["gap"] for i in infos), "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
+        "clocks": clk.summary(),
+        "per_request": [{"n": sp["n"], "p": sp["p"], "k": sp["k"],
+                         "loss": "lsq" if sp["kind"] == synth.LSQ else "logistic", "rho": sp["rho"],
+                         "batch": i["batch"], "nodes": i["nodes"], "gap": i["gap"], "state": i["state"],
+                         "latency_s": round(i["t_done"] - i["t_submit"], 3)} for sp, i in zip(specs, infos)],
+    }
+
+
+def run_serving(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    barrier()
+    out = serving_summary(args)
+    secs, units = reduce_max_sum(out["wall_s"], out["value"] * out["wall_s"])
     if rank != 0:
         return
     line = {
         "metric": "aggregate node bounds/sec and time-to-certified-optimality p50/p99 (serving mix)",
         "value": units / secs, "unit": "nodes/s", "n_gpus": world, "steps": 1, "warmup": 0,
         "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": SERVING, "requests": len(specs), "arrival_rate_per_s": args.rate,
+        "dtype": args.serve_prec, "data": "synthetic",
+        "config": {"workload": SERVING, "requests": out["requests"], "arrival_rate_per_s": args.rate,
                    "max_active": args.max_active, "request_time_limit_s": args.request_limit,
-                   "products": args.prec, "certificate": "fp64", "iters": 200, "check_every": 10,
-                   "budget_bytes": st["budget"], "parallelism": "replicas" if world > 1 else "single"},
-        "latency_s": {"p50": pct(50), "p99": pct(99), "max": lat[-1] if lat else None, "unit": "s",
-                      "of": "requests certified within the limit"},
-        "certified": len(cert), "not_certified": len(infos) - len(cert),
-        "failed": sum(1 for i in infos if i["state"] == kglm.REQ_FAILED),
-        "worst_gap": max(i["gap"] for i in infos),
-        "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
-        "clocks": clk.summary(),
-        "requests": [{"n": sp["n"], "p": sp["p"], "k": sp["k"], "loss": "lsq" if sp["kind"] == synth.LSQ else "logistic",
-                      "rho": sp["rho"], "batch": i["batch"], "nodes": i["nodes"], "gap": i["gap"],
-                      "status": i["status"], "state": i["state"], "message": i["message"],
-                      "t_submit": round(i["t_submit"], 4), "t_admit": round(i["t_admit"], 4),
-                      "t_done": round(i["t_done"], 4)} for sp, i in zip(specs, infos)],
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "serving": out,
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(X, y, c, T, args):
-    """The oracle as it stands on the host cores, on a bounded sample of the workload's nodes."""
-    from oracle import node as on
-    L = on.lipschitz(X, c["kind"])
-    cores = os.cpu_count() or 1
+def cpu_baseline(pool, c, T, cores, args):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload's
+    nodes (one process per core), sized from a first timed node to about args.cpu_seconds."""
     rng = np.random.default_rng(77)
-    nodes = synth.csr_to_sets(*synth.random_nodes(cores * args.cpu_nodes_per_core, c["p"], c["k"], rng))
-    pool = oracle_pool(X, y, c, L, cores)
-    try:
-        pool.map(_oracle_node, [(J0, J1, 2) for J0, J1 in nodes[:cores]], chunksize=1)   # warm the workers
-        rate, dt = oracle_rate(pool, nodes, T, cores)
-    finally:
-        pool.close()
-        pool.join()
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+    probe = synth.csr_to_sets(*synth.random_nodes(cores, c["p"], c["k"], rng))
+    _, dt1 = oracle_run(pool, probe, T)                # one node per core: warms the workers, times a node
+    per_node = dt1
+    reps = max(1, int(args.cpu_seconds / max(per_node, 1e-3)))
+    nodes = synth.csr_to_sets(*synth.random_nodes(cores * reps, c["p"], c["k"], rng))
+    _, dt = oracle_run(pool, nodes, T)
+    return {"value": len(nodes) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d nodes of the workload (T=%d, certificate, rounding, re-opt, branch index), "
                       "one process per core, %.1f s" % (len(nodes), T, dt)}
 
 
 def run_reference(args):
-    """The FP64 oracle timed on the host cores: same metric, bounded samples per step."""
+    """The FP64 oracle timed on the host cores: same metric and workload, bounded samples per step."""
     rank, world, _ = rank_info()
     if rank != 0:
         return
@@ -610,19 +732,22 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed per node-bound workload; "
                           "this workload has no oracle arm"}))
         return
-    from oracle import node as on
+    c0 = synth.CONFIGS[args.workload]
+    m = args.nodes or c0.get("m", 1024)
+    T = args.iters or c0.get("T", 50)
     c, X, y, _ = synth.config_instance(args.workload, seed=0, kind=loss_kind(args))
-    T = args.iters
-    L = on.lipschitz(X, c["kind"])
     cores = os.cpu_count() or 1
-    per_step = cores * args.ref_nodes_per_core
     rng = np.random.default_rng(1000)
-    pool = oracle_pool(X, y, c, L, cores)
+    pool = oracle_pool(X, y, c, cores)
+    # nodes per step: one per core, more while a step stays under about args.ref_step_seconds
+    probe = synth.csr_to_sets(*synth.random_nodes(cores, c["p"], c["k"], rng))
+    _, dt1 = oracle_run(pool, probe, T)
+    per_step = cores * max(1, int(args.ref_step_seconds / max(dt1, 1e-3)))
     total_nodes, total_s = 0, 0.0
     try:
         for i in range(args.warmup + args.steps):
             nodes = synth.csr_to_sets(*synth.random_nodes(per_step, c["p"], c["k"], rng))
-            _, dt = oracle_rate(pool, nodes, T, cores)
+            _, dt = oracle_run(pool, nodes, T)
             if i >= args.warmup:
                 total_nodes += len(nodes)
                 total_s += dt
@@ -634,10 +759,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": c["n"], "p": c["p"], "k": c["k"], "lambda2": c["lam2"],
-                   "M": c["M"], "iters": T, "sample_nodes_per_step": per_step},
+        "config": workload_config(args.workload, c, m, T, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d nodes per step, one process per core" % per_step},
+                         "sample": "%d nodes of the workload per step (of %d in a batch), one process per core"
+                                   % (per_step, m)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -646,25 +771,27 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "bf16", "tf32", "tf32x3"])
-    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "bf16", "tf32", "tf32x3"])
+    ap.add_argument("--iters", type=int, default=0, help="FISTA iterations per node (0: the workload's, else 50)")
     ap.add_argument("--nodes", type=int, default=0, help="nodes per batch (0: the workload's)")
     ap.add_argument("--loss", default=None, choices=[None, "lsq", "logistic"],
                     help="override the workload's loss (the microbench runs both)")
-    ap.add_argument("--cpu-nodes-per-core", type=int, default=150)
-    ap.add_argument("--ref-nodes-per-core", type=int, default=30)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU baseline: target wall seconds")
+    ap.add_argument("--ref-step-seconds", type=float, default=2.0, help="reference arm: target seconds per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-ttz", action="store_true", help="skip the time-to-zero-gap solves")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="only the headline line (no logistic/precision/solve/c2/serving/sweep keys)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles (profiling runs)")
     ap.add_argument("--tiles", default="", help="fixed tiles instead of tuning: link,grad,split_cap,sub_batches")
     ap.add_argument("--rate", type=float, default=2.0, help="serving mix: Poisson arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving mix: requests solved at once")
     ap.add_argument("--request-limit", type=float, default=20.0, help="serving mix: seconds per request")
+    ap.add_argument("--serve-prec", default="bf16", help="serving mix: product precision")
+    ap.add_argument("--sweep-iters", type=int, default=50, help="batch sweep: iterations per evaluation")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank, world, local = rank_info()
