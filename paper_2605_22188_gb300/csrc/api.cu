@@ -40,6 +40,7 @@ struct kglm_ctx {
     int *kbar = nullptr, *pf = nullptr;
     void *B = nullptr, *V = nullptr, *G = nullptr, *R = nullptr;
     double *tmom = nullptr, *zeta = nullptr, *Q = nullptr;
+    float* phint = nullptr;       // per node: the streaming prox's selection and threshold hints
     int *active = nullptr, *iters_done = nullptr, *support = nullptr, *jstar = nullptr;
     double *sum_loss = nullptr, *sum_conj = nullptr, *lb_now = nullptr, *primal_now = nullptr;
     double *lb_best = nullptr, *primal_last = nullptr, *ub = nullptr, *beta_re = nullptr;
@@ -455,6 +456,7 @@ void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
     a.in_mask = c->in_mask + (size_t)row0 * c->W; a.out_mask = c->out_mask + (size_t)row0 * c->W;
     a.kbar = c->kbar + row0; a.pf = c->pf + row0;
     a.tmom = c->tmom + row0; a.active = c->active + row0;
+    a.hint = c->phint + 2 * (size_t)row0;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
     a.pdl = pdl;
     a.threads = c->prox_threads;
@@ -487,6 +489,7 @@ void iterate(kglm_ctx* c) {
     a.G = c->G; a.V = c->V; a.B = c->B;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.tmom = c->tmom; a.active = c->active;
+    a.hint = c->phint;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
     a.threads = c->prox_threads;
     Scope sc(c, PH_PROX, 1, (c->f64 ? 8.0 : 4.0) * 5.0 * c->sum_pa);
@@ -730,7 +733,7 @@ void push_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_idx,
                                            (int)nnz_out, nullptr);
         check_launch();
         c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, slot, c->pool_slots, c->pool, wb,
-                                          c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK, c->tc_kind == 0, c->tmom, c->active);
+                                          c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK, c->tc_kind == 0, c->tmom, c->active, c->phint);
         check_launch();
     }
     sync(c);   // host arrays may be pageable and reused by the caller
@@ -759,7 +762,7 @@ void push_dev_impl(kglm_ctx* c, int m, const int32_t* in_ptr, const int32_t* in_
                                               c->out_mask, warm_slot, c->pool_slots, c->d_err);
         check_launch();
         c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, warm_slot, c->pool_slots, c->pool, nullptr,
-                                          c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK, c->tc_kind == 0, c->tmom, c->active);
+                                          c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK, c->tc_kind == 0, c->tmom, c->active, c->phint);
         check_launch();
     }
     {
@@ -855,7 +858,7 @@ size_t footprint(const kglm_desc& d) {
     add(4 * mc * W); add(4 * mc * W); add(4 * mc); add(4 * mc);
     add(mc * p * ws); add(mc * p * ws); add(mc * p * ws);
     add(mc * n * std::max(ws, (size_t)4));
-    add(8 * mc); add(4 * mc); add(4 * mc);
+    add(8 * mc); add(4 * mc); add(8 * mc); add(4 * mc);
     add(8 * mc * n); add(8 * mc * p);
     for (int t = 0; t < 7; ++t) add(8 * mc);
     add(8 * mc * k); add(4 * mc * k); add(4 * mc); add(mc);
@@ -1555,6 +1558,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->R = dalloc(c, mc * n * std::max(ws, sizeof(float)));
         c->tmom = dalloc_t<double>(c, mc);
         c->active = dalloc_t<int>(c, mc);
+        c->phint = dalloc_t<float>(c, 2 * mc);
         c->iters_done = dalloc_t<int>(c, mc);
         c->zeta = dalloc_t<double>(c, mc * n);
         c->Q = dalloc_t<double>(c, mc * p);

@@ -147,6 +147,8 @@ struct ProxArgs {
     int restart;
     int pdl;              // launch with programmatic stream serialization
     int threads;          // FP32, p > 512: threads per node (0: 8 coordinates per thread)
+    float* hint;          // per node (2 floats): the last step's kbar-th largest free |u| and
+                          // block threshold, for the streaming FP32 prox (0: none; NULL: unused)
 };
 // One FISTA step per node: u = v - eta*G, beta' = prox(u), restart, next v.
 int prox_fista_f64(cudaStream_t s, const ProxArgs& a);
@@ -228,7 +230,7 @@ int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out
                     int nslots, int* err);
 int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
                 const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, float* Vop_lo, int op_ld,
-                int op_bf16, double* tmom, int* active);
+                int op_bf16, double* tmom, int* active, float* hint);
 // rows x cols FP64 (row stride ld_in) -> BF16 or TF32-in-FP32 with row stride ld_out, zero padded;
 // with lo != NULL also the low part bf16/tf32(x - hi) into lo.
 void convert_pad(cudaStream_t s, const double* in, int rows, int cols, int ld_in, void* out, int ld_out, int to_bf16,

@@ -113,11 +113,12 @@ __global__ void k_convert_pad_f32(const float* in, int rows, int cols, void* out
     store_operand2(out, lo, t, c < cols ? in[(size_t)r * cols + c] : 0.f, to_bf16);
 }
 
-__global__ void k_node_init(int m, double t0, double* tmom, int* active) {
+__global__ void k_node_init(int m, double t0, double* tmom, int* active, float* hint) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= m) return;
     tmom[b] = t0;
     active[b] = 1;
+    if (hint) hint[2 * b] = hint[2 * b + 1] = 0.f;
 }
 
 template <typename T>
@@ -192,7 +193,7 @@ int layout_validate(cudaStream_t s, int m, int k, int W, int nnz_in, int nnz_out
 
 int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot, int nslots, const void* pool,
                 const double* warmB, const uint32_t* out_mask, void* B, void* V, void* Vop, float* Vop_lo, int op_ld,
-                int op_bf16, double* tmom, int* active) {
+                int op_bf16, double* tmom, int* active, float* hint) {
     const size_t n = (size_t)m * p;
     if (is_f64)
         k_warm<double><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const double*)pool, warmB, out_mask,
@@ -201,7 +202,7 @@ int layout_warm(cudaStream_t s, int m, int p, int W, int is_f64, const int* slot
         k_warm<float><<<blocks(n, 256), 256, 0, s>>>(m, p, W, slot, nslots, (const float*)pool, warmB, out_mask,
                                                      (float*)B, (float*)V, Vop, Vop_lo, op_ld, op_bf16);
     // t_1 = 1 (Beck and Teboulle): the first extrapolation, after x_1, takes no momentum
-    k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 1.0, tmom, active);
+    k_node_init<<<blocks(m, 256), 256, 0, s>>>(m, 1.0, tmom, active, hint);
     return 2;
 }
 

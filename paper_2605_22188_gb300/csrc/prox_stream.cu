@@ -13,29 +13,37 @@
 // What differs is the schedule.  The CTA-per-node kernel holds a node's
 // coordinates in registers and spends most of its time in barrier-separated
 // phases with three nodes per SM, so HBM idles.  Here a warp copies the node's
-// rows of G (or its first split slice), V and beta into shared memory with
+// rows of G (or its first split slice) and V into shared memory with
 // asynchronous 16-byte copies (one round trip per node, no registers held),
 // and every later pass runs on shared memory with warp shuffles only, so that
-// an SM keeps several nodes in flight and their copies overlap the others'
-// passes.  Global memory sees each input once and each output once.
+// an SM keeps a dozen nodes in flight and their copies overlap the others'
+// passes.  beta_old is read once, by the write pass.  Global memory sees each
+// input once and each output once.
 //
 // Per node (one warp):
-//  A. copy G, V, beta and the two fixing-mask rows; u = v - eta G replaces G
+//  A. copy G, V and the two fixing-mask rows; u = v - eta G replaces G
 //     (J0 and J1 entries set to 0, so that every later pass sees only free
 //     coordinates: 0 never exceeds a non-negative threshold, and the passes
 //     need neither masks nor branches); J1 entries go to a short list
 //     (index, u); each lane keeps its two largest free |u|.
-//  B. tau = the kbar-th largest of the 64 lane top-two values (so at least
-//     kbar free coordinates have |u| >= tau); the free |u| >= tau are gathered
-//     (at most kCandCap) as keys (|u| bits, complemented index) and ranked:
-//     the kbar best are the top set (ties to the smaller index), the next one
-//     is the largest tail value.  If more than kCandCap qualify, kbar rounds
-//     of a warp argmax over shared memory select the top set instead.
+//  B. the free |u| above a threshold tau are gathered (at most kCandCap) as
+//     keys (|u| bits, complemented index) and ranked: the kbar best are the top
+//     set (ties to the smaller index), the next one is the largest tail value.
+//     tau comes from the node's previous step (7/8 of its kbar-th largest |u|;
+//     the gathering then happens in pass A) when that gathers more than kbar
+//     and at most kCandCap entries; else tau = the kbar-th largest of the 64
+//     lane top-two values (at least kbar free |u| reach it) and one more pass
+//     gathers.  If more than kCandCap qualify, kbar rounds of a warp argmax
+//     over shared memory select the top set instead.
 //  C. the top coordinates are set to 0 too; theta on the piece of f between
-//     top entry points that holds the root (the last piece is tested first:
-//     with small c every entry point is tiny and the root lies above all of
-//     them; else a binary search), then Newton steps from the piece's left end
-//     (f is convex there), each a pass over the tail in shared memory.
+//     top entry points that holds the root, then Newton steps on it (f is
+//     convex there), each a pass over the tail in shared memory.  The first
+//     pass tests 0.97 times the node's previous threshold: if f > 0 there, the
+//     root lies above it on the last piece and Newton starts there.  Else the
+//     last piece is tested at its left end (with small c every entry point is
+//     tiny and the root lies above all of them), else a binary search finds
+//     the piece and Newton starts at its left end.  Every start is left of
+//     the root, so the steps converge to it from below.
 //  D. beta in shared memory (tail formula, 0 for the other entries, then the
 //     top and J1 lists scattered in); one pass writes beta and
 //     v' = beta + ((t-1)/t')(beta - beta_old) (and the tensor-core operand
@@ -57,6 +65,12 @@ constexpr int kSMs = 152;
 constexpr int kStreamMaxWarps = 16;
 constexpr int kStreamMinWarps = 6;      // below this the CTA-per-node kernel is used
 constexpr size_t kSmemPerSM = 227 * 1024;
+// Hints carried from the previous step of the same node: the candidates are
+// gathered during the first pass above this fraction of the last kbar-th
+// largest free |u|, and Newton starts at this fraction of the last threshold
+// (each only after a check that it is usable; otherwise the full search runs).
+constexpr float kTauHint = 0.875f;
+constexpr float kThetaHint = 0.97f;
 
 struct WarpHdr {
     unsigned long long cand[kCandCap];
@@ -74,9 +88,10 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size
 // a row of p floats padded to a multiple of 4 (the padding stays 0)
 __host__ __device__ inline size_t row_bytes(int p) { return align16((size_t)p * sizeof(float)); }
 __host__ __device__ inline size_t mask_bytes(int W) { return align16((size_t)W * sizeof(uint32_t)); }
-// per warp: header, two mask rows, then the u (G), v and beta rows
+// per warp: header, two mask rows, then the u (G) and v rows (beta_old is read
+// from global memory by the write pass, its only use)
 __host__ __device__ inline size_t warp_bytes(int p, int W) {
-    return align16(sizeof(WarpHdr)) + 2 * mask_bytes(W) + 3 * row_bytes(p);
+    return align16(sizeof(WarpHdr)) + 2 * mask_bytes(W) + 2 * row_bytes(p);
 }
 
 __device__ __forceinline__ float entry_pt(float a, float c, float M) {
@@ -190,9 +205,8 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
     uint32_t* smo = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(smi) + mask_bytes(W));
     float* su = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smo) + mask_bytes(W));
     float* sv = su + row_bytes(p) / sizeof(float);
-    float* sb = sv + row_bytes(p) / sizeof(float);
     float4* su4 = reinterpret_cast<float4*>(su);
-    for (int j = p + lane; j < 4 * p4; j += 32) su[j] = sv[j] = sb[j] = 0.f;   // padding: 0 for good
+    for (int j = p + lane; j < 4 * p4; j += 32) su[j] = sv[j] = 0.f;   // padding: 0 for good
     const float eta = (float)a.eta, c = (float)a.c, M = (float)a.M, c1 = 1.f + c;
     const int nq = p / VEC;
 
@@ -204,6 +218,10 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
         const float* G0 = a.gsplits == 0 ? static_cast<const float*>(a.G) + base : a.Gpart + base;
         const int kb = a.kbar[b], pf = a.pf[b];
         const double tprev = lane == 0 ? a.tmom[b] : 0.0;
+        const bool sel = kb > 0 && pf > kb;         // a top set to select and a block to pool
+        float tau_h = 0.f, th_h = 0.f;
+        if (a.hint != nullptr && sel) { tau_h = a.hint[2 * b]; th_h = a.hint[2 * b + 1]; }
+        const float tg = tau_h > 0.f ? tau_h * kTauHint : __builtin_huge_valf();
 
         // ---- A. rows to shared memory in one round trip
         for (int q = lane; q < W; q += 32) {
@@ -214,18 +232,18 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
             if constexpr (VEC == 4) {
                 cp_async16(su + 4 * q, G0 + 4 * q);
                 cp_async16(sv + 4 * q, V + 4 * q);
-                cp_async16(sb + 4 * q, Bm + 4 * q);
             } else {
                 cp_async4(su + q, G0 + q);
                 cp_async4(sv + q, V + q);
-                cp_async4(sb + q, Bm + q);
             }
         }
         if (lane == 0) { h.nj1 = 0; h.ncand = 0; }
         cp_async_wait_all();
         __syncwarp();
-        // u = v - eta G (split slices after the first are added from global memory, in order)
-        float t1 = 0.f, t2 = 0.f;
+        // u = v - eta G (split slices after the first are added from global memory, in
+        // order); J0 entries become 0 now, J1 entries once they are listed below.
+        // Two running top-two pairs (even and odd positions) keep the chains short.
+        float t1 = 0.f, t2 = 0.f, t1b = 0.f, t2b = 0.f;
         for (int q = lane; q < p4; q += 32) {
             float4 g = su4[q];
             const float4 v = reinterpret_cast<const float4*>(sv)[q];
@@ -242,26 +260,51 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
             float o[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                const bool inb = j0 + t < p, in = inb && ((wi >> t) & 1u), fr = inb && !(((wi | wo) >> t) & 1u);
-                if (in) {                              // J1: at most k per node
-                    const int qq = atomicAdd(&h.nj1, 1);
-                    h.j1i[qq] = j0 + t;
-                    h.j1u[qq] = uu[t];
-                }
+                const bool inb = j0 + t < p, out = (wo >> t) & 1u, fr = inb && !(((wi | wo) >> t) & 1u);
                 const float au = fr ? fabsf(uu[t]) : 0.f;
-                t2 = fmaxf(t2, fminf(t1, au));
-                t1 = fmaxf(t1, au);
-                o[t] = fr ? uu[t] : 0.f;
+                if (t & 1) { t2b = fmaxf(t2b, fminf(t1b, au)); t1b = fmaxf(t1b, au); }
+                else { t2 = fmaxf(t2, fminf(t1, au)); t1 = fmaxf(t1, au); }
+                if (au >= tg) {                        // candidate above the hinted threshold
+                    const int qq = atomicAdd(&h.ncand, 1);
+                    if (qq < kCandCap)
+                        h.cand[qq] = ((unsigned long long)__float_as_uint(au) << 32) | (0xffffffffu - (uint32_t)(j0 + t));
+                }
+                o[t] = inb && !out ? uu[t] : 0.f;
             }
             su4[q] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        t2 = fmaxf(fminf(t1, t1b), fmaxf(t2, t2b));     // the lane's two largest
+        t1 = fmaxf(t1, t1b);
+        __syncwarp();
+        // J1 (at most k entries): listed from the mask words, then set to 0
+        for (int q = lane; q < W; q += 32) {
+            uint32_t bits = smi[q];
+            while (bits) {
+                const int j = 32 * q + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int qq = atomicAdd(&h.nj1, 1);
+                h.j1i[qq] = j;
+                h.j1u[qq] = su[j];
+                su[j] = 0.f;
+            }
         }
         __syncwarp();
 
         // ---- B. top-kbar selection over the free coordinates
         float theta = 0.f;
         int ntop = 0;
-        if (kb > 0 && pf > kb) {
+        if (sel) {
             ntop = kb;
+            // a top slot stays empty (si -1, value 0) only if fewer than kbar free
+            // |u| are positive; an empty slot stands for a zero entry
+            for (int i = lane; i < kb; i += 32) { h.si[i] = -1; h.sv[i] = 0.f; }
+            __syncwarp();
+            int total = h.ncand;
+            float amax_lo = 0.f;
+            if (!(tau_h > 0.f && total >= kb + 1 && total <= kCandCap)) {
+            // no usable hint: tau from the lane top-two values, then a gathering pass
+            if (lane == 0) h.ncand = 0;
+            __syncwarp();
             uint32_t k0 = __float_as_uint(t1), k1 = __float_as_uint(t2);
             sort64(k0, k1, lane);
             const int pos = 64 - kb;                           // kb-th largest of 64 (kb <= kMaxK = 64)
@@ -283,12 +326,10 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
                     }
                 }
             }
-            // a top slot stays empty (si -1, value 0) only if fewer than kbar free
-            // |u| are positive; an empty slot stands for a zero entry
-            for (int i = lane; i < kb; i += 32) { h.si[i] = -1; h.sv[i] = 0.f; }
             __syncwarp();
-            const int total = h.ncand;
-            const float amax_lo = warp_max(lo_max);
+            total = h.ncand;
+            amax_lo = warp_max(lo_max);
+            }
             if (total <= kCandCap) {
                 for (int i = lane; i < total; i += 32) {
                     const unsigned long long ci = h.cand[i];
@@ -366,19 +407,47 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
                         if (lane + 32 < kb && h.ep[lane + 32] < x) f -= fmaxf(hx - h.sv[lane + 32], 0.f);
                         return warp_sum(f);
                     };
+                    // top part of f on the last piece (every entry point below amax counts)
+                    auto top_last = [&](float x) -> float {
+                        const float hx = x + fminf(x / c, M);
+                        float f = 0.f;
+                        if (lane < kb && h.ep[lane] < amax) f += fmaxf(hx - h.sv[lane], 0.f);
+                        if (lane + 32 < kb && h.ep[lane + 32] < amax) f += fmaxf(hx - h.sv[lane + 32], 0.f);
+                        return warp_sum(f);
+                    };
+                    const float xr = r > 0 ? h.ep[kb - r] : 0.f;   // the largest entry point below amax
                     int lo = 0, hi = r + 1;
-                    if (r > 0 && f_at(r) > 0.f) lo = r;        // the last piece holds the root
-                    else hi = r;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (f_at(mid) > 0.f) lo = mid; else hi = mid;
+                    float th = 0.f, nl = 0.f, Sl = 0.f;
+                    bool started = false;
+                    const float start = th_h * kThetaHint;
+                    if (start > xr && start < amax) {
+                        // the last step's threshold, lowered: if f > 0 there, the root is
+                        // above it on the last piece and Newton can start there
+                        tail_above(su4, p4, lane, start, nl, Sl);
+                        if (Sl - start * nl - top_last(start) > 0.f) { lo = r; th = start; started = true; }
+                    }
+                    if (!started && r > 0) {
+                        // f at the largest entry point below amax (one pass, also Newton's first)
+                        tail_above(su4, p4, lane, xr, nl, Sl);
+                        const float hx = xr + fminf(xr / c, M);
+                        float tp = 0.f;
+                        if (lane < kb && h.ep[lane] < xr) tp += fmaxf(hx - h.sv[lane], 0.f);
+                        if (lane + 32 < kb && h.ep[lane + 32] < xr) tp += fmaxf(hx - h.sv[lane + 32], 0.f);
+                        if (Sl - xr * nl - warp_sum(tp) > 0.f) { lo = r; th = xr; started = true; }
+                        else hi = r;
+                    }
+                    if (!started) {
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (f_at(mid) > 0.f) lo = mid; else hi = mid;
+                        }
+                        th = xval(lo);
+                        tail_above(su4, p4, lane, th, nl, Sl);
                     }
                     const float xlo = xval(lo), xhi = xval(hi);
                     float nt = 0.f, St = 0.f;
                     for (int i = 0; i < kb; ++i)
                         if (h.ep[i] <= xlo) { nt += 1.f; St += h.sv[i]; }
-                    float th = xlo, nl, Sl;
-                    tail_above(su4, p4, lane, th, nl, Sl);
                     for (int it = 0; it < 4 * kMaxK + 64; ++it) {
                         float tn = model_root_f(nt, St, nl, Sl, c, M);
                         tn = fminf(fmaxf(tn, th), xhi);
@@ -428,30 +497,46 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
         const float coef = (float)__shfl_sync(0xffffffffu, c_keep, 0);
         float d0 = 0.f, d1 = 0.f;
         const size_t ob = (size_t)b * a.op_ld;
-        for (int q = lane; q < nq; q += 32) {
-            if constexpr (VEC == 4) {
-                const float4 v = reinterpret_cast<const float4*>(sv)[q];
-                const float4 bo = reinterpret_cast<const float4*>(sb)[q];
-                const float4 bn = su4[q];
-                d0 += (v.x - bn.x) * (bn.x - bo.x) + (v.z - bn.z) * (bn.z - bo.z);
-                d1 += (v.y - bn.y) * (bn.y - bo.y) + (v.w - bn.w) * (bn.w - bo.w);
-                const float4 vn = make_float4(bn.x + coef * (bn.x - bo.x), bn.y + coef * (bn.y - bo.y),
-                                              bn.z + coef * (bn.z - bo.z), bn.w + coef * (bn.w - bo.w));
-                reinterpret_cast<float4*>(Bm)[q] = bn;
-                reinterpret_cast<float4*>(V)[q] = vn;
-                if (a.Vop != nullptr) store_operand4(a.Vop, a.Vop_lo, ob + 4 * q, vn, a.op_bf16);
-            } else {
-                const float v = sv[q], bo = sb[q], bn = su[q];
-                d0 += (v - bn) * (bn - bo);
-                const float vn = bn + coef * (bn - bo);
-                Bm[q] = bn;
-                V[q] = vn;
-                if (a.Vop != nullptr) store_operand2(a.Vop, a.Vop_lo, ob + q, vn, a.op_bf16);
+        constexpr int UN = VEC == 4 ? 4 : 8;          // beta_old loads in flight per lane
+        using VT = typename std::conditional<VEC == 4, float4, float>::type;
+        for (int q0 = lane; q0 < nq; q0 += 32 * UN) {
+            VT bo[UN];
+#pragma unroll
+            for (int r = 0; r < UN; ++r)
+                if (q0 + 32 * r < nq) bo[r] = reinterpret_cast<const VT*>(Bm)[q0 + 32 * r];
+#pragma unroll
+            for (int r = 0; r < UN; ++r) {
+                const int q = q0 + 32 * r;
+                if (q >= nq) break;
+                if constexpr (VEC == 4) {
+                    const float4 v = reinterpret_cast<const float4*>(sv)[q];
+                    const float4 bn = su4[q];
+                    d0 += (v.x - bn.x) * (bn.x - bo[r].x) + (v.z - bn.z) * (bn.z - bo[r].z);
+                    d1 += (v.y - bn.y) * (bn.y - bo[r].y) + (v.w - bn.w) * (bn.w - bo[r].w);
+                    const float4 vn = make_float4(bn.x + coef * (bn.x - bo[r].x), bn.y + coef * (bn.y - bo[r].y),
+                                                  bn.z + coef * (bn.z - bo[r].z), bn.w + coef * (bn.w - bo[r].w));
+                    reinterpret_cast<float4*>(Bm)[q] = bn;
+                    reinterpret_cast<float4*>(V)[q] = vn;
+                    if (a.Vop != nullptr) store_operand4(a.Vop, a.Vop_lo, ob + 4 * q, vn, a.op_bf16);
+                } else {
+                    const float v = sv[q], bn = su[q];
+                    d0 += (v - bn) * (bn - bo[r]);
+                    const float vn = bn + coef * (bn - bo[r]);
+                    Bm[q] = bn;
+                    V[q] = vn;
+                    if (a.Vop != nullptr) store_operand2(a.Vop, a.Vop_lo, ob + q, vn, a.op_bf16);
+                }
             }
         }
         const float dot = warp_sum(d0 + d1);
         const bool rs = a.restart && dot > 0.f;
-        if (lane == 0) a.tmom[b] = rs ? 1.0 : t_keep;   // restart: start over from beta, t = 1
+        if (lane == 0) {
+            a.tmom[b] = rs ? 1.0 : t_keep;   // restart: start over from beta, t = 1
+            if (a.hint != nullptr) {
+                a.hint[2 * b] = sel ? h.sv[kb - 1] : 0.f;
+                a.hint[2 * b + 1] = sel ? theta : 0.f;
+            }
+        }
         if (rs) {
             // momentum off: v' = beta
             for (int j = lane; j < p; j += 32) {
