@@ -32,6 +32,7 @@ struct kglm_ctx {
     std::vector<void*> allocs;
     // instance (device)
     double *X64 = nullptr, *Xt64 = nullptr, *y64 = nullptr, *gram = nullptr, *Xty = nullptr;
+    double yty = 0.0;             // y^T y (host, FP64)
     float *X32 = nullptr, *Xt32 = nullptr, *y32 = nullptr;
     // node batch (device), capacity mcap
     int mcap = 0, m = 0;
@@ -638,6 +639,7 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
     r.y32 = c->f64 ? nullptr : c->y32;
     r.support = c->support; r.B = c->B; r.b_is_f64 = c->f64;
     r.ub = c->ub; r.beta_re = c->beta_re;
+    r.yty = c->yty;
     {
         Scope sc(c, PH_REOPT, 1, 0.0);
         if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
@@ -1437,6 +1439,8 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         CK(cudaMemcpyAsync(c->X64, X, sizeof(double) * n * p, cudaMemcpyHostToDevice, c->st));
         CK(cudaMemcpyAsync(c->Xt64, Xt.data(), sizeof(double) * n * p, cudaMemcpyHostToDevice, c->st));
         CK(cudaMemcpyAsync(c->y64, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+        c->yty = 0.0;
+        for (size_t i = 0; i < (size_t)n; ++i) c->yty += y[i] * y[i];
         if (!c->f64) {
             c->X32 = dalloc_t<float>(c, n * p);
             c->Xt32 = dalloc_t<float>(c, n * p);

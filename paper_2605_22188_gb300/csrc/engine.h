@@ -212,6 +212,7 @@ struct ReoptArgs {
     int b_is_f64;
     double* ub;            // out: v(S_b)
     double* beta_re;       // out: m x k
+    double yty;            // y^T y (least squares: v(S) = y^T y + b^T (G_SS + lambda2 I) b - 2 c^T b)
 };
 // returns 0, or -1 if the dynamic shared memory for k cannot be granted
 int reopt_launch(cudaStream_t s, const ReoptArgs& a);

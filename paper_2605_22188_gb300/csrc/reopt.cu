@@ -1,6 +1,8 @@
 // Re-optimization on the rounded support of each node (§4.3):
 //   v(S) = min { F(X_S b) + lambda2 ||b||^2 : ||b||_inf <= M },
-// one CTA per node, warm-started from the node's relaxed beta on S.
+// warm-started from the node's relaxed beta on S: for the logistic loss one
+// CTA per node; for least squares one warp per node on the Gram block
+// (k_reopt_lsq_warp below).
 //
 // §4.3 allows any proximal-gradient method whose prox is the projection onto
 // [-M, M]; the problem has at most k variables, so this kernel takes
@@ -28,6 +30,7 @@
 // returned v(S) is recomputed in a final pass over the samples: FP64 in the
 // FP64 mode; in the others an FP64 predictor with the logistic loss and its
 // rigorous rounding margin in FP32 (rounded upward), an upper bound of v(S).
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -500,6 +503,180 @@ __global__ __launch_bounds__(NT, sizeof(TI) == 4 ? 4 : 1) void k_reopt(ReoptArgs
     for (int r = tid; r < k; r += NT) a.beta_re[(size_t)b * k + r] = r < ks ? sh.b[r] : 0.0;
 }
 
+// Least squares, one warp per node.  The whole problem lives on the Gram block:
+//   f(b) = b^T (G_SS + lambda2 I) b - 2 c^T b,  c = (X^T y)_S,  g = 2 ((G_SS + lambda2 I) b - c),
+// and v(S) = y^T y + f(b*), so no pass over the n samples is needed; the
+// projected Newton iteration of k_reopt (held set, Newton step on the free set
+// by Cholesky, Armijo backtracking along the projection arc, the same stopping
+// tests) runs in FP64 inside one warp, without CTA barriers, several nodes per
+// CTA.  Per-warp shared memory: A = G_SS + lambda2 I and the factor L (k x k
+// FP64 each) and a few k-vectors.
+struct WarpLsq {
+    double c[kMaxK], b[kMaxK], bn[kMaxK], d[kMaxK], g[2][kMaxK];
+    int S[kMaxK], fidx[kMaxK];
+};
+__host__ __device__ inline size_t lsq_warp_bytes(int k) {
+    return (sizeof(WarpLsq) + 2 * sizeof(double) * (size_t)k * k + 15) / 16 * 16;
+}
+
+// f and g at vec (k-vector in shared memory): rows r = lane, lane + 32.
+__device__ __forceinline__ double lsq_eval(const double* A, const WarpLsq& w, int k, int ks, const double* vec,
+                                           double* g, int lane) {
+    double part = 0.0;
+    for (int r = lane; r < ks; r += 32) {
+        double s = 0.0;
+        for (int q = 0; q < ks; ++q) s += A[r * k + q] * vec[q];
+        part += vec[r] * s - 2.0 * w.c[r] * vec[r];
+        g[r] = 2.0 * (s - w.c[r]);
+    }
+    __syncwarp();
+    return warp_sum(part);
+}
+
+__global__ __launch_bounds__(256) void k_reopt_lsq_warp(ReoptArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int b = blockIdx.x * wpc + warp;
+    if (b >= a.m) return;
+    const int k = a.k, p = a.p;
+    const double M = a.M;
+    unsigned char* base = dyn_raw + (size_t)warp * lsq_warp_bytes(k);
+    WarpLsq& w = *reinterpret_cast<WarpLsq*>(base);
+    double* A = reinterpret_cast<double*>(base + sizeof(WarpLsq));
+    double* L = A + (size_t)k * k;
+    // the support (ascending, -1 padded) and the warm start clipped to the box
+    int ks = 0;
+    for (int r0 = 0; r0 < k; r0 += 32) {
+        const int r = r0 + lane;
+        const int j = r < k ? a.support[(size_t)b * k + r] : -1;
+        const unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
+        if (j >= 0) w.S[ks + __popc(bal & ((1u << lane) - 1u))] = j;
+        ks += __popc(bal);
+    }
+    __syncwarp();
+    for (int r = lane; r < ks; r += 32) {
+        const int j = w.S[r];
+        w.c[r] = a.Xty[j];
+        const size_t bj = (size_t)b * p + j;
+        const double v = a.b_is_f64 ? static_cast<const double*>(a.B)[bj] : (double)static_cast<const float*>(a.B)[bj];
+        w.b[r] = fmin(M, fmax(-M, v));
+    }
+    __syncwarp();
+    for (int t = lane; t < ks * ks; t += 32) {
+        const int r = t / ks, q = t % ks;
+        A[r * k + q] = a.gram[(size_t)w.S[r] * p + w.S[q]] + (r == q ? a.lam2 : 0.0);
+    }
+    __syncwarp();
+    double fcur = 0.0;
+    int cur = 0;
+    if (ks > 0) {
+        fcur = lsq_eval(A, w, k, ks, w.b, w.g[0], lane);
+        double g2 = 0.0;
+        for (int r = lane; r < ks; r += 32) g2 += w.g[0][r] * w.g[0][r];
+        const double gnorm0 = fmax(1.0, sqrt(warp_sum(g2)));
+        for (int it = 0; it < a.max_iter; ++it) {
+            const double* g = w.g[cur];
+            double pg = 0.0;
+            for (int r = lane; r < ks; r += 32) {
+                const double t = w.b[r] - fmin(M, fmax(-M, w.b[r] - g[r]));
+                pg += t * t;
+            }
+            pg = sqrt(warp_sum(pg));
+            if (pg <= a.tol * gnorm0) break;
+            // held set (bound reached, gradient outward), Newton step on the rest
+            const double eps = fmin(1e-3 * M, pg);
+            int nf = 0;
+            for (int r0 = 0; r0 < ks; r0 += 32) {
+                const int r = r0 + lane;
+                bool fr = false;
+                if (r < ks) {
+                    const bool held = (w.b[r] <= -M + eps && g[r] > 0.0) || (w.b[r] >= M - eps && g[r] < 0.0);
+                    fr = !held;
+                    w.d[r] = 0.0;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, fr);
+                if (fr) w.fidx[nf + __popc(bal & ((1u << lane) - 1u))] = r;
+                nf += __popc(bal);
+            }
+            __syncwarp();
+            // L L^T = 2 A_FF (lower triangle), then 2 A_FF d_F = -g_F
+            for (int i = lane; i < nf; i += 32) {
+                const int ri = w.fidx[i];
+                for (int j = 0; j <= i; ++j) L[i * k + j] = 2.0 * A[ri * k + w.fidx[j]];
+                w.bn[i] = -g[ri];               // right-hand side, then the solution
+            }
+            __syncwarp();
+            for (int j = 0; j < nf; ++j) {
+                // A_FF is positive definite (>= lambda2 I); a pivot lost to rounding is floored
+                const double floor_j = 1e-14 * 2.0 * A[w.fidx[j] * k + w.fidx[j]];
+                const double piv = L[j * k + j];
+                const double dj = sqrt(piv > floor_j ? piv : floor_j);
+                __syncwarp();
+                for (int i = lane; i < nf; i += 32) {
+                    if (i == j) L[j * k + j] = dj;
+                    else if (i > j) L[i * k + j] /= dj;
+                }
+                __syncwarp();
+                for (int i = lane; i < nf; i += 32) {
+                    if (i <= j) continue;
+                    const double lij = L[i * k + j];
+                    for (int q = j + 1; q <= i; ++q) L[i * k + q] -= lij * L[q * k + j];
+                }
+                __syncwarp();
+            }
+            for (int j = 0; j < nf; ++j) {                // L y = -g_F
+                if (lane == (j & 31)) w.bn[j] /= L[j * k + j];
+                __syncwarp();
+                const double zj = w.bn[j];
+                for (int i = lane; i < nf; i += 32)
+                    if (i > j) w.bn[i] -= L[i * k + j] * zj;
+                __syncwarp();
+            }
+            for (int j = nf - 1; j >= 0; --j) {           // L^T d = y
+                if (lane == (j & 31)) w.bn[j] /= L[j * k + j];
+                __syncwarp();
+                const double zj = w.bn[j];
+                for (int i = lane; i < nf; i += 32)
+                    if (i < j) w.bn[i] -= L[j * k + i] * zj;
+                __syncwarp();
+            }
+            for (int i = lane; i < nf; i += 32) w.d[w.fidx[i]] = w.bn[i];
+            __syncwarp();
+            // Armijo backtracking along the projection arc (every trial evaluates f and g)
+            const int nxt = 1 - cur;
+            double alpha = 1.0, fn = 0.0;
+            int accept = 0;
+            bool done = false;
+            for (int ls = 0; ls < 40 && !accept; ++ls) {
+                for (int r = lane; r < ks; r += 32) w.bn[r] = fmin(M, fmax(-M, w.b[r] + alpha * w.d[r]));
+                __syncwarp();
+                fn = lsq_eval(A, w, k, ks, w.bn, w.g[nxt], lane);
+                double dec = 0.0, step = 0.0;
+                for (int r = lane; r < ks; r += 32) {
+                    dec += g[r] * (w.bn[r] - w.b[r]);
+                    step = fmax(step, fabs(w.bn[r] - w.b[r]));
+                }
+                dec = warp_sum(dec);
+                step = warp_max(step);
+                // a predicted decrease below the rounding level of f cannot be checked:
+                // take the step (Newton is then in its quadratic region)
+                const bool tiny = fabs(dec) <= 1e-14 * (1.0 + fabs(fcur));
+                accept = (fn <= fcur + 1e-4 * dec || tiny) ? 1 : (step <= 1e-16 * M ? 2 : 0);
+                if (accept == 1 && ((tiny && ls == 0) || step <= 1e-15 * M)) done = true;
+                if (!accept) alpha *= 0.5;
+            }
+            if (accept != 1) break;                       // no progress possible
+            for (int r = lane; r < ks; r += 32) w.b[r] = w.bn[r];
+            __syncwarp();
+            fcur = fn;
+            cur = nxt;
+            if (done) break;
+        }
+    }
+    if (lane == 0) a.ub[b] = a.yty + fcur;
+    for (int r = lane; r < k; r += 32) a.beta_re[(size_t)b * k + r] = r < ks ? w.b[r] : 0.0;
+}
+
 // FP64 objective F(X_S b) + lambda2 ||b||^2 of one coefficient vector (one CTA).
 __global__ __launch_bounds__(NT) void k_objective64(const double* Xt, const double* y, int n, int kind,
                                                     double lam2, const int* S, const double* b, int ks,
@@ -540,6 +717,23 @@ static std::mutex g_reopt_launch_mu;
 
 int reopt_launch(cudaStream_t s, const ReoptArgs& a) {
     if (a.m <= 0) return 0;
+    if (a.kind == kLSQ) {
+        const size_t per = lsq_warp_bytes(a.k);
+        const int wpc = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per));
+        {
+            static std::mutex mu;
+            static bool opted = false;
+            std::lock_guard<std::mutex> lock(mu);
+            if (!opted) {
+                if (cudaFuncSetAttribute(k_reopt_lsq_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         96 << 10) != cudaSuccess)
+                    return -1;
+                opted = true;
+            }
+        }
+        k_reopt_lsq_warp<<<(a.m + wpc - 1) / wpc, 32 * wpc, wpc * per, s>>>(a);
+        return 0;
+    }
     const bool f32 = a.kind == kLOGISTIC && a.Xt32 != nullptr && a.y32 != nullptr;
     const size_t smem = f32 ? dyn_bytes<float>(a.k, true) : dyn_bytes<double>(a.k, a.kind == kLOGISTIC);
     // the opt-in covers static + dynamic shared memory above the 48 KB default
