@@ -168,6 +168,30 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
                        double time_limit_s, double* opt, int32_t* opt_support,
                        double* opt_beta, double* gap, int64_t* nodes, int64_t* batches);
 
+/* Stop kglm_solve after max_batches node batches (0: no limit), counted per
+ * call; the open queue it leaves can be checkpointed.  (A deployment aid for
+ * long searches; the paper's loop runs to completion or a time limit.) */
+kglm_status kglm_set_solve_limit(kglm_ctx* ctx, int64_t max_batches);
+
+/* Checkpoint of an unfinished certified solve (Fig. 1's loop stopped by its
+ * time limit, its batch limit or cancellation): writes to `path` the open node
+ * queue (each node's J0, J1, parent bound and warm start beta) and the
+ * incumbent (objective, support, coefficients) with the node and batch counts,
+ * and a signature of the instance (n, p, k, loss, lambda2, M and the sum of X
+ * and y).  KGLM_ESTATE if the last kglm_solve on ctx completed (nothing is
+ * left open); KGLM_EINVAL if the file cannot be written. */
+kglm_status kglm_solve_checkpoint(kglm_ctx* ctx, const char* path);
+
+/* Continue a checkpointed solve on a context of the same instance (any
+ * precision or batch size): the search restarts from the stored open nodes,
+ * warm starts and incumbent, and the outputs are those of kglm_solve for the
+ * whole search (node and batch counts include the checkpointed part).
+ * KGLM_EINVAL if the file is unreadable, malformed or written for another
+ * instance. */
+kglm_status kglm_solve_resume(kglm_ctx* ctx, const char* path, int32_t batch, int32_t iters, int32_t check_every,
+                              double time_limit_s, double* opt, int32_t* opt_support, double* opt_beta,
+                              double* gap, int64_t* nodes, int64_t* batches);
+
 /* kglm_push_nodes with the CSR arrays (and warm_slot, if not NULL) already
  * in device memory: in_ptr/out_ptr hold m+1 offsets, nnz_in = in_ptr[m] and
  * nnz_out = out_ptr[m] are passed by value.  The arrays are read on the

@@ -2,6 +2,7 @@
 // push, the batched evaluation pipeline, pruning/branching, and the hybrid
 // CPU-GPU branch-and-bound loop of §4.1 (Fig. 1).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -20,6 +21,23 @@
 
 using namespace kglm;
 
+// An unfinished certified solve (the open node queue and the incumbent), kept
+// when kglm_solve stops before the queue is empty, for kglm_solve_checkpoint.
+struct SavedNode {
+    double lb;                    // the parent's bound
+    int64_t id;
+    std::vector<int> J0, J1;
+    std::vector<double> wb;       // warm start (p values; empty: start at 0)
+};
+struct SavedSolve {
+    bool valid = false;
+    std::vector<SavedNode> open;
+    double ub = INFINITY;
+    std::vector<int> sup;
+    std::vector<double> coef;
+    int64_t nodes = 0, batches = 0, next_id = 0;
+};
+
 struct kglm_ctx {
     kglm_desc d{};
     cudaStream_t st = nullptr;
@@ -28,6 +46,9 @@ struct kglm_ctx {
     int n = 0, p = 0, k = 0, W = 0, kind = 0, prec = 0;
     bool f64 = true;
     double lam2 = 0, M = 0, L = 0, eta = 0, c = 0, gap_tol = 1e-6;
+    double data_sum = 0;          // sum of X and y (instance signature of checkpoints)
+    int64_t solve_max_batches = 0;   // kglm_solve stops after this many node batches (0: no limit)
+    SavedSolve saved;
     size_t bytes = 0;
     std::vector<void*> allocs;
     // instance (device)
@@ -905,7 +926,8 @@ struct RashomonOpts {
 };
 
 void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
-                const std::atomic<int>* cancel, SolveOut& out, const RashomonOpts* rs = nullptr) {
+                const std::atomic<int>* cancel, SolveOut& out, const RashomonOpts* rs = nullptr,
+                const SavedSolve* resume = nullptr) {
     REQ(batch >= 1 && batch <= ctx->mcap, "batch must be in [1, max_batch]");
     REQ(iters >= 1, "iters must be >= 1");
     struct Open {
@@ -913,6 +935,7 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
         int64_t id;
         std::vector<int> J0, J1;
         int slot;
+        std::vector<double> wb;   // host warm start (resumed nodes), used when slot < 0
     };
     struct Cmp {
         bool operator()(const Open* a, const Open* b) const {
@@ -930,11 +953,25 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
         if (s >= 0 && --slot_ref[s] == 0) free_slots.push_back(s);
     };
     int64_t next_id = 0, n_nodes = 0, n_batches = 0;
-    open.push(new Open{-INFINITY, next_id++, {}, {}, -1});
     double ub = INFINITY;
     std::vector<int> best_sup(ctx->k, -1);
     std::vector<double> best_coef(ctx->k, 0.0);
     const int k = ctx->k;
+    if (resume) {
+        // continue a checkpointed search: its open nodes (with their warm starts), incumbent and counts
+        ub = resume->ub;
+        best_sup = resume->sup;
+        best_coef = resume->coef;
+        n_nodes = resume->nodes;
+        n_batches = resume->batches;
+        next_id = resume->next_id;
+        for (const SavedNode& sn : resume->open) open.push(new Open{sn.lb, sn.id, sn.J0, sn.J1, -1, sn.wb});
+    } else {
+        open.push(new Open{-INFINITY, next_id++, {}, {}, -1, {}});
+    }
+    const int64_t batch0 = n_batches;
+    ctx->saved = SavedSolve{};
+    std::vector<double> warm_host;
     std::vector<int> in_ptr, in_idx, out_ptr, out_idx, wslot;
     std::vector<double> lb(batch), ubc(batch), bre((size_t)batch * k);
     std::vector<int> sup((size_t)batch * k), bj(batch);
@@ -953,6 +990,7 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
     try {
         while (!open.empty()) {
             if (time_limit_s > 0 && elapsed() > time_limit_s) break;
+            if (ctx->solve_max_batches > 0 && n_batches - batch0 >= ctx->solve_max_batches) break;
             if (cancel && cancel->load(std::memory_order_relaxed)) {
                 out.cancelled = true;
                 break;
@@ -976,14 +1014,23 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
             in_idx.clear();
             out_idx.clear();
             wslot.resize(m);
+            bool host_warm = false;
             for (int b = 0; b < m; ++b) {
                 in_idx.insert(in_idx.end(), cur[b]->J1.begin(), cur[b]->J1.end());
                 out_idx.insert(out_idx.end(), cur[b]->J0.begin(), cur[b]->J0.end());
                 in_ptr.push_back((int)in_idx.size());
                 out_ptr.push_back((int)out_idx.size());
                 wslot[b] = cur[b]->slot;
+                host_warm |= cur[b]->slot < 0 && !cur[b]->wb.empty();
             }
-            push_impl(ctx, m, in_ptr.data(), in_idx.data(), out_ptr.data(), out_idx.data(), wslot.data(), nullptr);
+            if (host_warm) {                    // resumed nodes: warm starts from the checkpoint
+                warm_host.assign((size_t)m * ctx->p, 0.0);
+                for (int b = 0; b < m; ++b)
+                    if (cur[b]->slot < 0 && !cur[b]->wb.empty())
+                        std::copy(cur[b]->wb.begin(), cur[b]->wb.end(), warm_host.begin() + (size_t)b * ctx->p);
+            }
+            push_impl(ctx, m, in_ptr.data(), in_idx.data(), out_ptr.data(), out_idx.data(), wslot.data(),
+                      host_warm ? warm_host.data() : nullptr);
             if (rs) {
                 const double t = tau();
                 ctx->ub_inc = t + 2.0 * delta_of(ctx, t);   // stop iterating once the bound passes tau
@@ -1123,6 +1170,35 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
         q.filter(tau(), rs->cap);
     }
     out.complete = open.empty() && !out.cancelled;
+    if (!open.empty() && !rs) {
+        // stopped early: keep the open queue and the incumbent for kglm_solve_checkpoint
+        SavedSolve& sv = ctx->saved;
+        sv.valid = true;
+        sv.ub = ub;
+        sv.sup = best_sup;
+        sv.coef = best_coef;
+        sv.nodes = n_nodes;
+        sv.batches = n_batches;
+        sv.next_id = next_id;
+        std::vector<Open*> rest;
+        while (!open.empty()) { rest.push_back(open.top()); open.pop(); }
+        const size_t ws = ctx->f64 ? 8 : 4, pp = (size_t)ctx->p;
+        std::vector<unsigned char> row(pp * ws);
+        for (Open* o : rest) {
+            SavedNode sn{o->lb, o->id, o->J0, o->J1, o->wb};
+            if (o->slot >= 0) {
+                CK(cudaMemcpyAsync(row.data(), static_cast<const unsigned char*>(ctx->pool) + (size_t)o->slot * pp * ws,
+                                   pp * ws, cudaMemcpyDeviceToHost, ctx->st));
+                sync(ctx);
+                sn.wb.resize(pp);
+                for (size_t j = 0; j < pp; ++j)
+                    sn.wb[j] = ctx->f64 ? reinterpret_cast<const double*>(row.data())[j]
+                                        : (double)reinterpret_cast<const float*>(row.data())[j];
+            }
+            sv.open.push_back(std::move(sn));
+            open.push(o);
+        }
+    }
     double open_lb = INFINITY;
     while (!open.empty()) {
         open_lb = std::min(open_lb, open.top()->lb);
@@ -1417,8 +1493,11 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->lam2 = d.lambda2; c->M = d.M;
         c->gap_tol = d.gap_tol > 0 ? d.gap_tol : 1e-6;
         const size_t n = c->n, p = c->p;
-        for (size_t t = 0; t < n * p; ++t)
+        for (size_t t = 0; t < n * p; ++t) {
             if (!isfinite(X[t])) throw Fail{KGLM_ENUMERIC, "X has a non-finite entry"};
+            c->data_sum += X[t];
+        }
+        for (size_t i = 0; i < n; ++i) c->data_sum += y[i];
         for (size_t i = 0; i < n; ++i) {
             if (!isfinite(y[i])) throw Fail{KGLM_ENUMERIC, "y has a non-finite entry"};
             if (d.loss == KGLM_LOGISTIC) REQ(y[i] == 1.0 || y[i] == -1.0, "logistic labels must be -1 or +1");
@@ -1855,6 +1934,150 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
     });
 }
 
+
+// ---- checkpoint and resume of an unfinished certified solve
+// File: magic "KGLMCKP1", then int64 n, p; int32 k, loss; double lambda2, M, data_sum
+// (the instance signature); double ub; int32 sup[k]; double coef[k]; int64 nodes,
+// batches, next_id, count; then per open node: double lb; int64 id; int32 n0, n1,
+// has_warm; int32 J0[n0], J1[n1]; double warm[p] if has_warm.  Native byte order.
+namespace {
+constexpr char kCkpMagic[8] = {'K', 'G', 'L', 'M', 'C', 'K', 'P', '1'};
+
+struct File {
+    FILE* f = nullptr;
+    ~File() { if (f) fclose(f); }
+};
+void put_raw(FILE* f, const void* v, size_t size, size_t n) {
+    if (n && fwrite(v, size, n, f) != n) throw Fail{KGLM_EINVAL, "checkpoint: write failed"};
+}
+void get_raw(FILE* f, void* v, size_t size, size_t n) {
+    if (n && fread(v, size, n, f) != n) throw Fail{KGLM_EINVAL, "checkpoint: truncated or unreadable file"};
+}
+}  // namespace
+#define put(f, v, n) put_raw((f), (v), sizeof(*(v)), (n))
+#define get(f, v, n) get_raw((f), (v), sizeof(*(v)), (n))
+
+extern "C" kglm_status kglm_set_solve_limit(kglm_ctx* ctx, int64_t max_batches) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(max_batches >= 0, "max_batches must be >= 0");
+        ctx->solve_max_batches = max_batches;
+    });
+}
+
+extern "C" kglm_status kglm_solve_checkpoint(kglm_ctx* ctx, const char* path) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(path != nullptr, "path is required");
+        const SavedSolve& sv = ctx->saved;
+        if (!sv.valid) throw Fail{KGLM_ESTATE, "no unfinished solve to checkpoint (the last kglm_solve completed)"};
+        File fl;
+        fl.f = fopen(path, "wb");
+        if (!fl.f) throw Fail{KGLM_EINVAL, std::string("checkpoint: cannot open ") + path + " for writing"};
+        FILE* f = fl.f;
+        const int64_t np[2] = {ctx->n, ctx->p};
+        const int32_t kl[2] = {ctx->k, ctx->kind};
+        const double sig[3] = {ctx->lam2, ctx->M, ctx->data_sum};
+        put(f, kCkpMagic, 8);
+        put(f, np, 2);
+        put(f, kl, 2);
+        put(f, sig, 3);
+        put(f, &sv.ub, 1);
+        std::vector<int32_t> sup(sv.sup.begin(), sv.sup.end());
+        put(f, sup.data(), sup.size());
+        put(f, sv.coef.data(), sv.coef.size());
+        const int64_t cnt[4] = {sv.nodes, sv.batches, sv.next_id, (int64_t)sv.open.size()};
+        put(f, cnt, 4);
+        for (const SavedNode& sn : sv.open) {
+            const int32_t hdr[3] = {(int32_t)sn.J0.size(), (int32_t)sn.J1.size(), sn.wb.empty() ? 0 : 1};
+            put(f, &sn.lb, 1);
+            put(f, &sn.id, 1);
+            put(f, hdr, 3);
+            std::vector<int32_t> j0(sn.J0.begin(), sn.J0.end()), j1(sn.J1.begin(), sn.J1.end());
+            put(f, j0.data(), j0.size());
+            put(f, j1.data(), j1.size());
+            put(f, sn.wb.data(), sn.wb.size());
+        }
+        if (fflush(f) != 0) throw Fail{KGLM_EINVAL, "checkpoint: write failed"};
+    });
+}
+
+extern "C" kglm_status kglm_solve_resume(kglm_ctx* ctx, const char* path, int32_t batch, int32_t iters,
+                                         int32_t check_every, double time_limit_s, double* opt,
+                                         int32_t* opt_support, double* opt_beta, double* gap, int64_t* nodes,
+                                         int64_t* batches) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        REQ(path != nullptr, "path is required");
+        File fl;
+        fl.f = fopen(path, "rb");
+        if (!fl.f) throw Fail{KGLM_EINVAL, std::string("checkpoint: cannot open ") + path};
+        FILE* f = fl.f;
+        char magic[8];
+        int64_t np[2];
+        int32_t kl[2];
+        double sig[3];
+        get(f, magic, 8);
+        REQ(memcmp(magic, kCkpMagic, 8) == 0, "checkpoint: not a checkpoint file");
+        get(f, np, 2);
+        get(f, kl, 2);
+        get(f, sig, 3);
+        REQ(np[0] == ctx->n && np[1] == ctx->p && kl[0] == ctx->k && kl[1] == ctx->kind && sig[0] == ctx->lam2 &&
+                sig[1] == ctx->M && sig[2] == ctx->data_sum,
+            "checkpoint: written for another instance (n, p, k, loss, lambda2, M or data differ)");
+        SavedSolve sv;
+        sv.valid = true;
+        get(f, &sv.ub, 1);
+        std::vector<int32_t> sup(ctx->k);
+        get(f, sup.data(), sup.size());
+        sv.sup.assign(sup.begin(), sup.end());
+        sv.coef.resize(ctx->k);
+        get(f, sv.coef.data(), sv.coef.size());
+        int64_t cnt[4];
+        get(f, cnt, 4);
+        REQ(cnt[0] >= 0 && cnt[1] >= 0 && cnt[2] >= 0 && cnt[3] >= 0 && cnt[3] < (int64_t(1) << 40),
+            "checkpoint: bad counts");
+        sv.nodes = cnt[0];
+        sv.batches = cnt[1];
+        sv.next_id = cnt[2];
+        for (int64_t q = 0; q < cnt[3]; ++q) {
+            SavedNode sn;
+            int32_t hdr[3];
+            get(f, &sn.lb, 1);
+            get(f, &sn.id, 1);
+            get(f, hdr, 3);
+            REQ(hdr[0] >= 0 && hdr[0] <= ctx->p && hdr[1] >= 0 && hdr[1] <= ctx->k && hdr[2] >= 0 && hdr[2] <= 1,
+                "checkpoint: bad node record");
+            std::vector<int32_t> j0(hdr[0]), j1(hdr[1]);
+            get(f, j0.data(), j0.size());
+            get(f, j1.data(), j1.size());
+            std::vector<char> seen(ctx->p, 0);
+            for (int32_t j : j0) { REQ(j >= 0 && j < ctx->p && !seen[j], "checkpoint: bad fixing index"); seen[j] = 1; }
+            for (int32_t j : j1) { REQ(j >= 0 && j < ctx->p && !seen[j], "checkpoint: bad fixing index"); seen[j] = 1; }
+            sn.J0.assign(j0.begin(), j0.end());
+            sn.J1.assign(j1.begin(), j1.end());
+            if (hdr[2]) {
+                sn.wb.resize(ctx->p);
+                get(f, sn.wb.data(), sn.wb.size());
+            }
+            sv.open.push_back(std::move(sn));
+        }
+        if (batch == 0) {
+            if (ctx->tuned_batch == 0) autotune_impl(ctx, std::min(iters, 20), 1, nullptr);
+            batch = ctx->tuned_batch;
+        }
+        SolveOut o;
+        solve_impl(ctx, batch, iters, check_every, time_limit_s, nullptr, o, nullptr, &sv);
+        if (opt) *opt = o.opt;
+        if (gap) *gap = o.gap;
+        if (nodes) *nodes = o.nodes;
+        if (batches) *batches = o.batches;
+        if (opt_support) std::copy(o.support.begin(), o.support.end(), opt_support);
+        if (opt_beta) std::copy(o.beta.begin(), o.beta.end(), opt_beta);
+    });
+}
+#undef put
+#undef get
 
 // Checks of kglm_create that need no data (sizes, ranges, enums).
 static kglm_status check_desc(const kglm_desc* d) {

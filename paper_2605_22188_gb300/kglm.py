@@ -68,6 +68,10 @@ _SIGS = {
     "kglm_autotune": (C.c_int, [P, C.c_int32, C.c_uint64, C.c_void_p]),
     "kglm_configure": (C.c_int, [P, C.c_void_p]),
     "kglm_selftest_timeout": (C.c_int, [P, C.c_int32]),
+    "kglm_set_solve_limit": (C.c_int, [P, C.c_int64]),
+    "kglm_solve_checkpoint": (C.c_int, [P, C.c_char_p]),
+    "kglm_solve_resume": (C.c_int, [P, C.c_char_p, C.c_int32, C.c_int32, C.c_int32, C.c_double, D, I32, D, D, I64,
+                                    I64]),
     "kglm_pool_create": (C.c_int, [C.c_int32, C.POINTER(P)]),
     "kglm_pool_insert": (C.c_int, [P, C.c_int32, I32, D, C.c_double, I64]),
     "kglm_pool_size": (C.c_int, [P, I64, I64, I64]),
@@ -318,6 +322,27 @@ def kglm_solve(ctx, k, p, batch, iters, check_every=10, time_limit=0.0):
                 nodes=nodes.value, batches=batches.value)
 
 
+def kglm_set_solve_limit(ctx, max_batches):
+    _check(lib().kglm_set_solve_limit(ctx, int(max_batches)), ctx)
+
+
+def kglm_solve_checkpoint(ctx, path):
+    _check(lib().kglm_solve_checkpoint(ctx, os.fsencode(path)), ctx)
+
+
+def kglm_solve_resume(ctx, path, k, p, batch, iters, check_every=10, time_limit=0.0):
+    opt, gap = C.c_double(), C.c_double()
+    nodes, batches = C.c_int64(), C.c_int64()
+    sup = np.empty(k, dtype=np.int32)
+    beta = np.empty(p)
+    st = lib().kglm_solve_resume(ctx, os.fsencode(path), int(batch), int(iters), int(check_every), float(time_limit),
+                                 C.byref(opt), _ptr(sup, I32), _ptr(beta, D), C.byref(gap), C.byref(nodes),
+                                 C.byref(batches))
+    _check(st, ctx)
+    return dict(opt=opt.value, support=[int(s) for s in sup if s >= 0], beta=beta, gap=gap.value,
+                nodes=nodes.value, batches=batches.value)
+
+
 def kglm_autotune(ctx, iters=20, seed=1):
     """Tile shapes and batch size picked by timing (see kglm.h); returns the choice."""
     t = kglm_tune()
@@ -405,6 +430,15 @@ class Engine:
 
     def solve(self, batch, iters, check_every=10, time_limit=0.0):
         return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit)
+
+    def set_solve_limit(self, max_batches):
+        kglm_set_solve_limit(self.ctx, max_batches)
+
+    def checkpoint(self, path):
+        kglm_solve_checkpoint(self.ctx, path)
+
+    def resume(self, path, batch, iters, check_every=10, time_limit=0.0):
+        return kglm_solve_resume(self.ctx, path, self.k, self.p, batch, iters, check_every, time_limit)
 
     def close(self):
         if self.ctx:
