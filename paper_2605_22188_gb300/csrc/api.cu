@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "engine.h"
 #include "kglm.h"
@@ -251,11 +253,24 @@ cudaEvent_t take_event(kglm_ctx* c) {
 
 // Brackets the launches of one phase with events on the context's stream
 // (only while timing is enabled) and adds the phase's algorithmic work.
+// NVTX range on the host thread (header-only NVTX v3: a no-op unless a tool such as
+// Nsight Systems or ncu --nvtx is attached), so that a profile shows the phases
+// of a node batch and the calls of the C ABI.
+struct Nvtx {
+    explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+};
+
 struct Scope {
     kglm_ctx* c;
     int ph;
     cudaEvent_t a = nullptr;
+    bool ranged = false;
     Scope(kglm_ctx* c_, int ph_, int launches, double work) : c(c_), ph(ph_) {
+        if (!c->capturing) {
+            nvtxRangePushA(kPhaseNames[ph]);
+            ranged = true;
+        }
         if (c->capturing) {                        // counted per graph launch instead
             c->cap->launches[ph] += launches;
             c->cap->work[ph] += work;
@@ -272,6 +287,7 @@ struct Scope {
         }
     }
     ~Scope() {
+        if (ranged) nvtxRangePop();
         if (!a) return;
         cudaEvent_t b = nullptr;
         if (c->capturing) {
@@ -361,6 +377,7 @@ void xtzeta(kglm_ctx* c, int m, CertArgs& a) {
 }
 
 void certify(kglm_ctx* c) {
+    Nvtx range("certificate");
     const int m = c->m, n = c->n, p = c->p;
     CertArgs a{};
     a.m = m; a.n = n; a.p = p; a.W = c->W; a.k = c->k; a.kind = c->kind;
@@ -612,6 +629,7 @@ void run_iters(kglm_ctx* c, int count) {
 }
 
 void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
+    Nvtx range("kglm evaluate: iterations, certificate, rounding, re-optimization");
     const int m = c->m;
     const unsigned gb = (unsigned)((m + 255) / 256);
     {
@@ -996,6 +1014,7 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
                 break;
             }
             cur.clear();
+            Nvtx range("bnb batch");
             const double dl = delta_of(ctx, ub);
             while (!open.empty() && (int)cur.size() < batch) {
                 Open* o = open.top();
