@@ -319,7 +319,7 @@ class Arm:
             self.tune["batch"] = m
         elif isinstance(tune, dict):
             cfg = {k: tune[k] for k in ("link_tile_cols", "grad_tile_cols", "grad_split_cap", "sub_batches", "pdl",
-                                        "prox_threads") if k in tune}
+                                        "prox_threads", "pair") if k in tune}
             self.eng.configure(**cfg)
             self.tune = dict(tune, fixed=True)
         else:
@@ -418,8 +418,10 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     tune = "auto"
     if args.tiles:
-        l1, g2, cap, ns = (int(v) for v in args.tiles.split(","))
-        tune = {"link_tile_cols": l1, "grad_tile_cols": g2, "grad_split_cap": cap, "sub_batches": ns}
+        v = [int(x) for x in args.tiles.split(",")]
+        tune = {"link_tile_cols": v[0], "grad_tile_cols": v[1], "grad_split_cap": v[2], "sub_batches": v[3]}
+        if len(v) > 4:
+            tune["pair"] = v[4]
     elif args.no_autotune:
         tune = None
     arm = Arm(args.workload, args.prec, m, T, stream, kind=loss_kind(args), tune=tune, seed=1000 + rank)
@@ -786,7 +788,8 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="only the headline line (no logistic/precision/solve/c2/serving/sweep keys)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tiles (profiling runs)")
-    ap.add_argument("--tiles", default="", help="fixed tiles instead of tuning: link,grad,split_cap,sub_batches")
+    ap.add_argument("--tiles", default="",
+                    help="fixed tiles instead of tuning: link,grad,split_cap,sub_batches[,pair (1 on, -1 off)]")
     ap.add_argument("--rate", type=float, default=2.0, help="serving mix: Poisson arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving mix: requests solved at once")
     ap.add_argument("--request-limit", type=float, default=20.0, help="serving mix: seconds per request")

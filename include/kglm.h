@@ -280,7 +280,8 @@ const char* kglm_phase_name(int32_t phase);
  * the iteration kernels (each kernel's prologue overlapping the previous
  * kernel) is timed on and off at the chosen tiles, then 1, 2 or 4 sub-batches
  * (node ranges iterated side by side on forked streams, tensor-core modes),
- * and for p > 512 in the FP32-type modes the prox's threads per node.  The context keeps the
+ * in the BF16 mode CTA pairs for the products on and off, and for p > 512 in
+ * the FP32-type modes the prox's threads per node.  The context keeps the
  * fastest configuration; the batch chosen is the smallest within 5% of the best node rate
  * (kglm_solve with batch 0 uses it, tuning first with min(iters, 20) if
  * needed).  Discards the pushed batch (push again before kglm_evaluate). */
@@ -294,6 +295,8 @@ typedef struct {
     int32_t sub_batches;      /* iteration loop split into this many node ranges on parallel streams */
     int32_t prox_threads;     /* threads per node of the prox for p > 512 in the FP32-type modes (0: default;
                                  32: one warp per node, p <= 2048) */
+    int32_t pair;             /* BF16: the iteration products as CTA pairs (clusters of two) sharing each
+                                 B tile by TMA multicast: 1 on, -1 off (kglm_configure: 0 keeps) */
     double nodes_per_s;       /* node evaluations per second at the chosen batch */
     double best_nodes_per_s;  /* the best rate over all batch sizes */
 } kglm_tune;

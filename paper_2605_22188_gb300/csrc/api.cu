@@ -103,6 +103,7 @@ struct kglm_ctx {
     int bn1 = 0, bn2 = 0;
     int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
     bool pdl = false;             // programmatic dependent launch inside the iteration graph (tuned)
+    bool pair = false;            // BF16 iteration products as CTA pairs sharing B by multicast (tuned)
     // sub-batches of the iteration loop on forked streams (tensor-core modes, tuned)
     static constexpr int kMaxSub = 4;
     int nsub = 1;
@@ -462,6 +463,7 @@ void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
         g.ldo = c->nK; g.y = c->y32; g.loss = c->kind; g.err = c->d_tcerr;
         if (c->x3) { g.A2 = &c->mA1lo; g.out_lo = c->Rop_lo + (size_t)row0 * c->nK; }
         g.pdl = pdl;
+        g.pair = c->pair;
         if (tc_gemm(st, c->mA1, c->mB1, c->xlo ? &c->mB1lo : nullptr, g, sub ? nullptr : &c->gtc) != 0)
             throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
         check_launch();
@@ -477,6 +479,7 @@ void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
         g.max_splits = c->gsplit_max; g.splits_used = &splits;
         if (c->x3) g.A2 = &c->mA2lo;
         g.pdl = pdl;
+        g.pair = c->pair;
         if (tc_gemm(st, c->mA2, c->mB2, c->x3 ? &c->mB2lo : nullptr, g, &c->gtc) != 0)
             throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
         check_launch();
@@ -1368,6 +1371,18 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         }
         c->pdl = bp;
         destroy_graphs(c);
+        // BF16: the products as CTA pairs sharing each B tile, or one CTA per tile
+        if (c->tc_kind == 0 && !c->x3) {
+            bool bpair = c->pair;
+            const bool keep = c->pair;
+            c->pair = !keep;
+            destroy_graphs(c);
+            const double ms = time_eval(c, t, mc, iters, 3);
+            ++timed;
+            if (ms < best) { best = ms; bpair = c->pair; }
+            c->pair = bpair;
+            destroy_graphs(c);
+        }
         // sub-batches of the iteration loop side by side on forked streams
         int bsub = c->nsub;
         for (int ns : {1, 2, 4}) {
@@ -1385,6 +1400,7 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         r.grad_split_cap = bs;
     }
     r.pdl = c->pdl ? 1 : 0;
+    r.pair = c->pair ? 1 : -1;
     r.sub_batches = c->nsub;
     // threads per node of the prox (FP32 working type, p > 512)
     if (!c->f64) {
@@ -2155,6 +2171,11 @@ kglm_status kglm_configure(kglm_ctx* ctx, const kglm_tune* cfg) {
             ctx->tuned_batch = cfg->batch;
         }
         ctx->pdl = cfg->pdl != 0;
+        if (cfg->pair != 0) {
+            REQ(cfg->pair == 1 || cfg->pair == -1, "pair must be 1 (on), -1 (off) or 0 (keep)");
+            if (ctx->pair != (cfg->pair == 1)) destroy_graphs(ctx);
+            ctx->pair = cfg->pair == 1;
+        }
         if (cfg->prox_threads != 0) {
             int opts[4];
             const int no = prox_thread_options(ctx->p, opts);

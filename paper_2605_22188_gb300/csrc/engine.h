@@ -74,6 +74,8 @@ struct TcGemm {
     float* out_lo;   // TC_EPI_LINK_F32: TF32 low part of each output (NULL: none)
     int pdl;         // launch with programmatic stream serialization (prologue overlaps the previous kernel)
     int arow0;       // first row of A used (rows arow0 .. arow0 + M); outputs are indexed from row 0
+    int pair;        // 1: CTA pairs (clusters of two) sharing each B tile by multicast, where
+                     // supported (BF16, single operands, no split-K link); 0: one CTA per tile
 };
 // TMA map of a row-major rows x cols matrix (row stride ld elements) with
 // 128-byte boxes along cols and box_rows rows.  0 on success.

@@ -166,6 +166,31 @@ __device__ __forceinline__ Unit unit_of(const TcArgs& a, int u) {
     return w;
 }
 
+// The unit of a CTA pair (CL = 2): pair units run over (row-tile pair, column
+// tile, K range); the CTA of cluster rank r takes row tile 2 mp + r, so both CTAs
+// of a pair share the column tile and K range (the B tile).  A row tile past the
+// last one (odd row-tile count) reads rows past M and stores nothing.
+__device__ __forceinline__ Unit unit_of_pair(const TcArgs& a, int u, int crank) {
+    Unit w;
+    const int mtp = (a.mt + 1) >> 1;
+    const int tiles = mtp * a.nt;
+    w.z = u / tiles;
+    const int t = u - w.z * tiles;
+    int mp;
+    if (a.m_fast) { mp = t % mtp; w.ntile = t / mtp; }
+    else          { w.ntile = t % a.nt; mp = t / a.nt; }
+    w.mtile = 2 * mp + crank;
+    if (a.njobs > 0) {
+        const TcJob& jb = a.jobs[w.z];
+        w.ka = jb.ka; w.kb = jb.kb; w.nloc = jb.nkb; w.slice = jb.slice;
+    } else {
+        w.ka = w.kb = w.z * a.kb_per_split;
+        w.nloc = max(0, min(a.nkb, w.ka + a.kb_per_split) - w.ka);
+        w.slice = w.z;
+    }
+    return w;
+}
+
 // ------------------------------------------------------------------ PTX wrappers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -208,6 +233,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// The same tile into this CTA and its cluster peer (mask 0b11): the bytes land at
+// dst in both CTAs' shared memory and complete on the mbarrier at the same offset
+// in each.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of both CTAs of the cluster.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -245,6 +294,13 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Arrive on the mbarrier at this offset in every CTA of `mask` once the issued products finish.
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(mask)
+                 : "memory");
 }
 
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
@@ -287,7 +343,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int KIND, int NB, int NA>
+template <int KIND, int NB, int NA, int CL>
 __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB,
                                                    const __grid_constant__ CUtensorMap tmB2,
@@ -313,7 +369,12 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = KIND == 0 ? 64 : 32;          // elements per 128-byte row
     const uint32_t stage_bytes = (uint32_t)NA * STAGE_A + (uint32_t)NB * a.bn * ROWB;
-    const int units = a.mt * a.nt * a.nz;
+    // CL = 2: CTA pairs (clusters of two) walk pair units, sharing the B tile (one
+    // multicast copy); every MMA completion frees the stage in both CTAs
+    const int crank = CL == 2 ? (int)cluster_ctarank() : 0;
+    const int units = (CL == 2 ? (a.mt + 1) / 2 : a.mt) * a.nt * a.nz;
+    const int ucta = blockIdx.x / CL, ustride = gridDim.x / CL;
+    auto unit = [&](int u) { return CL == 2 ? unit_of_pair(a, u, crank) : unit_of(a, u); };
 
     pdl_trigger();
     if (threadIdx.x == 32) {
@@ -324,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
         if (NA == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
     }
     if (threadIdx.x == 0) {
-        for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), 1); }
+        for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), CL); }
         for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 32 * EPI_WARPS); }
         mbar_init(smem_u32(drain), 1);
         s_consumed = 0;
@@ -334,6 +395,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     tc_fence_before();
     __syncwarp();                    // whole warps at the CTA barrier (lane 0 of warp 0 ran the setup)
     __syncthreads();
+    if constexpr (CL == 2) cluster_sync();   // both CTAs' barriers initialised before any remote arrival
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     pdl_wait();                      // operands and outputs belong to the previous grid until it completes
@@ -344,8 +406,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             // producer
             int g = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-                const Unit w = unit_of(a, u);
+            for (int u = ucta; u < units && ok; u += ustride) {
+                const Unit w = unit(u);
                 const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
                 for (int i = 0; i < w.nloc; ++i, ++g) {
                     const int s = g % STAGES;
@@ -357,8 +419,15 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     uint8_t* sp = smem + (size_t)s * SSTR;
                     tma_load_2d(smem_u32(sp), &tmA, kxa, a.arow0 + m0, fb);
                     if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), &tmA2, kxa, a.arow0 + m0, fb);
-                    tma_load_2d(smem_u32(sp + offB), &tmB, kxb, n0, fb);
-                    if (NB == 2) tma_load_2d(smem_u32(sp + offB2), &tmB2, kxb, n0, fb);
+                    if constexpr (CL == 2) {
+                        if (crank == 0) {                   // B once, into both CTAs
+                            tma_load_2d_mc(smem_u32(sp + offB), &tmB, kxb, n0, fb, (uint16_t)3);
+                            if (NB == 2) tma_load_2d_mc(smem_u32(sp + offB2), &tmB2, kxb, n0, fb, (uint16_t)3);
+                        }
+                    } else {
+                        tma_load_2d(smem_u32(sp + offB), &tmB, kxb, n0, fb);
+                        if (NB == 2) tma_load_2d(smem_u32(sp + offB2), &tmB2, kxb, n0, fb);
+                    }
                     issued = g + 1;
                 }
             }
@@ -368,8 +437,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             // MMA issuer
             int g = 0, li = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++li) {
-                const Unit w = unit_of(a, u);
+            for (int u = ucta; u < units && ok; u += ustride, ++li) {
+                const Unit w = unit(u);
                 const int b = li & 1;
                 const uint32_t use = (uint32_t)(li >> 1) & 1u;
                 if (!mbar_wait(smem_u32(&tempty[b]), use ^ 1u, a.err)) break;
@@ -390,7 +459,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                         if (NA == 2)
                             umma<KIND>(acc, smem_desc(aa + STAGE_A + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
                     }
-                    umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
+                    if constexpr (CL == 2) umma_commit_mc(smem_u32(&empty[s]), (uint16_t)3);   // in both CTAs
+                    else umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
                     s_consumed = g + 1;
                 }
                 umma_commit(smem_u32(&tfull[b]));       // the accumulator is complete (or abandoned)
@@ -408,8 +478,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
         const int h = (warp - 2) >> 2;
         float* tb = sT + (warp - 2) * 32 * TPAD;
         int li = 0;
-        for (int u = blockIdx.x; u < units; u += gridDim.x, ++li) {
-            const Unit w = unit_of(a, u);
+        for (int u = ucta; u < units; u += ustride, ++li) {
+            const Unit w = unit(u);
             const int b = li & 1;
             const uint32_t use = (uint32_t)(li >> 1) & 1u;
             // the link's y of this warp's columns (lane l < 16 holds column c + l of
@@ -586,6 +656,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
+    // neither CTA of a pair leaves while the other may still copy into or signal it
+    if constexpr (CL == 2) {
+        __syncwarp();
+        cluster_sync();
+    }
 }
 
 // A wait that nothing ends: one thread waits on an mbarrier no thread arrives
@@ -620,12 +695,37 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int KIND, int NB, int NA>
+template <int KIND, int NB, int NA, int CL = 1>
 int set_smem_attr() {
     // once per process (thread-safe static initialisation: serving contexts launch from several threads)
-    static const int rc = cudaFuncSetAttribute(k_tc_gemm<KIND, NB, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static const int rc = cudaFuncSetAttribute(k_tc_gemm<KIND, NB, NA, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)kSmemMax) == cudaSuccess ? 0 : -1;
     return rc;
+}
+
+// Clusters of two of k_tc_gemm<0, 1, 1, 2> that can be resident at once (once per process).
+int pair_clusters() {
+    static const int n = [] {
+        if (set_smem_attr<0, 1, 1, 2>() != 0) return 0;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2 * SMS);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = kSmemMax;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, k_tc_gemm<0, 1, 1, 2>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            c = 0;
+        }
+        return c;
+    }();
+    return n;
 }
 
 }  // namespace
@@ -634,7 +734,7 @@ void wait_probe(cudaStream_t s, uint32_t rounds, int* err) { k_wait_probe<<<1, 3
 
 int tc_prepare() {
     return set_smem_attr<0, 1, 1>() | set_smem_attr<0, 2, 1>() | set_smem_attr<1, 1, 1>() | set_smem_attr<1, 2, 1>() |
-           set_smem_attr<1, 2, 2>();
+           set_smem_attr<1, 2, 2>() | set_smem_attr<0, 1, 1, 2>() | (pair_clusters() > 0 ? 0 : 0);
 }
 
 int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, int ld, int box_rows) {
@@ -716,22 +816,39 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const CUtensorMap& mb2 = *reinterpret_cast<const CUtensorMap*>((B2 ? B2 : &B)->bytes);
     const CUtensorMap& ma2 = *reinterpret_cast<const CUtensorMap*>((g.A2 ? g.A2 : &A)->bytes);
+    // CTA pairs: BF16 single operands, at least two row tiles, no split-K link epilogue
+    // (its partial tiles and arrival counters are indexed per tile)
+    const bool pair = g.pair && g.kind == 0 && nb == 1 && na == 1 && a.mt >= 2 &&
+                      (splits == 1 || g.epi == TC_EPI_PARTIAL) && a.njobs == 0 && pair_clusters() > 0;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid_of(tiles * splits));
+    cfg.gridDim = dim3(pair ? 2 * std::max(1, std::min(((a.mt + 1) / 2) * a.nt * splits, pair_clusters()))
+                            : grid_of(tiles * splits));
     cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[2];
+    int na_ = 0;
+    if (g.pdl) {
+        attr[na_].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na_].val.programmaticStreamSerializationAllowed = 1;
+        ++na_;
+    }
+    if (pair) {
+        attr[na_].id = cudaLaunchAttributeClusterDimension;
+        attr[na_].val.clusterDim.x = 2;
+        attr[na_].val.clusterDim.y = 1;
+        attr[na_].val.clusterDim.z = 1;
+        ++na_;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = g.pdl ? 1 : 0;
+    cfg.numAttrs = na_;
     cudaError_t e;
-    if (na == 2) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 2>, ma, mb, mb2, ma2, a);
-    else if (g.kind == 0) e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1>, ma, mb, mb2, ma, a)
-                                      : cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 2, 1>, ma, mb, mb2, ma, a);
-    else e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 1, 1>, ma, mb, mb2, ma, a)
-                     : cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 1>, ma, mb, mb2, ma, a);
+    if (pair) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1, 2>, ma, mb, mb2, ma, a);
+    else if (na == 2) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 2, 1>, ma, mb, mb2, ma2, a);
+    else if (g.kind == 0) e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1, 1>, ma, mb, mb2, ma, a)
+                                      : cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 2, 1, 1>, ma, mb, mb2, ma, a);
+    else e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 1, 1, 1>, ma, mb, mb2, ma, a)
+                     : cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 1, 1>, ma, mb, mb2, ma, a);
     return e == cudaSuccess ? 0 : -7;
 }
 
@@ -756,7 +873,7 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
     const dim3 grid(grid_of(a.mt * a.nt * njobs));
-    k_tc_gemm<0, 1, 1><<<grid, NT, smem_for(1, 1, bn), s>>>(ma, mb, mb, ma, a);
+    k_tc_gemm<0, 1, 1, 1><<<grid, NT, smem_for(1, 1, bn), s>>>(ma, mb, mb, ma, a);
     return 0;
 }
 

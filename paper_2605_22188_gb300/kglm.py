@@ -115,7 +115,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 class kglm_tune(C.Structure):
     _fields_ = [("batch", C.c_int32), ("link_tile_cols", C.c_int32), ("grad_tile_cols", C.c_int32),
                 ("grad_split_cap", C.c_int32), ("timed", C.c_int32), ("pdl", C.c_int32),
-                ("sub_batches", C.c_int32), ("prox_threads", C.c_int32),
+                ("sub_batches", C.c_int32), ("prox_threads", C.c_int32), ("pair", C.c_int32),
                 ("nodes_per_s", C.c_double), ("best_nodes_per_s", C.c_double)]
 XTR_NOALLOC_MAX_TILES = 256
 NPHASE = 11
@@ -351,10 +351,11 @@ def kglm_autotune(ctx, iters=20, seed=1):
 
 
 def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_cap=0, pdl=0, sub_batches=0,
-                   prox_threads=0):
-    """Set tile shapes, split cap, batch, launch mode, sub-batches and prox threads by hand."""
+                   prox_threads=0, pair=0):
+    """Set tile shapes, split cap, batch, launch mode, sub-batches, prox threads and CTA pairs by hand."""
     t = kglm_tune(batch=batch, link_tile_cols=link_tile_cols, grad_tile_cols=grad_tile_cols,
-                  grad_split_cap=grad_split_cap, pdl=pdl, sub_batches=sub_batches, prox_threads=prox_threads)
+                  grad_split_cap=grad_split_cap, pdl=pdl, sub_batches=sub_batches, prox_threads=prox_threads,
+                  pair=pair)
     _check(lib().kglm_configure(ctx, C.byref(t)), ctx)
 
 
