@@ -13,6 +13,8 @@
 // argmax_{Jf} |beta_j| of §4.3 (ties to the smaller index).
 #include <float.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "engine.h"
 #include "exact.cuh"
@@ -263,6 +265,347 @@ __global__ __launch_bounds__(NT) void k_cert_bound(const __grid_constant__ CertA
     for (int i = threadIdx.x; i < a.k; i += NT) a.support[(size_t)b * a.k + i] = i < ns ? sh.sups[i] : -1;
 }
 
+// ---- the same bound, primal, support and branching index with a warp per node,
+// for FP32 beta with X^T zeta as exact-splitting partials (BF16/TF32 modes).
+// The CTA kernel above spends its time in FP64 arithmetic on every coordinate
+// (the slice combine, H_M, the sums) and in the barriers of two block-wide
+// radix selections.  Here FP64 work is confined to the few coordinates whose
+// values are summed:
+// * one pass over the free coordinates combines the slices in FP32 with a
+//   rigorous error bound and keeps in shared memory an upper bound u_j, and in
+//   registers the lane's two largest lower bounds l_j, of the value
+//   v_j = (|q~_j| + err_j) / (2 lambda2) that the FP64 combine gives
+//   (l_j <= v_j <= u_j); the beta sums of Theorem 4.1 run in compensated FP32;
+// * TopSum: the kbar-th largest of the 64 lane samples, t, is at most the
+//   kbar-th largest l, hence at most the kbar-th largest v, so every coordinate
+//   of the top kbar has u_j >= t; those (normally a few more than kbar) get
+//   their exact FP64 v_j (the combine of the CTA kernel) and are ranked; when
+//   more than kCertCap qualify (near-ties), they are streamed through an exact
+//   top-kbar list instead;
+// * top-kbar |beta| over Jf (ties to the smaller index): lane samples of the
+//   beta keys, a gather of the candidates and their ranks; zeros tie-break by
+//   index directly (the smallest free indices with beta = 0).
+constexpr int kCertCap = 128;
+constexpr int kCertMaxWarps = 16;
+
+struct CertWarp {
+    int cand[kCertCap];
+    union {
+        double cval[kCertCap];                 // exact v of the TopSum candidates
+        unsigned long long bkey[kCertCap];     // (|beta| key, ~j) of the beta candidates
+    };
+    double tv[kMaxK];
+    float sv[kMaxK];
+    int si[kMaxK];
+    int sup[2 * kMaxK];
+    int ncand, nsup;
+};
+
+__host__ __device__ inline size_t cert_row(int p) { return ((size_t)p + 3) / 4 * 4; }
+__host__ __device__ inline size_t cert_hdr() { return (sizeof(CertWarp) + 15) / 16 * 16; }
+__host__ __device__ inline size_t cert_warp_bytes(int p) { return cert_hdr() + cert_row(p) * sizeof(uint32_t); }
+__host__ __device__ inline size_t cert_cta_bytes(int p, int wpc) {
+    return (kTcMaxJobs + cert_row(p)) * sizeof(float) + wpc * cert_warp_bytes(p);
+}
+
+// compensated FP32 accumulation (Knuth's two-sum; the product error by an FMA)
+__device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
+    const float s = hi + x, bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+__device__ __forceinline__ void acc2_sq(float& hi, float& lo, float x) {
+    const float pr = x * x;
+    acc2(hi, lo, pr);
+    lo += fmaf(x, x, -pr);
+}
+
+__device__ __forceinline__ double cert_exact_v(const CertArgs& a, size_t base, int j, int b, double inv2l) {
+    double err;
+    const double qv = exact_q(a.Qs, a.nqs, a.qs_stride, a.qs_w, base + j, a.xsig[j] * a.ztau[b], a.ebound, &err);
+    return (fabs(qv) + err) * inv2l;
+}
+
+__global__ __launch_bounds__(32 * kCertMaxWarps) void k_cert_bound_warp(const __grid_constant__ CertArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int p = a.p, nq = a.nqs;
+    float* wf = reinterpret_cast<float*>(smem);                 // slice weights (powers of two) in FP32
+    float* xs = wf + kTcMaxJobs;                                // sigma_j in FP32 (shared by the CTA)
+    unsigned char* wb = smem + (kTcMaxJobs + cert_row(p)) * sizeof(float) + (size_t)warp * cert_warp_bytes(p);
+    CertWarp& h = *reinterpret_cast<CertWarp*>(wb);
+    uint32_t* su = reinterpret_cast<uint32_t*>(wb + cert_hdr());
+    for (int j = threadIdx.x; j < p; j += blockDim.x) xs[j] = (float)a.xsig[j];
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) wf[t] = (float)a.qs_w[t];
+    __syncthreads();
+    const double M = a.M, inv2l = 1.0 / (2.0 * a.lam2);
+    const double mth = M * (1.0 + kFeasRtol);
+    const float mth_f = __double2float_rd(mth);                // |b| > mth  <=>  |b| > mth_f for FP32 b
+    const float ebf = (float)a.ebound;
+    const float gam = (float)(nq + 2) * 0x1p-23f;               // |acc_f - acc| <= gam * sum |w P|, with margin
+    const float rlo = 1.0f - 0x1p-19f, rhi = 1.0f + 0x1p-19f;   // covers the FP32 roundings below
+    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) {
+        const size_t base = (size_t)b * p;
+        const uint32_t* im = a.in_mask + (size_t)b * a.W;
+        const uint32_t* om = a.out_mask + (size_t)b * a.W;
+        const int kb = a.kbar[b], pf = a.pf[b];
+        const float* B = static_cast<const float*>(a.B) + base;
+        const float zf = (float)(a.ztau[b] * inv2l);
+        if (lane == 0) { h.ncand = 0; h.nsup = 0; }
+        // ---- pass over the coordinates: u_j to shared memory, lane samples, free beta sums
+        float s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f;       // free sum |beta|, sum beta^2
+        int nnz = 0, infeas = 0;
+        uint32_t l1 = 0, l2 = 0, b1 = 0, b2 = 0;                 // two largest l keys, beta keys
+        for (int j = lane; j < p; j += 32) {
+            const uint32_t w = j >> 5, bit = 1u << (j & 31);
+            const bool in = (im[w] & bit) != 0, out = !in && (om[w] & bit) != 0;
+            uint32_t ukey = 0;
+            if (!in && !out) {
+                const float* qp = a.Qs + base + j;
+                float accf = 0.f, absf = 0.f;
+                for (int t0 = 0; t0 < nq; t0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) v[t] = (t0 + t < nq) ? __ldg(qp + (size_t)(t0 + t) * a.qs_stride) : 0.f;
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        if (t0 + t < nq) {
+                            const float wt = wf[t0 + t];
+                            accf = fmaf(wt, v[t], accf);
+                            absf = fmaf(wt, fabsf(v[t]), absf);
+                        }
+                    }
+                }
+                const float cf = xs[j] * zf, d = gam * absf, aa = fabsf(accf);
+                float vl = cf * ((aa - d) + ebf) * rlo - 4.0f * FLT_MIN;
+                float vu = cf * ((aa + d) + ebf) * rhi + 4.0f * FLT_MIN;
+                vl = fminf(fmaxf(vl, 0.f), 0.5f * FLT_MAX);          // an overflowed l: v is larger still
+                if (!(vu >= 0.f) || !(cf >= FLT_MIN)) {              // NaN, or sigma tau / 2 lambda2 below
+                    vu = INFINITY;                                   // the normal range: no bound, always
+                    vl = 0.f;                                        // a candidate
+                }
+                ukey = __float_as_uint(vu) + 1u;
+                const uint32_t lkey = __float_as_uint(vl) + 1u;
+                if (lkey > l1) { l2 = l1; l1 = lkey; } else if (lkey > l2) { l2 = lkey; }
+                const float bv = B[j], ab = fabsf(bv);
+                acc2(s1h, s1l, ab);
+                acc2_sq(s2h, s2l, ab);
+                nnz += ab > 0.f;
+                infeas += ab > mth_f;
+                const uint32_t bk = __float_as_uint(ab) + 1u;
+                if (bk > b1) { b2 = b1; b1 = bk; } else if (bk > b2) { b2 = bk; }
+            } else if (out) {
+                infeas += B[j] != 0.f;
+            }
+            su[j] = ukey;
+        }
+        const double total = warp_sum((double)s1h + (double)s1l);
+        const double sumsq = warp_sum((double)s2h + (double)s2l);
+        nnz = warp_sum(nnz);
+        // ---- J1: exact v, beta^2 and feasibility (at most k coordinates)
+        for (int w = lane; w < a.W; w += 32) {
+            uint32_t bits = im[w];
+            while (bits) {
+                const int j = 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int c = atomicAdd(&h.nsup, 1);
+                if (c < kMaxK) h.sup[c] = j;                         // |J1| <= k <= kMaxK for validated nodes
+            }
+        }
+        __syncwarp();
+        const int n1 = min(h.nsup, kMaxK);
+        double hj1 = 0.0, bj1 = 0.0;
+        for (int i = lane; i < n1; i += 32) {
+            const int j = h.sup[i];
+            hj1 += huber64(cert_exact_v(a, base, j, b, inv2l), M);
+            const double bv = (double)B[j];
+            bj1 += bv * bv;
+            infeas += fabs(bv) > mth;
+        }
+        hj1 = warp_sum(hj1);
+        bj1 = warp_sum(bj1);
+        infeas = warp_sum(infeas);
+        const bool leaf = kb == 0 || pf <= kb;
+        // ---- TopSum_kbar {H_M(v_j)}_{j in Jf}
+        double part = 0.0;
+        if (!leaf) {
+            uint32_t k0 = l1, k1 = l2;
+            sort64(k0, k1, lane);
+            const int pos = 64 - kb;
+            const uint32_t ta = __shfl_sync(0xffffffffu, k0, pos >> 1), tb = __shfl_sync(0xffffffffu, k1, pos >> 1);
+            const uint32_t tau = max((pos & 1) ? tb : ta, 1u);
+            for (int j = lane; j < p; j += 32)
+                if (su[j] >= tau) {
+                    const int c = atomicAdd(&h.ncand, 1);
+                    if (c < kCertCap) h.cand[c] = j;
+                }
+            __syncwarp();
+            const int total_c = h.ncand;
+            if (total_c <= kCertCap) {
+                for (int i = lane; i < total_c; i += 32) h.cval[i] = cert_exact_v(a, base, h.cand[i], b, inv2l);
+                __syncwarp();
+                for (int i = lane; i < total_c; i += 32) {
+                    const double ci = h.cval[i];
+                    int r = 0;
+                    for (int t = 0; t < total_c; ++t) r += h.cval[t] > ci || (h.cval[t] == ci && t < i);
+                    if (r < kb) part += huber64(ci, M);
+                }
+            } else {
+                // near-ties: every qualifying coordinate through an exact top-kbar list (descending)
+                int nt = 0;
+                double vmin = -1.0;
+                for (int j0 = 0; j0 < p; j0 += 32) {
+                    const int j = j0 + lane;
+                    double v = -1.0;
+                    if (j < p && su[j] >= tau) v = cert_exact_v(a, base, j, b, inv2l);
+                    uint32_t bal = __ballot_sync(0xffffffffu, v > vmin);
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const double x = __shfl_sync(0xffffffffu, v, src);
+                        if (nt == kb && !(x > vmin)) continue;
+                        if (lane == 0) {
+                            int i = nt < kb ? nt : kb - 1;
+                            while (i > 0 && h.tv[i - 1] < x) { h.tv[i] = h.tv[i - 1]; --i; }
+                            h.tv[i] = x;
+                        }
+                        __syncwarp();
+                        nt = min(nt + 1, kb);
+                        vmin = nt == kb ? h.tv[kb - 1] : -1.0;
+                    }
+                }
+                for (int i = lane; i < nt; i += 32) part += huber64(h.tv[i], M);
+            }
+            __syncwarp();
+            if (lane == 0) h.ncand = 0;
+        } else if (kb > 0) {
+            // every free coordinate fits the budget (pf <= kbar <= kMaxK): all join the sum and the support
+            for (int j = lane; j < p; j += 32)
+                if (su[j] != 0u) {
+                    part += huber64(cert_exact_v(a, base, j, b, inv2l), M);
+                    const int c = atomicAdd(&h.nsup, 1);
+                    if (c < 2 * kMaxK) h.sup[c] = j;
+                }
+        }
+        const double topsum = warp_sum(part);
+        const double lb = -a.sum_conj[b] - 2.0 * a.lam2 * (hj1 + topsum);
+        __syncwarp();
+        // ---- top-kbar |beta| over Jf, ties to the smaller index
+        if (!leaf) {
+            uint32_t k0 = b1, k1 = b2;
+            sort64(k0, k1, lane);
+            const int pos = 64 - kb;
+            const uint32_t ta = __shfl_sync(0xffffffffu, k0, pos >> 1), tb = __shfl_sync(0xffffffffu, k1, pos >> 1);
+            const uint32_t tau = max((pos & 1) ? tb : ta, 2u);     // nonzero |beta| only; zeros below
+            for (int j = lane; j < p; j += 32) {
+                if (su[j] == 0u) continue;
+                const uint32_t key = __float_as_uint(fabsf(B[j])) + 1u;
+                if (key >= tau) {
+                    const int c = atomicAdd(&h.ncand, 1);
+                    if (c < kCertCap) h.bkey[c] = ((unsigned long long)key << 32) | (0xffffffffu - (uint32_t)j);
+                }
+            }
+            __syncwarp();
+            const int total_c = h.ncand;
+            int got = 0;
+            if (total_c <= kCertCap) {
+                for (int i = lane; i < total_c; i += 32) {
+                    const unsigned long long ci = h.bkey[i];
+                    int r = 0;
+                    for (int t = 0; t < total_c; ++t) r += h.bkey[t] > ci;
+                    if (r < kb) {
+                        h.sv[r] = __uint_as_float((uint32_t)(ci >> 32) - 1u);
+                        h.si[r] = (int)(0xffffffffu - (uint32_t)ci);
+                    }
+                }
+                got = min(total_c, kb);
+            } else {
+                unsigned long long last = ~0ull;                    // kb rounds of a warp argmax
+                for (int r = 0; r < kb; ++r) {
+                    unsigned long long best = 0ull;
+                    for (int j = lane; j < p; j += 32) {
+                        if (su[j] == 0u) continue;
+                        const uint32_t key = __float_as_uint(fabsf(B[j])) + 1u;
+                        const unsigned long long pk = ((unsigned long long)key << 32) | (0xffffffffu - (uint32_t)j);
+                        if (key >= 2u && pk < last && pk > best) best = pk;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, o);
+                        best = x > best ? x : best;
+                    }
+                    if (best == 0ull) break;
+                    last = best;
+                    if (lane == 0) {
+                        h.sv[r] = __uint_as_float((uint32_t)(best >> 32) - 1u);
+                        h.si[r] = (int)(0xffffffffu - (uint32_t)best);
+                    }
+                    ++got;
+                }
+            }
+            __syncwarp();
+            // fewer than kbar nonzero: the free zeros of smallest index fill the rest
+            for (int j0 = 0; j0 < p && got < kb; j0 += 32) {
+                const int j = j0 + lane;
+                const bool z = j < p && su[j] != 0u && B[j] == 0.f;
+                uint32_t bal = __ballot_sync(0xffffffffu, z);
+                const int before = __popc(bal & ((1u << lane) - 1u));
+                if (z && got + before < kb) {
+                    h.sv[got + before] = 0.f;
+                    h.si[got + before] = j;
+                }
+                got = min(kb, got + __popc(bal));
+            }
+            __syncwarp();
+            for (int i = lane; i < kb; i += 32) h.sup[n1 + i] = h.si[i];
+            __syncwarp();
+            if (lane == 0) h.nsup = n1 + kb;
+        }
+        __syncwarp();
+        // ---- support ascending (the warp); Theorem 4.1 and the outputs (lane 0)
+        const int ns = min(h.nsup, kMaxK);
+        int srt[2] = {-1, -1};
+        for (int i = lane, t = 0; i < ns && t < 2; i += 32, ++t) {
+            const int v = h.sup[i];
+            int r = 0;
+            for (int q = 0; q < ns; ++q) r += h.sup[q] < v;
+            srt[t] = r;
+        }
+        const int vals[2] = {lane < ns ? h.sup[lane] : -1, lane + 32 < ns ? h.sup[lane + 32] : -1};
+        __syncwarp();
+        for (int t = 0; t < 2; ++t)
+            if (srt[t] >= 0) h.sup[srt[t]] = vals[t];
+        __syncwarp();
+        for (int i = lane; i < a.k; i += 32) a.support[(size_t)b * a.k + i] = i < ns ? h.sup[i] : -1;
+        if (lane == 0) {
+            double gf;
+            if (infeas > 0) gf = INFINITY;
+            else if (kb == 0) gf = total > 0.0 ? INFINITY : 0.0;
+            else if (total / M > kb * (1.0 + kFeasRtol)) gf = INFINITY;
+            else if (nnz <= kb) gf = 0.5 * sumsq;
+            else {
+                // s = the smallest index with tau_s >= |beta|_(s+1) (Theorem 4.1), s = kbar - 1
+                // taken also if rounding in total - pre says otherwise
+                double pre = 0.0, presq = 0.0;
+                int s = 0;
+                for (; s < kb - 1; ++s) {
+                    const double v = (double)h.sv[s];
+                    if ((total - pre) / (kb - s) >= v) break;
+                    pre += v;
+                    presq += v * v;
+                }
+                const double tail = total - pre;
+                gf = 0.5 * (presq + tail / (kb - s) * tail);
+            }
+            const double g = 0.5 * bj1 + gf;
+            a.lb[b] = lb;
+            a.primal[b] = isinf(g) ? INFINITY : a.sum_loss[b] + 2.0 * a.lam2 * g;
+            a.jstar[b] = leaf ? -1 : h.si[0];
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 void cert_dual_point(cudaStream_t s, const CertArgs& a) {
@@ -271,9 +614,35 @@ void cert_dual_point(cudaStream_t s, const CertArgs& a) {
     else k_dual_point_f32<256><<<a.m, 256, 0, s>>>(a);
 }
 
+// The warp kernel's FP32 combine needs weights that are powers of two (products
+// with the FP32 slices exact) within FP32's normal range.
+static bool cert_warp_ok(const CertArgs& a) {
+    if (a.nqs < 1 || a.nqs > kTcMaxJobs) return false;
+    for (int t = 0; t < a.nqs; ++t) {
+        int e = 0;
+        if (frexp(a.qs_w[t], &e) != 0.5 || e < -90 || e > 40) return false;
+    }
+    return true;
+}
+
 int cert_bound(cudaStream_t s, const CertArgs& a) {
     const int p = a.p, m = a.m;
     if (m <= 0) return 0;
+    if (!a.b_is_f64 && a.Qs && p > 512 && p <= 16384 && cert_warp_ok(a)) {
+        // a warp per node (as many as fit in shared memory, at most 16 per CTA)
+        static const int opted = [] {
+            return cudaFuncSetAttribute(k_cert_bound_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) ==
+                   cudaSuccess;
+        }();
+        int wpc = kCertMaxWarps;
+        while (wpc > 1 && cert_cta_bytes(p, wpc) > (227u << 10)) --wpc;
+        if (opted && cert_cta_bytes(p, wpc) <= (227u << 10)) {
+            const int per_sm = std::max(1, (int)((228u << 10) / (cert_cta_bytes(p, wpc) + 1024)));
+            const int grid = std::max(1, std::min(152 * per_sm, (m + wpc - 1) / wpc));
+            k_cert_bound_warp<<<grid, 32 * wpc, cert_cta_bytes(p, wpc), s>>>(a);
+            return 0;
+        }
+    }
 #define KGLM_CERT(NT_, E_) k_cert_bound<NT_, E_><<<m, NT_, 0, s>>>(a)
     if (p <= 64) KGLM_CERT(32, 2);
     else if (p <= 128) KGLM_CERT(64, 2);

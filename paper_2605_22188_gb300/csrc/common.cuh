@@ -51,6 +51,34 @@ __device__ __forceinline__ double huber64(double q, double M) {
     return a <= M ? 0.5 * a * a : M * a - 0.5 * M * M;
 }
 
+// Bitonic sort (ascending) of 64 keys held two per lane (element 2*lane + s).
+template <typename T>
+__device__ __forceinline__ void sort64(T& k0, T& k1, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 1) {
+                const int g = 2 * lane;                  // pair (g, g+1) in this lane
+                const bool asc = (g & k) == 0;
+                const T lo = k0 < k1 ? k0 : k1, hi = k0 < k1 ? k1 : k0;
+                k0 = asc ? lo : hi;
+                k1 = asc ? hi : lo;
+            } else {
+                const int lj = j >> 1;                   // partner lane
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    T& x = s ? k1 : k0;
+                    const T o = __shfl_xor_sync(0xffffffffu, x, lj);
+                    const int g = 2 * lane + s;
+                    const bool asc = (g & k) == 0, lower = (g & j) == 0;
+                    x = (asc == lower) ? (x < o ? x : o) : (x < o ? o : x);
+                }
+            }
+        }
+    }
+}
+
 // FP32 rounded to the nearest TF32 value (low 13 mantissa bits cleared).
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;

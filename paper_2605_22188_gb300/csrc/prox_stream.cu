@@ -117,33 +117,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// Bitonic sort (ascending) of 64 keys held two per lane (element 2*lane + s).
-__device__ __forceinline__ void sort64(uint32_t& k0, uint32_t& k1, int lane) {
-#pragma unroll
-    for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j == 1) {
-                const int g = 2 * lane;                  // pair (g, g+1) in this lane
-                const bool asc = (g & k) == 0;
-                const uint32_t lo = min(k0, k1), hi = max(k0, k1);
-                k0 = asc ? lo : hi;
-                k1 = asc ? hi : lo;
-            } else {
-                const int lj = j >> 1;                   // partner lane
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    uint32_t& x = s ? k1 : k0;
-                    const uint32_t o = __shfl_xor_sync(0xffffffffu, x, lj);
-                    const int g = 2 * lane + s;
-                    const bool asc = (g & k) == 0, lower = (g & j) == 0;
-                    x = (asc == lower) ? min(x, o) : max(x, o);
-                }
-            }
-        }
-    }
-}
-
 // Tensor-core operand copy of 4 consecutive values of v' (index i, a multiple of 4).
 __device__ __forceinline__ void store_operand4(void* base, float* lo, size_t i, float4 v, int bf16) {
     if (bf16) {
