@@ -82,6 +82,8 @@ typedef struct {
     int32_t max_batch;    /* node-batch capacity m_max, >= 1 */
     int32_t pool_slots;   /* warm-start slots kept on the device (0: 4*max_batch) */
     int64_t hbm_budget;   /* bytes the context may hold on the device; 0: no limit */
+    int64_t open_cap;     /* open nodes the device-resident queue holds (kglm_solve_device);
+                             0: no device queue */
 } kglm_desc;
 
 #define KGLM_MAX_K 64
@@ -167,6 +169,20 @@ kglm_status kglm_branch(kglm_ctx* ctx, double ub, int32_t* parent, int32_t* bran
 kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t check_every,
                        double time_limit_s, double* opt, int32_t* opt_support,
                        double* opt_beta, double* gap, int64_t* nodes, int64_t* batches);
+
+/* kglm_solve with the open-node queue on the device (the context must be
+ * created with desc.open_cap > 0): the open nodes (fixing masks, parent bound,
+ * warm-start slot) stay in a device pool sorted by (bound, id), and each round
+ * selects the first `batch` nodes, evaluates them, updates the incumbent and
+ * merges the children into the pool on the device; pruning is a truncation of
+ * the sorted pool.  The host reads a few scalars per round.  Nodes are
+ * evaluated in the order of kglm_solve (best bound, ties to the older node)
+ * and the certified optimum is the same.  Outputs as kglm_solve; a search
+ * whose open nodes would exceed open_cap stops with *gap > 0.  No checkpoint
+ * is kept (kglm_solve_checkpoint returns KGLM_ESTATE after it). */
+kglm_status kglm_solve_device(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t check_every,
+                              double time_limit_s, double* opt, int32_t* opt_support,
+                              double* opt_beta, double* gap, int64_t* nodes, int64_t* batches);
 
 /* Stop kglm_solve after max_batches node batches (0: no limit), counted per
  * call; the open queue it leaves can be checkpointed.  (A deployment aid for

@@ -74,6 +74,8 @@ struct kglm_ctx {
     double* d_warmB = nullptr;
     void* pool = nullptr;
     int pool_slots = 0;
+    DevQueue dq;                  // device-resident open-node queue (desc.open_cap > 0)
+    bool dq_on = false;
     double ub_inc = INFINITY;
     int* d_err = nullptr;
     GemmScratch gs32{}, gs64{};   // split-K scratch of the CUDA-core GEMMs
@@ -144,7 +146,8 @@ struct kglm_ctx {
     size_t off_tcerr() const { return off_err() + 8; }
     size_t off_kbar() const { return off_err() + 16; }
     size_t off_pf() const { return off_kbar() + 4 * pin_m; }
-    size_t pin_bytes() const { return off_pf() + 4 * pin_m; }
+    size_t off_dq() const { return off_pf() + 4 * pin_m; }
+    size_t pin_bytes() const { return off_dq() + 128; }
     double sum_pa = 0.0;   // sum over the batch of p - |J0(b)|
     // per-phase device timers and launch counters
     struct Rec {
@@ -910,6 +913,14 @@ size_t footprint(const kglm_desc& d) {
     const size_t slots = d.pool_slots > 0 ? (size_t)d.pool_slots : 4 * mc;
     add(slots * p * ws);
     add(4 * mc * k); add(4 * mc * p);
+    if (d.open_cap > 0) {
+        const size_t cap = (size_t)d.open_cap, W2 = 2 * W, m2 = 2 * mc;
+        for (int b = 0; b < 2; ++b) { add(8 * cap); add(8 * cap); add(4 * cap); add(4 * cap * W2); }
+        add(8 * m2); add(8 * m2); add(4 * m2); add(4 * m2 * W2); add(4 * m2);
+        add(8 * mc); add(4 * mc); add(4 * mc); add(4 * mc);
+        add(4 * slots); add(4 * slots); add(4 * k); add(8 * k);
+        add(sizeof(DqState));
+    }
     ExactPlan x{};
     if (!f64 && exact_plan((int)n, 6, 7, &x)) {
         const size_t K2 = (size_t)x.nd * x.npad;
@@ -945,6 +956,153 @@ struct RashomonOpts {
     int64_t cap = 0;
     kglm_pool* pool = nullptr;
 };
+
+// FP64 objective F(X_S b) + lambda2 ||b||^2 of a support (k entries, -1 padded)
+// with its coefficients; `fallback` when the support is empty.
+double exact_objective(kglm_ctx* ctx, const std::vector<int>& sup, const std::vector<double>& coef,
+                       double fallback) {
+    std::vector<int> Sv;
+    std::vector<double> bv;
+    for (int r = 0; r < ctx->k; ++r)
+        if (sup[r] >= 0) { Sv.push_back(sup[r]); bv.push_back(coef[r]); }
+    const int ks = (int)Sv.size();
+    if (ks == 0) return fallback;
+    CK(cudaMemcpyAsync(ctx->d_rows, Sv.data(), sizeof(int) * ks, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->beta_re, bv.data(), sizeof(double) * ks, cudaMemcpyHostToDevice, ctx->st));
+    objective64_launch(ctx->st, ctx->Xt64, ctx->y64, ctx->n, ctx->kind, ctx->lam2, ctx->d_rows, ctx->beta_re, ks,
+                       ctx->ub);
+    check_launch();
+    double exact = fallback;
+    CK(cudaMemcpyAsync(&exact, ctx->ub, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    sync(ctx);
+    return exact;
+}
+
+// The hybrid loop of Fig. 1 with the open-node queue on the device (queue.cu),
+// in steps so that a scheduler can interleave the batches of several
+// contexts: begin(); per round select() (0: nothing open), the batch's
+// evaluation, update(); finish().  The host reads the queue's state (a few
+// scalars) once after each step; node data never leaves the device.
+struct DevSolve {
+    kglm_ctx* c = nullptr;
+    int batch = 0;
+    DqState hs{};
+    int64_t nodes = 0, batches = 0;
+    bool overflow = false;
+
+    void read_state() {
+        CK(cudaMemcpyAsync(c->pinned<DqState>(c->off_dq()), c->dq.st, sizeof(DqState), cudaMemcpyDeviceToHost, c->st));
+        sync(c);
+        hs = *c->pinned<DqState>(c->off_dq());
+    }
+    void begin() {
+        c->saved = SavedSolve{};                       // a device-queue search leaves no host checkpoint
+        dq_init(c->st, c->dq);
+        check_launch();
+        read_state();
+    }
+    // the next batch into the batch arrays; its size
+    int select() {
+        if (hs.N == 0 || overflow) return 0;
+        {
+            Scope sc(c, PH_LAYOUT, 2, 8.0 * c->W * batch);
+            dq_select(c->st, c->dq, batch, c->gap_tol, c->in_mask, c->out_mask, c->kbar, c->pf);
+            check_launch();
+        }
+        read_state();
+        const int m = hs.m;
+        if (m == 0) return 0;
+        {
+            Scope sc(c, PH_LAYOUT, 0, (c->f64 ? 16.0 : 8.0) * m * c->p);
+            c->st_n[PH_LAYOUT] += layout_warm(c->st, m, c->p, c->W, c->f64, c->dq.bslot, c->pool_slots, c->pool,
+                                              nullptr, c->out_mask, c->B, c->V, c->Vop, c->Vop_lo, c->pK,
+                                              c->tc_kind == 0, c->tmom, c->active, c->phint);
+            check_launch();
+        }
+        c->m = m;
+        c->pushed = true;
+        c->evaluated = false;
+        c->sum_pa = (double)m * c->p - (double)hs.sum_out;
+        c->ub_inc = hs.ub;
+        return m;
+    }
+    // incumbent, closing and branching, children and the merged pool
+    void update() {
+        {
+            Scope sc(c, PH_SMALL, 7, 0.0);
+            dq_update(c->st, c->dq, c->m, hs.N, c->gap_tol, c->lb_best, c->ub, c->jstar, c->support, c->beta_re,
+                      c->in_mask, c->out_mask, c->B, c->f64, c->pool);
+            check_launch();
+        }
+        read_state();
+        finish_tc_check(c);
+        harvest(c);
+        c->evaluated = true;
+        nodes += c->m;
+        ++batches;
+        overflow = hs.overflow != 0;
+    }
+    void finish(SolveOut& out, bool stopped) {
+        const int k = c->k;
+        std::vector<int> sup(k);
+        std::vector<double> coef(k);
+        double open_lb = INFINITY;
+        CK(cudaMemcpyAsync(c->pinned<int>(c->off_support()), c->dq.best_sup, sizeof(int) * k, cudaMemcpyDeviceToHost,
+                           c->st));
+        CK(cudaMemcpyAsync(c->pinned<double>(c->off_beta()), c->dq.best_coef, sizeof(double) * k,
+                           cudaMemcpyDeviceToHost, c->st));
+        if (hs.N > 0)                                   // the pool is sorted: its first bound is the least
+            CK(cudaMemcpyAsync(c->pinned<double>(c->off_lb()), c->dq.lb[c->dq.cur], sizeof(double),
+                               cudaMemcpyDeviceToHost, c->st));
+        sync(c);
+        memcpy(sup.data(), c->pinned<int>(c->off_support()), sizeof(int) * k);
+        memcpy(coef.data(), c->pinned<double>(c->off_beta()), sizeof(double) * k);
+        if (hs.N > 0) open_lb = *c->pinned<double>(c->off_lb());
+        double ub = hs.ub;
+        if (!c->f64 && isfinite(ub)) ub = exact_objective(c, sup, coef, ub);
+        out.complete = hs.N == 0 && !overflow && !stopped;
+        const double glb = std::min(open_lb, ub);
+        out.opt = ub;
+        out.gap = isfinite(ub) ? (ub - glb) / fmax(1.0, fabs(ub)) : INFINITY;
+        out.nodes = nodes;
+        out.batches = batches;
+        out.support = sup;
+        out.beta.assign(c->p, 0.0);
+        for (int r = 0; r < k; ++r)
+            if (sup[r] >= 0) out.beta[sup[r]] = coef[r];
+    }
+};
+
+void solve_dev_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
+                    const std::atomic<int>* cancel, SolveOut& out) {
+    REQ(ctx->dq_on, "the context has no device queue (created with open_cap = 0)");
+    REQ(batch >= 1 && batch <= ctx->mcap, "batch must be in [1, max_batch]");
+    REQ(iters >= 1, "iters must be >= 1");
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+    DevSolve d;
+    d.c = ctx;
+    d.batch = batch;
+    d.begin();
+    bool stopped = false;
+    for (;;) {
+        if ((time_limit_s > 0 && elapsed() > time_limit_s) ||
+            (ctx->solve_max_batches > 0 && d.batches >= ctx->solve_max_batches)) {
+            stopped = true;
+            break;
+        }
+        if (cancel && cancel->load(std::memory_order_relaxed)) {
+            out.cancelled = true;
+            stopped = true;
+            break;
+        }
+        Nvtx range("bnb batch (device queue)");
+        if (d.select() == 0) break;
+        evaluate_impl(ctx, iters, check_every);
+        d.update();
+    }
+    d.finish(out, stopped);
+}
 
 void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
                 const std::atomic<int>* cancel, SolveOut& out, const RashomonOpts* rs = nullptr,
@@ -1151,24 +1309,7 @@ void solve_impl(kglm_ctx* ctx, int batch, int iters, int check_every, double tim
     }
     // the reduced-precision modes keep an upper bound of each incumbent's
     // objective during the search; report the exact FP64 objective
-    if (!ctx->f64 && isfinite(ub)) {
-        std::vector<int> Sv;
-        std::vector<double> bv;
-        for (int r = 0; r < k; ++r)
-            if (best_sup[r] >= 0) { Sv.push_back(best_sup[r]); bv.push_back(best_coef[r]); }
-        const int ks = (int)Sv.size();
-        if (ks > 0) {
-            CK(cudaMemcpyAsync(ctx->d_rows, Sv.data(), sizeof(int) * ks, cudaMemcpyHostToDevice, ctx->st));
-            CK(cudaMemcpyAsync(ctx->beta_re, bv.data(), sizeof(double) * ks, cudaMemcpyHostToDevice, ctx->st));
-            objective64_launch(ctx->st, ctx->Xt64, ctx->y64, ctx->n, ctx->kind, ctx->lam2, ctx->d_rows,
-                               ctx->beta_re, ks, ctx->ub);
-            check_launch();
-            double exact = ub;
-            CK(cudaMemcpyAsync(&exact, ctx->ub, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-            sync(ctx);
-            ub = exact;
-        }
-    }
+    if (!ctx->f64 && isfinite(ub)) ub = exact_objective(ctx, best_sup, best_coef, ub);
     if (rs && !ctx->f64 && !rs->pool->leaf.empty()) {
         // the reduced modes store upper estimates of v(S): replace them by the FP64
         // objective of each record's coefficients, then filter at the final tau
@@ -1516,6 +1657,7 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
                 d.prec == KGLM_TF32X3,
             "unknown precision");
         REQ(d.max_batch >= 1, "max_batch must be >= 1");
+        REQ(d.open_cap >= 0 && d.open_cap <= (int64_t)1 << 28, "open_cap must be in [0, 2^28]");
         REQ(d.p <= (d.prec == KGLM_FP64 ? 4096 : 8192), "p above the prox kernel limit for this precision");
         c->d = d;
         c->n = (int)d.n; c->p = (int)d.p; c->k = d.k; c->kind = d.loss; c->prec = d.prec;
@@ -1701,6 +1843,34 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
         c->pool = dalloc(c, (size_t)c->pool_slots * p * ws);
         c->d_in_idx = dalloc_t<int>(c, mc * c->k);
         c->d_out_idx = dalloc_t<int>(c, mc * p);
+        if (d.open_cap > 0) {
+            // the device-resident open-node queue: two pool buffers, the children of a
+            // batch, per-batch bookkeeping, slot counts, the incumbent and the state
+            DevQueue& q = c->dq;
+            q.cap = (int)d.open_cap; q.W = c->W; q.p = c->p; q.k = c->k; q.nslots = c->pool_slots;
+            const size_t cap = (size_t)d.open_cap, W2 = 2 * (size_t)c->W, m2 = 2 * mc;
+            for (int b = 0; b < 2; ++b) {
+                q.lb[b] = dalloc_t<double>(c, cap);
+                q.id[b] = dalloc_t<long long>(c, cap);
+                q.slot[b] = dalloc_t<int>(c, cap);
+                q.mask[b] = dalloc_t<uint32_t>(c, cap * W2);
+            }
+            q.clb = dalloc_t<double>(c, m2);
+            q.cid = dalloc_t<long long>(c, m2);
+            q.cslot = dalloc_t<int>(c, m2);
+            q.cmask = dalloc_t<uint32_t>(c, m2 * W2);
+            q.cperm = dalloc_t<int>(c, m2);
+            q.lbp = dalloc_t<double>(c, mc);
+            q.bslot = dalloc_t<int>(c, mc);
+            q.brank = dalloc_t<int>(c, mc);
+            q.cslot_b = dalloc_t<int>(c, mc);
+            q.sref = dalloc_t<int>(c, (size_t)c->pool_slots);
+            q.sfree = dalloc_t<int>(c, (size_t)c->pool_slots);
+            q.best_sup = dalloc_t<int>(c, (size_t)c->k);
+            q.best_coef = dalloc_t<double>(c, (size_t)c->k);
+            q.st = static_cast<DqState*>(dalloc(c, sizeof(DqState)));
+            c->dq_on = true;
+        }
         // reduced-precision modes: digits of X for the exact certificate product
         // (6-bit digits, 7 per value), when the jobs and the HBM budget allow
         if (!c->f64 && exact_plan((int)n, 6, 7, &c->xplan)) {
@@ -1969,6 +2139,26 @@ kglm_status kglm_solve(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t chec
     });
 }
 
+
+kglm_status kglm_solve_device(kglm_ctx* ctx, int32_t batch, int32_t iters, int32_t check_every, double time_limit_s,
+                              double* opt, int32_t* opt_support, double* opt_beta, double* gap, int64_t* nodes,
+                              int64_t* batches) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+        if (batch == 0) {
+            if (ctx->tuned_batch == 0) autotune_impl(ctx, std::min(iters, 20), 1, nullptr);
+            batch = ctx->tuned_batch;
+        }
+        SolveOut o;
+        solve_dev_impl(ctx, batch, iters, check_every, time_limit_s, nullptr, o);
+        if (opt) *opt = o.opt;
+        if (gap) *gap = o.gap;
+        if (nodes) *nodes = o.nodes;
+        if (batches) *batches = o.batches;
+        if (opt_support) std::copy(o.support.begin(), o.support.end(), opt_support);
+        if (opt_beta) std::copy(o.beta.begin(), o.beta.end(), opt_beta);
+    });
+}
 
 // ---- checkpoint and resume of an unfinished certified solve
 // File: magic "KGLMCKP1", then int64 n, p; int32 k, loss; double lambda2, M, data_sum

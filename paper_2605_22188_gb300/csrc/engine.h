@@ -255,6 +255,49 @@ void convert_to_f64(cudaStream_t s, const void* in, int is_f64, double* out, siz
 // ---- host side shared by the C ABI and the serving loop (api.cu)
 // Device bytes kglm_create allocates for desc (see kglm_estimate_bytes).
 size_t device_footprint(const kglm_desc& d);
+// Device-resident open-node queue of the hybrid loop (queue.cu).
+struct DqState {
+    long long next_id;   // the next node id
+    long long id_base;   // first id of this round's children
+    double ub;           // incumbent objective
+    long long sum_out;   // sum of |J0| over the selected batch
+    int N;               // open nodes in the pool
+    int m;               // nodes of the selected batch
+    int nbranch;         // branching nodes of the last batch
+    int nfree;           // free warm-start slots
+    int nkeep;           // pool entries kept by the last merge
+    int overflow;        // the last merge had more entries than the capacity
+};
+struct DevQueue {
+    int cap = 0, W = 0, p = 0, k = 0, nslots = 0, cur = 0;
+    double* lb[2] = {nullptr, nullptr};      // pool buffers: parent bound, id, slot, masks (J1 then J0, 2W words)
+    long long* id[2] = {nullptr, nullptr};
+    int* slot[2] = {nullptr, nullptr};
+    uint32_t* mask[2] = {nullptr, nullptr};
+    double* clb = nullptr;                   // children of a batch (2 per node)
+    long long* cid = nullptr;
+    int* cslot = nullptr;
+    uint32_t* cmask = nullptr;
+    int* cperm = nullptr;                    // children in key order
+    double* lbp = nullptr;                   // batch: parent bound (then the children's bound)
+    int* bslot = nullptr;                    // batch: warm-start slot
+    int* brank = nullptr;                    // batch: rank among the branching nodes, -1 if closed
+    int* cslot_b = nullptr;                  // batch: the new slot of a branching node
+    int* sref = nullptr;                     // slot reference counts
+    int* sfree = nullptr;                    // stack of free slots
+    int* best_sup = nullptr;                 // incumbent support and coefficients
+    double* best_coef = nullptr;
+    DqState* st = nullptr;
+};
+void dq_init(cudaStream_t s, DevQueue& q);
+// k_dq_select + layout of the first min(batch, N) pool entries into the batch arrays
+void dq_select(cudaStream_t s, DevQueue& q, int batch, double gap_tol, uint32_t* in_mask, uint32_t* out_mask,
+               int* kbar, int* pf);
+// incumbent, close/branch, children, merge (m, N: the host's copies of the state)
+void dq_update(cudaStream_t s, DevQueue& q, int m, int N, double gap_tol, const double* lb_best, const double* ubc,
+               const int* jstar, const int* support, const double* beta_re, const uint32_t* in_mask,
+               const uint32_t* out_mask, const void* B, int is_f64, void* pool);
+
 struct SolveResult {
     double opt = 0, gap = 0;
     std::vector<int> support;

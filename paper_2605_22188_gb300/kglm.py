@@ -25,7 +25,7 @@ class kglm_desc(C.Structure):
         ("n", C.c_int64), ("p", C.c_int64), ("k", C.c_int32), ("loss", C.c_int32),
         ("prec", C.c_int32), ("restart", C.c_int32), ("lambda2", C.c_double), ("M", C.c_double),
         ("lipschitz", C.c_double), ("gap_tol", C.c_double), ("max_batch", C.c_int32),
-        ("pool_slots", C.c_int32), ("hbm_budget", C.c_int64),
+        ("pool_slots", C.c_int32), ("hbm_budget", C.c_int64), ("open_cap", C.c_int64),
     ]
 
 
@@ -52,6 +52,7 @@ _SIGS = {
     "kglm_prune": (C.c_int, [P, C.c_double, U8, I32]),
     "kglm_branch": (C.c_int, [P, C.c_double, I32, I32, I32]),
     "kglm_solve": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_double, D, I32, D, D, I64, I64]),
+    "kglm_solve_device": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_double, D, I32, D, D, I64, I64]),
     "kglm_last_error": (C.c_char_p, [P]),
     "kglm_destroy": (None, [P]),
     "kglm_version": (C.c_char_p, []),
@@ -168,11 +169,11 @@ def kglm_version():
 
 
 def make_desc(n, p, k, lambda2, M, loss, prec="fp64", max_batch=1024, lipschitz=0.0, gap_tol=0.0,
-              restart=True, pool_slots=0, hbm_budget=0):
+              restart=True, pool_slots=0, hbm_budget=0, open_cap=0):
     return kglm_desc(n=int(n), p=int(p), k=int(k), loss=int(loss), prec=PREC.get(prec, prec),
                      restart=int(bool(restart)), lambda2=float(lambda2), M=float(M), lipschitz=float(lipschitz),
                      gap_tol=float(gap_tol), max_batch=int(max_batch), pool_slots=int(pool_slots),
-                     hbm_budget=int(hbm_budget))
+                     hbm_budget=int(hbm_budget), open_cap=int(open_cap))
 
 
 def kglm_estimate_bytes(desc):
@@ -201,11 +202,12 @@ def kglm_suggest_batch(desc, budget, cap=1 << 16):
 
 
 def kglm_create(X, y, k, lambda2, M, loss, prec="fp64", max_batch=1024, lipschitz=0.0, gap_tol=0.0,
-                restart=True, pool_slots=0, hbm_budget=0, stream=None):
+                restart=True, pool_slots=0, hbm_budget=0, stream=None, open_cap=0):
     X = _f64(X)
     n, p = X.shape
     y = _f64(y, (n,))
-    d = make_desc(n, p, k, lambda2, M, loss, prec, max_batch, lipschitz, gap_tol, restart, pool_slots, hbm_budget)
+    d = make_desc(n, p, k, lambda2, M, loss, prec, max_batch, lipschitz, gap_tol, restart, pool_slots, hbm_budget,
+                  open_cap)
     out = P()
     st = lib().kglm_create(C.byref(d), _ptr(X, D), _ptr(y, D), P(stream) if stream else None, C.byref(out))
     _check(st, None)
@@ -310,12 +312,13 @@ def kglm_branch(ctx, m, ub):
     return parent[:cnt.value].copy(), j[:cnt.value].copy()
 
 
-def kglm_solve(ctx, k, p, batch, iters, check_every=10, time_limit=0.0):
+def kglm_solve(ctx, k, p, batch, iters, check_every=10, time_limit=0.0, device_queue=False):
     opt, gap = C.c_double(), C.c_double()
     nodes, batches = C.c_int64(), C.c_int64()
     sup = np.empty(k, dtype=np.int32)
     beta = np.empty(p)
-    st = lib().kglm_solve(ctx, int(batch), int(iters), int(check_every), float(time_limit), C.byref(opt),
+    fn = lib().kglm_solve_device if device_queue else lib().kglm_solve
+    st = fn(ctx, int(batch), int(iters), int(check_every), float(time_limit), C.byref(opt),
                           _ptr(sup, I32), _ptr(beta, D), C.byref(gap), C.byref(nodes), C.byref(batches))
     _check(st, ctx)
     return dict(opt=opt.value, support=[int(s) for s in sup if s >= 0], beta=beta, gap=gap.value,
@@ -431,6 +434,10 @@ class Engine:
 
     def solve(self, batch, iters, check_every=10, time_limit=0.0):
         return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit)
+
+    def solve_device(self, batch, iters, check_every=10, time_limit=0.0):
+        """kglm_solve_device: the open-node queue stays on the device (needs open_cap > 0)."""
+        return kglm_solve(self.ctx, self.k, self.p, batch, iters, check_every, time_limit, device_queue=True)
 
     def set_solve_limit(self, max_batches):
         kglm_set_solve_limit(self.ctx, max_batches)
