@@ -391,16 +391,23 @@ kglm_status kglm_rashomon(kglm_ctx* ctx, double eps, int64_t max_models, int32_t
                           int32_t* complete);
 
 /* ---- Serving loop: certified solves of many instances, admitted as they
- * arrive (continuous batching at request granularity).  Each admitted
- * request is a kglm_solve (the hybrid loop of Fig. 1) on its own context,
- * stream and host worker thread; requests in flight share the GPU (their
- * kernels run side by side on the SMs) and each one's host tree work
- * overlaps the others' device work.  Admission is FIFO: the request at the
- * head of the queue starts once a worker is free and its device footprint
- * (kglm_estimate_bytes) fits in the budget the running requests leave; a
- * request's memory returns to the budget when it finishes.  A request runs
- * the same kernels in the same order as kglm_solve alone, so its result
- * (objective, support, node count) does not depend on the other requests. */
+ * arrive (continuous batching at node-batch granularity).  Each admitted
+ * request keeps X and its open-node queue on the device (kglm_solve_device's
+ * queue) on a context that runs on the server's stream.  One scheduler
+ * thread runs rounds: every running request's next node batch (up to its
+ * max_batch nodes, best bound first) is selected on the device, the selected
+ * batches are evaluated together -- the FISTA iterations of the BF16
+ * requests as shared launches (per iteration one grouped S = X V + link, one
+ * grouped G = X^T R and one prox launch over all their nodes, up to 8
+ * requests per launch), the other precisions with their own launches on the
+ * same stream -- and each batch is then closed, branched and merged into
+ * its request's queue on the device.  Admission is FIFO at round
+ * boundaries: the request at the head of the queue starts once a slot is
+ * free (max_active) and its device footprint (kglm_estimate_bytes, queue
+ * included) fits in the budget the running requests leave; a request's
+ * memory returns to the budget when it finishes.  A request's nodes see the
+ * same arithmetic whatever shares the launches, so its result (objective,
+ * support, node count) does not depend on the other requests. */
 typedef struct kglm_server kglm_server;
 
 typedef struct {
@@ -410,6 +417,7 @@ typedef struct {
     int32_t iters;        /* FISTA iterations per node evaluation (kglm_solve's iters), >= 1 */
     int32_t check_every;  /* certificate every check_every iterations (kglm_solve's), >= 0 */
     double time_limit_s;  /* per request, counted from admission; <= 0: none */
+    int64_t open_cap;     /* open nodes each request's device queue holds; 0: max(4096, 16 max_batch) */
 } kglm_server_desc;
 
 enum { KGLM_REQ_QUEUED = 0, KGLM_REQ_RUNNING = 1, KGLM_REQ_DONE = 2, KGLM_REQ_FAILED = 3, KGLM_REQ_CANCELLED = 4 };
@@ -433,9 +441,12 @@ typedef struct {
     int32_t active, peak_active;
     int64_t bytes_in_use, peak_bytes, budget;
     double elapsed_s;
+    int64_t rounds;           /* scheduler rounds with at least one batch evaluated */
+    int64_t round_batches;    /* node batches evaluated in those rounds */
+    int64_t shared_launches;  /* iteration launches that carried the nodes of more than one request */
 } kglm_server_stats_t;
 
-/* Start a server on the current CUDA device with max_active worker threads. */
+/* Start a server on the current CUDA device (its scheduler thread and stream). */
 kglm_status kglm_server_create(const kglm_server_desc* desc, kglm_server** out);
 
 /* Queue an instance (the arguments of kglm_create; desc->hbm_budget is

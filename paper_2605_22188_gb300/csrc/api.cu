@@ -93,6 +93,8 @@ struct kglm_ctx {
     void *Xop = nullptr, *Xop_lo = nullptr, *Xtop = nullptr, *Vop = nullptr, *Rop = nullptr;
     float *Xtop_lo = nullptr, *Vop_lo = nullptr, *Rop_lo = nullptr;   // low parts (FP32-accurate mode)
     TcMap mA1{}, mB1{}, mB1lo{}, mA2{}, mB2{}, mA1lo{}, mA2lo{}, mB2lo{};
+    TcMap gB1{}, gB2{};            // X and X^T maps at the bucketed tile widths of grouped launches
+    int gbn1 = 0, gbn2 = 0;
     // FP32-accurate mode: beta as a TF32 hi + lo operand for the certificate's X beta
     float *Bop = nullptr, *Bop_lo = nullptr;
     TcMap mAb{}, mAblo{};
@@ -446,6 +448,32 @@ __global__ void k_filli(int m, int* x, int v) {
     if (b < m) x[b] = v;
 }
 
+// The prox of batch rows [row0, row0 + mr) after a tensor-core iteration's
+// products (G as `splits` partial slices).
+ProxArgs prox_args_rows(kglm_ctx* c, int row0, int mr, int splits, bool pdl) {
+    const int p = c->p;
+    const size_t es = c->tc_kind == 0 ? 2 : 4;
+    ProxArgs a{};
+    a.m = mr; a.p = p; a.W = c->W;
+    a.G = nullptr;
+    a.V = static_cast<float*>(c->V) + (size_t)row0 * p;
+    a.B = static_cast<float*>(c->B) + (size_t)row0 * p;
+    a.Gpart = c->Gpart + (size_t)row0 * p;
+    a.gsplits = splits;
+    a.gstride = (size_t)c->mcap * p;
+    a.Vop = static_cast<char*>(c->Vop) + (size_t)row0 * c->pK * es;
+    a.Vop_lo = c->Vop_lo ? c->Vop_lo + (size_t)row0 * c->pK : nullptr;
+    a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
+    a.in_mask = c->in_mask + (size_t)row0 * c->W; a.out_mask = c->out_mask + (size_t)row0 * c->W;
+    a.kbar = c->kbar + row0; a.pf = c->pf + row0;
+    a.tmom = c->tmom + row0; a.active = c->active + row0;
+    a.hint = c->phint + 2 * (size_t)row0;
+    a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
+    a.pdl = pdl ? 1 : 0;
+    a.threads = c->prox_threads;
+    return a;
+}
+
 // One FISTA iteration of batch rows [row0, row0 + mr) on stream st (tensor-core
 // modes): S = X V with the link, G = X^T R as split slices, the prox.  Rows of
 // different calls touch disjoint rows of every buffer, and the link product
@@ -487,24 +515,7 @@ void iterate_rows(kglm_ctx* c, cudaStream_t st, int row0, int mr, bool sub) {
             throw Fail{KGLM_ECUDA, "tensor-core product setup failed"};
         check_launch();
     }
-    ProxArgs a{};
-    a.m = mr; a.p = p; a.W = c->W;
-    a.G = nullptr;
-    a.V = static_cast<float*>(c->V) + (size_t)row0 * p;
-    a.B = static_cast<float*>(c->B) + (size_t)row0 * p;
-    a.Gpart = c->Gpart + (size_t)row0 * p;
-    a.gsplits = splits;
-    a.gstride = (size_t)c->mcap * p;
-    a.Vop = static_cast<char*>(c->Vop) + (size_t)row0 * c->pK * es;
-    a.Vop_lo = c->Vop_lo ? c->Vop_lo + (size_t)row0 * c->pK : nullptr;
-    a.op_ld = c->pK; a.op_bf16 = c->tc_kind == 0;
-    a.in_mask = c->in_mask + (size_t)row0 * c->W; a.out_mask = c->out_mask + (size_t)row0 * c->W;
-    a.kbar = c->kbar + row0; a.pf = c->pf + row0;
-    a.tmom = c->tmom + row0; a.active = c->active + row0;
-    a.hint = c->phint + 2 * (size_t)row0;
-    a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
-    a.pdl = pdl;
-    a.threads = c->prox_threads;
+    const ProxArgs a = prox_args_rows(c, row0, mr, splits, pdl);
     Scope sc(c, PH_PROX, 1, 4.0 * 5.0 * c->sum_pa * share);
     if (prox_fista_f32(st, a) != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
     check_launch();
@@ -634,41 +645,37 @@ void run_iters(kglm_ctx* c, int count) {
     }
 }
 
-void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
-    Nvtx range("kglm evaluate: iterations, certificate, rounding, re-optimization");
+// The steps of one batch evaluation: the bound and iteration counters reset,
+// a certificate check after `it` iterations (bounds kept, finished nodes frozen,
+// the active flags copied to h asynchronously: the caller synchronises), and the
+// final certificate, bound fold and re-optimization.
+void evaluate_begin(kglm_ctx* c, int iters) {
     const int m = c->m;
     const unsigned gb = (unsigned)((m + 255) / 256);
+    Scope sc(c, PH_SMALL, 2, 0.0);
+    k_fill<<<gb, 256, 0, c->st>>>(m, c->lb_best, -INFINITY);
+    k_filli<<<gb, 256, 0, c->st>>>(m, c->iters_done, iters);
+    check_launch();
+}
+
+void evaluate_check(kglm_ctx* c, int it, std::vector<int>& h) {
+    const int m = c->m;
+    const double thr = c->ub_inc - delta_of(c, c->ub_inc);
+    certify(c);
     {
-        Scope sc(c, PH_SMALL, 2, 0.0);
-        k_fill<<<gb, 256, 0, c->st>>>(m, c->lb_best, -INFINITY);
-        k_filli<<<gb, 256, 0, c->st>>>(m, c->iters_done, iters);
+        Scope sc(c, PH_SMALL, 1, 0.0);
+        check_update(c->st, m, c->lb_now, c->primal_now, c->lb_best, c->primal_last, c->active, c->iters_done, it, thr,
+                     1e-9);
         check_launch();
     }
-    const double thr = c->ub_inc - delta_of(c, c->ub_inc);
-    std::vector<int> h_active;
-    for (int it = 0; it < iters;) {
-        const int seg = check_every > 0 ? std::min(check_every, iters - it) : iters - it;
-        run_iters(c, seg);
-        it += seg;
-        if (check_every > 0 && it % check_every == 0 && it < iters) {
-            certify(c);
-            {
-                Scope sc(c, PH_SMALL, 1, 0.0);
-                check_update(c->st, m, c->lb_now, c->primal_now, c->lb_best, c->primal_last, c->active,
-                             c->iters_done, it, thr, 1e-9);
-                check_launch();
-            }
-            h_active.resize(m);
-            {
-                Scope sc(c, PH_COPY, 0, 4.0 * m);
-                CK(cudaMemcpyAsync(h_active.data(), c->active, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
-            }
-            sync(c);
-            bool any = false;
-            for (int v : h_active) any |= (v != 0);
-            if (!any) break;
-        }
-    }
+    h.resize(m);
+    Scope sc(c, PH_COPY, 0, 4.0 * m);
+    CK(cudaMemcpyAsync(h.data(), c->active, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+}
+
+void evaluate_end(kglm_ctx* c) {
+    const int m = c->m;
+    const unsigned gb = (unsigned)((m + 255) / 256);
     certify(c);
     {
         Scope sc(c, PH_SMALL, 1, 0.0);
@@ -695,6 +702,138 @@ void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
         CK(cudaMemcpyAsync(c->pinned<int>(c->off_tcerr()), c->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         c->tc_check_pending = true;
     }
+}
+
+void evaluate_impl(kglm_ctx* c, int iters, int check_every) {
+    Nvtx range("kglm evaluate: iterations, certificate, rounding, re-optimization");
+    evaluate_begin(c, iters);
+    std::vector<int> h_active;
+    for (int it = 0; it < iters;) {
+        const int seg = check_every > 0 ? std::min(check_every, iters - it) : iters - it;
+        run_iters(c, seg);
+        it += seg;
+        if (check_every > 0 && it % check_every == 0 && it < iters) {
+            evaluate_check(c, it, h_active);
+            sync(c);
+            bool any = false;
+            for (int v : h_active) any |= (v != 0);
+            if (!any) break;
+        }
+    }
+    evaluate_end(c);
+}
+
+// ---- several contexts' batches in shared launches (the serving loop)
+// BF16 contexts with single operands and p in the streaming prox's range take
+// part: per FISTA iteration one launch of S = X V + link and one of G = X^T R
+// for every (tile width, up to 8 contexts), and one streaming prox launch for
+// up to 8 contexts' nodes.  Each context keeps its own split-K (set from its
+// own shape) and node-level work, so its results do not depend on the others;
+// the tile width is bucketed from its own n and p.  Other contexts run their
+// iterations with their own launches in the same round.
+bool groupable(const kglm_ctx* c) {
+    return c->tc && c->tc_kind == 0 && !c->x3 && !c->xlo && c->p <= kStreamMaxP && c->m > 0;
+}
+
+int bucket_bn(int N) { return N >= 256 ? 256 : (N >= 128 ? 128 : 64); }
+
+void group_maps(kglm_ctx* c) {
+    const int b1 = bucket_bn(c->n), b2 = bucket_bn(c->p);
+    if (c->gbn1 == b1 && c->gbn2 == b2) return;
+    if (tc_make_map(&c->gB1, c->Xop, 1, c->n, c->p, c->pK, b1) ||
+        tc_make_map(&c->gB2, c->Xtop, 1, c->p, c->n, c->nK, b2))
+        throw Fail{KGLM_ECUDA, "cuTensorMapEncodeTiled failed for a grouped product"};
+    c->gbn1 = b1;
+    c->gbn2 = b2;
+}
+
+void iterate_group(const std::vector<kglm_ctx*>& A, int64_t* shared) {
+    std::vector<kglm_ctx*> g;
+    for (kglm_ctx* c : A) {
+        if (groupable(c)) {
+            group_maps(c);
+            g.push_back(c);
+        } else {
+            iterate(c);
+        }
+    }
+    if (g.empty()) return;
+    cudaStream_t st = g[0]->st;
+    std::vector<int> splits(g.size(), 1);
+    for (int grad = 0; grad < 2; ++grad) {
+        std::vector<char> done(g.size(), 0);
+        for (size_t i = 0; i < g.size(); ++i) {
+            if (done[i]) continue;
+            const int bn = grad ? g[i]->gbn2 : g[i]->gbn1;
+            std::vector<TcGroupItem> items;
+            for (size_t j = i; j < g.size() && (int)items.size() < kGroupMax; ++j) {
+                if (done[j] || (grad ? g[j]->gbn2 : g[j]->gbn1) != bn) continue;
+                done[j] = 1;
+                kglm_ctx* c = g[j];
+                TcGroupItem it{};
+                it.M = c->m;
+                if (!grad) {
+                    it.A = &c->mA1; it.B = &c->gB1; it.N = c->n; it.K = c->p;
+                    it.out = c->Rop; it.ldo = c->nK; it.y = c->y32; it.loss = c->kind;
+                } else {
+                    it.A = &c->mA2; it.B = &c->gB2; it.N = c->p; it.K = c->n;
+                    it.pout = c->Gpart; it.pstride = (size_t)c->mcap * c->p; it.pld = c->p;
+                    it.max_splits = c->gsplit_max; it.splits_bn = c->bn2; it.splits_used = &splits[j];
+                }
+                items.push_back(it);
+            }
+            Scope sc(g[i], grad ? PH_GEMM_GRAD : PH_GEMM_LINK, 1, 0.0);
+            if (tc_gemm_group(st, items.data(), (int)items.size(), bn, grad ? TC_EPI_PARTIAL : TC_EPI_LINK_BF16,
+                              g[i]->d_tcerr) != 0)
+                throw Fail{KGLM_ECUDA, "grouped tensor-core product setup failed"};
+            check_launch();
+            if (shared && items.size() > 1) ++*shared;
+        }
+    }
+    for (size_t i0 = 0; i0 < g.size(); i0 += kGroupMax) {
+        ProxGroup pg{};
+        pg.np = (int)std::min<size_t>(kGroupMax, g.size() - i0);
+        for (int t = 0; t < pg.np; ++t) pg.a[t] = prox_args_rows(g[i0 + t], 0, g[i0 + t]->m, splits[i0 + t], false);
+        Scope sc(g[i0], PH_PROX, 1, 0.0);
+        const int rc = prox_stream_group(st, pg);
+        if (rc < 0) throw Fail{KGLM_ECUDA, "prox kernel: shared memory attribute refused"};
+        if (rc == 1)
+            for (int t = 0; t < pg.np; ++t)
+                if (prox_fista_f32(st, pg.a[t]) != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
+        check_launch();
+        if (shared && rc == 0 && pg.np > 1) ++*shared;
+    }
+}
+
+// evaluate_impl of every context (all on one stream), their iterations in shared
+// launches (*shared counts the launches that carried more than one context)
+void evaluate_group(const std::vector<kglm_ctx*>& cs, int iters, int check_every, int64_t* shared) {
+    Nvtx range("kglm evaluate (grouped contexts)");
+    for (kglm_ctx* c : cs) {
+        REQ(c->pushed, "evaluate before push");
+        REQ(c->st == cs[0]->st, "grouped contexts must share one stream");
+    }
+    for (kglm_ctx* c : cs) evaluate_begin(c, iters);
+    std::vector<kglm_ctx*> A(cs);
+    std::vector<std::vector<int>> h;
+    for (int it = 0; it < iters && !A.empty();) {
+        const int seg = check_every > 0 ? std::min(check_every, iters - it) : iters - it;
+        for (int i = 0; i < seg; ++i) iterate_group(A, shared);
+        it += seg;
+        if (check_every > 0 && it % check_every == 0 && it < iters) {
+            h.resize(A.size());
+            for (size_t i = 0; i < A.size(); ++i) evaluate_check(A[i], it, h[i]);
+            sync(A[0]);
+            std::vector<kglm_ctx*> keep;
+            for (size_t i = 0; i < A.size(); ++i) {
+                bool any = false;
+                for (int v : h[i]) any |= (v != 0);
+                if (any) keep.push_back(A[i]);
+            }
+            A.swap(keep);
+        }
+    }
+    for (kglm_ctx* c : cs) evaluate_end(c);
 }
 
 // After a synchronisation that follows evaluate_impl: the tensor-core error flag
@@ -1594,6 +1733,59 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
 namespace kglm {
 
 size_t device_footprint(const kglm_desc& d) { return footprint(d); }
+
+struct ServeSolve {
+    DevSolve d;
+};
+
+kglm_status serve_begin(kglm_ctx* c, int batch, ServeSolve** out) {
+    if (!c || !out) return KGLM_EINVAL;
+    *out = nullptr;
+    return guarded(c, [&] {
+        REQ(c->dq_on, "the context has no device queue (created with open_cap = 0)");
+        REQ(batch >= 1 && batch <= c->mcap, "batch must be in [1, max_batch]");
+        ServeSolve* s = new ServeSolve();
+        s->d.c = c;
+        s->d.batch = batch;
+        try {
+            s->d.begin();
+        } catch (...) {
+            delete s;
+            throw;
+        }
+        *out = s;
+    });
+}
+
+kglm_status serve_select(ServeSolve* s, int* m) {
+    *m = 0;
+    return guarded(s->d.c, [&] { *m = s->d.select(); });
+}
+
+kglm_status serve_evaluate(kglm_ctx* const* cs, int count, int iters, int check_every, int64_t* shared) {
+    if (count <= 0) return KGLM_OK;
+    return guarded(cs[0], [&] {
+        REQ(iters >= 1 && check_every >= 0, "iters must be >= 1 and check_every >= 0");
+        evaluate_group(std::vector<kglm_ctx*>(cs, cs + count), iters, check_every, shared);
+    });
+}
+
+kglm_status serve_update(ServeSolve* s) { return guarded(s->d.c, [&] { s->d.update(); }); }
+
+kglm_status serve_finish(ServeSolve* s, bool stopped, SolveResult* r) {
+    SolveOut o;
+    const kglm_status st = guarded(s->d.c, [&] { s->d.finish(o, stopped); });
+    r->opt = o.opt;
+    r->gap = o.gap;
+    r->support = o.support;
+    r->nodes = o.nodes;
+    r->batches = o.batches;
+    r->cancelled = stopped;
+    delete s;
+    return st;
+}
+
+void serve_free(ServeSolve* s) { delete s; }
 
 kglm_status solve_cancellable(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
                               const std::atomic<int>* cancel, SolveResult* r) {

@@ -126,6 +126,26 @@ void exact_combine(cudaStream_t s, int m, int p, const float* Qs, int nq, size_t
                    const double* sigma, const double* tau, double ebound, double* Q, double* E);
 int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, const TcGemm& g,
             const GemmScratch* scr);
+// One problem of a grouped BF16 product (single operands): out[r][c] = sum_k A[arow0 + r][k] B[c][k],
+// r < M, c < N, k < K; the link epilogue (BF16 R, y, loss) or partial slices (pout, pstride, pld)
+// with split-K set from the problem alone (its tile count at width splits_bn, at most max_splits).
+struct TcGroupItem {
+    const TcMap* A;      // box rows 128
+    const TcMap* B;      // box rows = the launch's bn
+    int M, N, K, arow0;
+    void* out;
+    int ldo;
+    const float* y;
+    int loss;
+    float* pout;
+    size_t pstride;
+    int pld;
+    int max_splits;
+    int splits_bn;
+    int* splits_used;
+};
+// Up to 8 problems in one persistent launch of tile width bn, epi TC_EPI_LINK_BF16 or TC_EPI_PARTIAL.
+int tc_gemm_group(cudaStream_t s, const TcGroupItem* items, int np, int bn, int epi, int* err);
 
 struct ProxArgs {
     int m, p, W;
@@ -164,6 +184,17 @@ int prox_thread_options(int p, int* out);
 // launched, 1 when p is outside its range (no launch), -1 on a CUDA error.
 constexpr int kStreamMaxP = 4096;
 int prox_stream_f32(cudaStream_t s, const ProxArgs& a);
+// The streaming prox over the nodes of up to kGroupMax problems in one launch
+// (fills nbase, pmax, Wmax); 0 launched, 1 not this kernel's range (p above
+// the streaming limit or too few warps per SM), -1 attribute refused.
+constexpr int kGroupMax = 8;
+struct ProxGroup {
+    int np;
+    int nbase[kGroupMax + 1];
+    int pmax, Wmax;
+    ProxArgs a[kGroupMax];
+};
+int prox_stream_group(cudaStream_t s, ProxGroup& g);
 
 struct CertArgs {
     int m, n, p, W, k, kind;
@@ -304,6 +335,19 @@ struct SolveResult {
     int64_t nodes = 0, batches = 0;
     bool cancelled = false;
 };
+// The serving loop's steps on contexts with a device queue (open_cap > 0):
+// serve_begin starts a search, serve_select puts its next batch in place
+// (*m = 0: nothing open), serve_evaluate evaluates the selected batches of
+// several contexts that share one stream with the iterations in shared
+// launches (*shared: the launches that carried more than one), serve_update closes, branches and merges, serve_finish reports
+// (and frees the state; serve_free frees it without a report).
+struct ServeSolve;
+kglm_status serve_begin(kglm_ctx* c, int batch, ServeSolve** out);
+kglm_status serve_select(ServeSolve* s, int* m);
+kglm_status serve_evaluate(kglm_ctx* const* cs, int count, int iters, int check_every, int64_t* shared);
+kglm_status serve_update(ServeSolve* s);
+kglm_status serve_finish(ServeSolve* s, bool stopped, SolveResult* r);
+void serve_free(ServeSolve* s);
 // kglm_solve that also stops (between batches) once *cancel is non-zero.
 kglm_status solve_cancellable(kglm_ctx* ctx, int batch, int iters, int check_every, double time_limit_s,
                               const std::atomic<int>* cancel, SolveResult* r);

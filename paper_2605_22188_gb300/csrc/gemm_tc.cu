@@ -48,6 +48,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <string.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -113,6 +115,34 @@ struct TcArgs {
     TcJob jobs[kTcMaxJobs];
 };
 
+// One problem of a grouped launch (BF16, single operands, no split-K link):
+// its operand maps, shape, tiling and outputs; the fields the kernel reads per
+// unit carry the names of TcArgs.
+struct TcProb {
+    CUtensorMap tmA, tmB;
+    int M, N, arow0, mt, nt, nz, nkb, kb_per_split, m_fast;
+    void* out;
+    float* out_lo;
+    int ldo;
+    const float* y;
+    int loss;
+    float* pout;
+    size_t pstride;
+    int pld;
+    float* part;
+    int* counters;
+};
+// A grouped launch: the shared parameters (tile width, ring, instruction
+// descriptor, epilogue kind, error flag) in a, and up to kTcGroupMax problems
+// whose units are numbered consecutively (problem pi owns units ubase[pi] ..).
+constexpr int kTcGroupMax = 8;
+struct TcGroupArgs {
+    TcArgs a;
+    int np;
+    int ubase[kTcGroupMax + 1];
+    TcProb prob[kTcGroupMax];
+};
+
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -128,28 +158,30 @@ __device__ __forceinline__ float dloss_fast(float s, float y, int kind) {
     return kind == kLSQ ? 2.0f * (s - y) : __fdividef(-y, 1.0f + __expf(y * s));
 }
 
-// One output value v at (r, c) (r < M, c < N checked by the caller).
-__device__ __forceinline__ void tc_store(const TcArgs& a, int r, int c, float v, float yc, int zs) {
+// One output value v at (r, c) of problem q (r < M, c < N checked by the caller).
+template <class Q>
+__device__ __forceinline__ void tc_store(const TcArgs& a, const Q& q, int r, int c, float v, float yc, int zs) {
     if (a.epi == TC_EPI_PARTIAL) {
-        a.pout[(size_t)zs * a.pstride + (size_t)r * a.pld + c] = v;
+        q.pout[(size_t)zs * q.pstride + (size_t)r * q.pld + c] = v;
     } else if (a.epi == TC_EPI_STORE_F32) {
-        static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = v;
+        static_cast<float*>(q.out)[(size_t)r * q.ldo + c] = v;
     } else if (a.epi == TC_EPI_LINK_F32) {
-        const float d = dloss_fast(v, yc, a.loss);
+        const float d = dloss_fast(v, yc, q.loss);
         const float h = a.round_tf32 ? tf32_rn(d) : d;
-        static_cast<float*>(a.out)[(size_t)r * a.ldo + c] = h;
-        if (a.out_lo) a.out_lo[(size_t)r * a.ldo + c] = tf32_rn(d - h);
+        static_cast<float*>(q.out)[(size_t)r * q.ldo + c] = h;
+        if (q.out_lo) q.out_lo[(size_t)r * q.ldo + c] = tf32_rn(d - h);
     } else {
-        static_cast<__nv_bfloat16*>(a.out)[(size_t)r * a.ldo + c] = __float2bfloat16(dloss_fast(v, yc, a.loss));
+        static_cast<__nv_bfloat16*>(q.out)[(size_t)r * q.ldo + c] = __float2bfloat16(dloss_fast(v, yc, q.loss));
     }
 }
 
 // The unit's tile and K range.
 struct Unit {
-    int mtile, ntile, z, ka, kb, nloc, slice;
+    int mtile, ntile, z, ka, kb, nloc, slice, pi;   // pi: the problem (grouped launches), else 0
 };
 __device__ __forceinline__ Unit unit_of(const TcArgs& a, int u) {
     Unit w;
+    w.pi = 0;
     const int tiles = a.mt * a.nt;
     w.z = u / tiles;
     const int t = u - w.z * tiles;
@@ -172,6 +204,7 @@ __device__ __forceinline__ Unit unit_of(const TcArgs& a, int u) {
 // last one (odd row-tile count) reads rows past M and stores nothing.
 __device__ __forceinline__ Unit unit_of_pair(const TcArgs& a, int u, int crank) {
     Unit w;
+    w.pi = 0;
     const int mtp = (a.mt + 1) >> 1;
     const int tiles = mtp * a.nt;
     w.z = u / tiles;
@@ -343,12 +376,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int KIND, int NB, int NA, int CL>
-__global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                   const __grid_constant__ CUtensorMap tmB,
-                                                   const __grid_constant__ CUtensorMap tmB2,
-                                                   const __grid_constant__ CUtensorMap tmA2,
-                                                   const __grid_constant__ TcArgs a) {
+// The kernel body over a source of units and problems: SrcOne (the launch's
+// operand maps and TcArgs) or SrcGroup (a table of problems).
+template <int KIND, int NB, int NA, int CL, class S>
+__device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     const int STAGES = a.stages;
     const uint32_t SSTR = stage_stride(NA, NB, a.bn);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -372,17 +403,14 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
     // CL = 2: CTA pairs (clusters of two) walk pair units, sharing the B tile (one
     // multicast copy); every MMA completion frees the stage in both CTAs
     const int crank = CL == 2 ? (int)cluster_ctarank() : 0;
-    const int units = (CL == 2 ? (a.mt + 1) / 2 : a.mt) * a.nt * a.nz;
+    const int units = src.units(CL);
     const int ucta = blockIdx.x / CL, ustride = gridDim.x / CL;
-    auto unit = [&](int u) { return CL == 2 ? unit_of_pair(a, u, crank) : unit_of(a, u); };
+    auto unit = [&](int u) { return src.unit(u, CL, crank); };
 
     pdl_trigger();
     if (threadIdx.x == 32) {
         // descriptors of the operand maps into the TMA unit's cache before the first copy
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-        if (NB == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB2)) : "memory");
-        if (NA == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
+        src.prefetch(NB, NA);
     }
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), CL); }
@@ -408,6 +436,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
             bool ok = true;
             for (int u = ucta; u < units && ok; u += ustride) {
                 const Unit w = unit(u);
+                const auto& pq = src.q(w.pi);
                 const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
                 for (int i = 0; i < w.nloc; ++i, ++g) {
                     const int s = g % STAGES;
@@ -417,16 +446,16 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     mbar_expect_tx(fb, stage_bytes);
                     const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
                     uint8_t* sp = smem + (size_t)s * SSTR;
-                    tma_load_2d(smem_u32(sp), &tmA, kxa, a.arow0 + m0, fb);
-                    if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), &tmA2, kxa, a.arow0 + m0, fb);
+                    tma_load_2d(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, fb);
+                    if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), src.mapA2(w.pi), kxa, pq.arow0 + m0, fb);
                     if constexpr (CL == 2) {
                         if (crank == 0) {                   // B once, into both CTAs
-                            tma_load_2d_mc(smem_u32(sp + offB), &tmB, kxb, n0, fb, (uint16_t)3);
-                            if (NB == 2) tma_load_2d_mc(smem_u32(sp + offB2), &tmB2, kxb, n0, fb, (uint16_t)3);
+                            tma_load_2d_mc(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb, (uint16_t)3);
+                            if (NB == 2) tma_load_2d_mc(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb, (uint16_t)3);
                         }
                     } else {
-                        tma_load_2d(smem_u32(sp + offB), &tmB, kxb, n0, fb);
-                        if (NB == 2) tma_load_2d(smem_u32(sp + offB2), &tmB2, kxb, n0, fb);
+                        tma_load_2d(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb);
+                        if (NB == 2) tma_load_2d(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb);
                     }
                     issued = g + 1;
                 }
@@ -480,26 +509,27 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
         int li = 0;
         for (int u = ucta; u < units; u += ustride, ++li) {
             const Unit w = unit(u);
+            const auto& pq = src.q(w.pi);
             const int b = li & 1;
             const uint32_t use = (uint32_t)(li >> 1) & 1u;
             // the link's y of this warp's columns (lane l < 16 holds column c + l of
             // its chunk q at c = 16 h + 32 q), loaded before the wait so that the
             // epilogue does not wait on them per chunk
             float ypre[MAXBN / 32];
-            const bool linky = a.y != nullptr && a.nz == 1 && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16);
+            const bool linky = pq.y != nullptr && pq.nz == 1 && (a.epi == TC_EPI_LINK_F32 || a.epi == TC_EPI_LINK_BF16);
 #pragma unroll
             for (int q = 0; q < MAXBN / 32; ++q) {
                 const int cc = 16 * h + 32 * q + (lane & 15);
                 const int col = w.ntile * a.bn + cc;
-                ypre[q] = (linky && cc < a.bn && col < a.N) ? __ldg(a.y + col) : 0.f;
+                ypre[q] = (linky && cc < a.bn && col < pq.N) ? __ldg(pq.y + col) : 0.f;
             }
             const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[b]), use, a.err));
             if (!ok) break;
             tc_fence_after();
             const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
             const int rbase = m0 + quad * 32;             // this warp's 32 rows
-            const bool split = a.nz > 1 && a.epi != TC_EPI_PARTIAL;
-            const int tile = w.mtile * a.nt + w.ntile;
+            const bool split = pq.nz > 1 && a.epi != TC_EPI_PARTIAL;
+            const int tile = w.mtile * pq.nt + w.ntile;
             const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * MAXBN);
 #pragma unroll 1
             for (int c = 16 * h, q = 0; c < a.bn; c += 32, ++q) {
@@ -518,7 +548,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     for (int t = 0; t < MAXBN / 32; ++t)
                         if (t == q) yl = ypre[t];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), a.loss);
+                    for (int j = 0; j < 16; ++j) v[j] = dloss_fast(v[j], __shfl_sync(0xffffffffu, yl, j), pq.loss);
                 }
 #pragma unroll
                 for (int j = 0; j < 16; j += 4)                         // row lane, columns j..j+3
@@ -526,7 +556,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                 __syncwarp();
                 if (split) {
                     // 8 rows x 64 bytes per instruction
-                    float* pt = a.part + (((size_t)w.z * (a.mt * a.nt) + tile) * BM + quad * 32) * MAXBN + c;
+                    float* pt = pq.part + (((size_t)w.z * (pq.mt * pq.nt) + tile) * BM + quad * 32) * MAXBN + c;
                     const int qq = lane & 3, r0 = lane >> 2;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -536,16 +566,16 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     }
                 } else if (a.epi == TC_EPI_LINK_BF16) {
                     // 16 rows x 32 bytes per instruction (8 BF16 per lane)
-                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out);
+                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(pq.out);
                     const int qq = lane & 1, r0 = lane >> 1;
-                    const bool vec = (a.ldo % 8) == 0 && c0 + 8 * qq + 8 <= a.N;
+                    const bool vec = (pq.ldo % 8) == 0 && c0 + 8 * qq + 8 <= pq.N;
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const int r = r0 + 16 * i, row = rbase + r;
-                        if (row >= a.M) continue;
+                        if (row >= pq.M) continue;
                         const float4 x0 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * qq);
                         const float4 x1 = *reinterpret_cast<const float4*>(tb + r * TPAD + 8 * qq + 4);
-                        __nv_bfloat16* dst = o + (size_t)row * a.ldo + c0 + 8 * qq;
+                        __nv_bfloat16* dst = o + (size_t)row * pq.ldo + c0 + 8 * qq;
                         if (vec) {
                             __nv_bfloat162 hh[4] = {__floats2bfloat162_rn(x0.x, x0.y), __floats2bfloat162_rn(x0.z, x0.w),
                                                     __floats2bfloat162_rn(x1.x, x1.y), __floats2bfloat162_rn(x1.z, x1.w)};
@@ -554,25 +584,25 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                             const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
                             for (int t = 0; t < 8; ++t)
-                                if (c0 + 8 * qq + t < a.N) dst[t] = __float2bfloat16(xs[t]);
+                                if (c0 + 8 * qq + t < pq.N) dst[t] = __float2bfloat16(xs[t]);
                         }
                     }
                 } else {
                     // FP32 outputs (product, link, partial slice): 8 rows x 64 bytes per instruction
                     float* o;
                     size_t ld;
-                    if (a.epi == TC_EPI_PARTIAL) { o = a.pout + (size_t)w.slice * a.pstride; ld = (size_t)a.pld; }
-                    else { o = static_cast<float*>(a.out); ld = (size_t)a.ldo; }
+                    if (a.epi == TC_EPI_PARTIAL) { o = pq.pout + (size_t)w.slice * pq.pstride; ld = (size_t)pq.pld; }
+                    else { o = static_cast<float*>(pq.out); ld = (size_t)pq.ldo; }
                     const bool link = a.epi == TC_EPI_LINK_F32;
                     const bool rnd = link && a.round_tf32;
-                    float* ol = link ? a.out_lo : nullptr;
+                    float* ol = link ? pq.out_lo : nullptr;
                     const int qq = lane & 3, r0 = lane >> 2;
                     const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(o) % 16) == 0 &&
-                                     (ol == nullptr || (reinterpret_cast<uintptr_t>(ol) % 16) == 0) && c0 + 4 * qq + 4 <= a.N;
+                                     (ol == nullptr || (reinterpret_cast<uintptr_t>(ol) % 16) == 0) && c0 + 4 * qq + 4 <= pq.N;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int r = r0 + 8 * i, row = rbase + r;
-                        if (row >= a.M) continue;
+                        if (row >= pq.M) continue;
                         const float4 x = *reinterpret_cast<const float4*>(tb + r * TPAD + 4 * qq);
                         float xs[4] = {x.x, x.y, x.z, x.w}, ls[4] = {0.f, 0.f, 0.f, 0.f};
                         if (rnd) {
@@ -591,7 +621,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                         } else {
 #pragma unroll
                             for (int t = 0; t < 4; ++t)
-                                if (c0 + 4 * qq + t < a.N) {
+                                if (c0 + 4 * qq + t < pq.N) {
                                     dst[t] = xs[t];
                                     if (dlo) dlo[t] = ls[t];
                                 }
@@ -611,7 +641,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                 __syncwarp();
                 const int slab = (tile * 4 + quad) * 2 + h;
                 int last = 0;
-                if (lane == 0) last = atomicAdd(&a.counters[slab], 1) == a.nz - 1;
+                if (lane == 0) last = atomicAdd(&pq.counters[slab], 1) == pq.nz - 1;
                 last = __shfl_sync(0xffffffffu, last, 0);
                 if (last) {
                     __threadfence();
@@ -621,24 +651,24 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
                     for (int c = 16 * h; c < a.bn; c += 64) {
                         const int cc = c + (lane < 16 ? lane : 16 + lane);
                         const int col = n0 + cc;
-                        const bool in = cc < a.bn && col < a.N;
-                        const float yc = (in && a.y != nullptr) ? __ldg(a.y + col) : 0.f;
+                        const bool in = cc < a.bn && col < pq.N;
+                        const float yc = (in && pq.y != nullptr) ? __ldg(pq.y + col) : 0.f;
                         for (int r0 = 0; r0 < 32; r0 += 8) {
                             float acc[8];
 #pragma unroll
                             for (int rr = 0; rr < 8; ++rr) acc[rr] = 0.f;
                             if (in)
-                                for (int z = 0; z < a.nz; ++z) {
-                                    const float* pz = a.part + (((size_t)z * (a.mt * a.nt) + tile) * BM + quad * 32 + r0) * MAXBN + cc;
+                                for (int z = 0; z < pq.nz; ++z) {
+                                    const float* pz = pq.part + (((size_t)z * (pq.mt * pq.nt) + tile) * BM + quad * 32 + r0) * MAXBN + cc;
 #pragma unroll
                                     for (int rr = 0; rr < 8; ++rr) acc[rr] += __ldcg(pz + (size_t)rr * MAXBN);
                                 }
 #pragma unroll
                             for (int rr = 0; rr < 8; ++rr)
-                                if (in && rbase + r0 + rr < a.M) tc_store(a, rbase + r0 + rr, col, acc[rr], yc, 0);
+                                if (in && rbase + r0 + rr < pq.M) tc_store(a, pq, rbase + r0 + rr, col, acc[rr], yc, 0);
                         }
                     }
-                    if (lane == 0) a.counters[slab] = 0;
+                    if (lane == 0) pq.counters[slab] = 0;
                 }
             }
         }
@@ -661,6 +691,77 @@ __global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUten
         __syncwarp();
         cluster_sync();
     }
+}
+
+struct SrcOne {
+    const CUtensorMap *A, *B, *B2, *A2;
+    const TcArgs& a;
+    __device__ int units(int CL) const { return (CL == 2 ? (a.mt + 1) / 2 : a.mt) * a.nt * a.nz; }
+    __device__ Unit unit(int u, int CL, int crank) const { return CL == 2 ? unit_of_pair(a, u, crank) : unit_of(a, u); }
+    __device__ const TcArgs& q(int) const { return a; }
+    __device__ const CUtensorMap* mapA(int) const { return A; }
+    __device__ const CUtensorMap* mapB(int) const { return B; }
+    __device__ const CUtensorMap* mapB2(int) const { return B2; }
+    __device__ const CUtensorMap* mapA2(int) const { return A2; }
+    __device__ void prefetch(int nb, int na) const {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(A)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(B)) : "memory");
+        if (nb == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(B2)) : "memory");
+        if (na == 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(A2)) : "memory");
+    }
+};
+
+// The units of problem pi: its tiles (row tiles fastest if m_fast) times its K ranges.
+__device__ __forceinline__ Unit unit_of_prob(const TcProb& q, int u) {
+    Unit w;
+    const int tiles = q.mt * q.nt;
+    w.z = u / tiles;
+    const int t = u - w.z * tiles;
+    if (q.m_fast) { w.mtile = t % q.mt; w.ntile = t / q.mt; }
+    else          { w.ntile = t % q.nt; w.mtile = t / q.nt; }
+    w.ka = w.kb = w.z * q.kb_per_split;
+    w.nloc = max(0, min(q.nkb, w.ka + q.kb_per_split) - w.ka);
+    w.slice = w.z;
+    return w;
+}
+
+struct SrcGroup {
+    const TcGroupArgs& g;
+    __device__ int units(int) const { return g.ubase[g.np]; }
+    __device__ Unit unit(int u, int, int) const {
+        int pi = 0;
+        while (pi + 1 < g.np && u >= g.ubase[pi + 1]) ++pi;
+        Unit w = unit_of_prob(g.prob[pi], u - g.ubase[pi]);
+        w.pi = pi;
+        return w;
+    }
+    __device__ const TcProb& q(int pi) const { return g.prob[pi]; }
+    __device__ const CUtensorMap* mapA(int pi) const { return &g.prob[pi].tmA; }
+    __device__ const CUtensorMap* mapB(int pi) const { return &g.prob[pi].tmB; }
+    __device__ const CUtensorMap* mapB2(int pi) const { return &g.prob[pi].tmB; }
+    __device__ const CUtensorMap* mapA2(int pi) const { return &g.prob[pi].tmA; }
+    __device__ void prefetch(int, int) const {
+        for (int i = 0; i < g.np; ++i) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&g.prob[i].tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&g.prob[i].tmB)) : "memory");
+        }
+    }
+};
+
+template <int KIND, int NB, int NA, int CL>
+__global__ void __launch_bounds__(NT, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                   const __grid_constant__ CUtensorMap tmB,
+                                                   const __grid_constant__ CUtensorMap tmB2,
+                                                   const __grid_constant__ CUtensorMap tmA2,
+                                                   const __grid_constant__ TcArgs a) {
+    const SrcOne src{&tmA, &tmB, &tmB2, &tmA2, a};
+    tc_body<KIND, NB, NA, CL>(a, src);
+}
+
+// Several problems (the instances of the serving loop) in one persistent launch.
+__global__ void __launch_bounds__(NT, 1) k_tc_gemm_group(const __grid_constant__ TcGroupArgs g) {
+    const SrcGroup src{g};
+    tc_body<0, 1, 1, 1>(g.a, src);
 }
 
 // A wait that nothing ends: one thread waits on an mbarrier no thread arrives
@@ -850,6 +951,65 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     else e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 1, 1, 1>, ma, mb, mb2, ma, a)
                      : cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 1, 1>, ma, mb, mb2, ma, a);
     return e == cudaSuccess ? 0 : -7;
+}
+
+int tc_gemm_group(cudaStream_t s, const TcGroupItem* items, int np, int bn, int epi, int* err) {
+    static_assert(sizeof(TcGroupArgs) <= 32764, "kernel parameters of a grouped launch");
+    if (np <= 0) return 0;
+    if (np > kTcGroupMax || bn < 16 || bn > MAXBN || bn % 16 != 0) return -4;
+    if (epi != TC_EPI_LINK_BF16 && epi != TC_EPI_PARTIAL) return -4;
+    static const int rc = cudaFuncSetAttribute(k_tc_gemm_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kSmemMax) == cudaSuccess ? 0 : -1;
+    if (rc) return -5;
+    TcGroupArgs g{};
+    g.a.bn = bn;
+    g.a.epi = epi;
+    g.a.stages = ring_stages(1, 1, bn);
+    g.a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    g.a.round_tf32 = 0;
+    g.a.err = err;
+    g.np = np;
+    int units = 0;
+    for (int i = 0; i < np; ++i) {
+        const TcGroupItem& it = items[i];
+        TcProb& q = g.prob[i];
+        memcpy(&q.tmA, it.A->bytes, sizeof(CUtensorMap));
+        memcpy(&q.tmB, it.B->bytes, sizeof(CUtensorMap));
+        q.M = std::max(0, it.M);
+        q.N = it.N;
+        q.arow0 = it.arow0;
+        q.nkb = (it.K + 63) / 64;
+        q.mt = (q.M + BM - 1) / BM;
+        q.nt = (it.N + bn - 1) / bn;
+        // split-K of a partial product from the problem alone: its tile count at its
+        // own width, so that its slices do not depend on the other problems
+        int splits = 1;
+        if (epi == TC_EPI_PARTIAL && q.M > 0) {
+            const int tiles_alone = q.mt * ((it.N + it.splits_bn - 1) / it.splits_bn);
+            splits = std::max(1, std::min(it.max_splits, std::min((q.nkb + 3) / 4, std::max(1, SMS / tiles_alone))));
+        }
+        q.kb_per_split = (q.nkb + splits - 1) / splits;
+        splits = std::max(1, (q.nkb + q.kb_per_split - 1) / q.kb_per_split);
+        q.nz = splits;
+        if (it.splits_used) *it.splits_used = splits;
+        q.m_fast = it.N >= q.M;
+        q.out = it.out;
+        q.out_lo = nullptr;
+        q.ldo = it.ldo;
+        q.y = it.y;
+        q.loss = it.loss;
+        q.pout = it.pout;
+        q.pstride = it.pstride;
+        q.pld = it.pld;
+        q.part = nullptr;
+        q.counters = nullptr;
+        g.ubase[i] = units;
+        units += q.M > 0 ? q.mt * q.nt * q.nz : 0;
+    }
+    g.ubase[np] = units;
+    if (units == 0) return 0;
+    k_tc_gemm_group<<<grid_of(units), NT, smem_for(1, 1, bn), s>>>(g);
+    return 0;
 }
 
 int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, int bn, const TcJob* jobs,

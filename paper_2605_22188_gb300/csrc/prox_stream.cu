@@ -165,26 +165,31 @@ __device__ __forceinline__ void tail_above(const float4* su4, int p4, int lane, 
 // VEC = 4: 16-byte copies and stores (p a multiple of 4, 16-byte aligned rows);
 // VEC = 1: 4-byte ones.  Shared-memory passes use 16-byte accesses either way
 // (the padded rows).
+// Zero padding of a warp's rows past p (the passes read whole float4s).
+__device__ __forceinline__ void stream_pad(unsigned char* wbase, int p, int W, int lane) {
+    uint32_t* smi = reinterpret_cast<uint32_t*>(wbase + align16(sizeof(WarpHdr)));
+    float* su = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smi) + 2 * mask_bytes(W));
+    float* sv = su + row_bytes(p) / sizeof(float);
+    const int p4 = (p + 3) >> 2;
+    for (int j = p + lane; j < 4 * p4; j += 32) su[j] = sv[j] = 0.f;
+    __syncwarp();
+}
+
+// One node b of problem a by one warp, in the warp's shared-memory region wbase
+// (laid out for a.p and a.W, padding zeroed).
 template <int VEC>
-__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+__device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, unsigned char* wbase) {
     const int p = a.p, p4 = (p + 3) >> 2, W = a.W;
-    unsigned char* wbase = smem + (size_t)warp * warp_bytes(p, W);
     WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
     uint32_t* smi = reinterpret_cast<uint32_t*>(wbase + align16(sizeof(WarpHdr)));
     uint32_t* smo = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(smi) + mask_bytes(W));
     float* su = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smo) + mask_bytes(W));
     float* sv = su + row_bytes(p) / sizeof(float);
     float4* su4 = reinterpret_cast<float4*>(su);
-    for (int j = p + lane; j < 4 * p4; j += 32) su[j] = sv[j] = 0.f;   // padding: 0 for good
     const float eta = (float)a.eta, c = (float)a.c, M = (float)a.M, c1 = 1.f + c;
     const int nq = p / VEC;
-
-    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) {
-        if (a.active != nullptr && a.active[b] == 0) continue;
+    {
+        if (a.active != nullptr && a.active[b] == 0) return;
         const size_t base = (size_t)b * p;
         float* __restrict__ V = static_cast<float*>(a.V) + base;
         float* __restrict__ Bm = static_cast<float*>(a.B) + base;
@@ -523,6 +528,39 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
 }
 
 template <int VEC>
+__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    unsigned char* wbase = smem + (size_t)warp * warp_bytes(a.p, a.W);
+    stream_pad(wbase, a.p, a.W, lane);
+    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) stream_node<VEC>(a, b, lane, wbase);
+}
+
+// The nodes of several problems (instances of the serving loop) in one launch:
+// node t < total belongs to the problem pi with nbase[pi] <= t < nbase[pi + 1];
+// every warp's region is sized for the largest p and W and laid out anew (its
+// padding zeroed) when the warp moves to another problem.
+template <int VEC>
+__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream_group(const __grid_constant__ ProxGroup g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    unsigned char* wbase = smem + (size_t)warp * warp_bytes(g.pmax, g.Wmax);
+    int last = -1;
+    for (int t = blockIdx.x * wpc + warp; t < g.nbase[g.np]; t += gridDim.x * wpc) {
+        int pi = 0;
+        while (pi + 1 < g.np && t >= g.nbase[pi + 1]) ++pi;
+        const ProxArgs& a = g.a[pi];
+        if (pi != last) {
+            stream_pad(wbase, a.p, a.W, lane);
+            last = pi;
+        }
+        stream_node<VEC>(a, t - g.nbase[pi], lane, wbase);
+    }
+}
+
+template <int VEC>
 int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
     const size_t smem = (size_t)wpc * warp_bytes(a.p, a.W);
     auto kern = k_prox_stream<VEC>;
@@ -557,6 +595,54 @@ int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
 
 int prox_stream_warps(int p, int W) {
     return (int)std::min<size_t>(kStreamMaxWarps, kSmemPerSM / warp_bytes(p, W));
+}
+
+namespace {
+bool stream_vec_ok(const ProxArgs& a) {
+    return (a.p % 4 == 0) && ((uintptr_t)a.V % 16 == 0) && ((uintptr_t)a.B % 16 == 0) &&
+           (a.Vop == nullptr || (a.op_ld % 4 == 0 && (uintptr_t)a.Vop % 16 == 0 &&
+                                 (a.Vop_lo == nullptr || (uintptr_t)a.Vop_lo % 16 == 0))) &&
+           (a.gsplits == 0 ? ((uintptr_t)a.G % 16 == 0) : ((uintptr_t)a.Gpart % 16 == 0 && a.gstride % 4 == 0));
+}
+
+template <int VEC>
+int launch_stream_group(cudaStream_t s, const ProxGroup& g, int wpc) {
+    auto kern = k_prox_stream_group<VEC>;
+    {
+        static std::mutex mu;
+        static bool opted = false;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!opted) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPerSM) != cudaSuccess)
+                return -1;
+            opted = true;
+        }
+    }
+    const int total = g.nbase[g.np];
+    const int grid = std::max(1, std::min(kSMs, (total + wpc - 1) / wpc));
+    kern<<<grid, 32 * wpc, (size_t)wpc * warp_bytes(g.pmax, g.Wmax), s>>>(g);
+    return 0;
+}
+}  // namespace
+
+int prox_stream_group(cudaStream_t s, ProxGroup& g) {
+    if (g.np <= 0 || g.np > kGroupMax) return 1;
+    g.pmax = 0;
+    g.Wmax = 0;
+    bool vec = true;
+    g.nbase[0] = 0;
+    for (int i = 0; i < g.np; ++i) {
+        const ProxArgs& a = g.a[i];
+        if (a.p > kStreamMaxP) return 1;
+        g.pmax = std::max(g.pmax, a.p);
+        g.Wmax = std::max(g.Wmax, a.W);
+        vec = vec && stream_vec_ok(a);
+        g.nbase[i + 1] = g.nbase[i] + std::max(0, a.m);
+    }
+    if (g.nbase[g.np] == 0) return 0;
+    const int wpc = prox_stream_warps(g.pmax, g.Wmax);
+    if (wpc < kStreamMinWarps) return 1;
+    return vec ? launch_stream_group<4>(s, g, wpc) : launch_stream_group<1>(s, g, wpc);
 }
 
 int prox_stream_f32(cudaStream_t s, const ProxArgs& a) {

@@ -1,16 +1,22 @@
 // Serving loop: BnB instances (problem (intro_sparse_glm) of §1, each certified
-// by the hybrid loop of Fig. 1) admitted as they arrive, solved concurrently.
+// by the hybrid loop of Fig. 1) admitted as they arrive and solved together.
 //
-// Requests wait in a FIFO.  A request is admitted when a worker is free and
-// its device footprint (the exact byte count kglm_create will allocate) fits
-// in what the admitted requests leave of the HBM budget; it then gets its own
-// context, stream and host worker thread, so its node batches run on the
-// device while other requests' batches do (kernels of different streams share
-// the SMs) and its host-side tree work overlaps their device work.  When it
-// finishes, its memory returns to the budget and the next request in line is
-// admitted: continuous batching at request granularity.  Every request runs
-// the same deterministic kernels in the same order as kglm_solve alone, so
-// its result does not depend on the mix.
+// Requests wait in a FIFO.  A request is admitted when a slot is free
+// (max_active) and its device footprint (the exact byte count kglm_create
+// will allocate, its device-resident open-node queue included) fits in what
+// the admitted requests leave of the HBM budget.  Its X and node queue then
+// live on the device, and one scheduler thread runs rounds: every running
+// request's next node batch is selected on the device, the selected batches
+// are evaluated together -- the FISTA iterations of the BF16 requests as
+// shared launches (one grouped S = X V + link, one grouped G = X^T R and one
+// prox over all of their nodes per iteration), the others with their own
+// launches on the same stream -- and each request's batch is closed,
+// branched and merged into its queue on the device.  A request that arrives
+// while others run is admitted at the next round that has a slot and memory
+// for it: continuous batching at node-batch granularity.  Each request's
+// nodes see the same arithmetic whatever else shares the launches (its tiles,
+// split-K slices and node-level work depend on its own shapes only), so its
+// result does not depend on the mix.
 #include <math.h>
 #include <stdio.h>
 
@@ -57,7 +63,9 @@ struct kglm_server {
     int active = 0, peak_active = 0;
     bool stopping = false;
     std::atomic<int> cancel{0};
-    std::vector<std::thread> workers;
+    std::thread scheduler;
+    cudaStream_t stream = nullptr;     // every request's context runs on it
+    int64_t rounds = 0, round_batches = 0, shared_launches = 0;
     std::string err = "no error";
 };
 
@@ -65,65 +73,165 @@ namespace {
 
 double since(const kglm_server* s) { return std::chrono::duration<double>(Clock::now() - s->t0).count(); }
 
-// Solve one admitted request on its own context and stream (no lock held;
-// the result is published by the caller under the lock).
-kglm_request_info run_request(kglm_server* s, Req* r, kglm_request_info in) {
-    kglm_desc d = r->d;
-    d.hbm_budget = in.device_bytes + 65536;   // the admitted share (plus rounding of small arrays)
+// The scheduler: one host thread runs rounds over the admitted requests.  A
+// round admits what the queue, the slots and the budget allow (each admitted
+// request gets a context on the server's stream with its open-node queue on
+// the device, and starts its search), selects the next node batch of every
+// running request on the device, evaluates all selected batches together
+// (serve_evaluate: the iterations of the BF16 requests as shared launches),
+// and closes, branches and merges each request's batch on the device.  A
+// request whose queue is empty (or whose time limit passed) is finished: its
+// result is published and its memory returns to the budget.
+struct Running {
+    Req* r = nullptr;
     kglm_ctx* ctx = nullptr;
-    kglm_status st = kglm_create(&d, r->X.data(), r->y.data(), nullptr, &ctx);
-    const char* msg = st == KGLM_OK ? "" : kglm_last_error(nullptr);
-    if (st == KGLM_OK) {
-        SolveResult res;
-        st = solve_cancellable(ctx, d.max_batch, s->d.iters, s->d.check_every, s->d.time_limit_s, &s->cancel, &res);
-        if (st != KGLM_OK) msg = kglm_last_error(ctx);
-        if (st == KGLM_OK) {
-            in.opt = res.opt;
-            in.gap = res.gap;
-            in.nodes = res.nodes;
-            in.batches = res.batches;
-            for (int t = 0; t < KGLM_MAX_K; ++t) in.support[t] = t < (int)res.support.size() ? res.support[t] : -1;
-            in.state = res.cancelled ? KGLM_REQ_CANCELLED : KGLM_REQ_DONE;
-        }
-        if (st != KGLM_OK) snprintf(in.message, sizeof(in.message), "%s", msg);
-        kglm_destroy(ctx);
-    } else {
-        snprintf(in.message, sizeof(in.message), "%s", msg);
-    }
-    if (st != KGLM_OK) in.state = KGLM_REQ_FAILED;
-    in.status = st;
-    std::vector<double>().swap(r->X);   // the host copy is no longer needed
-    std::vector<double>().swap(r->y);
-    return in;
+    ServeSolve* sv = nullptr;
+    Clock::time_point t_start;
+};
+
+// Publish a finished request and release its slot and memory (the caller holds no lock).
+void publish(kglm_server* s, Running& a, const kglm_request_info& info) {
+    std::vector<double>().swap(a.r->X);   // the host copy is no longer needed
+    std::vector<double>().swap(a.r->y);
+    std::lock_guard<std::mutex> g(s->mu);
+    a.r->info = info;
+    a.r->info.t_done = since(s);
+    s->used -= a.r->info.device_bytes;
+    --s->active;
+    ++s->finished;
+    s->cv_done.notify_all();
 }
 
-void worker_main(kglm_server* s) {
+void fail(kglm_server* s, Running& a, kglm_status st, const char* msg) {
+    kglm_request_info info = a.r->info;
+    info.state = KGLM_REQ_FAILED;
+    info.status = st;
+    snprintf(info.message, sizeof(info.message), "%s", msg);
+    if (a.sv) serve_free(a.sv);
+    a.sv = nullptr;
+    if (a.ctx) kglm_destroy(a.ctx);
+    a.ctx = nullptr;
+    publish(s, a, info);
+}
+
+void finish(kglm_server* s, Running& a, bool stopped, bool cancelled) {
+    SolveResult res;
+    const kglm_status st = serve_finish(a.sv, stopped, &res);
+    a.sv = nullptr;
+    if (st != KGLM_OK) {
+        fail(s, a, st, kglm_last_error(a.ctx));
+        return;
+    }
+    kglm_request_info info = a.r->info;
+    info.opt = res.opt;
+    info.gap = res.gap;
+    info.nodes = res.nodes;
+    info.batches = res.batches;
+    for (int t = 0; t < KGLM_MAX_K; ++t) info.support[t] = t < (int)res.support.size() ? res.support[t] : -1;
+    info.state = cancelled ? KGLM_REQ_CANCELLED : KGLM_REQ_DONE;
+    info.status = KGLM_OK;
+    kglm_destroy(a.ctx);
+    a.ctx = nullptr;
+    publish(s, a, info);
+}
+
+// Context and search of an admitted request on the server's stream.
+bool start(kglm_server* s, Running& a) {
+    kglm_desc d = a.r->d;
+    d.hbm_budget = a.r->info.device_bytes + 65536;   // the admitted share (plus rounding of small arrays)
+    kglm_status st = kglm_create(&d, a.r->X.data(), a.r->y.data(), s->stream, &a.ctx);
+    if (st != KGLM_OK) {
+        a.ctx = nullptr;
+        fail(s, a, st, kglm_last_error(nullptr));
+        return false;
+    }
+    st = serve_begin(a.ctx, d.max_batch, &a.sv);
+    if (st != KGLM_OK) {
+        fail(s, a, st, kglm_last_error(a.ctx));
+        return false;
+    }
+    a.t_start = Clock::now();
+    return true;
+}
+
+void scheduler_main(kglm_server* s) {
     cudaSetDevice(s->device);
-    std::unique_lock<std::mutex> lk(s->mu);
+    std::vector<Running> run;
     for (;;) {
-        s->cv.wait(lk, [&] {
-            return s->stopping || (!s->pending.empty() && s->used + s->pending.front()->info.device_bytes <= s->budget);
-        });
-        if (s->stopping) return;
-        Req* r = s->pending.front();
-        s->pending.pop_front();
-        s->used += r->info.device_bytes;
-        s->peak_used = std::max(s->peak_used, s->used);
-        s->peak_active = std::max(s->peak_active, ++s->active);
-        r->info.state = KGLM_REQ_RUNNING;
-        r->info.t_admit = since(s);
-        const kglm_request_info start = r->info;
-        s->cv.notify_all();   // another worker may admit the next one
-        lk.unlock();
-        const kglm_request_info res = run_request(s, r, start);
-        lk.lock();
-        r->info = res;
-        r->info.t_done = since(s);
-        s->used -= r->info.device_bytes;
-        --s->active;
-        ++s->finished;
-        s->cv.notify_all();
-        s->cv_done.notify_all();
+        std::vector<Running> admitted;
+        bool stop = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (run.empty()) s->cv.wait(lk, [&] { return s->stopping || !s->pending.empty(); });
+            stop = s->stopping;
+            while (!stop && !s->pending.empty() && (int)(run.size() + admitted.size()) < s->d.max_active &&
+                   s->used + s->pending.front()->info.device_bytes <= s->budget) {
+                Req* r = s->pending.front();
+                s->pending.pop_front();
+                s->used += r->info.device_bytes;
+                s->peak_used = std::max(s->peak_used, s->used);
+                s->peak_active = std::max(s->peak_active, ++s->active);
+                r->info.state = KGLM_REQ_RUNNING;
+                r->info.t_admit = since(s);
+                Running a;
+                a.r = r;
+                admitted.push_back(a);
+            }
+        }
+        for (Running& a : admitted)
+            if (start(s, a)) run.push_back(a);
+        if (stop || s->cancel.load()) {
+            for (Running& a : run) finish(s, a, true, true);
+            return;
+        }
+        if (run.empty()) continue;
+        // select every running request's next batch; finished ones leave
+        std::vector<Running> next;
+        std::vector<kglm_ctx*> sel;
+        std::vector<size_t> who;
+        for (Running& a : run) {
+            const double el = std::chrono::duration<double>(Clock::now() - a.t_start).count();
+            if (s->d.time_limit_s > 0 && el > s->d.time_limit_s) {
+                finish(s, a, true, false);
+                continue;
+            }
+            int m = 0;
+            const kglm_status st = serve_select(a.sv, &m);
+            if (st != KGLM_OK) {
+                fail(s, a, st, kglm_last_error(a.ctx));
+                continue;
+            }
+            if (m == 0) {
+                finish(s, a, false, false);
+                continue;
+            }
+            who.push_back(next.size());
+            next.push_back(a);
+            sel.push_back(a.ctx);
+        }
+        run.swap(next);
+        if (sel.empty()) continue;
+        int64_t shared = 0;
+        const kglm_status st = serve_evaluate(sel.data(), (int)sel.size(), s->d.iters, s->d.check_every, &shared);
+        if (st != KGLM_OK) {
+            const std::string msg = kglm_last_error(sel[0]);
+            for (Running& a : run) fail(s, a, st, msg.c_str());
+            run.clear();
+            continue;
+        }
+        std::vector<Running> keep;
+        for (Running& a : run) {
+            const kglm_status su = serve_update(a.sv);
+            if (su != KGLM_OK) fail(s, a, su, kglm_last_error(a.ctx));
+            else keep.push_back(a);
+        }
+        run.swap(keep);
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            ++s->rounds;
+            s->round_batches += (int64_t)sel.size();
+            s->shared_launches += shared;
+        }
     }
 }
 
@@ -162,8 +270,14 @@ kglm_status kglm_server_create(const kglm_server_desc* desc, kglm_server** out) 
     s->device = dev;
     s->budget = budget;
     s->t0 = Clock::now();
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s->stream = nullptr;
+        kglm_server_destroy(s);
+        return KGLM_ECUDA;
+    }
     try {
-        for (int w = 0; w < desc->max_active; ++w) s->workers.emplace_back(worker_main, s);
+        s->scheduler = std::thread(scheduler_main, s);
     } catch (...) {
         kglm_server_destroy(s);
         return KGLM_ENOMEM;
@@ -194,6 +308,8 @@ kglm_status kglm_server_submit(kglm_server* s, const kglm_desc* desc, const doub
         }
         d.max_batch = m;
     }
+    // the request's open nodes stay on the device
+    d.open_cap = s->d.open_cap > 0 ? s->d.open_cap : std::max<int64_t>(4096, 16 * (int64_t)d.max_batch);
     int64_t bytes = 0;
     kglm_status st = kglm_estimate_bytes(&d, &bytes);
     if (st != KGLM_OK) {
@@ -292,6 +408,9 @@ kglm_status kglm_server_stats(kglm_server* s, kglm_server_stats_t* out) {
     out->peak_bytes = s->peak_used;
     out->budget = s->budget;
     out->elapsed_s = since(s);
+    out->rounds = s->rounds;
+    out->round_batches = s->round_batches;
+    out->shared_launches = s->shared_launches;
     return KGLM_OK;
 }
 
@@ -309,8 +428,8 @@ void kglm_server_destroy(kglm_server* s) {
     }
     s->cancel.store(1);
     s->cv.notify_all();
-    for (auto& t : s->workers)
-        if (t.joinable()) t.join();
+    if (s->scheduler.joinable()) s->scheduler.join();
+    if (s->stream) cudaStreamDestroy(s->stream);
     for (auto& kv : s->reqs) delete kv.second;
     delete s;
 }

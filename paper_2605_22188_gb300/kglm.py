@@ -93,7 +93,8 @@ _SIGS = {
 }
 class kglm_server_desc(C.Structure):
     _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int32), ("batch_cap", C.c_int32),
-                ("iters", C.c_int32), ("check_every", C.c_int32), ("time_limit_s", C.c_double)]
+                ("iters", C.c_int32), ("check_every", C.c_int32), ("time_limit_s", C.c_double),
+                ("open_cap", C.c_int64)]
 
 
 class kglm_request_info(C.Structure):
@@ -107,7 +108,8 @@ class kglm_request_info(C.Structure):
 class kglm_server_stats_t(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("finished", C.c_int64), ("queued", C.c_int64),
                 ("active", C.c_int32), ("peak_active", C.c_int32), ("bytes_in_use", C.c_int64),
-                ("peak_bytes", C.c_int64), ("budget", C.c_int64), ("elapsed_s", C.c_double)]
+                ("peak_bytes", C.c_int64), ("budget", C.c_int64), ("elapsed_s", C.c_double),
+                ("rounds", C.c_int64), ("round_batches", C.c_int64), ("shared_launches", C.c_int64)]
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
@@ -478,9 +480,11 @@ def _info_dict(i):
 class Server:
     """kglm_server_*: certified solves of many instances admitted as they arrive."""
 
-    def __init__(self, max_active=8, hbm_budget=0, iters=200, check_every=10, time_limit_s=0.0, batch_cap=0):
+    def __init__(self, max_active=8, hbm_budget=0, iters=200, check_every=10, time_limit_s=0.0, batch_cap=0,
+                 open_cap=0):
         d = kglm_server_desc(hbm_budget=int(hbm_budget), max_active=int(max_active), batch_cap=int(batch_cap),
-                             iters=int(iters), check_every=int(check_every), time_limit_s=float(time_limit_s))
+                             iters=int(iters), check_every=int(check_every), time_limit_s=float(time_limit_s),
+                             open_cap=int(open_cap))
         out = P()
         st = lib().kglm_server_create(C.byref(d), C.byref(out))
         if st != KGLM_OK:

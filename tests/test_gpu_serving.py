@@ -1,9 +1,14 @@
 """The serving loop (kglm_server_*) and the device footprint used for its admission.
 
-* Every result is the same alone and in the mix: each request runs the same
-  deterministic kernels in the same order as kglm_solve on a private context,
-  so objective, support and node count are compared exactly (FP64 and reduced
-  precision alike); two small instances are also checked against brute force.
+* Every result is the same alone and in the mix: a request's nodes see the
+  same arithmetic whatever shares its rounds and launches, so objective,
+  support and node count are compared exactly with the request alone on the
+  server (FP64 and reduced precision alike); requests whose iterations run
+  their own launches also equal kglm_solve exactly, BF16 ones its certified
+  optimum; small instances are also checked against brute force.
+* Shared launches: BF16 requests in flight together are evaluated by grouped
+  products and a grouped prox (the server counts the launches that carried
+  more than one request).
 * Admission: FIFO order, the bytes in use never pass the budget, the footprint
   kglm_estimate_bytes predicts is what kglm_create allocates.
 * Failures stay inside their request: bad data fails that request only, an
@@ -54,14 +59,29 @@ ITERS, CHECK = 200, 10
 
 
 def _alone(inst):
+    """The request on a server of its own (nothing shares its rounds or launches)."""
+    with kglm.Server(max_active=1, iters=ITERS, check_every=CHECK) as srv:
+        r = srv.submit(inst["X"], inst["y"], inst["k"], inst["lam2"], inst["M"], inst["kind"], prec=inst["prec"],
+                       max_batch=inst["batch"])
+        return srv.wait(r, timeout=300)
+
+
+def _engine(inst):
     with kglm.Engine(inst["X"], inst["y"], inst["k"], inst["lam2"], inst["M"], inst["kind"], prec=inst["prec"],
                      max_batch=inst["batch"]) as eng:
         return eng.solve(inst["batch"], ITERS, CHECK)
 
 
 def test_each_result_is_the_same_alone_and_in_the_mix():
+    """Bit for bit against the request alone on the server; against kglm_solve
+    (host queue, the context's own launches): identical in the precisions whose
+    iterations do not share launches (the device queue evaluates the host queue's
+    nodes in its order), the same certified optimum and support in BF16 (its
+    grouped products tile the link product without split-K, which rounds S
+    differently)."""
     mix = _mix()
     alone = [_alone(inst) for inst in mix]
+    eng = [_engine(inst) for inst in mix]
     fp = [kglm.kglm_estimate_bytes(kglm.make_desc(i["X"].shape[0], i["X"].shape[1], i["k"], i["lam2"], i["M"],
                                                   i["kind"], i["prec"], i["batch"])) for i in mix]
     budget = int(sum(sorted(fp)[-3:]))          # at most three at once: later requests queue
@@ -72,12 +92,17 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         infos = [srv.info(r) for r in ids]
         st = srv.stats()
     assert st["finished"] == len(mix) and st["peak_bytes"] <= budget and st["peak_active"] <= 4
-    for a, b in zip(alone, infos):
+    for inst, a, b, e in zip(mix, alone, infos, eng):
         assert b["state"] == kglm.REQ_DONE and b["status"] == 0
         assert b["opt"] == a["opt"], (b["opt"], a["opt"])
         assert b["support"] == a["support"]
         assert b["nodes"] == a["nodes"] and b["batches"] == a["batches"]
         assert b["gap"] <= 1e-6
+        if inst["prec"] == "bf16":
+            assert abs(b["opt"] - e["opt"]) <= 2e-6 * max(1.0, abs(e["opt"])) and b["support"] == e["support"]
+        else:
+            assert (b["opt"], b["support"], b["nodes"], b["batches"]) == (e["opt"], e["support"], e["nodes"],
+                                                                          e["batches"])
     # the two smallest are also checked against brute force
     for inst, b in list(zip(mix, infos))[:2]:
         top = ro.brute_force(inst["X"], inst["y"], inst["k"], inst["lam2"], inst["M"], inst["kind"], top=1)
@@ -162,3 +187,32 @@ def test_contexts_with_different_k_evaluate_concurrently():
     for t in ts:
         t.join()
     assert not errors, errors
+
+
+def test_bf16_requests_share_launches_and_keep_their_results():
+    """Five BF16 requests of different n, p, k and both losses run at once: their
+    iterations go through grouped launches (the server counts launches that carried
+    more than one request) and each result equals the request alone, bit for bit;
+    the small ones equal brute force."""
+    specs = [(synth.LSQ, 200, 20, 3, 1e-3, 0.8, 2.0, 32), (synth.LOGISTIC, 300, 18, 3, 2e-2, 0.6, 5.0, 64),
+             (synth.LSQ, 500, 260, 6, 1e-3, 0.5, 4.0, 128), (synth.LOGISTIC, 700, 150, 5, 1e-2, 0.5, 5.0, 96),
+             (synth.LSQ, 1200, 300, 8, 1e-3, 0.6, 3.0, 256)]
+    mix = []
+    for i, (kind, n, p, k, lam2, rho, snr, batch) in enumerate(specs):
+        X, y, _ = synth.instance(n, p, k, kind, rho=rho, snr=snr, seed=300 + i)
+        mix.append(dict(X=X, y=y, k=k, lam2=lam2, M=2.0, kind=kind, prec="bf16", batch=batch))
+    alone = [_alone(inst) for inst in mix]
+    with kglm.Server(max_active=8, iters=ITERS, check_every=CHECK) as srv:
+        ids = [srv.submit(i["X"], i["y"], i["k"], i["lam2"], i["M"], i["kind"], prec="bf16", max_batch=i["batch"])
+               for i in mix]
+        srv.drain(timeout=300)
+        infos = [srv.info(r) for r in ids]
+        st = srv.stats()
+    assert st["shared_launches"] > 0 and st["round_batches"] > st["rounds"], st
+    for a, b in zip(alone, infos):
+        assert b["state"] == kglm.REQ_DONE and b["gap"] <= 1e-6
+        assert (b["opt"], b["support"], b["nodes"], b["batches"]) == (a["opt"], a["support"], a["nodes"],
+                                                                      a["batches"])
+    for inst, b in list(zip(mix, infos))[:2]:
+        top = ro.brute_force(inst["X"], inst["y"], inst["k"], inst["lam2"], inst["M"], inst["kind"], top=1)
+        assert abs(b["opt"] - top[0][0]) <= 1e-6 * max(1.0, abs(top[0][0]))
