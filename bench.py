@@ -680,6 +680,7 @@ def serving_summary(args):
         "certified": len(cert), "not_certified": len(infos) - len(cert),
         "failed": sum(1 for i in infos if i["state"] == kglm.REQ_FAILED),
         "worst_gap": max(i["gap"] for i in infos), "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
+        "rounds": st["rounds"], "round_batches": st["round_batches"], "shared_launches": st["shared_launches"],
         "clocks": clk.summary(),
         "per_request": [{"n": sp["n"], "p": sp["p"], "k": sp["k"],
                          "loss": "lsq" if sp["kind"] == synth.LSQ else "logistic", "rho": sp["rho"],

@@ -417,7 +417,9 @@ typedef struct {
     int32_t iters;        /* FISTA iterations per node evaluation (kglm_solve's iters), >= 1 */
     int32_t check_every;  /* certificate every check_every iterations (kglm_solve's), >= 0 */
     double time_limit_s;  /* per request, counted from admission; <= 0: none */
-    int64_t open_cap;     /* open nodes each request's device queue holds; 0: max(4096, 16 max_batch) */
+    int64_t open_cap;     /* open nodes each request's device queue holds; 0: what a quarter of
+                             budget / max_active holds (at most 1 GiB or 2^22 nodes, at least
+                             64 max_batch) */
 } kglm_server_desc;
 
 enum { KGLM_REQ_QUEUED = 0, KGLM_REQ_RUNNING = 1, KGLM_REQ_DONE = 2, KGLM_REQ_FAILED = 3, KGLM_REQ_CANCELLED = 4 };

@@ -308,8 +308,16 @@ kglm_status kglm_server_submit(kglm_server* s, const kglm_desc* desc, const doub
         }
         d.max_batch = m;
     }
-    // the request's open nodes stay on the device
-    d.open_cap = s->d.open_cap > 0 ? s->d.open_cap : std::max<int64_t>(4096, 16 * (int64_t)d.max_batch);
+    // the request's open nodes stay on the device: by default as many as a quarter
+    // of one slot's share of the budget holds (two buffers of masks, bound, id and
+    // slot per node), at most 1 GiB or 2^22 nodes and at least 64 batches
+    if (s->d.open_cap > 0) {
+        d.open_cap = s->d.open_cap;
+    } else {
+        const int64_t per = 2 * (20 + 8 * ((d.p + 31) / 32));
+        const int64_t bytes = std::min<int64_t>(1LL << 30, s->budget / (4 * std::max(1, s->d.max_active)));
+        d.open_cap = std::max<int64_t>(64 * (int64_t)d.max_batch, std::min<int64_t>(1 << 22, bytes / per));
+    }
     int64_t bytes = 0;
     kglm_status st = kglm_estimate_bytes(&d, &bytes);
     if (st != KGLM_OK) {
