@@ -88,10 +88,13 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size
 // a row of p floats padded to a multiple of 4 (the padding stays 0)
 __host__ __device__ inline size_t row_bytes(int p) { return align16((size_t)p * sizeof(float)); }
 __host__ __device__ inline size_t mask_bytes(int W) { return align16((size_t)W * sizeof(uint32_t)); }
-// per warp: header, two mask rows, then the u (G) and v rows (beta_old is read
-// from global memory by the write pass, its only use)
-__host__ __device__ inline size_t warp_bytes(int p, int W) {
-    return align16(sizeof(WarpHdr)) + 2 * mask_bytes(W) + 2 * row_bytes(p);
+// per warp: a header, then `sets` row sets of two mask rows and the u (G) and v
+// rows (beta_old is read from global memory by the write pass, its only use).
+// With two sets the rows of the warp's next node arrive while it works on the
+// current one.
+__host__ __device__ inline size_t set_bytes(int p, int W) { return 2 * mask_bytes(W) + 2 * row_bytes(p); }
+__host__ __device__ inline size_t warp_bytes(int p, int W, int sets = 1) {
+    return align16(sizeof(WarpHdr)) + (size_t)sets * set_bytes(p, W);
 }
 
 __device__ __forceinline__ float entry_pt(float a, float c, float M) {
@@ -112,10 +115,7 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 // Tensor-core operand copy of 4 consecutive values of v' (index i, a multiple of 4).
 __device__ __forceinline__ void store_operand4(void* base, float* lo, size_t i, float4 v, int bf16) {
@@ -165,35 +165,59 @@ __device__ __forceinline__ void tail_above(const float4* su4, int p4, int lane, 
 // VEC = 4: 16-byte copies and stores (p a multiple of 4, 16-byte aligned rows);
 // VEC = 1: 4-byte ones.  Shared-memory passes use 16-byte accesses either way
 // (the padded rows).
-// Zero padding of a warp's rows past p (the passes read whole float4s).
-__device__ __forceinline__ void stream_pad(unsigned char* wbase, int p, int W, int lane) {
-    uint32_t* smi = reinterpret_cast<uint32_t*>(wbase + align16(sizeof(WarpHdr)));
-    float* su = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smi) + 2 * mask_bytes(W));
+// Zero padding of a row set's rows past p (the passes read whole float4s).
+__device__ __forceinline__ void stream_pad(unsigned char* rows, int p, int W, int lane) {
+    float* su = reinterpret_cast<float*>(rows + 2 * mask_bytes(W));
     float* sv = su + row_bytes(p) / sizeof(float);
     const int p4 = (p + 3) >> 2;
     for (int j = p + lane; j < 4 * p4; j += 32) su[j] = sv[j] = 0.f;
     __syncwarp();
 }
 
-// One node b of problem a by one warp, in the warp's shared-memory region wbase
-// (laid out for a.p and a.W, padding zeroed).
+// A. node b's masks, G and V rows into the row set `rows` (asynchronous copies,
+// one commit group).
 template <int VEC>
-__device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, unsigned char* wbase) {
+__device__ __forceinline__ void stream_issue(const ProxArgs& a, int b, int lane, unsigned char* rows) {
+    const int p = a.p, W = a.W, nq = p / VEC;
+    uint32_t* smi = reinterpret_cast<uint32_t*>(rows);
+    uint32_t* smo = reinterpret_cast<uint32_t*>(rows + mask_bytes(W));
+    float* su = reinterpret_cast<float*>(rows + 2 * mask_bytes(W));
+    float* sv = su + row_bytes(p) / sizeof(float);
+    const size_t base = (size_t)b * p;
+    const float* V = static_cast<const float*>(a.V) + base;
+    const float* G0 = a.gsplits == 0 ? static_cast<const float*>(a.G) + base : a.Gpart + base;
+    for (int q = lane; q < W; q += 32) {
+        cp_async4(smi + q, a.in_mask + (size_t)b * W + q);
+        cp_async4(smo + q, a.out_mask + (size_t)b * W + q);
+    }
+    for (int q = lane; q < nq; q += 32) {
+        if constexpr (VEC == 4) {
+            cp_async16(su + 4 * q, G0 + 4 * q);
+            cp_async16(sv + 4 * q, V + 4 * q);
+        } else {
+            cp_async4(su + q, G0 + q);
+            cp_async4(sv + q, V + q);
+        }
+    }
+    cp_async_commit();
+}
+
+// B-E. node b of problem a by one warp: header h, rows loaded (stream_issue,
+// completed and visible to the warp), laid out for a.p and a.W with the padding zeroed.
+template <int VEC>
+__device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, WarpHdr& h, unsigned char* rows) {
     const int p = a.p, p4 = (p + 3) >> 2, W = a.W;
-    WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
-    uint32_t* smi = reinterpret_cast<uint32_t*>(wbase + align16(sizeof(WarpHdr)));
-    uint32_t* smo = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(smi) + mask_bytes(W));
-    float* su = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(smo) + mask_bytes(W));
+    uint32_t* smi = reinterpret_cast<uint32_t*>(rows);
+    uint32_t* smo = reinterpret_cast<uint32_t*>(rows + mask_bytes(W));
+    float* su = reinterpret_cast<float*>(rows + 2 * mask_bytes(W));
     float* sv = su + row_bytes(p) / sizeof(float);
     float4* su4 = reinterpret_cast<float4*>(su);
     const float eta = (float)a.eta, c = (float)a.c, M = (float)a.M, c1 = 1.f + c;
     const int nq = p / VEC;
     {
-        if (a.active != nullptr && a.active[b] == 0) return;
         const size_t base = (size_t)b * p;
         float* __restrict__ V = static_cast<float*>(a.V) + base;
         float* __restrict__ Bm = static_cast<float*>(a.B) + base;
-        const float* G0 = a.gsplits == 0 ? static_cast<const float*>(a.G) + base : a.Gpart + base;
         const int kb = a.kbar[b], pf = a.pf[b];
         const double tprev = lane == 0 ? a.tmom[b] : 0.0;
         const bool sel = kb > 0 && pf > kb;         // a top set to select and a block to pool
@@ -201,22 +225,7 @@ __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, 
         if (a.hint != nullptr && sel) { tau_h = a.hint[2 * b]; th_h = a.hint[2 * b + 1]; }
         const float tg = tau_h > 0.f ? tau_h * kTauHint : __builtin_huge_valf();
 
-        // ---- A. rows to shared memory in one round trip
-        for (int q = lane; q < W; q += 32) {
-            cp_async4(smi + q, a.in_mask + (size_t)b * W + q);
-            cp_async4(smo + q, a.out_mask + (size_t)b * W + q);
-        }
-        for (int q = lane; q < nq; q += 32) {
-            if constexpr (VEC == 4) {
-                cp_async16(su + 4 * q, G0 + 4 * q);
-                cp_async16(sv + 4 * q, V + 4 * q);
-            } else {
-                cp_async4(su + q, G0 + q);
-                cp_async4(sv + q, V + q);
-            }
-        }
         if (lane == 0) { h.nj1 = 0; h.ncand = 0; }
-        cp_async_wait_all();
         __syncwarp();
         // u = v - eta G (split slices after the first are added from global memory, in
         // order); J0 entries become 0 now, J1 entries once they are listed below.
@@ -528,14 +537,44 @@ __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, 
 }
 
 template <int VEC>
-__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a) {
+__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a, int sets) {
     extern __shared__ __align__(16) unsigned char smem[];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    unsigned char* wbase = smem + (size_t)warp * warp_bytes(a.p, a.W);
-    stream_pad(wbase, a.p, a.W, lane);
-    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) stream_node<VEC>(a, b, lane, wbase);
+    unsigned char* wbase = smem + (size_t)warp * warp_bytes(a.p, a.W, sets);
+    WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
+    unsigned char* rows0 = wbase + align16(sizeof(WarpHdr));
+    const size_t sb = set_bytes(a.p, a.W);
+    for (int t = 0; t < sets; ++t) stream_pad(rows0 + t * sb, a.p, a.W, lane);
+    const int stride = gridDim.x * wpc;
+    auto next_active = [&](int b) {
+        while (b < a.m && a.active != nullptr && a.active[b] == 0) b += stride;
+        return b;
+    };
+    int b = next_active(blockIdx.x * wpc + warp);
+    if (sets == 1) {
+        for (; b < a.m; b = next_active(b + stride)) {
+            stream_issue<VEC>(a, b, lane, rows0);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            stream_node<VEC>(a, b, lane, h, rows0);
+        }
+        return;
+    }
+    // two row sets: node b's rows were requested before; request the next node's
+    // into the other set, then work on b
+    int cur = 0;
+    if (b < a.m) stream_issue<VEC>(a, b, lane, rows0);
+    while (b < a.m) {
+        const int nb = next_active(b + stride);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        if (nb < a.m) stream_issue<VEC>(a, nb, lane, rows0 + (cur ^ 1) * sb);
+        stream_node<VEC>(a, b, lane, h, rows0 + cur * sb);
+        b = nb;
+        cur ^= 1;
+    }
 }
 
 // The nodes of several problems (instances of the serving loop) in one launch:
@@ -547,22 +586,29 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream_group(c
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
     unsigned char* wbase = smem + (size_t)warp * warp_bytes(g.pmax, g.Wmax);
+    WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
+    unsigned char* rows = wbase + align16(sizeof(WarpHdr));
     int last = -1;
     for (int t = blockIdx.x * wpc + warp; t < g.nbase[g.np]; t += gridDim.x * wpc) {
         int pi = 0;
         while (pi + 1 < g.np && t >= g.nbase[pi + 1]) ++pi;
         const ProxArgs& a = g.a[pi];
+        const int b = t - g.nbase[pi];
+        if (a.active != nullptr && a.active[b] == 0) continue;
         if (pi != last) {
-            stream_pad(wbase, a.p, a.W, lane);
+            stream_pad(rows, a.p, a.W, lane);
             last = pi;
         }
-        stream_node<VEC>(a, t - g.nbase[pi], lane, wbase);
+        stream_issue<VEC>(a, b, lane, rows);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        stream_node<VEC>(a, b, lane, h, rows);
     }
 }
 
 template <int VEC>
-int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
-    const size_t smem = (size_t)wpc * warp_bytes(a.p, a.W);
+int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc, int sets) {
+    const size_t smem = (size_t)wpc * warp_bytes(a.p, a.W, sets);
     auto kern = k_prox_stream<VEC>;
     {
         // set once per kernel to the SM's whole shared memory, so that no launch
@@ -587,14 +633,14 @@ int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = a.pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kern, a);   // errors surface at the caller's check
+    cudaLaunchKernelEx(&cfg, kern, a, sets);   // errors surface at the caller's check
     return 0;
 }
 
 }  // namespace
 
-int prox_stream_warps(int p, int W) {
-    return (int)std::min<size_t>(kStreamMaxWarps, kSmemPerSM / warp_bytes(p, W));
+int prox_stream_warps(int p, int W, int sets) {
+    return (int)std::min<size_t>(kStreamMaxWarps, kSmemPerSM / warp_bytes(p, W, sets));
 }
 
 namespace {
@@ -640,21 +686,28 @@ int prox_stream_group(cudaStream_t s, ProxGroup& g) {
         g.nbase[i + 1] = g.nbase[i] + std::max(0, a.m);
     }
     if (g.nbase[g.np] == 0) return 0;
-    const int wpc = prox_stream_warps(g.pmax, g.Wmax);
+    const int wpc = prox_stream_warps(g.pmax, g.Wmax, 1);
     if (wpc < kStreamMinWarps) return 1;
     return vec ? launch_stream_group<4>(s, g, wpc) : launch_stream_group<1>(s, g, wpc);
 }
 
 int prox_stream_f32(cudaStream_t s, const ProxArgs& a) {
     if (a.m <= 0) return 0;
-    const int wpc = prox_stream_warps(a.p, a.W);
-    if (a.p > kStreamMaxP || wpc < kStreamMinWarps) return 1;     // not this kernel's range
+    const int wpc1 = prox_stream_warps(a.p, a.W, 1);
+    if (a.p > kStreamMaxP || wpc1 < kStreamMinWarps) return 1;     // not this kernel's range
+    // two row sets (the next node's rows in flight) only where they cost no warps: a
+    // node's passes over shared memory are a chain of dependent steps, and fewer
+    // warps per SM leave them exposed (C4, p = 2000: 12 warps with one set take
+    // 62 us per 4096-node launch, 6 warps with two sets 142 us)
+    const int wpc2 = prox_stream_warps(a.p, a.W, 2);
+    const int sets = wpc2 >= wpc1 ? 2 : 1;
+    const int wpc = wpc1;
     const bool vec = (a.p % 4 == 0) && ((uintptr_t)a.V % 16 == 0) && ((uintptr_t)a.B % 16 == 0) &&
                      (a.Vop == nullptr || (a.op_ld % 4 == 0 && (uintptr_t)a.Vop % 16 == 0 &&
                                            (a.Vop_lo == nullptr || (uintptr_t)a.Vop_lo % 16 == 0))) &&
                      (a.gsplits == 0 ? ((uintptr_t)a.G % 16 == 0)
                                      : ((uintptr_t)a.Gpart % 16 == 0 && a.gstride % 4 == 0));
-    return vec ? launch_stream<4>(s, a, wpc) : launch_stream<1>(s, a, wpc);
+    return vec ? launch_stream<4>(s, a, wpc, sets) : launch_stream<1>(s, a, wpc, sets);
 }
 
 }  // namespace kglm

@@ -211,3 +211,29 @@ def test_second_and_third_steps_with_momentum(p, k, prec):
         assert np.max(np.abs(b3 - on.prox_node(u, nd, rho, M_BOX))) <= tol, (b, 3)
         checked += 1
     assert checked == len(nodes)
+
+
+@pytest.mark.parametrize("p", [600, 2000])
+def test_streaming_prox_with_several_nodes_per_warp(p):
+    """6000 nodes: every warp of the streaming kernel takes several nodes in turn (at
+    p = 600 with the next node's rows requested while it works on the current one,
+    at p = 2000 one node's rows at a time); a sample of nodes spread over the batch,
+    including the last, against Algorithm 1 on the same u."""
+    k = 20
+    X, y, L, lam2 = _instance(p, seed=5 * p, dup=False)
+    rng = np.random.default_rng(13 * p)
+    nodes = _nodes(p, k, rng) + synth.csr_to_sets(*synth.random_nodes(6000 - 16, p, k, rng))
+    B0 = _warm(p, nodes, rng, False)
+    rho = 1.0 / (2.0 * lam2 / L)
+    with kglm.Engine(X, y, k, lam2, M_BOX, synth.LSQ, prec="fp32", max_batch=len(nodes), lipschitz=L) as eng:
+        eng.push(*synth.sets_to_csr(nodes), warm_B=B0)
+        eng.evaluate(1)
+        B1, _ = eng.read_batch(zeta=False)
+    for b in list(range(0, len(nodes), 97)) + [len(nodes) - 1]:
+        J0, J1 = nodes[b]
+        nd = on.Node(p, k, J0, J1)
+        u = _u(X, y, L, B0[b])
+        want = on.prox_node(u, nd, rho, M_BOX)
+        tol = 2.0 ** -18 * max(1.0, np.max(np.abs(u)))
+        err = np.max(np.abs(B1[b] - want))
+        assert err <= tol, (p, b, err, tol)
