@@ -88,13 +88,14 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size
 // a row of p floats padded to a multiple of 4 (the padding stays 0)
 __host__ __device__ inline size_t row_bytes(int p) { return align16((size_t)p * sizeof(float)); }
 __host__ __device__ inline size_t mask_bytes(int W) { return align16((size_t)W * sizeof(uint32_t)); }
-// per warp: a header, then `sets` row sets of two mask rows and the u (G) and v
-// rows (beta_old is read from global memory by the write pass, its only use).
-// With two sets the rows of the warp's next node arrive while it works on the
-// current one.
-__host__ __device__ inline size_t set_bytes(int p, int W) { return 2 * mask_bytes(W) + 2 * row_bytes(p); }
-__host__ __device__ inline size_t warp_bytes(int p, int W, int sets = 1) {
-    return align16(sizeof(WarpHdr)) + (size_t)sets * set_bytes(p, W);
+// per warp: a header, then the rows of its node: two mask rows and the u (G) and
+// v rows (beta_old is read from global memory by the write pass, its only use).
+// A second row set, for the next node's rows to arrive during the current
+// node's passes, halves the warps per SM at p = 2000 and slowed the kernel
+// 2.3x: a node's passes are a chain of dependent shared-memory steps that
+// other warps must cover.
+__host__ __device__ inline size_t warp_bytes(int p, int W) {
+    return align16(sizeof(WarpHdr)) + 2 * mask_bytes(W) + 2 * row_bytes(p);
 }
 
 __device__ __forceinline__ float entry_pt(float a, float c, float M) {
@@ -202,8 +203,9 @@ __device__ __forceinline__ void stream_issue(const ProxArgs& a, int b, int lane,
     cp_async_commit();
 }
 
-// B-E. node b of problem a by one warp: header h, rows loaded (stream_issue,
-// completed and visible to the warp), laid out for a.p and a.W with the padding zeroed.
+// B-E. node b of problem a by one warp: header h, its rows requested by
+// stream_issue (the node's scalars are read while they arrive), laid out for
+// a.p and a.W with the padding zeroed.
 template <int VEC>
 __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, WarpHdr& h, unsigned char* rows) {
     const int p = a.p, p4 = (p + 3) >> 2, W = a.W;
@@ -226,6 +228,7 @@ __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, 
         const float tg = tau_h > 0.f ? tau_h * kTauHint : __builtin_huge_valf();
 
         if (lane == 0) { h.nj1 = 0; h.ncand = 0; }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
         // u = v - eta G (split slices after the first are added from global memory, in
         // order); J0 entries become 0 now, J1 entries once they are listed below.
@@ -537,43 +540,19 @@ __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, 
 }
 
 template <int VEC>
-__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a, int sets) {
+__global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    unsigned char* wbase = smem + (size_t)warp * warp_bytes(a.p, a.W, sets);
+    unsigned char* wbase = smem + (size_t)warp * warp_bytes(a.p, a.W);
     WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
-    unsigned char* rows0 = wbase + align16(sizeof(WarpHdr));
-    const size_t sb = set_bytes(a.p, a.W);
-    for (int t = 0; t < sets; ++t) stream_pad(rows0 + t * sb, a.p, a.W, lane);
-    const int stride = gridDim.x * wpc;
-    auto next_active = [&](int b) {
-        while (b < a.m && a.active != nullptr && a.active[b] == 0) b += stride;
-        return b;
-    };
-    int b = next_active(blockIdx.x * wpc + warp);
-    if (sets == 1) {
-        for (; b < a.m; b = next_active(b + stride)) {
-            stream_issue<VEC>(a, b, lane, rows0);
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncwarp();
-            stream_node<VEC>(a, b, lane, h, rows0);
-        }
-        return;
-    }
-    // two row sets: node b's rows were requested before; request the next node's
-    // into the other set, then work on b
-    int cur = 0;
-    if (b < a.m) stream_issue<VEC>(a, b, lane, rows0);
-    while (b < a.m) {
-        const int nb = next_active(b + stride);
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncwarp();
-        if (nb < a.m) stream_issue<VEC>(a, nb, lane, rows0 + (cur ^ 1) * sb);
-        stream_node<VEC>(a, b, lane, h, rows0 + cur * sb);
-        b = nb;
-        cur ^= 1;
+    unsigned char* rows = wbase + align16(sizeof(WarpHdr));
+    stream_pad(rows, a.p, a.W, lane);
+    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) {
+        if (a.active != nullptr && a.active[b] == 0) continue;
+        stream_issue<VEC>(a, b, lane, rows);
+        stream_node<VEC>(a, b, lane, h, rows);
     }
 }
 
@@ -600,15 +579,13 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream_group(c
             last = pi;
         }
         stream_issue<VEC>(a, b, lane, rows);
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncwarp();
         stream_node<VEC>(a, b, lane, h, rows);
     }
 }
 
 template <int VEC>
-int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc, int sets) {
-    const size_t smem = (size_t)wpc * warp_bytes(a.p, a.W, sets);
+int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
+    const size_t smem = (size_t)wpc * warp_bytes(a.p, a.W);
     auto kern = k_prox_stream<VEC>;
     {
         // set once per kernel to the SM's whole shared memory, so that no launch
@@ -633,14 +610,14 @@ int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc, int sets) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = a.pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kern, a, sets);   // errors surface at the caller's check
+    cudaLaunchKernelEx(&cfg, kern, a);   // errors surface at the caller's check
     return 0;
 }
 
 }  // namespace
 
-int prox_stream_warps(int p, int W, int sets) {
-    return (int)std::min<size_t>(kStreamMaxWarps, kSmemPerSM / warp_bytes(p, W, sets));
+int prox_stream_warps(int p, int W) {
+    return (int)std::min<size_t>(kStreamMaxWarps, kSmemPerSM / warp_bytes(p, W));
 }
 
 namespace {
@@ -686,28 +663,21 @@ int prox_stream_group(cudaStream_t s, ProxGroup& g) {
         g.nbase[i + 1] = g.nbase[i] + std::max(0, a.m);
     }
     if (g.nbase[g.np] == 0) return 0;
-    const int wpc = prox_stream_warps(g.pmax, g.Wmax, 1);
+    const int wpc = prox_stream_warps(g.pmax, g.Wmax);
     if (wpc < kStreamMinWarps) return 1;
     return vec ? launch_stream_group<4>(s, g, wpc) : launch_stream_group<1>(s, g, wpc);
 }
 
 int prox_stream_f32(cudaStream_t s, const ProxArgs& a) {
     if (a.m <= 0) return 0;
-    const int wpc1 = prox_stream_warps(a.p, a.W, 1);
-    if (a.p > kStreamMaxP || wpc1 < kStreamMinWarps) return 1;     // not this kernel's range
-    // two row sets (the next node's rows in flight) only where they cost no warps: a
-    // node's passes over shared memory are a chain of dependent steps, and fewer
-    // warps per SM leave them exposed (C4, p = 2000: 12 warps with one set take
-    // 62 us per 4096-node launch, 6 warps with two sets 142 us)
-    const int wpc2 = prox_stream_warps(a.p, a.W, 2);
-    const int sets = wpc2 >= wpc1 ? 2 : 1;
-    const int wpc = wpc1;
+    const int wpc = prox_stream_warps(a.p, a.W);
+    if (a.p > kStreamMaxP || wpc < kStreamMinWarps) return 1;     // not this kernel's range
     const bool vec = (a.p % 4 == 0) && ((uintptr_t)a.V % 16 == 0) && ((uintptr_t)a.B % 16 == 0) &&
                      (a.Vop == nullptr || (a.op_ld % 4 == 0 && (uintptr_t)a.Vop % 16 == 0 &&
                                            (a.Vop_lo == nullptr || (uintptr_t)a.Vop_lo % 16 == 0))) &&
                      (a.gsplits == 0 ? ((uintptr_t)a.G % 16 == 0)
                                      : ((uintptr_t)a.Gpart % 16 == 0 && a.gstride % 4 == 0));
-    return vec ? launch_stream<4>(s, a, wpc, sets) : launch_stream<1>(s, a, wpc, sets);
+    return vec ? launch_stream<4>(s, a, wpc) : launch_stream<1>(s, a, wpc);
 }
 
 }  // namespace kglm

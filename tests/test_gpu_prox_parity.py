@@ -215,10 +215,9 @@ def test_second_and_third_steps_with_momentum(p, k, prec):
 
 @pytest.mark.parametrize("p", [600, 2000])
 def test_streaming_prox_with_several_nodes_per_warp(p):
-    """6000 nodes: every warp of the streaming kernel takes several nodes in turn (at
-    p = 600 with the next node's rows requested while it works on the current one,
-    at p = 2000 one node's rows at a time); a sample of nodes spread over the batch,
-    including the last, against Algorithm 1 on the same u."""
+    """6000 nodes: every warp of the streaming kernel takes several nodes in turn, its
+    shared-memory rows reused from node to node; a sample of nodes spread over the
+    batch, including the last, against Algorithm 1 on the same u."""
     k = 20
     X, y, L, lam2 = _instance(p, seed=5 * p, dup=False)
     rng = np.random.default_rng(13 * p)
