@@ -311,8 +311,9 @@ typedef struct {
     int32_t sub_batches;      /* iteration loop split into this many node ranges on parallel streams */
     int32_t prox_threads;     /* threads per node of the prox for p > 512 in the FP32-type modes (0: default;
                                  32: one warp per node, p <= 2048) */
-    int32_t pair;             /* BF16: the iteration products as CTA pairs (clusters of two) sharing each
-                                 B tile by TMA multicast: 1 on, -1 off (kglm_configure: 0 keeps) */
+    int32_t pair;             /* BF16: the iteration products as CTA pairs (clusters of two), each pair
+                                 computing a 256-row tile with one cta_group::2 product and each CTA
+                                 holding half of the B tile: 1 on, -1 off (kglm_configure: 0 keeps) */
     double nodes_per_s;       /* node evaluations per second at the chosen batch */
     double best_nodes_per_s;  /* the best rate over all batch sizes */
 } kglm_tune;

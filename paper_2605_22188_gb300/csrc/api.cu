@@ -107,7 +107,7 @@ struct kglm_ctx {
     int bn1 = 0, bn2 = 0;
     int tuned_batch = 0;          // kglm_autotune's choice (0: not tuned)
     bool pdl = false;             // programmatic dependent launch inside the iteration graph (tuned)
-    bool pair = false;            // BF16 iteration products as CTA pairs sharing B by multicast (tuned)
+    bool pair = false;            // BF16 iteration products as CTA pairs with 256-row tiles (tuned)
     // sub-batches of the iteration loop on forked streams (tensor-core modes, tuned)
     static constexpr int kMaxSub = 4;
     int nsub = 1;
@@ -1651,7 +1651,7 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         }
         c->pdl = bp;
         destroy_graphs(c);
-        // BF16: the products as CTA pairs sharing each B tile, or one CTA per tile
+        // BF16: the products as CTA pairs (256-row tiles, half of B in each CTA), or one CTA per tile
         if (c->tc_kind == 0 && !c->x3) {
             bool bpair = c->pair;
             const bool keep = c->pair;

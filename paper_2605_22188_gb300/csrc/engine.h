@@ -51,6 +51,11 @@ void gemm_link_f32(cudaStream_t s, int m, int n, int p, const float* V, const fl
 // ---- tensor-core products (tcgen05, TMA); see gemm_tc.cu
 struct TcMap {
     alignas(64) unsigned char bytes[128];   // a CUtensorMap
+    // the same tensor with half the box rows: the B operand of a CTA pair, whose
+    // CTAs each hold half of the tile's columns (made when the box rows are a
+    // multiple of 16)
+    alignas(64) unsigned char half[128];
+    int has_half;
 };
 // TC_EPI_PARTIAL: split z writes its partial product to pout + z*pstride (row
 // stride pld); the consumer sums the slices (no reduction in the kernel).
@@ -74,8 +79,10 @@ struct TcGemm {
     float* out_lo;   // TC_EPI_LINK_F32: TF32 low part of each output (NULL: none)
     int pdl;         // launch with programmatic stream serialization (prologue overlaps the previous kernel)
     int arow0;       // first row of A used (rows arow0 .. arow0 + M); outputs are indexed from row 0
-    int pair;        // 1: CTA pairs (clusters of two) sharing each B tile by multicast, where
-                     // supported (BF16, single operands, no split-K link); 0: one CTA per tile
+    int pair;        // 1: CTA pairs (clusters of two) computing 256-row tiles with one
+                     // cta_group::2 MMA, each CTA holding its 128 rows of A and half of
+                     // the B tile, where supported (BF16, single operands, no split-K
+                     // link, a B map with a half box); 0: one CTA per 128-row tile
 };
 // TMA map of a row-major rows x cols matrix (row stride ld elements) with
 // 128-byte boxes along cols and box_rows rows.  0 on success.

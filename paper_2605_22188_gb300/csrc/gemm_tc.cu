@@ -8,8 +8,11 @@
 // optionally, into K ranges (split-K slices or the jobs of the certificate):
 // one work unit is one (tile, K range).  The kernel is persistent: one CTA per
 // SM walks the units u = blockIdx.x, blockIdx.x + gridDim.x, ... with
-//   warp 0, lane 0   TMA producer: 128-byte-swizzled K slices of A and B
-//                    (cp.async.bulk.tensor.2d) into a ring of stages;
+//   warps 0 and 10,  TMA producers: 128-byte-swizzled K slices of A and B
+//   lane 0           (cp.async.bulk.tensor.2d) into a ring of stages, warp 0
+//                    the even slices and warp 10 the odd ones (one issuing
+//                    thread takes a few hundred cycles per stage, small or
+//                    large, and would leave the tensor pipe waiting);
 //   warp 1, lane 0   MMA issuer: tcgen05.mma.cta_group::1 (kind::f16 with BF16
 //                    operands, or kind::tf32) into one of two FP32
 //                    accumulators in tensor memory (512 columns), so that the
@@ -42,6 +45,13 @@
 // the last epilogue warp to finish a 32-row slab and column half of a tile
 // (an arrival counter for each) sums its partials in fixed order; no warp
 // waits on another.
+// CTA pairs (BF16, single operands): a cluster of two CTAs computes a 256-row
+// tile with tcgen05.mma.cta_group::2 (M = 256) issued by the even CTA.  Each
+// CTA copies its own 128 rows of A and half of the B tile's rows into its own
+// ring, so that an SM takes in 32 KB instead of 48 KB per 128 x 256 x 64
+// slice of products; both copies complete on the even CTA's stage barrier,
+// and each CTA's epilogue drains its 128 rows of the accumulator from its own
+// tensor memory.
 // Every mbarrier wait is bounded; a wait that runs out sets an error flag,
 // the roles stop, the MMA issuer drains its products and the producer its
 // copies before the tensor memory is freed.
@@ -61,8 +71,9 @@ namespace {
 constexpr int BM = 128;                 // rows per tile (one UMMA M = 128)
 constexpr int ROWB = 128;               // bytes of K per stage and row (one swizzle row)
 constexpr int MAXBN = 256;
-constexpr int NT = 320;                 // ten warps: producer, MMA, eight epilogue warps
+constexpr int NT = 352;                 // eleven warps: producer, MMA, eight epilogue warps, second producer
 constexpr int EPI_WARPS = 8;
+constexpr int PROD2_WARP = 2 + EPI_WARPS;   // fills the odd ring slices (warp 0 the even ones)
 constexpr uint32_t STAGE_A = BM * ROWB;
 constexpr uint32_t TMEM_COLS = 512;     // two accumulators of up to 256 columns
 constexpr int TPAD = 20;                // transpose buffer row: 16 + 4 (16-byte rows, no 128-bit bank conflicts on write)
@@ -199,9 +210,10 @@ __device__ __forceinline__ Unit unit_of(const TcArgs& a, int u) {
 }
 
 // The unit of a CTA pair (CL = 2): pair units run over (row-tile pair, column
-// tile, K range); the CTA of cluster rank r takes row tile 2 mp + r, so both CTAs
-// of a pair share the column tile and K range (the B tile).  A row tile past the
-// last one (odd row-tile count) reads rows past M and stores nothing.
+// tile, K range); the CTA of cluster rank r takes row tile 2 mp + r and columns
+// [n0 + r bn/2, n0 + (r + 1) bn/2) of the B tile, so both CTAs of a pair share the
+// column tile and K range.  A row tile past the last one (odd row-tile count)
+// reads rows past M (or zeros) and stores nothing.
 __device__ __forceinline__ Unit unit_of_pair(const TcArgs& a, int u, int crank) {
     Unit w;
     w.pi = 0;
@@ -266,16 +278,26 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// The same tile into this CTA and its cluster peer (mask 0b11): the bytes land at
-// dst in both CTAs' shared memory and complete on the mbarrier at the same offset
-// in each.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
-                                               uint16_t mask) {
+// A copy of this CTA's part of a pair's stage (cta_group::2): the bytes land in
+// this CTA's shared memory at dst and complete on the mbarrier at the cluster
+// address bar, the even CTA's stage barrier.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+
+// The cluster address of the shared-memory word at this CTA's offset addr in the CTA of rank r.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t r) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(r));
+    return out;
+}
+
+// One arrival on an mbarrier given by its cluster address (this CTA's or the peer's).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -293,13 +315,24 @@ __device__ __forceinline__ void cluster_sync() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// CG = 2: one warp of each CTA of the pair takes part (the same columns in both).
+template <int CG>
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t cols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
 }
 
+template <int CG>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+    if constexpr (CG == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
 }
 
 template <int KIND>
@@ -325,15 +358,33 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
     }
 }
 
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+// The pair's product (BF16, M = 256): issued by the even CTA; A and B descriptors
+// name the same offsets in both CTAs, the accumulator the same columns.
+__device__ __forceinline__ void umma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
-// Arrive on the mbarrier at this offset in every CTA of `mask` once the issued products finish.
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
+// Arrive on the mbarrier at this offset in both CTAs of the pair once the pair's issued products finish.
+__device__ __forceinline__ void umma_commit_pair_mc(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"((uint16_t)3)
                  : "memory");
+}
+
+// Arrive on this CTA's mbarrier once the pair's issued products finish.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
@@ -380,12 +431,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // operand maps and TcArgs) or SrcGroup (a table of problems).
 template <int KIND, int NB, int NA, int CL, class S>
 __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
+    static_assert(CL == 1 || (KIND == 0 && NA == 1 && NB == 1), "CTA pairs: BF16 single operands");
     const int STAGES = a.stages;
-    const uint32_t SSTR = stage_stride(NA, NB, a.bn);
+    // B rows per CTA: a pair's CTAs hold half of the tile's columns each
+    const int bnl = CL == 2 ? a.bn / 2 : a.bn;
+    const uint32_t SSTR = stage_stride(NA, NB, bnl);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // stage s at smem + s SSTR: A, A2 (NA = 2), B, B2 (NB = 2); every part 1024-byte aligned
-    const uint32_t offB = (uint32_t)NA * STAGE_A, offB2 = offB + (uint32_t)a.bn * ROWB;
+    const uint32_t offB = (uint32_t)NA * STAGE_A, offB2 = offB + (uint32_t)bnl * ROWB;
     float* sT = reinterpret_cast<float*>(smem + (size_t)STAGES * SSTR);            // 4 x 32 x TPAD
     uint64_t* bars = reinterpret_cast<uint64_t*>(sT + EPI_WARPS * 32 * TPAD);
     // bars: full[S], empty[S], tfull[2], tempty[2], drain
@@ -396,13 +450,17 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     uint64_t* drain = bars + 2 * kMaxStages + 4;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 5);
     __shared__ int s_consumed;       // ring slices the MMA issuer consumed (producer drain at exit)
+    __shared__ int s_issued[2];      // per producer: one past the last ring slice it filled
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = KIND == 0 ? 64 : 32;          // elements per 128-byte row
-    const uint32_t stage_bytes = (uint32_t)NA * STAGE_A + (uint32_t)NB * a.bn * ROWB;
-    // CL = 2: CTA pairs (clusters of two) walk pair units, sharing the B tile (one
-    // multicast copy); every MMA completion frees the stage in both CTAs
+    const uint32_t stage_bytes = (uint32_t)NA * STAGE_A + (uint32_t)NB * bnl * ROWB;
+    // CL = 2: CTA pairs (clusters of two) walk pair units; the even CTA (the
+    // leader) waits for both CTAs' copies on its stage barriers, issues the pair's
+    // products and frees each stage, and publishes each accumulator, in both
+    // CTAs; both epilogues release an accumulator on the leader's barrier
     const int crank = CL == 2 ? (int)cluster_ctarank() : 0;
+    const bool leader = crank == 0;
     const int units = src.units(CL);
     const int ucta = blockIdx.x / CL, ustride = gridDim.x / CL;
     auto unit = [&](int u) { return src.unit(u, CL, crank); };
@@ -413,13 +471,19 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
         src.prefetch(NB, NA);
     }
     if (threadIdx.x == 0) {
-        for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), CL); }
-        for (int q = 0; q < 2; ++q) { mbar_init(smem_u32(&tfull[q]), 1); mbar_init(smem_u32(&tempty[q]), 32 * EPI_WARPS); }
+        for (int q = 0; q < STAGES; ++q) { mbar_init(smem_u32(&full[q]), 1); mbar_init(smem_u32(&empty[q]), 1); }
+        // accumulator releases: every epilogue thread of this CTA, or one per
+        // epilogue warp of both CTAs of a pair
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(smem_u32(&tfull[q]), 1);
+            mbar_init(smem_u32(&tempty[q]), CL == 2 ? 2 * EPI_WARPS : 32 * EPI_WARPS);
+        }
         mbar_init(smem_u32(drain), 1);
         s_consumed = 0;
+        s_issued[0] = s_issued[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    if (warp == 1) tmem_alloc<CL>(smem_u32(tmem_slot), TMEM_COLS);
     tc_fence_before();
     __syncwarp();                    // whole warps at the CTA barrier (lane 0 of warp 0 ran the setup)
     __syncthreads();
@@ -427,42 +491,49 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     pdl_wait();                      // operands and outputs belong to the previous grid until it completes
-    int issued = 0;                  // producer: ring slices whose copies were started
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // producer
-            int g = 0;
-            bool ok = true;
-            for (int u = ucta; u < units && ok; u += ustride) {
-                const Unit w = unit(u);
-                const auto& pq = src.q(w.pi);
-                const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
-                for (int i = 0; i < w.nloc; ++i, ++g) {
-                    const int s = g % STAGES;
-                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-                    if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.err)) { ok = false; break; }
-                    const uint32_t fb = smem_u32(&full[s]);
+    // Two producers, lane 0 of warp 0 (even ring slices) and of warp PROD2_WARP (odd
+    // ones): a thread that issues TMA copies takes a few hundred cycles per stage
+    // whatever its size, so one thread alone cannot keep the tensor pipe fed.
+    if (warp == 0 || warp == PROD2_WARP) {
+      // lanes 1-31 of both producer warps wait at the exit barrier
+      if (lane == 0) {
+        const int pidx = warp == 0 ? 0 : 1;
+        int g = 0, mine = 0;
+        bool ok = true;
+        for (int u = ucta; u < units && ok; u += ustride) {
+            const Unit w = unit(u);
+            const auto& pq = src.q(w.pi);
+            const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
+            for (int i = 0; i < w.nloc; ++i, ++g) {
+                if ((g & 1) != pidx) continue;
+                const int s = g % STAGES;
+                const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.err)) { ok = false; break; }
+                const uint32_t fb = smem_u32(&full[s]);
+                const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
+                uint8_t* sp = smem + (size_t)s * SSTR;
+                if constexpr (CL == 2) {
+                    // this CTA's rows of A and half of B, completing on the leader's barrier
+                    if (leader) mbar_expect_tx(fb, 2 * stage_bytes);
+                    const uint32_t lb = mapa_rank(fb, 0);
+                    tma_load_2d_pair(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, lb);
+                    tma_load_2d_pair(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0 + crank * bnl, lb);
+                } else {
                     mbar_expect_tx(fb, stage_bytes);
-                    const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
-                    uint8_t* sp = smem + (size_t)s * SSTR;
                     tma_load_2d(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, fb);
                     if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), src.mapA2(w.pi), kxa, pq.arow0 + m0, fb);
-                    if constexpr (CL == 2) {
-                        if (crank == 0) {                   // B once, into both CTAs
-                            tma_load_2d_mc(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb, (uint16_t)3);
-                            if (NB == 2) tma_load_2d_mc(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb, (uint16_t)3);
-                        }
-                    } else {
-                        tma_load_2d(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb);
-                        if (NB == 2) tma_load_2d(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb);
-                    }
-                    issued = g + 1;
+                    tma_load_2d(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb);
+                    if (NB == 2) tma_load_2d(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb);
                 }
+                mine = g + 1;
             }
         }
+        s_issued[pidx] = mine;
+      }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (CL == 2 && !leader) {
+            // the odd CTA of a pair issues no products
+        } else if (lane == 0) {
             // MMA issuer
             int g = 0, li = 0;
             bool ok = true;
@@ -481,6 +552,11 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
                     const uint32_t aa = smem_u32(smem + (size_t)s * SSTR), bb = aa + offB;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K each (per B part)
+                        if constexpr (CL == 2) {
+                            umma_pair(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc,
+                                      (i > 0 || kk > 0) ? 1u : 0u);
+                            continue;
+                        }
                         umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc,
                                    (i > 0 || kk > 0) ? 1u : 0u);
                         if (NB == 2)
@@ -488,17 +564,20 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
                         if (NA == 2)
                             umma<KIND>(acc, smem_desc(aa + STAGE_A + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
                     }
-                    if constexpr (CL == 2) umma_commit_mc(smem_u32(&empty[s]), (uint16_t)3);   // in both CTAs
+                    if constexpr (CL == 2) umma_commit_pair_mc(smem_u32(&empty[s]));   // in both CTAs
                     else umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
                     s_consumed = g + 1;
                 }
-                umma_commit(smem_u32(&tfull[b]));       // the accumulator is complete (or abandoned)
+                // the accumulator is complete (or abandoned)
+                if constexpr (CL == 2) umma_commit_pair_mc(smem_u32(&tfull[b]));
+                else umma_commit(smem_u32(&tfull[b]));
             }
             // every product issued so far has finished once this commit arrives
-            umma_commit(smem_u32(drain));
+            if constexpr (CL == 2) umma_commit_pair(smem_u32(drain));
+            else umma_commit(smem_u32(drain));
             mbar_wait(smem_u32(drain), 0u, a.err);
         }
-    } else {
+    } else if (warp < 2 + EPI_WARPS) {
         // epilogue: warps 2..9; warp w reads the TMEM lane quadrant w % 4 (the
         // tile's rows 32 (w % 4) ..) and every other 16-column chunk of the tile,
         // starting at chunk h = (w - 2) / 4, so that two warps per SM
@@ -632,7 +711,12 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
             }
             // the accumulator may be overwritten by the unit after next
             tc_fence_before();
-            mbar_arrive(smem_u32(&tempty[b]));
+            if constexpr (CL == 2) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(mapa_rank(smem_u32(&tempty[b]), 0));
+            } else {
+                mbar_arrive(smem_u32(&tempty[b]));
+            }
             if (split) {
                 // per-warp arrival: the last of the nz units of this tile to finish
                 // this warp's 32 rows and chunks sums their partials (no warp waits
@@ -678,18 +762,30 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     __syncwarp();
     __syncthreads();
     if (warp == 0 && lane == 0) {
+        const int issued = max(s_issued[0], s_issued[1]);
         // copies still in flight (a wait that ran out) land before the CTA exits
-        for (int g = s_consumed; g < issued; ++g)
-            mbar_wait(smem_u32(&full[g % STAGES]), (uint32_t)(g / STAGES) & 1u, a.err);
+        // (a pair's copies all complete on the leader's barriers)
+        if (leader)
+            for (int g = s_consumed; g < issued; ++g)
+                mbar_wait(smem_u32(&full[g % STAGES]), (uint32_t)(g / STAGES) & 1u, a.err);
+        if constexpr (CL == 2) {
+            // the leader's releases of this CTA's last ring slices (commits that
+            // arrive here from the other SM) land before the CTA frees or leaves
+            if (a.err == nullptr || *reinterpret_cast<volatile int*>(a.err) == 0)
+                for (int g = max(0, issued - STAGES); g < issued; ++g)
+                    if (!mbar_wait(smem_u32(&empty[g % STAGES]), (uint32_t)(g / STAGES) & 1u, a.err)) break;
+        }
     }
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, TMEM_COLS);
-    }
-    // neither CTA of a pair leaves while the other may still copy into or signal it
+    // a pair: the leader's products (which read both CTAs' shared memory and write
+    // both CTAs' tensor memory) and both epilogues are done before either CTA
+    // frees its tensor memory or leaves
     if constexpr (CL == 2) {
         __syncwarp();
         cluster_sync();
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc<CL>(tmem, TMEM_COLS);
     }
 }
 
@@ -848,10 +944,22 @@ int tc_make_map(TcMap* out, const void* base, int is_bf16, int rows, int cols, i
     cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
     cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(reinterpret_cast<CUtensorMap*>(out->bytes), is_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                    2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? 0 : -3;
+    const auto dt = is_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(out->bytes), dt, 2, const_cast<void*>(base), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -3;
+    out->has_half = 0;
+    if (box_rows % 16 == 0) {
+        // half the box rows: each CTA of a pair copies half of a B tile
+        box[1] = (cuuint32_t)(box_rows / 2);
+        r = fn(reinterpret_cast<CUtensorMap*>(out->half), dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return -3;
+        out->has_half = 1;
+    }
+    return 0;
 }
 
 int tc_tile_cols(int N) { return N >= MAXBN ? MAXBN : ((N + 15) / 16) * 16; }
@@ -907,8 +1015,6 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const uint32_t ab = g.kind == 0 ? 1u : 2u;
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(g.bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     a.epi = g.epi; a.out = g.out; a.out_lo = g.out_lo; a.ldo = g.ldo; a.y = g.y; a.loss = g.loss;
-    a.stages = ring_stages(na, nb, g.bn);
-    const size_t smem = smem_for(na, nb, g.bn);
     a.round_tf32 = g.kind == 1;
     a.part = splits > 1 ? static_cast<float*>(scr->part) : nullptr;
     a.counters = splits > 1 ? scr->counters : nullptr;
@@ -918,9 +1024,15 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const CUtensorMap& mb2 = *reinterpret_cast<const CUtensorMap*>((B2 ? B2 : &B)->bytes);
     const CUtensorMap& ma2 = *reinterpret_cast<const CUtensorMap*>((g.A2 ? g.A2 : &A)->bytes);
     // CTA pairs: BF16 single operands, at least two row tiles, no split-K link epilogue
-    // (its partial tiles and arrival counters are indexed per tile)
+    // (its partial tiles and arrival counters are indexed per tile), a B map with a
+    // half box
     const bool pair = g.pair && g.kind == 0 && nb == 1 && na == 1 && a.mt >= 2 &&
-                      (splits == 1 || g.epi == TC_EPI_PARTIAL) && a.njobs == 0 && pair_clusters() > 0;
+                      (splits == 1 || g.epi == TC_EPI_PARTIAL) && a.njobs == 0 && B.has_half &&
+                      pair_clusters() > 0;
+    // a pair's ring holds this CTA's half of each B slice; its products have M = 256
+    a.stages = pair ? ring_stages(1, 1, g.bn / 2) : ring_stages(na, nb, g.bn);
+    const size_t smem = pair ? smem_for(1, 1, g.bn / 2) : smem_for(na, nb, g.bn);
+    if (pair) a.idesc = (a.idesc & ~(0x1Fu << 24)) | ((uint32_t)((2 * BM) >> 4) << 24);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(pair ? 2 * std::max(1, std::min(((a.mt + 1) / 2) * a.nt * splits, pair_clusters()))
                             : grid_of(tiles * splits));
@@ -944,7 +1056,8 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     cfg.attrs = attr;
     cfg.numAttrs = na_;
     cudaError_t e;
-    if (pair) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1, 2>, ma, mb, mb2, ma, a);
+    const CUtensorMap& mbh = *reinterpret_cast<const CUtensorMap*>(B.half);
+    if (pair) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1, 2>, ma, mbh, mbh, ma, a);
     else if (na == 2) e = cudaLaunchKernelEx(&cfg, k_tc_gemm<1, 2, 2, 1>, ma, mb, mb2, ma2, a);
     else if (g.kind == 0) e = nb == 1 ? cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1, 1>, ma, mb, mb2, ma, a)
                                       : cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 2, 1, 1>, ma, mb, mb2, ma, a);

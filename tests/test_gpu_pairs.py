@@ -1,13 +1,15 @@
-"""GPU: the BF16 products as CTA pairs (clusters of two sharing each B tile by
-TMA multicast) give bit-for-bit the results of one CTA per tile.
+"""GPU: the BF16 products as CTA pairs (clusters of two computing 256-row tiles
+with one cta_group::2 product, each CTA holding its 128 rows of A and half of
+the B tile) give bit-for-bit the results of one CTA per 128-row tile.
 
-A pair only changes who copies the shared operand tile (one multicast copy
-into both CTAs instead of one copy each); every accumulator sees the same
-products in the same order, so bounds, iterates, supports and branching
-indices must be identical, including an odd number of row tiles (the last
-pair's second CTA has no rows to store), sub-batches (row offsets into the
-operand), split-K slices of G = X^T R, and both losses.  The bound is also
-checked as a certificate against the oracle at the GPU's own dual point.
+A pair only changes where the operand slices sit (each CTA's rows of A and half
+of the B columns in its own shared memory) and which SM issues the products;
+every accumulator row still sees the same K slices in the same order, so
+bounds, iterates, supports and branching indices must be identical, including
+an odd number of row tiles (the last pair's second CTA has no rows to store),
+sub-batches (row offsets into the operand), split-K slices of G = X^T R, tile
+widths whose half is not a multiple of 16 columns, and both losses.  The bound
+is also checked as a certificate against the oracle at the GPU's own dual point.
 """
 
 import numpy as np
@@ -20,8 +22,9 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("kind", [synth.LSQ, synth.LOGISTIC])
-@pytest.mark.parametrize("m,sub,cap", [(640, 1, 1), (1152, 2, 4), (300, 1, 2)])
-def test_pairs_match_single_ctas_bit_for_bit(kind, m, sub, cap):
+@pytest.mark.parametrize("m,sub,cap,bn", [(640, 1, 1, (256, 224)), (1152, 2, 4, (256, 224)), (300, 1, 2, (256, 224)),
+                                          (520, 1, 1, (112, 48))])
+def test_pairs_match_single_ctas_bit_for_bit(kind, m, sub, cap, bn):
     n, p, k = 3000, 700, 10
     X, y, _ = synth.instance(n, p, k, kind, rho=0.5, snr=5.0, seed=61)
     lam2, M, T = 1e-2, 2.0, 20
@@ -29,7 +32,7 @@ def test_pairs_match_single_ctas_bit_for_bit(kind, m, sub, cap):
     out = {}
     with kglm.Engine(X, y, k, lam2, M, kind, prec="bf16", max_batch=m) as eng:
         for pair in (-1, 1):
-            eng.configure(link_tile_cols=256, grad_tile_cols=224, grad_split_cap=cap, sub_batches=sub, pair=pair)
+            eng.configure(link_tile_cols=bn[0], grad_tile_cols=bn[1], grad_split_cap=cap, sub_batches=sub, pair=pair)
             eng.push(*csr)
             res = eng.evaluate(T)
             B, Z = eng.read_batch()
