@@ -371,7 +371,8 @@ void xtzeta(kglm_ctx* c, int m, CertArgs& a) {
     ExactPlan pl = x;
     const int tiles = ((p + c->bnx - 1) / c->bnx) * ((m + 127) / 128);
     exact_plan_widen(&pl, tiles, c->qs_slices * (size_t)c->mcap / (size_t)m);
-    if (tc_gemm_jobs(c->st, c->mAz, c->mBx, m, p, c->bnx, pl.jobs, pl.njobs, c->Qs, (size_t)m * p, p, c->d_tcerr) != 0)
+    if (tc_gemm_jobs(c->st, c->mAz, c->mBx, m, p, c->bnx, pl.jobs, pl.njobs, c->Qs, (size_t)m * p, p, c->d_tcerr,
+                     c->pair) != 0)
         throw Fail{KGLM_ECUDA, "tensor-core certificate product setup failed"};
     a.Qs = c->Qs;
     a.nqs = pl.njobs;
@@ -1612,6 +1613,19 @@ void autotune_impl(kglm_ctx* c, int iters, uint64_t seed, kglm_tune* out) {
         if (c->p > 64) t2.push_back(64);
         double best = INFINITY;
         int b1 = c->bn1, b2 = c->bn2, bs = cap;
+        // BF16: CTA pairs on or off at the starting tiles first, so that the tiles
+        // are tuned for the kind of launch that will run them (checked again below)
+        if (c->tc_kind == 0 && !c->x3) {
+            double tp[2] = {INFINITY, INFINITY};
+            for (int on = 0; on <= 1; ++on) {
+                c->pair = on != 0;
+                destroy_graphs(c);
+                tp[on] = time_eval(c, t, mc, iters, 3);
+                ++timed;
+            }
+            c->pair = tp[1] < tp[0];
+            destroy_graphs(c);
+        }
         for (int bn : t1) {
             set_tiles(c, bn, b2);
             const double ms = time_eval(c, t, mc, iters, 3);

@@ -107,8 +107,9 @@ struct TcJob {
 };
 // out slice jobs[z].slice (at pout + slice * pstride, row stride pld) =
 // A[:, K range of job z] . B[:, K range of job z]^T for every job, in one launch.
+// pair_on: as CTA pairs (256-row tiles) where the B map has a half box.
 int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, int bn, const TcJob* jobs,
-                 int njobs, float* pout, size_t pstride, int pld, int* err);
+                 int njobs, float* pout, size_t pstride, int pld, int* err, int pair_on);
 // Exact-splitting certificate product (cert_exact.cu): jobs of the level
 // products, their weights 2^(-beta l) and the bound n E per unit sigma tau.
 struct ExactPlan {

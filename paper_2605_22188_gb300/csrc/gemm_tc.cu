@@ -110,6 +110,7 @@ struct TcArgs {
     uint32_t idesc;           // instruction descriptor
     int epi;                  // TC_EPI_*
     int stages;               // ring stages (<= kMaxStages)
+    int ks;                   // K slices per stage (each with its own A and B parts)
     int round_tf32;           // round FP32 link outputs to TF32 (nearest) for the next product
     float* pout;              // TC_EPI_PARTIAL: slice z at pout + z * pstride, row stride pld
     size_t pstride;
@@ -435,7 +436,10 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     const int STAGES = a.stages;
     // B rows per CTA: a pair's CTAs hold half of the tile's columns each
     const int bnl = CL == 2 ? a.bn / 2 : a.bn;
-    const uint32_t SSTR = stage_stride(NA, NB, bnl);
+    // a stage holds KS consecutive K slices (one barrier, one release for all)
+    const int KS = a.ks;
+    const uint32_t SLSTR = stage_stride(NA, NB, bnl);
+    const uint32_t SSTR = (uint32_t)KS * SLSTR;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // stage s at smem + s SSTR: A, A2 (NA = 2), B, B2 (NB = 2); every part 1024-byte aligned
@@ -494,9 +498,15 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     // Two producers, lane 0 of warp 0 (even ring slices) and of warp PROD2_WARP (odd
     // ones): a thread that issues TMA copies takes a few hundred cycles per stage
     // whatever its size, so one thread alone cannot keep the tensor pipe fed.
+    // Only with an even number of stages: then every stage has one producer, which
+    // waits on its empty barrier at most one phase ahead.  With an odd count, fills
+    // g and g + STAGES of a stage would come from different producers, and one of
+    // them could test the barrier two phases ahead, where the parity cannot tell
+    // the phases apart; warp 0 then fills every slice.
+    const int nprod = (STAGES % 2 == 0) ? 2 : 1;
     if (warp == 0 || warp == PROD2_WARP) {
       // lanes 1-31 of both producer warps wait at the exit barrier
-      if (lane == 0) {
+      if (lane == 0 && (warp == 0 || nprod == 2)) {
         const int pidx = warp == 0 ? 0 : 1;
         int g = 0, mine = 0;
         bool ok = true;
@@ -504,26 +514,33 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
             const Unit w = unit(u);
             const auto& pq = src.q(w.pi);
             const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
-            for (int i = 0; i < w.nloc; ++i, ++g) {
-                if ((g & 1) != pidx) continue;
+            const int nst = (w.nloc + KS - 1) / KS;     // stages of this unit
+            for (int i = 0; i < nst; ++i, ++g) {
+                if (g % nprod != pidx) continue;
                 const int s = g % STAGES;
                 const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
                 if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.err)) { ok = false; break; }
                 const uint32_t fb = smem_u32(&full[s]);
-                const int kxa = (w.ka + i) * KE, kxb = (w.kb + i) * KE;
-                uint8_t* sp = smem + (size_t)s * SSTR;
+                const int nsl = min(KS, w.nloc - i * KS);   // K slices in this stage
                 if constexpr (CL == 2) {
-                    // this CTA's rows of A and half of B, completing on the leader's barrier
-                    if (leader) mbar_expect_tx(fb, 2 * stage_bytes);
-                    const uint32_t lb = mapa_rank(fb, 0);
-                    tma_load_2d_pair(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, lb);
-                    tma_load_2d_pair(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0 + crank * bnl, lb);
+                    if (leader) mbar_expect_tx(fb, 2 * stage_bytes * (uint32_t)nsl);
                 } else {
-                    mbar_expect_tx(fb, stage_bytes);
-                    tma_load_2d(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, fb);
-                    if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), src.mapA2(w.pi), kxa, pq.arow0 + m0, fb);
-                    tma_load_2d(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb);
-                    if (NB == 2) tma_load_2d(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb);
+                    mbar_expect_tx(fb, stage_bytes * (uint32_t)nsl);
+                }
+                for (int t = 0; t < nsl; ++t) {
+                    const int kxa = (w.ka + i * KS + t) * KE, kxb = (w.kb + i * KS + t) * KE;
+                    uint8_t* sp = smem + (size_t)s * SSTR + (size_t)t * SLSTR;
+                    if constexpr (CL == 2) {
+                        // this CTA's rows of A and half of B, completing on the leader's barrier
+                        const uint32_t lb = mapa_rank(fb, 0);
+                        tma_load_2d_pair(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, lb);
+                        tma_load_2d_pair(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0 + crank * bnl, lb);
+                    } else {
+                        tma_load_2d(smem_u32(sp), src.mapA(w.pi), kxa, pq.arow0 + m0, fb);
+                        if (NA == 2) tma_load_2d(smem_u32(sp + STAGE_A), src.mapA2(w.pi), kxa, pq.arow0 + m0, fb);
+                        tma_load_2d(smem_u32(sp + offB), src.mapB(w.pi), kxb, n0, fb);
+                        if (NB == 2) tma_load_2d(smem_u32(sp + offB2), src.mapB2(w.pi), kxb, n0, fb);
+                    }
                 }
                 mine = g + 1;
             }
@@ -544,25 +561,28 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
                 if (!mbar_wait(smem_u32(&tempty[b]), use ^ 1u, a.err)) break;
                 tc_fence_after();
                 const uint32_t acc = tmem + (uint32_t)(b * MAXBN);
-                for (int i = 0; i < w.nloc; ++i, ++g) {
+                const int nst = (w.nloc + KS - 1) / KS;
+                for (int i = 0; i < nst; ++i, ++g) {
                     const int s = g % STAGES;
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
                     if (!mbar_wait(smem_u32(&full[s]), ph, a.err)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t aa = smem_u32(smem + (size_t)s * SSTR), bb = aa + offB;
+                    const int nsl = min(KS, w.nloc - i * KS);
+                    for (int t = 0; t < nsl; ++t) {
+                        const uint32_t aa = smem_u32(smem + (size_t)s * SSTR + (size_t)t * SLSTR), bb = aa + offB;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K each (per B part)
-                        if constexpr (CL == 2) {
-                            umma_pair(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc,
-                                      (i > 0 || kk > 0) ? 1u : 0u);
-                            continue;
+                        for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K each (per B part)
+                            const uint32_t accf = (i > 0 || t > 0 || kk > 0) ? 1u : 0u;
+                            if constexpr (CL == 2) {
+                                umma_pair(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc, accf);
+                            } else {
+                                umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc, accf);
+                                if (NB == 2)
+                                    umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(aa + offB2 + kk * 32), a.idesc, 1u);
+                                if (NA == 2)
+                                    umma<KIND>(acc, smem_desc(aa + STAGE_A + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
+                            }
                         }
-                        umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(bb + kk * 32), a.idesc,
-                                   (i > 0 || kk > 0) ? 1u : 0u);
-                        if (NB == 2)
-                            umma<KIND>(acc, smem_desc(aa + kk * 32), smem_desc(aa + offB2 + kk * 32), a.idesc, 1u);
-                        if (NA == 2)
-                            umma<KIND>(acc, smem_desc(aa + STAGE_A + kk * 32), smem_desc(bb + kk * 32), a.idesc, 1u);
                     }
                     if constexpr (CL == 2) umma_commit_pair_mc(smem_u32(&empty[s]));   // in both CTAs
                     else umma_commit(smem_u32(&empty[s]));   // stage s is free once these MMAs finish
@@ -1029,9 +1049,17 @@ int tc_gemm(cudaStream_t s, const TcMap& A, const TcMap& B, const TcMap* B2, con
     const bool pair = g.pair && g.kind == 0 && nb == 1 && na == 1 && a.mt >= 2 &&
                       (splits == 1 || g.epi == TC_EPI_PARTIAL) && a.njobs == 0 && B.has_half &&
                       pair_clusters() > 0;
-    // a pair's ring holds this CTA's half of each B slice; its products have M = 256
-    a.stages = pair ? ring_stages(1, 1, g.bn / 2) : ring_stages(na, nb, g.bn);
-    const size_t smem = pair ? smem_for(1, 1, g.bn / 2) : smem_for(na, nb, g.bn);
+    // a pair's ring holds this CTA's half of each B slice, two K slices per stage:
+    // its copies are bound by their round trip, so fewer and larger stages
+    // (three of 64 KB at 256 columns) keep more bytes in flight per stage than six
+    // of 32 KB; its products have M = 256
+    a.ks = pair ? 2 : 1;
+    {
+        const size_t sl = pair ? stage_stride(1, 1, g.bn / 2) : stage_stride(na, nb, g.bn);
+        a.stages = (int)std::min<size_t>((kSmemMax - kSmemFixed) / ((size_t)a.ks * sl), kMaxStages);
+    }
+    const size_t smem = kSmemFixed + (size_t)a.stages * a.ks *
+                                         (pair ? stage_stride(1, 1, g.bn / 2) : stage_stride(na, nb, g.bn));
     if (pair) a.idesc = (a.idesc & ~(0x1Fu << 24)) | ((uint32_t)((2 * BM) >> 4) << 24);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(pair ? 2 * std::max(1, std::min(((a.mt + 1) / 2) * a.nt * splits, pair_clusters()))
@@ -1078,6 +1106,7 @@ int tc_gemm_group(cudaStream_t s, const TcGroupItem* items, int np, int bn, int 
     g.a.bn = bn;
     g.a.epi = epi;
     g.a.stages = ring_stages(1, 1, bn);
+    g.a.ks = 1;
     g.a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     g.a.round_tf32 = 0;
     g.a.err = err;
@@ -1126,7 +1155,7 @@ int tc_gemm_group(cudaStream_t s, const TcGroupItem* items, int np, int bn, int 
 }
 
 int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, int bn, const TcJob* jobs,
-                 int njobs, float* pout, size_t pstride, int pld, int* err) {
+                 int njobs, float* pout, size_t pstride, int pld, int* err, int pair_on) {
     if (M <= 0 || N <= 0 || njobs <= 0) return 0;
     if (bn < 16 || bn > MAXBN || bn % 16 != 0 || njobs > kTcMaxJobs) return -4;
     if (set_smem_attr<0, 1, 1>()) return -5;
@@ -1139,15 +1168,38 @@ int tc_gemm_jobs(cudaStream_t s, const TcMap& A, const TcMap& B, int M, int N, i
     a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     a.epi = TC_EPI_PARTIAL;
     a.stages = ring_stages(1, 1, bn);
+    a.ks = 1;
     a.pout = pout; a.pstride = pstride; a.pld = pld;
     a.err = err;
     a.njobs = njobs;
     for (int j = 0; j < njobs; ++j) a.jobs[j] = jobs[j];
     const CUtensorMap& ma = *reinterpret_cast<const CUtensorMap*>(A.bytes);
     const CUtensorMap& mb = *reinterpret_cast<const CUtensorMap*>(B.bytes);
-    const dim3 grid(grid_of(a.mt * a.nt * njobs));
-    k_tc_gemm<0, 1, 1, 1><<<grid, NT, smem_for(1, 1, bn), s>>>(ma, mb, mb, ma, a);
-    return 0;
+    // CTA pairs as in tc_gemm: 256-row tiles, half of B per CTA, two K slices per stage
+    const bool pair = pair_on && a.mt >= 2 && B.has_half && pair_clusters() > 0;
+    if (!pair) {
+        const dim3 grid(grid_of(a.mt * a.nt * njobs));
+        k_tc_gemm<0, 1, 1, 1><<<grid, NT, smem_for(1, 1, bn), s>>>(ma, mb, mb, ma, a);
+        return 0;
+    }
+    a.ks = 2;
+    const size_t sl = stage_stride(1, 1, bn / 2);
+    a.stages = (int)std::min<size_t>((kSmemMax - kSmemFixed) / (2 * sl), kMaxStages);
+    a.idesc = (a.idesc & ~(0x1Fu << 24)) | ((uint32_t)((2 * BM) >> 4) << 24);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * std::max(1, std::min(((a.mt + 1) / 2) * a.nt * njobs, pair_clusters())));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = kSmemFixed + (size_t)a.stages * 2 * sl;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const CUtensorMap& mbh = *reinterpret_cast<const CUtensorMap*>(B.half);
+    return cudaLaunchKernelEx(&cfg, k_tc_gemm<0, 1, 1, 2>, ma, mbh, mbh, ma, a) == cudaSuccess ? 0 : -7;
 }
 
 }  // namespace kglm
