@@ -57,6 +57,8 @@ struct kglm_ctx {
     double *X64 = nullptr, *Xt64 = nullptr, *y64 = nullptr, *gram = nullptr, *Xty = nullptr;
     double yty = 0.0;             // y^T y (host, FP64)
     float *X32 = nullptr, *Xt32 = nullptr, *y32 = nullptr;
+    float* ylo32 = nullptr;       // fl(y - y32): with y32, y to ~48 bits in FP32 pairs
+    std::vector<float> ylo_host;  // its host source (kept until the context goes)
     // node batch (device), capacity mcap
     int mcap = 0, m = 0;
     bool pushed = false, evaluated = false;
@@ -391,7 +393,7 @@ void certify(kglm_ctx* c) {
     a.lam2 = c->lam2; a.M = c->M;
     a.S = c->R;                                         // the m x n buffer is free here
     a.s_is_f64 = c->f64;
-    a.y = c->y64;
+    a.y = c->y64; a.y32 = c->y32; a.ylo = c->ylo32;
     a.zeta = c->zeta; a.sum_loss = c->sum_loss; a.sum_conj = c->sum_conj;
     a.Q = c->Q; a.B = c->B; a.b_is_f64 = c->f64;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
@@ -1022,7 +1024,7 @@ size_t footprint(const kglm_desc& d) {
     const bool x3 = d.prec == KGLM_TF32X3;
     const size_t ws = f64 ? 8 : 4, W = (p + 31) / 32;
     add(8 * n * p); add(8 * n * p); add(8 * n);
-    if (!f64) { add(4 * n * p); add(4 * n * p); add(4 * n); }
+    if (!f64) { add(4 * n * p); add(4 * n * p); add(4 * n); add(4 * n); }
     add(gemm_scratch_bytes(1)); add(4 * (size_t)gemm_scratch_counters(1));
     if (!f64) { add(gemm_scratch_bytes(0)); add(4 * (size_t)gemm_scratch_counters(0)); }
     bool tcerr = false;
@@ -1907,10 +1909,15 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->X32 = dalloc_t<float>(c, n * p);
             c->Xt32 = dalloc_t<float>(c, n * p);
             c->y32 = dalloc_t<float>(c, n);
+            c->ylo32 = dalloc_t<float>(c, n);
             convert_f64_to_f32(c->st, c->X64, c->X32, n * p);
             convert_f64_to_f32(c->st, c->Xt64, c->Xt32, n * p);
             convert_f64_to_f32(c->st, c->y64, c->y32, n);
             check_launch();
+            // the low part on the host (y is host data here; fl(y) is the same rounding as on the device)
+            c->ylo_host.resize(n);
+            for (size_t i = 0; i < (size_t)n; ++i) c->ylo_host[i] = (float)(y[i] - (double)(float)y[i]);
+            CK(cudaMemcpyAsync(c->ylo32, c->ylo_host.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->st));
         }
         // split-K scratch: a plan splits only when its tiles do not fill the GPU,
         // so (splits x tiles) stays below two waves plus one wave of tiles

@@ -27,9 +27,11 @@ constexpr double kFeasRtol = 1e-12;
 // Reduced-precision modes: the dual point is built in FP32 and the conjugate
 // sum is an upper bound with an explicit rounding margin, so that the bound
 // stays below Psi(zeta) for the zeta actually used (the FP32 value, exact in
-// FP64).  Least squares: zeta = -2(s - y) in FP32 (any zeta is admissible),
-// l*(-zeta) = -zeta*y + zeta^2/4 in FP64 with the FP64 data y (exact up to
-// FP64 rounding, no transcendental).  Logistic:
+// FP64).  Least squares: zeta = -2 r with r = fl(s - fl(y)) (any zeta is
+// admissible), l*(-zeta) = w y + w^2/4 with w = 2 r and the data y:
+//   w y + w^2/4 = 2 r y + r^2 = 2 r y32 + 2 r ylo + r^2,   y32 + ylo = y to ~2^-48,
+// where 2 r y32 and r^2 are formed exactly as FP32 pairs (product and its
+// FMA residual) and 2 r ylo (below 2^-24 of 2 r y) in FP32.  Logistic:
 // a = sigma(-y s) in FP32, zeta = y a (exact), and
 //   l*(-zeta) = a ln a + (1-a) ln(1-a)
 // with logf / log1pf, whose maximum errors in the CUDA C Programming Guide's
@@ -39,40 +41,64 @@ constexpr double kFeasRtol = 1e-12;
 //   |t2 - (1-a) ln(1-a)| <= (2^-22 + 2 * 2^-24)|...|     <= 2^-21 |t2|,
 // so each term carries the margin 2^-22|t1| + 2^-21|t2| + 2^-125 (the last
 // for denormal products); a term plus its margin is formed in FP32 rounded
-// upward (never below the exact sum of the same parts) and the terms are
-// summed in FP64.
+// upward (never below the exact sum of the same parts).
+// The running sums of a thread are FP32 pairs (hi, lo) updated by the exact
+// two-sum of Knuth (hi + a = s + err exactly in round-to-nearest), about 2^-44
+// relative per term, far below the logistic margins and of the order of the
+// FP64 rounding of the least-squares terms; they reach FP64 once per thread,
+// so that the GPU's slow FP64 pipe carries only the FP64 copy of zeta.
+// (The _rn intrinsics keep the compiler from contracting a product into the
+// two-sum's first addition, which would break its exactness.)
+struct FPair {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float s = __fadd_rn(hi, v);
+        const float bb = __fsub_rn(s, hi);
+        lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+        hi = s;
+    }
+    // the exact product a b as its rounded value plus the FMA residual
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float pr = __fmul_rn(a, b);
+        add(pr);
+        lo += fmaf(a, b, -pr);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <int NT>
 __global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
     __shared__ double red[2 * (NT / 32)];
     const int b = blockIdx.x;
     const size_t base = (size_t)b * a.n;
-    double acc[2] = {0.0, 0.0};
+    FPair sl, sc;
     const float* S = static_cast<const float*>(a.S);
     for (int i = threadIdx.x; i < a.n; i += NT) {
         const float s = S[base + i];
-        const float yi = (float)a.y[i];
+        const float yi = a.y32[i];
         if (a.kind == kLSQ) {
-            const float z = -2.0f * (s - yi);
-            a.zeta[base + i] = (double)z;
             const float r = s - yi;
-            acc[0] += (double)(r * r);
-            const double w = -(double)z;
-            acc[1] += w * a.y[i] + 0.25 * w * w;          // the exact FP64 y: l* is of the data
+            a.zeta[base + i] = (double)(-2.0f * r);
+            sl.add(__fmul_rn(r, r));                         // the loss term as the iterations form it
+            const float r2 = 2.0f * r;                        // w = -zeta, exact
+            sc.add_prod(r2, yi);                              // 2 r y32, exact as a pair
+            sc.add_prod(r, r);                                // r^2 = w^2 / 4, exact as a pair
+            sc.lo += r2 * a.ylo[i];                           // 2 r ylo
         } else {
             const float t = yi * s;
             const float e = __expf(-fabsf(t));
             const float sg = t >= 0.f ? e / (1.0f + e) : 1.0f / (1.0f + e);     // sigma(-t)
             a.zeta[base + i] = (double)(yi * sg);
-            acc[0] += (double)(fmaxf(-t, 0.f) + log1pf(e));
+            sl.add(fmaxf(-t, 0.f) + log1pf(e));
             float t1 = 0.f, t2 = 0.f;
             if (sg > 0.f) t1 = sg * logf(sg);
             if (sg < 1.f) t2 = (1.0f - sg) * log1pf(-sg);
-            // margin and sum in FP32 rounded upward (an upper bound, as the FP64 sum of the
-            // same terms was), so that only the running sum uses the slow FP64 pipe
+            // margin and term in FP32 rounded upward (an upper bound of the exact term)
             const float mg = __fadd_ru(__fadd_ru(fabsf(t1) * 0x1p-22f, fabsf(t2) * 0x1p-21f), 0x1p-125f);
-            acc[1] += (double)__fadd_ru(__fadd_ru(t1, t2), mg);
+            sc.add(__fadd_ru(__fadd_ru(t1, t2), mg));
         }
     }
+    double acc[2] = {sl.value(), sc.value()};
     block_sum<NT, 2, double>(acc, red);
     if (threadIdx.x == 0) {
         a.sum_loss[b] = acc[0];

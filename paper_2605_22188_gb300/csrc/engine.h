@@ -210,6 +210,8 @@ struct CertArgs {
     const void* S;        // S = X beta (m x n), working type or FP64 (s_is_f64)
     int s_is_f64;
     const double* y;
+    const float* y32;     // reduced-precision modes: y as FP32 high part y32 = fl(y) and low
+    const float* ylo;     // part ylo = fl(y - y32), for the compensated least-squares sums
     double* zeta;         // out: m x n FP64 dual points
     double* sum_loss;     // out: m
     double* sum_conj;     // out: m
