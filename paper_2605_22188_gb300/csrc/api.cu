@@ -369,7 +369,8 @@ void xtzeta(kglm_ctx* c, int m, CertArgs& a) {
         return;
     }
     const ExactPlan& x = c->xplan;
-    exact_digits(c->st, c->zeta, m, n, (size_t)n, x.npad, x.nd, x.beta, 1, c->DZ, c->ztau);
+    // the batch's certificate makes zeta's digits in its dual point pass
+    if (a.DZ == nullptr) exact_digits(c->st, c->zeta, m, n, (size_t)n, x.npad, x.nd, x.beta, 1, c->DZ, c->ztau);
     ExactPlan pl = x;
     const int tiles = ((p + c->bnx - 1) / c->bnx) * ((m + 127) / 128);
     exact_plan_widen(&pl, tiles, c->qs_slices * (size_t)c->mcap / (size_t)m);
@@ -398,6 +399,11 @@ void certify(kglm_ctx* c) {
     a.Q = c->Q; a.B = c->B; a.b_is_f64 = c->f64;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
     a.lb = c->lb_now; a.primal = c->primal_now; a.support = c->support; a.jstar = c->jstar;
+    if (c->cexact && !c->f64) {
+        // zeta's digits for the exact-splitting X^T zeta, made by the dual point pass
+        a.DZ = c->DZ; a.ztau = c->ztau;
+        a.dz_npad = c->xplan.npad; a.dz_nd = c->xplan.nd; a.dz_beta = c->xplan.beta;
+    }
     const double ws = c->f64 ? 8.0 : 4.0;
     {
         Scope sc(c, PH_CERT_XB, 1, 2.0 * n * c->sum_pa);

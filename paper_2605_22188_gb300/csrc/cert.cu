@@ -66,19 +66,56 @@ struct FPair {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// zeta of one sample in the reduced-precision modes (the value the certificate uses).
+__device__ __forceinline__ float dual_z(float s, float yi, int kind) {
+    if (kind == kLSQ) return -2.0f * (s - yi);
+    const float t = yi * s;
+    const float e = __expf(-fabsf(t));
+    return yi * (t >= 0.f ? e / (1.0f + e) : 1.0f / (1.0f + e));   // y sigma(-t)
+}
+
+// Digits of v = z / 2^e (|v| < 1) as in k_digits of cert_exact.cu, from the FP32
+// value alone: V = rint(v 2^62) by integer shifts of z's significand (nearest,
+// halves away from zero: |V - v 2^62| <= 1/2 as the error bound assumes), then
+// the same signed digits from the top, segment nd - a for digit a (reversed).
+__device__ __forceinline__ void dz_digits(float z, int e, int nd, int beta, __nv_bfloat16* d, size_t npad,
+                                          size_t i) {
+    long long V = 0;
+    const uint32_t u = __float_as_uint(z);
+    const int ex = (int)((u >> 23) & 0xffu);
+    if (ex != 0 || (u & 0x7fffffu) != 0) {
+        const long long mnt = ex ? (long long)((u & 0x7fffffu) | 0x800000u) : (long long)(u & 0x7fffffu);
+        const int sh = (ex ? ex : 1) - 150 + 62 - e;              // z = mnt 2^(ex - 150), v 2^62 = mnt 2^sh
+        long long mag = 0;
+        if (sh >= 0) mag = mnt << sh;                              // |v| < 1: below 2^62
+        else if (sh > -26) mag = (mnt + (1ll << (-sh - 1))) >> (-sh);
+        V = (u >> 31) ? -mag : mag;
+    }
+    for (int a = 1; a <= nd; ++a) {
+        const int sh = 62 - beta * a;
+        const long long dg = (V + (1ll << (sh - 1))) >> sh;        // nearest, halves up
+        V -= dg << sh;
+        d[(size_t)(nd - a) * npad + i] = __int2bfloat16_rn((int)dg);
+    }
+}
+
 template <int NT>
 __global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
     __shared__ double red[2 * (NT / 32)];
+    __shared__ float redf[NT / 32];
     const int b = blockIdx.x;
     const size_t base = (size_t)b * a.n;
     FPair sl, sc;
+    float zmax = 0.f;
     const float* S = static_cast<const float*>(a.S);
     for (int i = threadIdx.x; i < a.n; i += NT) {
         const float s = S[base + i];
         const float yi = a.y32[i];
+        const float z = dual_z(s, yi, a.kind);
+        zmax = fmaxf(zmax, fabsf(z));
         if (a.kind == kLSQ) {
             const float r = s - yi;
-            a.zeta[base + i] = (double)(-2.0f * r);
+            a.zeta[base + i] = (double)z;
             sl.add(__fmul_rn(r, r));                         // the loss term as the iterations form it
             const float r2 = 2.0f * r;                        // w = -zeta, exact
             sc.add_prod(r2, yi);                              // 2 r y32, exact as a pair
@@ -88,7 +125,7 @@ __global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
             const float t = yi * s;
             const float e = __expf(-fabsf(t));
             const float sg = t >= 0.f ? e / (1.0f + e) : 1.0f / (1.0f + e);     // sigma(-t)
-            a.zeta[base + i] = (double)(yi * sg);
+            a.zeta[base + i] = (double)z;
             sl.add(fmaxf(-t, 0.f) + log1pf(e));
             float t1 = 0.f, t2 = 0.f;
             if (sg > 0.f) t1 = sg * logf(sg);
@@ -103,6 +140,21 @@ __global__ __launch_bounds__(NT) void k_dual_point_f32(CertArgs a) {
     if (threadIdx.x == 0) {
         a.sum_loss[b] = acc[0];
         a.sum_conj[b] = acc[1];
+    }
+    if (a.DZ == nullptr) return;
+    // the digits of zeta for the exact-splitting X^T zeta: the row's scale from the
+    // first pass, then zeta again (the same FP32 operations) and its digits
+    zmax = warp_max(zmax);
+    if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = zmax;
+    __syncthreads();
+    float mx = 0.f;
+    for (int w = 0; w < NT / 32; ++w) mx = fmaxf(mx, redf[w]);
+    const int e = mx > 0.f ? ilogbf(mx) + 1 : 0;                   // 2^e > mx
+    if (threadIdx.x == 0) a.ztau[b] = mx > 0.f ? ldexp(1.0, e) : 0.0;   // a zero row is exact
+    __nv_bfloat16* d = a.DZ + (size_t)b * a.dz_nd * a.dz_npad;
+    for (int i = threadIdx.x; i < a.dz_npad; i += NT) {
+        const float z = i < a.n ? dual_z(S[base + i], a.y32[i], a.kind) : 0.f;
+        dz_digits(z, e, a.dz_nd, a.dz_beta, d, (size_t)a.dz_npad, (size_t)i);
     }
 }
 
@@ -389,12 +441,13 @@ __global__ __launch_bounds__(32 * kCertMaxWarps) void k_cert_bound_warp(const __
             if (!in && !out) {
                 const float* qp = a.Qs + base + j;
                 float accf = 0.f, absf = 0.f;
-                for (int t0 = 0; t0 < nq; t0 += 16) {
-                    float v[16];
+                // all the slices' loads of a coordinate in flight at once (up to 32)
+                for (int t0 = 0; t0 < nq; t0 += 32) {
+                    float v[32];
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) v[t] = (t0 + t < nq) ? __ldg(qp + (size_t)(t0 + t) * a.qs_stride) : 0.f;
+                    for (int t = 0; t < 32; ++t) v[t] = (t0 + t < nq) ? __ldg(qp + (size_t)(t0 + t) * a.qs_stride) : 0.f;
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
+                    for (int t = 0; t < 32; ++t) {
                         if (t0 + t < nq) {
                             const float wt = wf[t0 + t];
                             accf = fmaf(wt, v[t], accf);

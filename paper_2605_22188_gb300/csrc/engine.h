@@ -213,6 +213,11 @@ struct CertArgs {
     const float* y32;     // reduced-precision modes: y as FP32 high part y32 = fl(y) and low
     const float* ylo;     // part ylo = fl(y - y32), for the compensated least-squares sums
     double* zeta;         // out: m x n FP64 dual points
+    // reduced-precision modes with the exact-splitting certificate: the dual point
+    // pass also writes zeta's digits (the layout of exact_digits, reversed) and
+    // its row scales 2^e > max |zeta_b| (DZ NULL: not done there)
+    __nv_bfloat16* DZ;
+    int dz_npad, dz_nd, dz_beta;
     double* sum_loss;     // out: m
     double* sum_conj;     // out: m
     const double* Q;      // X^T zeta (m x p) FP64
@@ -233,7 +238,7 @@ struct CertArgs {
     size_t qs_stride;
     double qs_w[kTcMaxJobs];
     const double* xsig;
-    const double* ztau;
+    double* ztau;
     double ebound;
 };
 // zeta = -dl(S), row sums of l and l*(-zeta)   (§4.4 Eq. (batched_dual_candidate_matrix_form))
