@@ -554,6 +554,19 @@ def time_to_zero_gap(name, prec, stream, m):
     out["support"] = sols["mixed"]["support"]
     out["support_equal"] = sols["mixed"]["support"] == sols["fp64"]["support"]
     out["fp64_over_mixed_time"] = out["fp64_s"] / out["mixed_s"]
+    # c1 (n 200, p 30, k 5, FP64): the batched solve of the sequential-vs-batched
+    # comparison; the oracle's sequential BnB of the same instance is in
+    # cpu_baseline["sequential_bnb"]
+    c, X, y, _ = synth.config_instance(C1, seed=0)
+    with kglm.Engine(X, y, c["k"], c["lam2"], c["M"], c["kind"], prec="fp64", max_batch=64,
+                     stream=stream.cuda_stream) as e:
+        e.solve(64, 200, 10, 60.0)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        r = e.solve(64, 200, 10, 60.0)
+        dt = time.perf_counter() - t0
+    out["c1"] = {"workload": C1, "products": "fp64", "batch": 64, "seconds": dt, "nodes": r["nodes"],
+                 "gap": r["gap"], "opt": r["opt"], "support": r["support"]}
     return out
 
 
@@ -723,7 +736,25 @@ def cpu_baseline(pool, c, T, cores, args):
     _, dt = oracle_run(pool, nodes, T)
     return {"value": len(nodes) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d nodes of the workload (T=%d, certificate, rounding, re-opt, branch index), "
-                      "one process per core, %.1f s" % (len(nodes), T, dt)}
+                      "one process per core, %.1f s" % (len(nodes), T, dt),
+            "sequential_bnb": oracle_sequential_bnb()}
+
+
+C1 = "c1_lsq_n200_p30_k5"
+
+
+def oracle_sequential_bnb():
+    """The oracle's sequential best-bound BnB (one node per evaluation, one thread) on the
+    c1 instance, the baseline of the sequential-vs-batched comparison: wall time, nodes,
+    certified optimum and support (the GPU's batched solve of the same instance is in
+    time_to_zero_gap["c1"])."""
+    from oracle import bnb
+    c, X, y, _ = synth.config_instance(C1, seed=0)
+    t0 = time.perf_counter()
+    r = bnb.solve(X, y, c["k"], c["lam2"], c["M"], c["kind"], T_max=200, check_every=10)
+    return {"workload": C1, "seconds": time.perf_counter() - t0, "nodes": int(r["nodes"]), "opt": float(r["opt"]),
+            "support": [int(j) for j in r["support"]], "gap": float(r["gap"]), "threads": 1,
+            "T_max": 200, "check_every": 10}
 
 
 def run_reference(args):
