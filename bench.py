@@ -684,12 +684,18 @@ def serving_summary(args):
     cert = [i for i in infos if i["state"] == kglm.REQ_DONE and i["gap"] <= 1e-6]
     lat = sorted(i["t_done"] - i["t_submit"] for i in cert)
     pct = lambda q: float(np.percentile(lat, q)) if lat else None
+    # where the latency goes: waiting for a slot (admission) and being solved
+    wait = sorted(i["t_admit"] - i["t_submit"] for i in cert if i["t_admit"] >= 0)
+    serve = sorted(i["t_done"] - i["t_admit"] for i in cert if i["t_admit"] >= 0)
+    pq = lambda v, q: float(np.percentile(v, q)) if v else None
     return {
         "value": nodes / wall, "unit": "nodes/s", "wall_s": wall, "requests": len(specs),
         "arrival_rate_per_s": args.rate, "max_active": args.max_active, "request_time_limit_s": args.request_limit,
         "products": args.serve_prec, "budget_bytes": st["budget"],
         "latency_s": {"p50": pct(50), "p99": pct(99), "max": lat[-1] if lat else None,
                       "of": "requests certified within the limit"},
+        "admission_wait_s": {"p50": pq(wait, 50), "p99": pq(wait, 99)},
+        "solve_s": {"p50": pq(serve, 50), "p99": pq(serve, 99)},
         "certified": len(cert), "not_certified": len(infos) - len(cert),
         "failed": sum(1 for i in infos if i["state"] == kglm.REQ_FAILED),
         "worst_gap": max(i["gap"] for i in infos), "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
@@ -698,7 +704,9 @@ def serving_summary(args):
         "per_request": [{"n": sp["n"], "p": sp["p"], "k": sp["k"],
                          "loss": "lsq" if sp["kind"] == synth.LSQ else "logistic", "rho": sp["rho"],
                          "batch": i["batch"], "nodes": i["nodes"], "gap": i["gap"], "state": i["state"],
-                         "latency_s": round(i["t_done"] - i["t_submit"], 3)} for sp, i in zip(specs, infos)],
+                         "latency_s": round(i["t_done"] - i["t_submit"], 3),
+                         "wait_s": round(i["t_admit"] - i["t_submit"], 3) if i["t_admit"] >= 0 else None}
+                        for sp, i in zip(specs, infos)],
     }
 
 

@@ -429,11 +429,28 @@ __global__ __launch_bounds__(NT, sizeof(TI) == 4 ? 4 : 1) void k_reopt(ReoptArgs
             __syncthreads();
             if (sh.done) break;
             const int cur = sh.cur, nxt = 1 - cur;
-            // Armijo backtracking along the projection arc; every trial is a full evaluation
+            // Armijo backtracking along the projection arc; every trial is a full evaluation,
+            // except a first trial whose predicted decrease is below the working precision's
+            // resolution of f: it is accepted and ends the solve whatever f there is (the
+            // test below), so its evaluation (f, g and H over the samples) is skipped
             bool moved = false;
             for (int ls = 0; ls < 40; ++ls) {
                 for (int r = tid; r < ks; r += NT) sh.bn[r] = fmin(M, fmax(-M, sh.b[r] + sh.alpha * sh.d[r]));
                 __syncthreads();
+                if (ls == 0) {
+                    if (tid < 32) {
+                        double dec = 0.0;
+                        for (int r = lane; r < ks; r += 32) dec += sh.g[cur][r] * (sh.bn[r] - sh.b[r]);
+                        dec = warp_sum(dec);
+                        if (lane == 0) {
+                            const bool tiny = fabs(dec) <= tiny_rel * (1.0 + fabs(sh.f[cur]));
+                            sh.accept = tiny ? 1 : 0;
+                            if (tiny) sh.done = 1;
+                        }
+                    }
+                    __syncthreads();
+                    if (sh.done) { moved = true; break; }
+                }
                 evaluate<TI>(a, sh, dy, sh.bn, nxt);
                 if (tid < 32) {
                     double dec = 0.0, step = 0.0;
