@@ -1900,14 +1900,12 @@ kglm_status kglm_create(const kglm_desc* desc, const double* X, const double* y,
             c->own_stream = true;
         }
         // instance: FP64 X, X^T, y (+ FP32 working copies), Gram and X^T y for re-optimization
-        std::vector<double> Xt(n * p);
-        for (size_t i = 0; i < n; ++i)
-            for (size_t j = 0; j < p; ++j) Xt[j * n + i] = X[i * p + j];
         c->X64 = dalloc_t<double>(c, n * p);
         c->Xt64 = dalloc_t<double>(c, n * p);
         c->y64 = dalloc_t<double>(c, n);
         CK(cudaMemcpyAsync(c->X64, X, sizeof(double) * n * p, cudaMemcpyHostToDevice, c->st));
-        CK(cudaMemcpyAsync(c->Xt64, Xt.data(), sizeof(double) * n * p, cudaMemcpyHostToDevice, c->st));
+        transpose_f64(c->st, c->X64, c->Xt64, n, p);        // X^T on the device (one host copy of X)
+        check_launch();
         CK(cudaMemcpyAsync(c->y64, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
         c->yty = 0.0;
         for (size_t i = 0; i < (size_t)n; ++i) c->yty += y[i] * y[i];

@@ -296,6 +296,8 @@ void prune_launch(cudaStream_t s, int m, const double* lb, double thr, uint8_t* 
 void check_update(cudaStream_t s, int m, const double* lb_now, const double* primal_now, double* lb_best,
                   double* primal_last, int* active, int* iters_done, int it, double ub_thr, double gap_rtol);
 void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count);
+// out (cols x rows) = in^T for a row-major rows x cols FP64 matrix (device buffers)
+void transpose_f64(cudaStream_t s, const double* in, double* out, size_t rows, size_t cols);
 void convert_to_f64(cudaStream_t s, const void* in, int is_f64, double* out, size_t count);
 
 // ---- host side shared by the C ABI and the serving loop (api.cu)

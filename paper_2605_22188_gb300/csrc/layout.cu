@@ -156,6 +156,21 @@ __global__ void k_f64_to_f32(const double* in, float* out, size_t n) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) out[t] = (float)in[t];
 }
+// out (cols x rows) = in (rows x cols)^T, both row-major: 32 x 32 tiles through shared
+// memory (one padded column against bank conflicts), 32 x 8 threads.
+__global__ void k_transpose_f64(const double* in, double* out, size_t rows, size_t cols) {
+    __shared__ double t[32][33];
+    const size_t r0 = (size_t)blockIdx.x * 32, c0 = (size_t)blockIdx.y * 32;   // rows on x (up to 2^31 tiles)
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const size_t r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[k][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const size_t c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[c * rows + r] = t[threadIdx.x][k];
+    }
+}
 __global__ void k_f32_to_f64(const float* in, double* out, size_t n) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) out[t] = (double)in[t];
@@ -241,6 +256,12 @@ void check_update(cudaStream_t s, int m, const double* lb_now, const double* pri
 
 void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count) {
     if (count) k_f64_to_f32<<<blocks(count, 256), 256, 0, s>>>(in, out, count);
+}
+
+void transpose_f64(cudaStream_t s, const double* in, double* out, size_t rows, size_t cols) {
+    if (rows == 0 || cols == 0) return;
+    const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    k_transpose_f64<<<grid, dim3(32, 8), 0, s>>>(in, out, rows, cols);
 }
 
 void convert_to_f64(cudaStream_t s, const void* in, int is_f64, double* out, size_t count) {
