@@ -498,12 +498,12 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     // Two producers, lane 0 of warp 0 (even ring slices) and of warp PROD2_WARP (odd
     // ones): a thread that issues TMA copies takes a few hundred cycles per stage
     // whatever its size, so one thread alone cannot keep the tensor pipe fed.
-    // Only with an even number of stages: then every stage has one producer, which
-    // waits on its empty barrier at most one phase ahead.  With an odd count, fills
-    // g and g + STAGES of a stage would come from different producers, and one of
-    // them could test the barrier two phases ahead, where the parity cannot tell
-    // the phases apart; warp 0 then fills every slice.
-    const int nprod = (STAGES % 2 == 0) ? 2 : 1;
+    // The producers split the ring by stage, stage s to producer s % 2, so that every
+    // stage has one producer, which fills it in order and so waits on its empty
+    // barrier at most one phase ahead (were fills g and g + STAGES of a stage issued
+    // by different producers, one of them could test the barrier two phases ahead,
+    // where the parity cannot tell the phases apart).  A one-stage ring has one.
+    const int nprod = STAGES >= 2 ? 2 : 1;
     if (warp == 0 || warp == PROD2_WARP) {
       // lanes 1-31 of both producer warps wait at the exit barrier
       if (lane == 0 && (warp == 0 || nprod == 2)) {
@@ -516,7 +516,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
             const int m0 = w.mtile * BM, n0 = w.ntile * a.bn;
             const int nst = (w.nloc + KS - 1) / KS;     // stages of this unit
             for (int i = 0; i < nst; ++i, ++g) {
-                if (g % nprod != pidx) continue;
+                if ((g % STAGES) % nprod != pidx) continue;
                 const int s = g % STAGES;
                 const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
                 if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, a.err)) { ok = false; break; }
