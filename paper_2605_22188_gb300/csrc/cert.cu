@@ -87,7 +87,8 @@ __device__ __forceinline__ void dz_digits(float z, int e, int nd, int beta, __nv
         const long long mnt = ex ? (long long)((u & 0x7fffffu) | 0x800000u) : (long long)(u & 0x7fffffu);
         const int sh = (ex ? ex : 1) - 150 + 62 - e;              // z = mnt 2^(ex - 150), v 2^62 = mnt 2^sh
         long long mag = 0;
-        if (sh >= 0) mag = mnt << sh;                              // |v| < 1: below 2^62
+        if (sh >= 0) mag = sh <= 38 ? mnt << sh : 0;               // |v| < 1: below 2^62 (sh > 38 only
+                                                                   // for a non-finite z)
         else if (sh > -26) mag = (mnt + (1ll << (-sh - 1))) >> (-sh);
         V = (u >> 31) ? -mag : mag;
     }

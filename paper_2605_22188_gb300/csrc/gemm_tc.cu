@@ -10,9 +10,9 @@
 // SM walks the units u = blockIdx.x, blockIdx.x + gridDim.x, ... with
 //   warps 0 and 10,  TMA producers: 128-byte-swizzled K slices of A and B
 //   lane 0           (cp.async.bulk.tensor.2d) into a ring of stages, warp 0
-//                    the even slices and warp 10 the odd ones (one issuing
-//                    thread takes a few hundred cycles per stage, small or
-//                    large, and would leave the tensor pipe waiting);
+//                    filling the even stages and warp 10 the odd ones (one
+//                    issuing thread takes a few hundred cycles per stage,
+//                    small or large, and would leave the tensor pipe waiting);
 //   warp 1, lane 0   MMA issuer: tcgen05.mma.cta_group::1 (kind::f16 with BF16
 //                    operands, or kind::tf32) into one of two FP32
 //                    accumulators in tensor memory (512 columns), so that the
@@ -49,9 +49,10 @@
 // tile with tcgen05.mma.cta_group::2 (M = 256) issued by the even CTA.  Each
 // CTA copies its own 128 rows of A and half of the B tile's rows into its own
 // ring, so that an SM takes in 32 KB instead of 48 KB per 128 x 256 x 64
-// slice of products; both copies complete on the even CTA's stage barrier,
-// and each CTA's epilogue drains its 128 rows of the accumulator from its own
-// tensor memory.
+// slice of products; a pair's stage holds two K slices (fewer, larger stages:
+// the copies are bound by their round trip per stage); both CTAs' copies
+// complete on the even CTA's stage barrier, and each CTA's epilogue drains its
+// 128 rows of the accumulator from its own tensor memory.
 // Every mbarrier wait is bounded; a wait that runs out sets an error flag,
 // the roles stop, the MMA issuer drains its products and the producer its
 // copies before the tensor memory is freed.
@@ -73,7 +74,7 @@ constexpr int ROWB = 128;               // bytes of K per stage and row (one swi
 constexpr int MAXBN = 256;
 constexpr int NT = 352;                 // eleven warps: producer, MMA, eight epilogue warps, second producer
 constexpr int EPI_WARPS = 8;
-constexpr int PROD2_WARP = 2 + EPI_WARPS;   // fills the odd ring slices (warp 0 the even ones)
+constexpr int PROD2_WARP = 2 + EPI_WARPS;   // fills the odd ring stages (warp 0 the even ones)
 constexpr uint32_t STAGE_A = BM * ROWB;
 constexpr uint32_t TMEM_COLS = 512;     // two accumulators of up to 256 columns
 constexpr int TPAD = 20;                // transpose buffer row: 16 + 4 (16-byte rows, no 128-bit bank conflicts on write)
@@ -453,8 +454,8 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     uint64_t* tempty = bars + 2 * kMaxStages + 2;
     uint64_t* drain = bars + 2 * kMaxStages + 4;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 5);
-    __shared__ int s_consumed;       // ring slices the MMA issuer consumed (producer drain at exit)
-    __shared__ int s_issued[2];      // per producer: one past the last ring slice it filled
+    __shared__ int s_consumed;       // stage fills the MMA issuer consumed (producer drain at exit)
+    __shared__ int s_issued[2];      // per producer: one past the last stage fill it issued
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KE = KIND == 0 ? 64 : 32;          // elements per 128-byte row
@@ -495,7 +496,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     pdl_wait();                      // operands and outputs belong to the previous grid until it completes
-    // Two producers, lane 0 of warp 0 (even ring slices) and of warp PROD2_WARP (odd
+    // Two producers, lane 0 of warp 0 (even ring stages) and of warp PROD2_WARP (odd
     // ones): a thread that issues TMA copies takes a few hundred cycles per stage
     // whatever its size, so one thread alone cannot keep the tensor pipe fed.
     // The producers split the ring by stage, stage s to producer s % 2, so that every
@@ -789,7 +790,7 @@ __device__ __forceinline__ void tc_body(const TcArgs& a, const S& src) {
             for (int g = s_consumed; g < issued; ++g)
                 mbar_wait(smem_u32(&full[g % STAGES]), (uint32_t)(g / STAGES) & 1u, a.err);
         if constexpr (CL == 2) {
-            // the leader's releases of this CTA's last ring slices (commits that
+            // the leader's releases of this CTA's last stage fills (commits that
             // arrive here from the other SM) land before the CTA frees or leaves
             if (a.err == nullptr || *reinterpret_cast<volatile int*>(a.err) == 0)
                 for (int g = max(0, issued - STAGES); g < issued; ++g)
