@@ -83,12 +83,11 @@ __device__ __forceinline__ void dz_digits(float z, int e, int nd, int beta, __nv
     long long V = 0;
     const uint32_t u = __float_as_uint(z);
     const int ex = (int)((u >> 23) & 0xffu);
-    if (ex != 0 || (u & 0x7fffffu) != 0) {
+    if (ex != 255 && (ex != 0 || (u & 0x7fffffu) != 0)) {       // a non-finite z has no digits
         const long long mnt = ex ? (long long)((u & 0x7fffffu) | 0x800000u) : (long long)(u & 0x7fffffu);
         const int sh = (ex ? ex : 1) - 150 + 62 - e;              // z = mnt 2^(ex - 150), v 2^62 = mnt 2^sh
         long long mag = 0;
-        if (sh >= 0) mag = sh <= 38 ? mnt << sh : 0;               // |v| < 1: below 2^62 (sh > 38 only
-                                                                   // for a non-finite z)
+        if (sh >= 0) mag = sh < 63 ? mnt << sh : 0;                // |v| < 1: below 2^62, so sh < 62
         else if (sh > -26) mag = (mnt + (1ll << (-sh - 1))) >> (-sh);
         V = (u >> 31) ? -mag : mag;
     }
