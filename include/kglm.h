@@ -491,6 +491,22 @@ void kglm_server_destroy(kglm_server* s);
  * timeout was detected and reported (KGLM_ECUDA if it was not). */
 kglm_status kglm_selftest_timeout(kglm_ctx* ctx, int32_t rounds);
 
+/* Bounds-checked build (no counterpart in the paper; a debugging aid, since no
+ * device sanitizer runs where this library is tested).  The library built with
+ * KGLM_CHECKS=1 (libkglm_checks.so) checks, on the device, the indices its prox,
+ * certificate and re-optimization kernels write or gather with; a failed check
+ * records which kernel failed and skips the access, and the evaluation returns
+ * KGLM_EINVAL naming the kernel.  kglm_checks_enabled returns 1 for that build
+ * and 0 for the normal one (no device needed). */
+int32_t kglm_checks_enabled(void);
+
+/* Self-test of the bounds-checked build: launches one kernel that attempts a
+ * write one past the end of a context buffer through the checked path; the
+ * check catches it, the write does not happen, and the call returns KGLM_EINVAL
+ * with the context still usable.  In the normal build it launches nothing and
+ * returns KGLM_ESTATE. */
+kglm_status kglm_selftest_checks(kglm_ctx* ctx);
+
 /* Message of the last failed call on ctx (never NULL). */
 const char* kglm_last_error(const kglm_ctx* ctx);
 

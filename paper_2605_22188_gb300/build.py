@@ -1,7 +1,9 @@
 """Build libkglm.so (sm_103a) in-tree: one nvcc per translation unit, in parallel.
 
-Usage: python -m paper_2605_22188_gb300.build   (or build() from Python)
-The library lands in paper_2605_22188_gb300/lib/libkglm.so.
+Usage: python -m paper_2605_22188_gb300.build [--checks]   (or build() from Python)
+The library lands in paper_2605_22188_gb300/lib/libkglm.so; --checks builds the
+bounds-checked variant (KGLM_CHECKS=1) as lib/libkglm_checks.so, which the binding
+loads when KGLM_CHECKS=1 is set in the environment.
 """
 
 import concurrent.futures as cf
@@ -17,6 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libkglm.so")
+# the bounds-checked build (KGLM_CHECKS=1): its own objects and library
+LIB_CHECKS = os.path.join(LIBDIR, "libkglm_checks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -34,8 +38,8 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, bdir=BUILD):
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -43,25 +47,31 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, extra=()):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra=(), checks=False):
+    """Compile every translation unit and link the library; checks=True builds the
+    bounds-checked variant (KGLM_CHECKS=1) into libkglm_checks.so instead."""
+    bdir = os.path.join(BUILD, "checks") if checks else BUILD
+    lib = LIB_CHECKS if checks else LIB
+    extra = list(extra) + (["-DKGLM_CHECKS=1"] if checks else [])
+    os.makedirs(bdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, bdir), srcs))
     if verbose:
         for _, err in results:
             if err.strip():
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+    print(build(verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                checks="--checks" in sys.argv))

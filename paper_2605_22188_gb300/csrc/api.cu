@@ -395,6 +395,7 @@ void certify(kglm_ctx* c) {
     a.S = c->R;                                         // the m x n buffer is free here
     a.s_is_f64 = c->f64;
     a.y = c->y64; a.y32 = c->y32; a.ylo = c->ylo32;
+    a.chk = c->d_err;
     a.zeta = c->zeta; a.sum_loss = c->sum_loss; a.sum_conj = c->sum_conj;
     a.Q = c->Q; a.B = c->B; a.b_is_f64 = c->f64;
     a.in_mask = c->in_mask; a.out_mask = c->out_mask; a.kbar = c->kbar; a.pf = c->pf;
@@ -480,6 +481,7 @@ ProxArgs prox_args_rows(kglm_ctx* c, int row0, int mr, int splits, bool pdl) {
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
     a.pdl = pdl ? 1 : 0;
     a.threads = c->prox_threads;
+    a.chk = c->d_err;
     return a;
 }
 
@@ -557,6 +559,7 @@ void iterate(kglm_ctx* c) {
     a.hint = c->phint;
     a.eta = c->eta; a.c = c->c; a.M = c->M; a.restart = c->d.restart;
     a.threads = c->prox_threads;
+    a.chk = c->d_err;
     Scope sc(c, PH_PROX, 1, (c->f64 ? 8.0 : 4.0) * 5.0 * c->sum_pa);
     const int rc = c->f64 ? prox_fista_f64(c->st, a) : prox_fista_f32(c->st, a);
     if (rc != 0) throw Fail{KGLM_EINVAL, "p too large for the prox kernel"};
@@ -701,6 +704,7 @@ void evaluate_end(kglm_ctx* c) {
     r.support = c->support; r.B = c->B; r.b_is_f64 = c->f64;
     r.ub = c->ub; r.beta_re = c->beta_re;
     r.yty = c->yty;
+    r.chk = c->d_err;
     {
         Scope sc(c, PH_REOPT, 1, 0.0);
         if (reopt_launch(c->st, r) != 0) throw Fail{KGLM_ECUDA, "re-optimization kernel: shared memory for k refused"};
@@ -848,6 +852,21 @@ void evaluate_group(const std::vector<kglm_ctx*>& cs, int iters, int check_every
 // After a synchronisation that follows evaluate_impl: the tensor-core error flag
 // it sent to the pinned staging.
 void finish_tc_check(kglm_ctx* c) {
+#if KGLM_CHECKS
+    {
+        // the bounds-checked build: which kernel's device check failed, if any
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        sync(c);
+        if (h & kChkAll) {
+            CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+            sync(c);
+            throw Fail{KGLM_EINVAL, std::string("device bounds check failed in") + ((h & kChkProx) ? " the prox" : "") +
+                                        ((h & kChkCert) ? " the certificate" : "") +
+                                        ((h & kChkReopt) ? " the re-optimization" : "")};
+        }
+    }
+#endif
     if (!c->tc_check_pending) return;
     c->tc_check_pending = false;
     if (*c->pinned<int>(c->off_tcerr())) {
@@ -2652,6 +2671,28 @@ kglm_status kglm_selftest_timeout(kglm_ctx* ctx, int32_t rounds) {
         sync(ctx);
         if (h & 8) throw Fail{KGLM_ETIMEOUT, "self-test: the bounded device wait ran out and reported it"};
         throw Fail{KGLM_ECUDA, "self-test: the bounded device wait did not report its timeout"};
+    });
+}
+
+int32_t kglm_checks_enabled(void) { return KGLM_CHECKS ? 1 : 0; }
+
+kglm_status kglm_selftest_checks(kglm_ctx* ctx) {
+    if (!ctx) return KGLM_EINVAL;
+    return guarded(ctx, [&] {
+#if KGLM_CHECKS
+        CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st));
+        check_probe(ctx->st, ctx->kbar, ctx->mcap, ctx->d_err);
+        check_launch();
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        sync(ctx);
+        CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->st));
+        sync(ctx);
+        if (h & kChkSelf) throw Fail{KGLM_EINVAL, "self-test: the checked write one past the end was caught and skipped"};
+        throw Fail{KGLM_ECUDA, "self-test: the checked write one past the end was not caught"};
+#else
+        throw Fail{KGLM_ESTATE, "not the bounds-checked build (build with checks=True, load with KGLM_CHECKS=1)"};
+#endif
     });
 }
 

@@ -298,7 +298,10 @@ __global__ __launch_bounds__(NT) void k_cert_bound(const __grid_constant__ CertA
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < E; ++e)
-        if ((((fin | sel) >> e) & 1u)) sh.sup[atomicAdd(&sh.cnt, 1)] = threadIdx.x + e * NT;
+        if ((((fin | sel) >> e) & 1u)) {
+            const int c = atomicAdd(&sh.cnt, 1);
+            if (kglm_check(c < kMaxK, a.chk, kChkCert)) sh.sup[c] = threadIdx.x + e * NT;
+        }
     __syncthreads();
     const int ns = sh.cnt;
     if (threadIdx.x < 32) {
@@ -488,7 +491,7 @@ __global__ __launch_bounds__(32 * kCertMaxWarps) void k_cert_bound_warp(const __
                 const int j = 32 * w + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int c = atomicAdd(&h.nsup, 1);
-                if (c < kMaxK) h.sup[c] = j;                         // |J1| <= k <= kMaxK for validated nodes
+                if (kglm_check(c < kMaxK, a.chk, kChkCert) && c < kMaxK) h.sup[c] = j;   // |J1| <= k <= kMaxK when validated
             }
         }
         __syncwarp();
@@ -563,7 +566,7 @@ __global__ __launch_bounds__(32 * kCertMaxWarps) void k_cert_bound_warp(const __
                 if (su[j] != 0u) {
                     part += huber64(cert_exact_v(a, base, j, b, inv2l), M);
                     const int c = atomicAdd(&h.nsup, 1);
-                    if (c < 2 * kMaxK) h.sup[c] = j;
+                    if (kglm_check(c < 2 * kMaxK, a.chk, kChkCert) && c < 2 * kMaxK) h.sup[c] = j;
                 }
         }
         const double topsum = warp_sum(part);
@@ -629,7 +632,7 @@ __global__ __launch_bounds__(32 * kCertMaxWarps) void k_cert_bound_warp(const __
                 const bool z = j < p && su[j] != 0u && B[j] == 0.f;
                 uint32_t bal = __ballot_sync(0xffffffffu, z);
                 const int before = __popc(bal & ((1u << lane) - 1u));
-                if (z && got + before < kb) {
+                if (z && got + before < kb && kglm_check(got + before < kMaxK, a.chk, kChkCert)) {
                     h.sv[got + before] = 0.f;
                     h.si[got + before] = j;
                 }

@@ -16,6 +16,30 @@ constexpr int kLSQ = 0;
 constexpr int kLOGISTIC = 1;
 constexpr int kMaxK = 64;
 
+// ------------------------------------------------------------------ bounds-checked build
+// Compiled with KGLM_CHECKS=1 (libkglm_checks.so), the kernels check the indices
+// they write or gather with (J1 and top-set lists, supports) before using them: a
+// failed check sets its kernel's bit in the context's error word and the access is
+// skipped, and the evaluation that launched the kernel returns KGLM_EINVAL.  In the
+// normal build the condition is taken as true (the inputs are validated on the
+// host or by the push's device checks) and the guard compiles to nothing.
+#ifndef KGLM_CHECKS
+#define KGLM_CHECKS 0
+#endif
+constexpr int kChkProx = 1 << 16, kChkCert = 1 << 17, kChkReopt = 1 << 18, kChkSelf = 1 << 19;
+constexpr int kChkAll = kChkProx | kChkCert | kChkReopt | kChkSelf;
+__device__ __forceinline__ bool kglm_check(bool cond, int* word, int bit) {
+#if KGLM_CHECKS
+    if (!cond) {
+        if (word) atomicOr(word, bit);
+        return false;
+    }
+#else
+    (void)cond; (void)word; (void)bit;
+#endif
+    return true;
+}
+
 // ------------------------------------------------------------------ losses
 // l(s, y) = (s - y)^2 or log(1 + exp(-y s)); dl/ds; l*(w, y)   (§4.2, §4.4)
 

@@ -179,6 +179,7 @@ struct ProxArgs {
     int threads;          // FP32, p > 512: threads per node (0: 8 coordinates per thread)
     float* hint;          // per node (2 floats): the last step's kbar-th largest free |u| and
                           // block threshold, for the streaming FP32 prox (0: none; NULL: unused)
+    int* chk;             // bounds-checked build: the context's error word (kglm_check)
 };
 // One FISTA step per node: u = v - eta*G, beta' = prox(u), restart, next v.
 int prox_fista_f64(cudaStream_t s, const ProxArgs& a);
@@ -240,6 +241,7 @@ struct CertArgs {
     const double* xsig;
     double* ztau;
     double ebound;
+    int* chk;             // bounds-checked build: the context's error word (kglm_check)
 };
 // zeta = -dl(S), row sums of l and l*(-zeta)   (§4.4 Eq. (batched_dual_candidate_matrix_form))
 void cert_dual_point(cudaStream_t s, const CertArgs& a);
@@ -261,6 +263,7 @@ struct ReoptArgs {
     double* ub;            // out: v(S_b)
     double* beta_re;       // out: m x k
     double yty;            // y^T y (least squares: v(S) = y^T y + b^T (G_SS + lambda2 I) b - 2 c^T b)
+    int* chk;              // bounds-checked build: the context's error word (kglm_check)
 };
 // returns 0, or -1 if the dynamic shared memory for k cannot be granted
 int reopt_launch(cudaStream_t s, const ReoptArgs& a);
@@ -295,6 +298,8 @@ void prune_launch(cudaStream_t s, int m, const double* lb, double thr, uint8_t* 
 // early-stop bookkeeping at a check: best LB, freeze nodes
 void check_update(cudaStream_t s, int m, const double* lb_now, const double* primal_now, double* lb_best,
                   double* primal_last, int* active, int* iters_done, int it, double ub_thr, double gap_rtol);
+// bounds-checked build only: one checked write one past the end of buf (len entries)
+void check_probe(cudaStream_t s, int* buf, int len, int* word);
 void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count);
 // out (cols x rows) = in^T for a row-major rows x cols FP64 matrix (device buffers)
 void transpose_f64(cudaStream_t s, const double* in, double* out, size_t rows, size_t cols);

@@ -52,6 +52,16 @@ __global__ void k_validate(int m, int k, int W, int nnz_in, int nnz_out, const i
     if (bad) atomicOr(err, 2);
 }
 
+#if KGLM_CHECKS
+// The bounds-checked build's self-test: a write one past the end of buf (len
+// entries) through the checked path; the check catches it and skips the write.
+// Compiled only into that build: elsewhere the guard does not check.
+__global__ void k_check_probe(int* buf, int len, int* word) {
+    const int idx = len + (int)threadIdx.x;
+    if (kglm_check(idx < len, word, kChkSelf)) buf[idx] = 0;
+}
+#endif
+
 __global__ void k_check_slots(int m, const int* slot, int nslots, int* err) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < m && (slot[b] < -1 || slot[b] >= nslots)) atomicOr(err, 4);
@@ -253,6 +263,10 @@ void check_update(cudaStream_t s, int m, const double* lb_now, const double* pri
         k_check<<<blocks(m, 256), 256, 0, s>>>(m, lb_now, primal_now, lb_best, primal_last, active, iters_done, it,
                                                ub_thr, gap_rtol);
 }
+
+#if KGLM_CHECKS
+void check_probe(cudaStream_t s, int* buf, int len, int* word) { k_check_probe<<<1, 1, 0, s>>>(buf, len, word); }
+#endif
 
 void convert_f64_to_f32(cudaStream_t s, const double* in, float* out, size_t count) {
     if (count) k_f64_to_f32<<<blocks(count, 256), 256, 0, s>>>(in, out, count);

@@ -273,9 +273,12 @@ __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, 
                 const int j = 32 * q + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int qq = atomicAdd(&h.nj1, 1);
-                h.j1i[qq] = j;
-                h.j1u[qq] = su[j];
-                su[j] = 0.f;
+                if (kglm_check(qq < kMaxK, a.chk, kChkProx)) {
+                    const bool ok = kglm_check(j < p, a.chk, kChkProx);
+                    h.j1i[qq] = ok ? j : -1;
+                    h.j1u[qq] = ok ? su[j] : 0.f;
+                    if (ok) su[j] = 0.f;
+                }
             }
         }
         __syncwarp();
@@ -473,10 +476,11 @@ __device__ __forceinline__ void stream_node(const ProxArgs& a, int b, int lane, 
             su[j] = sgn_mag(u, fmaxf(fminf(fminf(au / c1, M), au - theta), 0.f));
         }
         __syncwarp();
-        const int nj1 = h.nj1;
+        const int nj1 = min(h.nj1, kMaxK);
         for (int i = lane; i < nj1; i += 32) {
             const float u = h.j1u[i];
-            su[h.j1i[i]] = sgn_mag(u, fminf(fabsf(u) / c1, M));
+            const int j = h.j1i[i];
+            if (kglm_check((unsigned)j < (unsigned)p, a.chk, kChkProx)) su[j] = sgn_mag(u, fminf(fabsf(u) / c1, M));
         }
         __syncwarp();
         double t_keep = 0.0, c_keep = 0.0;

@@ -400,7 +400,7 @@ __global__ __launch_bounds__(NT, sizeof(TI) == 4 ? 4 : 1) void k_reopt(ReoptArgs
         int ks = 0;
         for (int r = 0; r < k; ++r) {
             const int j = a.support[(size_t)b * k + r];
-            if (j >= 0) sh.S[ks++] = j;
+            if (j >= 0 && kglm_check(j < a.p, a.chk, kChkReopt)) sh.S[ks++] = j;
         }
         sh.ks = ks;
         sh.done = 0;
@@ -565,7 +565,8 @@ __global__ __launch_bounds__(256) void k_reopt_lsq_warp(ReoptArgs a) {
     int ks = 0;
     for (int r0 = 0; r0 < k; r0 += 32) {
         const int r = r0 + lane;
-        const int j = r < k ? a.support[(size_t)b * k + r] : -1;
+        const int j0 = r < k ? a.support[(size_t)b * k + r] : -1;
+        const int j = (j0 < 0 || kglm_check(j0 < a.p, a.chk, kChkReopt)) ? j0 : -1;
         const unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
         if (j >= 0) w.S[ks + __popc(bal & ((1u << lane) - 1u))] = j;
         ks += __popc(bal);

@@ -69,6 +69,8 @@ _SIGS = {
     "kglm_autotune": (C.c_int, [P, C.c_int32, C.c_uint64, C.c_void_p]),
     "kglm_configure": (C.c_int, [P, C.c_void_p]),
     "kglm_selftest_timeout": (C.c_int, [P, C.c_int32]),
+    "kglm_checks_enabled": (C.c_int32, []),
+    "kglm_selftest_checks": (C.c_int, [P]),
     "kglm_set_solve_limit": (C.c_int, [P, C.c_int64]),
     "kglm_solve_checkpoint": (C.c_int, [P, C.c_char_p]),
     "kglm_solve_resume": (C.c_int, [P, C.c_char_p, C.c_int32, C.c_int32, C.c_int32, C.c_double, D, I32, D, D, I64,
@@ -125,7 +127,8 @@ NPHASE = 11
 
 
 def lib_path():
-    return _build.LIB
+    """The normal library, or the bounds-checked one when KGLM_CHECKS=1 is set."""
+    return _build.LIB_CHECKS if os.environ.get("KGLM_CHECKS") == "1" else _build.LIB
 
 
 def lib():
@@ -367,6 +370,16 @@ def kglm_configure(ctx, batch=0, link_tile_cols=0, grad_tile_cols=0, grad_split_
 def kglm_selftest_timeout(ctx, rounds=10000):
     """Runs a bounded device wait that nothing ends; returns the status (KGLM_ETIMEOUT expected)."""
     return lib().kglm_selftest_timeout(ctx, int(rounds))
+
+
+def checks_enabled():
+    """True for the bounds-checked build (KGLM_CHECKS=1 in the environment selects it)."""
+    return bool(lib().kglm_checks_enabled())
+
+
+def kglm_selftest_checks(ctx):
+    """A checked out-of-range write; returns the status (KGLM_EINVAL in the checked build)."""
+    return lib().kglm_selftest_checks(ctx)
 
 
 def kglm_destroy(ctx):

@@ -40,6 +40,14 @@ def test_version(lib):
     assert "sm_103a" in kglm.kglm_version()
 
 
+def test_normal_build_is_not_the_checked_one(lib):
+    # kglm_checks_enabled needs no device; the checked build is a separate library
+    if os.environ.get("KGLM_CHECKS") == "1":
+        pytest.skip("the bounds-checked library is selected")
+    assert kglm.checks_enabled() is False
+    assert kglm.lib_path().endswith("libkglm.so")
+
+
 def _inst(n=20, p=6):
     rng = np.random.default_rng(0)
     return rng.standard_normal((n, p)), rng.standard_normal(n)
