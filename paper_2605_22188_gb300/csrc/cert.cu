@@ -425,7 +425,8 @@ __global__ __launch_bounds__(32 * kCertMaxWarps) void k_cert_bound_warp(const __
     const float ebf = (float)a.ebound;
     const float gam = (float)(nq + 2) * 0x1p-23f;               // |acc_f - acc| <= gam * sum |w P|, with margin
     const float rlo = 1.0f - 0x1p-19f, rhi = 1.0f + 0x1p-19f;   // covers the FP32 roundings below
-    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) {
+    // node b to CTA b mod grid: the CTAs (and SMs) hold equal shares of the nodes
+    for (int b = warp * gridDim.x + blockIdx.x; b < a.m; b += gridDim.x * wpc) {
         const size_t base = (size_t)b * p;
         const uint32_t* im = a.in_mask + (size_t)b * a.W;
         const uint32_t* om = a.out_mask + (size_t)b * a.W;
@@ -720,7 +721,7 @@ int cert_bound(cudaStream_t s, const CertArgs& a) {
         while (wpc > 1 && cert_cta_bytes(p, wpc) > (227u << 10)) --wpc;
         if (opted && cert_cta_bytes(p, wpc) <= (227u << 10)) {
             const int per_sm = std::max(1, (int)((228u << 10) / (cert_cta_bytes(p, wpc) + 1024)));
-            const int grid = std::max(1, std::min(152 * per_sm, (m + wpc - 1) / wpc));
+            const int grid = std::max(1, std::min(152 * per_sm, m));
             k_cert_bound_warp<<<grid, 32 * wpc, cert_cta_bytes(p, wpc), s>>>(a);
             return 0;
         }

@@ -553,7 +553,10 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream(ProxArg
     WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
     unsigned char* rows = wbase + align16(sizeof(WarpHdr));
     stream_pad(rows, a.p, a.W, lane);
-    for (int b = blockIdx.x * wpc + warp; b < a.m; b += gridDim.x * wpc) {
+    // nodes go round the CTAs first (node b to CTA b mod grid), so that every SM
+    // holds the same number of nodes and a last partial round is spread over all
+    // SMs rather than packed onto the first few
+    for (int b = warp * gridDim.x + blockIdx.x; b < a.m; b += gridDim.x * wpc) {
         if (a.active != nullptr && a.active[b] == 0) continue;
         stream_issue<VEC>(a, b, lane, rows);
         stream_node<VEC>(a, b, lane, h, rows);
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(32 * kStreamMaxWarps, 1) k_prox_stream_group(c
     WarpHdr& h = *reinterpret_cast<WarpHdr*>(wbase);
     unsigned char* rows = wbase + align16(sizeof(WarpHdr));
     int last = -1;
-    for (int t = blockIdx.x * wpc + warp; t < g.nbase[g.np]; t += gridDim.x * wpc) {
+    for (int t = warp * gridDim.x + blockIdx.x; t < g.nbase[g.np]; t += gridDim.x * wpc) {
         int pi = 0;
         while (pi + 1 < g.np && t >= g.nbase[pi + 1]) ++pi;
         const ProxArgs& a = g.a[pi];
@@ -603,7 +606,9 @@ int launch_stream(cudaStream_t s, const ProxArgs& a, int wpc) {
             opted = true;
         }
     }
-    const int grid = std::max(1, std::min(kSMs, (a.m + wpc - 1) / wpc));
+    // a CTA per SM (its shared memory is the SM's); fewer nodes than SMs take one
+    // SM each
+    const int grid = std::max(1, std::min(kSMs, a.m));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(32 * wpc);
@@ -646,7 +651,7 @@ int launch_stream_group(cudaStream_t s, const ProxGroup& g, int wpc) {
         }
     }
     const int total = g.nbase[g.np];
-    const int grid = std::max(1, std::min(kSMs, (total + wpc - 1) / wpc));
+    const int grid = std::max(1, std::min(kSMs, total));
     kern<<<grid, 32 * wpc, (size_t)wpc * warp_bytes(g.pmax, g.Wmax), s>>>(g);
     return 0;
 }
