@@ -137,7 +137,8 @@ def lib():
     if _LIB is None:
         path = lib_path()
         if not os.path.exists(path):
-            raise RuntimeError("libkglm.so is not built (%s); run paper_2605_22188_gb300.build.build()" % path)
+            how = "build(checks=True)" if path == _build.LIB_CHECKS else "build()"
+            raise RuntimeError("%s is not built; run paper_2605_22188_gb300.build.%s" % (path, how))
         L = C.CDLL(path)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)
