@@ -138,3 +138,14 @@ def test_server_rejects_bad_descriptions_before_touching_the_gpu(lib):
     assert lib.kglm_server_drain(None, 0.0) == kglm.KGLM_EINVAL
     assert lib.kglm_server_info(None, 1, None) == kglm.KGLM_EINVAL
     lib.kglm_server_destroy(None)
+
+
+@pytest.mark.parametrize("loss", [kglm.LSQ, kglm.LOGISTIC])
+def test_suggest_batch_rounds_a_capacity_near_two_to_the_sixteen(lib, loss):
+    """App. E.4's example: a safe capacity slightly above 2^16 nodes gives a batch of
+    65536, one slightly below gives 32768 (the largest power of two not above it)."""
+    d = kglm.make_desc(1000, 500, 10, 1e-3, 2.0, loss, "bf16", 1 << 16)
+    need = kglm.kglm_estimate_bytes(d)
+    d.max_batch = 1
+    assert kglm.kglm_suggest_batch(d, need + 4096, cap=1 << 20) == 1 << 16
+    assert kglm.kglm_suggest_batch(d, need - 1, cap=1 << 20) == 1 << 15
